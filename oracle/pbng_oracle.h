@@ -1,0 +1,101 @@
+/*
+ * PBNG FP64 oracle — TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, serial (optionally OpenMP over the vertices of one colour, which
+ * gives bit-identical results), obviously-correct double-precision restatement
+ * of Position-Based Nonlinear Gauss-Seidel (Chen, Han, Chen, Teran,
+ * arXiv 2306.09021).  Only tests/, the smoke check and the benchmark's CPU
+ * baseline leg call it.  It shares no code with the CUDA library.
+ *
+ * Conventions: 3x3 matrices are row-major double[9]; positions are absolute
+ * (x, not displacement), double[3*nv]; gradients g_j = dN_j/dX are the rows of
+ * B = Dm^{-1} for j = 1..3 and g_0 = -(g_1+g_2+g_3).
+ */
+#ifndef PBNG_ORACLE_H
+#define PBNG_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Eq. (lame): mu = E/(2(1+nu)), lambda = E nu / ((1+nu)(1-2nu)). */
+void ora_lame(double E, double nu, double* mu, double* lam);
+
+/* One-sided Jacobi SVD F = U diag(s) V^T, s descending, U, V orthogonal.
+ * Returns the number of Jacobi sweeps used. */
+int ora_svd3(const double* F, double* U, double* s, double* V);
+
+/* Rotation R in SO(3) of the polar decomposition used by the corotated model
+ * (Eq. cor): R = U diag(1,1,det(U V^T)) V^T, i.e. the smallest singular value
+ * takes the sign of det F.  shat (may be NULL) receives the signed values. */
+void ora_polar(const double* F, double* R, double* shat);
+
+/* Fixed-corotated energy density, Eq. (cor). */
+double ora_psi(const double* F, double mu, double lam);
+/* First Piola-Kirchhoff stress P = dPsi/dF = 2mu(F-R) + lam(J-1) cof F. */
+void ora_pk1(const double* F, double mu, double lam, double* P);
+/* True energy-density Hessian applied to dF (used by the Newton oracle). */
+void ora_dpk1(const double* F, const double* dF, double mu, double lam, double* dP);
+/* Modified density Hessian, Eq. (mod_hess_dens):
+ * C[(a*3+g)*9 + (b*3+d)] = 2mu d_ab d_gd + lam cof(F)_ag cof(F)_bd. */
+void ora_modified_density_hessian(const double* F, double mu, double lam, double* C81);
+/* Cofactor matrix det(F) F^{-T}, defined for every F. */
+void ora_cofactor(const double* F, double* C);
+
+/* Mesh + boundary data.  Copies every input.  status: 0 ok, 1 invalid input,
+ * 4 degenerate rest tetrahedron.  is_dir[nv] marks clamped vertices, whose
+ * positions are whatever the caller puts in x.  body_accel[3] and density[ne]
+ * may be NULL.  Springs tie vertex spr_idx[s] to spr_t[3s..] with stiffness
+ * spr_k[s] (energy k/2 |x-t|^2).  plane[4] = (n, d) or NULL: a vertex with
+ * n.x < d gets energy k_contact/2 (n.x-d)^2. */
+void* ora_create(int nv, const double* X, int ne, const int* tets,
+                 const double* young, const double* poisson,
+                 const unsigned char* is_dir,
+                 const double* body_accel, const double* density,
+                 int ns, const int* spr_idx, const double* spr_t, const double* spr_k,
+                 const double* plane, double k_contact, int* status);
+void ora_destroy(void* h);
+
+/* Greedy node colouring of Section "Coloring and Parallelism". */
+int ora_num_colours(const void* h);
+void ora_get_colours(const void* h, int* colour /* [nv], -1 = clamped */);
+void ora_get_tet_constants(const void* h, double* B9, double* V, double* mu, double* lam);
+void ora_get_fext(const void* h, double* fext3);
+
+/* Local right-hand side r = f_i + f^ext_i and modified Hessian A_i (Eq.
+ * pbgn_dx, Eq. mod_hess) of vertex i at positions x. */
+void ora_local_system(const void* h, const double* x, int i, double* r3, double* A9);
+
+/* Residual vector (f + f^ext) over free vertices (zero at clamped ones) and
+ * its 2-norm.  r_out may be NULL. */
+double ora_residual(const void* h, const double* x, double* r_out);
+/* Total potential sum V Psi + weak/contact energy - sum f^ext . x. */
+double ora_energy(const void* h, const double* x);
+
+/* nsweeps PBNG sweeps in place on x.  accel: 0 plain, 1 Chebyshev (rho,
+ * gamma), 2 SOR (omega), both applied after each whole sweep with
+ * x^{-1} = x^0.  skip_tol > 0 skips vertices with |r| <= skip_tol.
+ * res_hist (NULL or nsweeps+1 doubles) receives |r| before and after every
+ * sweep.  Returns 0, or 5 when a non-finite value appeared. */
+int ora_sweeps(const void* h, double* x, int nsweeps, int accel, double omega,
+               double rho, double gamma, double skip_tol, int nthreads, double* res_hist);
+
+/* Newton's method with the true Hessian, dense LU and a backtracking line
+ * search on the energy (tiny meshes only).  Returns iterations used, or -1
+ * when the tolerance was not met. */
+int ora_newton(const void* h, double* x, double rel_tol, int maxit, double* res_out);
+
+/* Dense true Hessian -d(f + f^ext)/dx over all 3nv DOFs (row-major). */
+void ora_hessian_dense(const void* h, const double* x, double* H);
+
+/* Dense adjoint at an equilibrium x: solve H_FF lam = dL/dx_F, then
+ * dL/dlogE_e = -sum_{i in e, free} lam_i . V_e P_e g_i and
+ * dL/dx_D = dL/dx_D - H_DF lam (nd = number of clamped vertices, ascending id).
+ * Returns 0 or 1 when H_FF is singular. */
+int ora_adjoint_dense(const void* h, const double* x, const double* dLdx,
+                      double* dLdlogE, double* dLdxD);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

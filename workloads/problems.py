@@ -1,0 +1,199 @@
+"""Synthetic quasistatic problems on box grids.
+
+The paper's scenes (muscle meshes, dropped shapes) are not available; these
+seeded box problems stand in for its block examples (stretch/twist blocks,
+the bar under gravity, weak-constraint springs and collision contact) with the
+paper's material values (E = 1e5, nu = 0.3, density 1000).  Each builder
+returns plain arrays; no PBNG arithmetic happens here.
+"""
+
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from .grids import box_grid
+from .rng import standard_normal, uniform01
+
+
+@dataclass
+class Problem:
+    name: str
+    X: np.ndarray                      # [nv, 3] float64 rest positions
+    tets: np.ndarray                   # [ne, 4] int32
+    young: np.ndarray                  # [ne] float64
+    poisson: np.ndarray                # [ne] float64
+    dirichlet: np.ndarray              # [nd] int32 clamped vertex ids (sorted)
+    x0: np.ndarray                     # [nv, 3] float64 initial positions (targets on clamped ids)
+    body_accel: Optional[np.ndarray] = None   # [3] float64 body acceleration
+    density: Optional[np.ndarray] = None      # [ne] float64 rest density
+    spr_idx: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    spr_target: np.ndarray = field(default_factory=lambda: np.zeros((0, 3)))
+    spr_k: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    plane: Optional[np.ndarray] = None        # [4] = (n, d): contact when n.x < d
+    k_contact: float = 0.0
+    seed: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nv(self) -> int:
+        return int(self.X.shape[0])
+
+    @property
+    def ne(self) -> int:
+        return int(self.tets.shape[0])
+
+    @property
+    def n_free(self) -> int:
+        return self.nv - int(self.dirichlet.shape[0])
+
+    def dirichlet_mask(self) -> np.ndarray:
+        m = np.zeros(self.nv, dtype=np.uint8)
+        m[self.dirichlet] = 1
+        return m
+
+
+def _twist_field(X, centre, angle, stretch, height):
+    """Rotation about the z axis through ``centre`` by angle*z/height plus a
+    z-translation stretch*z/height: the smooth extension of a twisted and
+    stretched top face to the whole block."""
+    t = (X[:, 2] - X[:, 2].min()) / height
+    th = angle * t
+    c, s = np.cos(th), np.sin(th)
+    dx = X[:, 0] - centre[0]
+    dy = X[:, 1] - centre[1]
+    out = X.copy()
+    out[:, 0] = centre[0] + c * dx - s * dy
+    out[:, 1] = centre[1] + s * dx + c * dy
+    out[:, 2] = X[:, 2] + stretch * t
+    return out
+
+
+def twist_block(n: int = 10, angle_deg: float = 90.0, stretch: float = 0.3,
+                young: float = 1e5, poisson: float = 0.3) -> Problem:
+    """Unit cube of n^3 cells; bottom face clamped at rest, top face rotated
+    by ``angle_deg`` about the vertical centre line and lifted by ``stretch``.
+    The initial guess applies the twist and stretch linearly in z."""
+    h = 1.0 / n
+    X, tets = box_grid(n, n, n, h)
+    z = X[:, 2]
+    bottom = np.flatnonzero(np.isclose(z, 0.0))
+    top = np.flatnonzero(np.isclose(z, 1.0))
+    dirichlet = np.union1d(bottom, top).astype(np.int32)
+    x0 = _twist_field(X, (0.5, 0.5), np.deg2rad(angle_deg), stretch, 1.0)
+    ne = tets.shape[0]
+    return Problem(
+        name=f"twist_{n}", X=X, tets=tets,
+        young=np.full(ne, young), poisson=np.full(ne, poisson),
+        dirichlet=dirichlet, x0=x0,
+        meta=dict(angle_deg=angle_deg, stretch=stretch, cells=(n, n, n)),
+    )
+
+
+def gravity_sag(n: int = 64, young: float = 1e5, poisson: float = 0.45,
+                density: float = 1000.0, g: float = 9.8) -> Problem:
+    """Unit cube of n^3 cells clamped on the face x = 0, loaded by gravity
+    (0, 0, -g) with the given density; starts from rest."""
+    h = 1.0 / n
+    X, tets = box_grid(n, n, n, h)
+    dirichlet = np.flatnonzero(np.isclose(X[:, 0], 0.0)).astype(np.int32)
+    ne = tets.shape[0]
+    return Problem(
+        name=f"sag_{n}", X=X, tets=tets,
+        young=np.full(ne, young), poisson=np.full(ne, poisson),
+        dirichlet=dirichlet, x0=X.copy(),
+        body_accel=np.array([0.0, 0.0, -g]), density=np.full(ne, density),
+        meta=dict(cells=(n, n, n)),
+    )
+
+
+def contact_bar(nx: int = 40, ny: int = 40, nz: int = 200, h: float = 0.005,
+                seed: int = 20230615, log_sigma: float = 0.5, poisson: float = 0.4,
+                spring_frac: float = 0.02, k_spring: float = 1e4,
+                pull: float = 0.05, target_sigma: float = 0.02,
+                k_contact: float = 1e8) -> Problem:
+    """Bar of nx x ny x nz cells resting on the plane z = 0, no clamped
+    vertices.  Per-tet Young's modulus is lognormal around 1e5; a random
+    ``spring_frac`` of the vertices is tied by zero-rest-length springs to
+    targets pulled ``pull`` below the rest position plus N(0, target_sigma^2)
+    noise, which presses the bar into the contact plane."""
+    X, tets = box_grid(nx, ny, nz, h)
+    ne, nv = tets.shape[0], X.shape[0]
+    young = np.exp(np.log(1e5) + log_sigma * standard_normal(seed, ne))
+    ns = int(round(spring_frac * nv))
+    order = np.argsort(uniform01(seed + 1, nv), kind="stable")
+    spr_idx = np.sort(order[:ns]).astype(np.int32)
+    noise = target_sigma * standard_normal(seed + 2, 3 * ns).reshape(ns, 3)
+    spr_target = X[spr_idx] + np.array([0.0, 0.0, -pull]) + noise
+    return Problem(
+        name=f"bar_{nx}x{ny}x{nz}", X=X, tets=tets,
+        young=young, poisson=np.full(ne, poisson),
+        dirichlet=np.zeros(0, np.int32), x0=X.copy(),
+        spr_idx=spr_idx, spr_target=spr_target, spr_k=np.full(ns, k_spring),
+        plane=np.array([0.0, 0.0, 1.0, 0.0]), k_contact=k_contact,
+        seed=seed, meta=dict(cells=(nx, ny, nz)),
+    )
+
+
+def batched_blocks(count: int = 256, side_lo: int = 8, side_hi: int = 32,
+                   seed: int = 4242, max_stretch: float = 0.4,
+                   max_twist_deg: float = 36.0) -> List[Problem]:
+    """``count`` unit cubes with side s ~ U{side_lo..side_hi} cells, bottom
+    clamped at rest, top clamped to a seeded stretch in [0, max_stretch] and
+    twist in [-max_twist_deg, max_twist_deg]; initial guess = the boundary
+    map extended linearly in z."""
+    u = uniform01(seed, 3 * count).reshape(count, 3)
+    sides = side_lo + np.minimum((u[:, 0] * (side_hi - side_lo + 1)).astype(int),
+                                 side_hi - side_lo)
+    out = []
+    for m in range(count):
+        s = int(sides[m])
+        stretch = max_stretch * u[m, 1]
+        twist = max_twist_deg * (2.0 * u[m, 2] - 1.0)
+        p = twist_block(s, twist, stretch)
+        p.name = f"batch{m}_{s}"
+        p.seed = seed
+        p.meta.update(index=m)
+        out.append(p)
+    return out
+
+
+def adjoint_block(n: int = 48, young: float = 1e5, poisson: float = 0.3) -> Problem:
+    """Unit cube of n^3 cells with its bottom face z = 0 clamped (at rest;
+    load cases move it) and gravity of density 1000."""
+    h = 1.0 / n
+    X, tets = box_grid(n, n, n, h)
+    dirichlet = np.flatnonzero(np.isclose(X[:, 2], 0.0)).astype(np.int32)
+    ne = tets.shape[0]
+    return Problem(
+        name=f"adjoint_{n}", X=X, tets=tets,
+        young=np.full(ne, young), poisson=np.full(ne, poisson),
+        dirichlet=dirichlet, x0=X.copy(),
+        body_accel=np.array([0.0, 0.0, -9.8]), density=np.full(ne, 1000.0),
+        meta=dict(cells=(n, n, n)),
+    )
+
+
+def adjoint_load_cases(p: Problem, count: int = 32, seed: int = 777,
+                       max_rot_deg: float = 5.0, max_trans: float = 0.02, g: float = 9.8):
+    """Seeded load cases for ``adjoint_block``: per case a rigid motion of the
+    clamped face (rotation angle <= max_rot_deg about a random axis through
+    the face centre, translation <= max_trans) and a gravity direction in the
+    lower hemisphere.  Returns (x_D [count, nd, 3], body_accel [count, 3])."""
+    u = uniform01(seed, 9 * count).reshape(count, 9)
+    Xd = p.X[p.dirichlet]
+    centre = np.array([0.5, 0.5, 0.0])
+    xds, accs = [], []
+    for c in range(count):
+        ax = u[c, 0:3] * 2.0 - 1.0
+        ax /= max(np.linalg.norm(ax), 1e-12)
+        ang = np.deg2rad(max_rot_deg) * u[c, 3]
+        K = np.array([[0, -ax[2], ax[1]], [ax[2], 0, -ax[0]], [-ax[1], ax[0], 0]])
+        Q = np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * (K @ K)
+        tr = max_trans * (u[c, 4:7] * 2.0 - 1.0) / np.sqrt(3.0)
+        xds.append((Xd - centre) @ Q.T + centre + tr)
+        phi = 2 * np.pi * u[c, 7]
+        cz = -u[c, 8]                       # lower hemisphere: z component <= 0
+        sz = np.sqrt(max(0.0, 1.0 - cz * cz))
+        accs.append(g * np.array([sz * np.cos(phi), sz * np.sin(phi), cz]))
+    return np.stack(xds), np.stack(accs)
