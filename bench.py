@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""PBNG benchmark: vertex-updates/s of the coloured nonlinear Gauss-Seidel sweep.
+
+Workload: unit cube of 64^3 cells split into 5 tetrahedra each (274,625
+vertices, 1,310,720 tets), fixed-corotated E = 1e5, nu = 0.45, face x = 0
+clamped, gravity (0, 0, -9.8) with density 1000 (the gravity-sag cube).
+Synthetic, seeded inputs; the per-incidence records (~294 MB) exceed L2.
+
+One step = the whole hot path once: `sweeps_per_step` PBNG sweeps (every
+colour pass + Chebyshev acceleration, rho 0.95, gamma 1.7) followed by the
+FP64 residual reduction, i.e. one convergence check of pbng_solve.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own replica:
+the path does not shard, there is no data-path collective; a barrier and a
+max-reduction of the timings bracket the timed region.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PBNG vertex-updates/s; time to rel. residual 1e-5 (plain vs batched+adjoint)"
+UNIT = "vertex-updates/s"
+# Algorithmic bytes of one colour pass (per-pass gather model): per
+# (vertex, incident tet) the three other displacements 36 B, dN/dX 36 B,
+# V 4 B, (mu, lambda) 8 B, three ids 12 B; per vertex u read + write 24 B,
+# f_ext 12 B, CSR offset 4 B.
+BYTES_PER_INCIDENCE = 96
+BYTES_PER_VERTEX = 40
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cells", type=int, default=64)
+    ap.add_argument("--sweeps-per-step", type=int, default=10)
+    ap.add_argument("--precision", choices=["compensated", "fp32"], default="compensated")
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-5 solves")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(cells):
+    import workloads as W
+    return W.gravity_sag(cells)
+
+
+def config_of(args, p):
+    return {
+        "workload": f"gravity-sag cube {args.cells}^3 cells, 5 tets/cell "
+                    f"({p.nv} verts, {p.ne} tets, {p.n_free} free), fixed-corotated "
+                    "E=1e5 nu=0.45, rho=1000, face x=0 clamped",
+        "sweeps_per_step": args.sweeps_per_step,
+        "accel": "chebyshev rho=0.95 gamma=1.7",
+        "precision": args.precision,
+        "l2": "inputs larger than L2 (per-incidence records ~294 MB streamed per sweep)",
+        "seed": "deterministic grid, no random draws",
+    }
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """Per-launch DRAM bytes of the colour pass from the committed ncu summary,
+    or None when the kernel source changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "colour_pass_traffic.json")
+    src = os.path.join(ROOT, "paper_2306_09021_gb300", "csrc", "pbng_kernels.cu")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        with open(src, "rb") as f:
+            h = hashlib.sha256(f.read()).hexdigest()
+        if d.get("kernel_sha256") != h:
+            return None
+        return d
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline(p, sweeps_budget_s=15.0, max_sweeps=12):
+    """The FP64 oracle, as it stands, on this host's cores: a bounded number of
+    Chebyshev sweeps of the same mesh."""
+    import oracle
+    ncpu = os.cpu_count() or 1
+    threads = oracle.threads_available(ncpu)
+    om = oracle.OracleMesh.from_problem(p)
+    x = p.x0.copy()
+    done, t0 = 0, time.perf_counter()
+    while done < max_sweeps:
+        x, st = om.sweeps(x, 1, accel="chebyshev", threads=threads)
+        done += 1
+        if time.perf_counter() - t0 > sweeps_budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": p.n_free * done / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{done} FP64 oracle sweeps of the full mesh ({done * p.n_free} vertex-updates, "
+                      f"{dt:.1f} s, OpenMP over each colour's vertices)"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores, same metric and
+    workload; each step is one oracle sweep of the whole mesh."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    p = workload(args.cells)
+    threads = oracle.threads_available(os.cpu_count() or 1)
+    om = oracle.OracleMesh.from_problem(p)
+    x = p.x0.copy()
+    for _ in range(args.warmup):
+        x, _ = om.sweeps(x, 1, accel="chebyshev", threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x, _ = om.sweeps(x, 1, accel="chebyshev", threads=threads)
+    dt = time.perf_counter() - t0
+    val = p.n_free * args.steps / dt
+    cfg = config_of(args, p)
+    cfg["sweeps_per_step"] = 1
+    out = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": cfg, "impl": "reference",
+           "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": f"{args.steps} FP64 oracle sweeps of the full mesh"},
+           "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2306_09021_gb300 import Mesh, default_params
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    p = workload(args.cells)
+    stream = torch.cuda.current_stream()
+    m = Mesh.from_problem(p, stream=stream)
+    u0 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    u = u0.clone()
+    S = args.sweeps_per_step
+    first = default_params(accel="chebyshev", precision=args.precision)
+    cont = default_params(accel="chebyshev", precision=args.precision, resume=1)
+
+    # warm-up (also loads the iterate and the acceleration history)
+    m.sweep(u, S, first, want_residual=True)
+    for _ in range(max(0, args.warmup - 1)):
+        m.sweep(u, S, cont, want_residual=True)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    m.set_profiling(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rel = None
+    for _ in range(args.steps):
+        rel = m.sweep(u, S, cont, want_residual=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prof = m.profile()
+    m.set_profiling(False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates_per_rank = p.n_free * S * args.steps
+    value = updates_per_rank * world / (ms * 1e-3)
+
+    # roofline of the dominant kernel (the colour pass)
+    peak, peak_kind = measured_peaks()
+    per_launch_ms = prof["colour_pass_ms"] / max(1, prof["colour_pass_launches"])
+    alg_bytes_sweep = BYTES_PER_INCIDENCE * prof["incidences"] + BYTES_PER_VERTEX * prof["free_vertices"]
+    alg_bytes_launch = alg_bytes_sweep / max(1, prof["ncolours"])
+    achieved = alg_bytes_launch / (per_launch_ms * 1e-3) / 1e9
+    tr = kernel_traffic()
+    roofline = {"kernel": "colour_pass_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": None if tr is None else tr["dram_bytes_per_launch"],
+                "alg_bytes_per_launch": alg_bytes_launch, "avg_launch_us": per_launch_ms * 1e3,
+                "launches_timed": prof["colour_pass_launches"],
+                "colour_pass_share_of_step": prof["colour_pass_ms"] / ms}
+
+    # end to end through the public API with host buffers
+    h_u = torch.empty_like(u, device="cpu").pin_memory()
+    h_u.copy_(u.cpu())
+    h_out = torch.empty_like(h_u).pin_memory()
+    e2e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        u.copy_(h_u, non_blocking=True)
+        m.sweep(u, S, first, want_residual=True)
+        h_out.copy_(u, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        u.copy_(h_u, non_blocking=True)
+        r = m.sweep(u, S, first, want_residual=True)
+        h_out.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+        h_u, h_out = h_out, h_u
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": p.n_free * S * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(u.numel() * 4), "d2h_bytes_per_step": int(u.numel() * 4 + 8),
+           "api": "Mesh.sweep (pbng_sweep, resume=0) with pinned host u copied in and out"}
+
+    # time to relative residual 1e-5 from rest (pbng_solve), per acceleration
+    ttr = {}
+    if not args.no_ttr:
+        for name, kw in (("chebyshev", dict(accel="chebyshev")), ("sor", dict(accel="sor", omega=1.5))):
+            uu = u0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, sweeps, relr = m.solve(uu, 1e-5, 20000,
+                                       default_params(precision=args.precision, residual_every=10, **kw),
+                                       raise_on_status=False)
+            torch.cuda.synchronize()
+            ttr[name] = {"status": int(st), "sweeps": int(sweeps), "rel_residual": float(relr[0]),
+                         "ms": 1e3 * (time.perf_counter() - t0)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": config_of(args, p), "clocks": clk, "roofline": roofline, "e2e": e2e,
+           "gpu_launches": int(prof["kernel_launches"]),
+           "rel_residual_end": None if rel is None else float(rel[0]),
+           "time_to_rel_1e-5": ttr}
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(p)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

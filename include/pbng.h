@@ -1,0 +1,176 @@
+/*
+ * pbng.h — C ABI of the GB300 (sm_103a) Position-Based Nonlinear Gauss-Seidel
+ * library (Chen, Han, Chen, Teran, "Position-Based Nonlinear Gauss-Seidel for
+ * Quasistatic Hyperelasticity", arXiv 2306.09021).
+ *
+ * The library solves the discrete quasistatic equilibrium of Section
+ * "Discretization" (Eq. fem_qs / Eq. fem_d) for P1 tetrahedral meshes with the
+ * fixed-corotated energy of Section "Constitutive Models" (Eq. cor), weak
+ * constraints of Section "Weak Constraints" (zero-rest-length springs to fixed
+ * targets, frictionless plane contact with k_tau = 0) and a constant body
+ * acceleration.  One sweep updates every free vertex once, colour by colour
+ * (Section "Coloring and Parallelism"), with the one-step modified-Newton node
+ * update of Eq. pbgn_update / Eq. pbgn_dx and the SPD nodal Hessian of
+ * Eq. mod_hess; Chebyshev or SOR acceleration (Section "Acceleration
+ * Techniques") is applied after each whole sweep.
+ *
+ * General rules for every entry point:
+ *  - No function aborts, throws or prints.  Each returns a pbng_status; the
+ *    text of the last failure of a handle is available from pbng_last_error.
+ *  - Host arrays passed in are copied; the caller keeps ownership.
+ *  - Device arrays ("_dev") are owned by the caller, must be 4-byte aligned,
+ *    contiguous and on the handle's device, and must stay valid until the
+ *    call returns.  All GPU work is enqueued on the handle's stream.
+ *  - A handle is not thread-safe.  After PBNG_ECUDA the handle must only be
+ *    destroyed.
+ *  - Vertex ids are 0-based int32 in the caller's order; the library keeps
+ *    its own colour-ordered layout internally and translates at the boundary.
+ *  - Displacements u = x - X are float32 [nv][3], row-major, in the caller's
+ *    vertex order.
+ */
+#ifndef PBNG_H
+#define PBNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PBNG_OK = 0,
+    PBNG_EINVAL = 1,          /* bad argument, size or index                  */
+    PBNG_ENOMEM = 2,          /* host or device allocation failed             */
+    PBNG_ECUDA = 3,           /* a CUDA runtime call failed                   */
+    PBNG_EDEGENERATE = 4,     /* rest tet of (near) zero volume, or a nodal
+                                 Hessian that is not positive definite         */
+    PBNG_EDIVERGED = 5,       /* non-finite value or residual > 1e3 r_0        */
+    PBNG_ETIMEOUT = 6,        /* a bounded device wait gave up                 */
+    PBNG_ENOTCONVERGED = 7    /* max_sweeps reached before rel_tol             */
+} pbng_status;
+
+typedef struct pbng_mesh pbng_mesh;   /* opaque, library-owned */
+
+enum { PBNG_ACCEL_NONE = 0, PBNG_ACCEL_CHEBYSHEV = 1, PBNG_ACCEL_SOR = 2 };
+enum { PBNG_PREC_FP32 = 0, PBNG_PREC_COMPENSATED = 1 };
+
+typedef struct {
+    int32_t model;          /* 0 = fixed corotated (Eq. cor); no other model yet  */
+    int32_t accel;          /* PBNG_ACCEL_*                                        */
+    double omega;           /* SOR weight (Section "Acceleration Techniques": 1.7) */
+    double rho;             /* Chebyshev spectral estimate (0.95)                  */
+    double gamma;           /* Chebyshev relaxation (1.7)                          */
+    double step;            /* scale of the Newton step of Eq. pbgn_dx (1.0)       */
+    double skip_tol;        /* skip nodes with |r_i| <= skip_tol; 0 = never skip   */
+    int32_t residual_every; /* pbng_solve: sweeps between residual checks (>= 1)   */
+    int32_t resume;         /* 1: continue from the handle's iterate, its
+                               acceleration history and sweep index; u_dev is
+                               then output only.  0: start from u_dev.             */
+    int32_t precision;      /* PBNG_PREC_FP32: the iterate is float32.
+                               PBNG_PREC_COMPENSATED: the iterate is kept as a
+                               float32 pair (hi + lo), neighbour differences and
+                               updates are formed in that pair; all element
+                               arithmetic stays float32.                          */
+    int32_t reserved[4];
+} pbng_params;
+
+/* Fills p with the paper's defaults: corotated, no acceleration, omega 1.7,
+ * rho 0.95, gamma 1.7, step 1, skip_tol 0, residual_every 10, resume 0,
+ * compensated precision. */
+void pbng_default_params(pbng_params* p);
+
+/* Creates a mesh handle (Section "Discretization": P1 tetrahedra, per-tet
+ * constant dN/dX and rest volume V^0; Eq. lame for (mu, lambda)).
+ *   rest_xyz  host double [nv][3]  rest positions X
+ *   tets      host int32  [ne][4]  vertex ids (either orientation)
+ *   young     host double [ne]     Young's modulus E_e > 0
+ *   poisson   host double [ne]     Poisson ratio, 0 <= nu < 0.5
+ *   mesh_id   host int32  [nv] or NULL: component id of each vertex for
+ *             batches of independent meshes (ids 0..ncomp-1); NULL = one mesh
+ *   stream    cudaStream_t as void*, or NULL for the legacy default stream
+ * The device is the one current at this call.  Fails with PBNG_EDEGENERATE if
+ * a rest tet has |det Dm|/6 <= 1e-12 h^3 (h = its largest edge component),
+ * PBNG_EINVAL on bad ids or sizes. */
+pbng_status pbng_create_mesh(const double* rest_xyz, int32_t nv, const int32_t* tets, int32_t ne,
+                             const double* young, const double* poisson, const int32_t* mesh_id,
+                             void* stream, pbng_mesh** out);
+
+/* Sets the boundary data (replaces earlier calls).  Eq. fem_d: clamped
+ * vertices dir_idx[nd] are held at dir_xyz (host double [nd][3], absolute
+ * positions).  Section "Weak Constraints": springs tie vertex spr_idx[s] to
+ * spr_target[s] (host double [ns][3]) with energy spr_k[s]/2 |x - t|^2.
+ * plane_nd (host double [4] = n, d, or NULL) adds contact energy
+ * k_contact/2 (n.x - d)^2 for n.x < d (n is normalised by the library).
+ * body_accel (host double [3] or NULL) with density (host double [ne], or
+ * NULL = 1) gives f^ext_i = sum_e rho_e a V_e / 4.  Re-colours the free
+ * vertices (Dirichlet vertices take no colour). */
+pbng_status pbng_set_constraints(pbng_mesh* m, const int32_t* dir_idx, const double* dir_xyz,
+                                 int32_t nd, const int32_t* spr_idx, const double* spr_target,
+                                 const double* spr_k, int32_t ns, const double* plane_nd,
+                                 double k_contact, const double* body_accel,
+                                 const double* density);
+
+/* Greedy node colouring of Section "Coloring and Parallelism": free vertices
+ * in ascending id take the least colour not used by any vertex sharing a tet.
+ * colour_out: host int32 [nv], -1 for clamped vertices.  ncolours: host. */
+pbng_status pbng_get_colouring(pbng_mesh* m, int32_t* colour_out, int32_t* ncolours);
+
+/* Runs nsweeps PBNG iterations on u_dev (device float [nv][3], in/out; the
+ * entries of clamped vertices are overwritten with x_D - X).  If
+ * rel_residual_out (host double[1] per component, or NULL) is given, the
+ * FP64 relative residual |f + f^ext|_free / r_0 after the last sweep is
+ * written, r_0 being the residual at the start (resume = 0) or the stored one.
+ * Synchronises the stream before returning. */
+pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_params* p,
+                       double* rel_residual_out);
+
+/* Sweeps until every component's relative residual is <= rel_tol (checked
+ * every p->residual_every sweeps) or max_sweeps is reached.  sweeps_out (host,
+ * may be NULL) receives the sweeps done; rel_residual_out (host double
+ * [ncomp], may be NULL) the final relative residuals.  Returns
+ * PBNG_ENOTCONVERGED when max_sweeps ran out, PBNG_EDIVERGED on a non-finite
+ * or growing (> 1e3 r_0) residual. */
+pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps,
+                       const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out);
+
+/* FP64 2-norm of (f + f^ext) over free vertices at u_dev (Section "PBNG vs.
+ * PBD and Limited Newton": the 2-norm of the Newton residual), per component
+ * (host double [ncomp]).  Does not modify u_dev. */
+pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out);
+
+/* Per-kernel timing on the handle's stream (tracing; Section "Coloring and
+ * Parallelism" reports per-iteration runtimes).  While enabled, each colour
+ * pass, acceleration and residual launch is bracketed by CUDA events.
+ * Counters accumulate from the pbng_set_profiling(m, 1) call. */
+typedef struct {
+    int64_t colour_pass_launches;
+    double colour_pass_ms;        /* summed event time of all colour passes   */
+    int64_t accel_launches;
+    double accel_ms;
+    int64_t residual_launches;    /* residual evaluations (all colours + sum) */
+    double residual_ms;
+    int64_t kernel_launches;      /* every kernel this handle launched        */
+    int64_t free_vertices;        /* of the current layout                    */
+    int64_t incidences;           /* (free vertex, incident tet) pairs        */
+    int32_t ncolours;
+    int32_t reserved;
+} pbng_profile;
+
+/* enable = 1 starts (and zeroes) the counters, 0 stops timing. */
+pbng_status pbng_set_profiling(pbng_mesh* m, int32_t enable);
+/* Synchronises the stream and returns the counters. */
+pbng_status pbng_get_profile(pbng_mesh* m, pbng_profile* out);
+
+/* Number of independent components (1 unless mesh_id was given). */
+int32_t pbng_num_components(const pbng_mesh* m);
+
+const char* pbng_status_string(pbng_status s);
+/* Text of the last failure on this handle ("" if none); valid until the next call. */
+const char* pbng_last_error(const pbng_mesh* m);
+void pbng_destroy(pbng_mesh* m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBNG_H */

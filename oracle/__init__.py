@@ -68,6 +68,7 @@ def lib():
             "ora_newton": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_double, ctypes.c_int, _D]),
             "ora_hessian_dense": (None, [ctypes.c_void_p, _D, _D]),
             "ora_adjoint_dense": (ctypes.c_int, [ctypes.c_void_p, _D, _D, _D, _D]),
+            "ora_threads_available": (ctypes.c_int, [ctypes.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -253,6 +254,11 @@ class OracleMesh:
         if st != 0:
             raise RuntimeError("singular Hessian in the dense adjoint")
         return dE, dD
+
+
+def threads_available(n):
+    """Threads the oracle's sweep would use when asked for n."""
+    return lib().ora_threads_available(int(n))
 
 
 def build():

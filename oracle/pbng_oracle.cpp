@@ -11,6 +11,9 @@
 #include <cstring>
 #include <set>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -684,11 +687,16 @@ int ora_newton(const void* h, double* x, double rel_tol, int maxit, double* res_
             for (int p = 0; p < nf; ++p) diag = std::max(diag, std::fabs(Hf[(size_t)p * nf + p]));
             shift = (shift == 0.0) ? 1e-6 * diag : 10.0 * shift;
         }
-        double E0 = energy(m, x), alpha = 1.0;
+        // Backtracking on the energy.  Near the solution the predicted energy
+        // decrease alpha (d . r) falls below the rounding of E itself; there a
+        // step that lowers the residual norm is accepted instead.
+        double E0 = energy(m, x), alpha = 1.0, dr = 0.0;
+        for (int p = 0; p < nf; ++p) dr += d[p] * b[p];
         std::vector<double> xt(x, x + n);
         for (int ls = 0; ls < 40; ++ls) {
             for (int p = 0; p < nf; ++p) xt[fdof[p]] = x[fdof[p]] + alpha * d[p];
             if (energy(m, xt.data()) <= E0) break;
+            if (alpha * dr < 1e-12 * std::fabs(E0) && residual(m, xt.data(), nullptr) < rn) break;
             alpha *= 0.5;
         }
         std::copy(xt.begin(), xt.end(), x);
@@ -744,6 +752,15 @@ int ora_adjoint_dense(const void* h, const double* x, const double* dLdx, double
         dLdxD[p] = s;
     }
     return 0;
+}
+
+int ora_threads_available(int nthreads) {
+#ifdef _OPENMP
+    return nthreads > 0 ? std::min(nthreads, omp_get_num_procs()) : 1;
+#else
+    (void)nthreads;
+    return 1;
+#endif
 }
 
 }  // extern "C"

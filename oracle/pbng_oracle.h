@@ -95,6 +95,9 @@ void ora_hessian_dense(const void* h, const double* x, double* H);
 int ora_adjoint_dense(const void* h, const double* x, const double* dLdx,
                       double* dLdlogE, double* dLdxD);
 
+/* Threads ora_sweeps can use for nthreads requested (1 without OpenMP). */
+int ora_threads_available(int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

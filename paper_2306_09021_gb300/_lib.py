@@ -1,0 +1,114 @@
+"""ctypes loader for libpbng.so (the C ABI of include/pbng.h).
+
+Argument marshalling only: every call goes straight to the C entry point of
+the same name.  The library must have been built (``build.py``); there is no
+fallback implementation, so a missing library is a hard error.
+"""
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpbng.so")
+
+PBNG_OK = 0
+STATUS_NAMES = {
+    0: "PBNG_OK", 1: "PBNG_EINVAL", 2: "PBNG_ENOMEM", 3: "PBNG_ECUDA",
+    4: "PBNG_EDEGENERATE", 5: "PBNG_EDIVERGED", 6: "PBNG_ETIMEOUT", 7: "PBNG_ENOTCONVERGED",
+}
+
+ACCEL = {"none": 0, "chebyshev": 1, "sor": 2}
+PRECISION = {"fp32": 0, "compensated": 1}
+
+
+class PbngParams(ctypes.Structure):
+    _fields_ = [
+        ("model", ctypes.c_int32),
+        ("accel", ctypes.c_int32),
+        ("omega", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("step", ctypes.c_double),
+        ("skip_tol", ctypes.c_double),
+        ("residual_every", ctypes.c_int32),
+        ("resume", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
+    ]
+
+
+class PbngProfile(ctypes.Structure):
+    _fields_ = [
+        ("colour_pass_launches", ctypes.c_int64),
+        ("colour_pass_ms", ctypes.c_double),
+        ("accel_launches", ctypes.c_int64),
+        ("accel_ms", ctypes.c_double),
+        ("residual_launches", ctypes.c_int64),
+        ("residual_ms", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
+        ("free_vertices", ctypes.c_int64),
+        ("incidences", ctypes.c_int64),
+        ("ncolours", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class PbngError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        msg = f"{where}: {STATUS_NAMES.get(status, status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI = ctypes.POINTER(ctypes.c_int32)
+
+# name -> (restype, argtypes); every function include/pbng.h declares
+SIGNATURES = {
+    "pbng_default_params": (None, [ctypes.POINTER(PbngParams)]),
+    "pbng_create_mesh": (_I32, [_PD, _I32, _PI, _I32, _PD, _PD, _PI, _P, ctypes.POINTER(_P)]),
+    "pbng_set_constraints": (_I32, [_P, _PI, _PD, _I32, _PI, _PD, _PD, _I32, _PD, _D, _PD, _PD]),
+    "pbng_get_colouring": (_I32, [_P, _PI, _PI]),
+    "pbng_sweep": (_I32, [_P, _P, _I32, ctypes.POINTER(PbngParams), _PD]),
+    "pbng_solve": (_I32, [_P, _P, _D, _I32, ctypes.POINTER(PbngParams), _PI, _PD]),
+    "pbng_residual": (_I32, [_P, _P, _PD]),
+    "pbng_set_profiling": (_I32, [_P, _I32]),
+    "pbng_get_profile": (_I32, [_P, ctypes.POINTER(PbngProfile)]),
+    "pbng_num_components": (_I32, [_P]),
+    "pbng_status_string": (ctypes.c_char_p, [_I32]),
+    "pbng_last_error": (ctypes.c_char_p, [_P]),
+    "pbng_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+def load():
+    """Loads libpbng.so once; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is missing: build it with paper_2306_09021_gb300.build.build() "
+            "(there is no non-CUDA implementation)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status, where, handle=None):
+    if status != PBNG_OK:
+        detail = ""
+        if handle:
+            detail = (load().pbng_last_error(handle) or b"").decode(errors="replace")
+        raise PbngError(status, where, detail)

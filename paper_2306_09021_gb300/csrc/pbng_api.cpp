@@ -1,0 +1,822 @@
+// Host runtime and C ABI of the PBNG library (declared in include/pbng.h).
+//
+// Mesh preparation (per-tet dN/dX, rest volume and Lame parameters), the
+// greedy node colouring, the colour-ordered device layout and the sweep
+// driver live here; every per-sweep step runs in the kernels of
+// pbng_kernels.cu.
+#include "pbng.h"
+#include "pbng_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace pbng;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct pbng_mesh {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int32_t nv = 0, ne = 0, ncomp = 1;
+    std::vector<double> X;          // 3 nv
+    std::vector<int32_t> tets;      // 4 ne
+    std::vector<double> B;          // 9 ne, rows g_1..g_3 of Dm^{-1}
+    std::vector<double> vol, mu, lam;
+    std::vector<int32_t> comp_of;   // nv (empty = single component)
+
+    // boundary data
+    std::vector<uint8_t> is_dir;    // nv
+    std::vector<double> dir_pos;    // 3 nv (valid where is_dir)
+    std::vector<double> spr_K;      // nv, total spring stiffness
+    std::vector<double> spr_KT;     // 3 nv, sum_s k_s t_s
+    bool has_plane = false;
+    double pn[3] = {0, 0, 1}, pd = 0.0, kc = 0.0;
+    std::vector<double> fext;       // 3 nv
+
+    // layout
+    bool dirty = true;
+    int32_t nfree = 0, ncol = 0;
+    std::vector<int32_t> colour;    // nv, -1 clamped
+    std::vector<int32_t> perm;      // internal -> caller id
+    std::vector<SegmentTable> tables;  // one per colour
+    std::vector<int32_t> table_partial_off;  // residual partial offset per colour
+    int32_t total_partials = 0;
+
+    // device buffers
+    DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
+    DevBuf d_dir_hi, d_dir_lo;
+    DevBuf d_state[4][2];           // cur, p1, p2, tmp; hi/lo
+    DevBuf d_partial, d_comp_sq, d_scalar, d_err;
+    double* h_pinned = nullptr;     // ncomp + 2 doubles for readbacks
+    DeviceMesh dm{};
+
+    // iteration state
+    bool has_state = false;
+    int32_t sweep_l = 0;
+    double omega_l = 1.0;
+    int p1_slot = 1, p2_slot = 2;
+    std::vector<double> r0;
+
+    // profiling (pbng_set_profiling): event pairs per timed launch
+    bool prof = false;
+    struct EvPair { cudaEvent_t a, b; int kind; };
+    std::vector<EvPair> ev_used;
+    std::vector<cudaEvent_t> ev_free;
+    int64_t prof_launches[3] = {0, 0, 0};   // colour pass, accel, residual
+    double prof_ms[3] = {0, 0, 0};
+    int64_t kernel_launches = 0;
+    int64_t ninc = 0;
+
+    std::string err;
+};
+
+namespace {
+
+enum { kProfColour = 0, kProfAccel = 1, kProfResidual = 2 };
+
+cudaError_t take_event(pbng_mesh* m, cudaEvent_t* e) {
+    if (!m->ev_free.empty()) {
+        *e = m->ev_free.back();
+        m->ev_free.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(e);
+}
+
+// Folds finished event pairs into the counters (synchronises the stream).
+cudaError_t prof_flush(pbng_mesh* m) {
+    if (m->ev_used.empty()) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) return e;
+    for (auto& p : m->ev_used) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, p.a, p.b);
+        if (e != cudaSuccess) return e;
+        m->prof_ms[p.kind] += ms;
+        m->ev_free.push_back(p.a);
+        m->ev_free.push_back(p.b);
+    }
+    m->ev_used.clear();
+    return cudaSuccess;
+}
+
+// Records the opening event of a timed launch; returns its slot or -1.
+int prof_begin(pbng_mesh* m, int kind) {
+    if (!m->prof) return -1;
+    if (m->ev_used.size() >= 8192 && prof_flush(m) != cudaSuccess) return -1;
+    pbng_mesh::EvPair p{};
+    p.kind = kind;
+    if (take_event(m, &p.a) != cudaSuccess || take_event(m, &p.b) != cudaSuccess) return -1;
+    if (cudaEventRecord(p.a, m->stream) != cudaSuccess) return -1;
+    m->ev_used.push_back(p);
+    return (int)m->ev_used.size() - 1;
+}
+
+void prof_end(pbng_mesh* m, int slot) {
+    if (slot < 0) return;
+    pbng_mesh::EvPair& p = m->ev_used[slot];
+    cudaEventRecord(p.b, m->stream);
+    m->prof_launches[p.kind]++;
+}
+
+pbng_status fail(pbng_mesh* m, pbng_status s, const std::string& msg) {
+    if (m) m->err = msg;
+    return s;
+}
+
+pbng_status cuda_fail(pbng_mesh* m, cudaError_t e, const char* what) {
+    return fail(m, PBNG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PBNG_CUDA(m, call)                                   \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(m, e_, #call); \
+    } while (0)
+
+void free_buf(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+cudaError_t ensure_buf(DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return cudaSuccess;
+    free_buf(b);
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) b.bytes = bytes;
+    return e;
+}
+
+template <class T>
+cudaError_t upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
+    cudaError_t e = ensure_buf(b, v.size() * sizeof(T));
+    if (e != cudaSuccess || v.empty()) return e;
+    e = cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);  // host vectors may go away after return
+}
+
+double det3(const double* F) {
+    return F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+           F[2] * (F[3] * F[7] - F[4] * F[6]);
+}
+
+// Section "Coloring and Parallelism" (node colouring): free vertices in
+// ascending id take the least colour that no element containing them has
+// registered yet, then register it in each of those elements.  Element
+// colour sets are bit masks of `words` 64-bit words.
+bool greedy_colour(const pbng_mesh& m, const std::vector<int32_t>& inc_off,
+                   const std::vector<int32_t>& inc_tet, int words, std::vector<int32_t>& colour,
+                   int32_t& ncol) {
+    std::vector<uint64_t> used((size_t)m.ne * words, 0);
+    std::vector<uint64_t> acc(words);
+    colour.assign(m.nv, -1);
+    ncol = 0;
+    for (int32_t i = 0; i < m.nv; ++i) {
+        if (m.is_dir[i]) continue;
+        std::fill(acc.begin(), acc.end(), 0);
+        for (int32_t k = inc_off[i]; k < inc_off[i + 1]; ++k) {
+            const uint64_t* u = &used[(size_t)inc_tet[k] * words];
+            for (int w = 0; w < words; ++w) acc[w] |= u[w];
+        }
+        int c = -1;
+        for (int w = 0; w < words && c < 0; ++w)
+            if (~acc[w]) {
+                uint64_t free_bits = ~acc[w];
+                int b = 0;
+                while (!(free_bits & 1ull)) { free_bits >>= 1; ++b; }
+                c = 64 * w + b;
+            }
+        if (c < 0) return false;
+        colour[i] = c;
+        ncol = std::max(ncol, c + 1);
+        for (int32_t k = inc_off[i]; k < inc_off[i + 1]; ++k)
+            used[(size_t)inc_tet[k] * words + (c >> 6)] |= 1ull << (c & 63);
+    }
+    return true;
+}
+
+int width_for(int deg) {
+    if (deg <= 4) return 4;
+    if (deg <= 8) return 8;
+    if (deg <= 16) return 16;
+    return 32;
+}
+
+// Builds the colour-ordered layout and uploads it.
+pbng_status build_layout(pbng_mesh* m) {
+    const int32_t nv = m->nv, ne = m->ne;
+    // vertex -> incident (tet, local) in ascending tet order
+    std::vector<int32_t> inc_off(nv + 1, 0), inc_tet(4 * (size_t)ne), inc_loc(4 * (size_t)ne);
+    for (int32_t v : m->tets) inc_off[v + 1]++;
+    for (int32_t i = 0; i < nv; ++i) inc_off[i + 1] += inc_off[i];
+    {
+        std::vector<int32_t> fill(inc_off.begin(), inc_off.end() - 1);
+        for (int32_t e = 0; e < ne; ++e)
+            for (int j = 0; j < 4; ++j) {
+                int32_t v = m->tets[4 * (size_t)e + j];
+                inc_tet[fill[v]] = e;
+                inc_loc[fill[v]] = j;
+                fill[v]++;
+            }
+    }
+    int words = 1;
+    while (!greedy_colour(*m, inc_off, inc_tet, words, m->colour, m->ncol)) {
+        words *= 2;
+        if (words > 64) return fail(m, PBNG_EINVAL, "colouring needs more than 4096 colours");
+    }
+    // internal order: colour, then lane-group width (widest first), then id
+    std::vector<int32_t> order;
+    order.reserve(nv);
+    for (int32_t i = 0; i < nv; ++i)
+        if (!m->is_dir[i]) order.push_back(i);
+    auto deg = [&](int32_t i) { return inc_off[i + 1] - inc_off[i]; };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        if (m->colour[a] != m->colour[b]) return m->colour[a] < m->colour[b];
+        return width_for(deg(a)) > width_for(deg(b));
+    });
+    m->nfree = (int32_t)order.size();
+    for (int32_t i = 0; i < nv; ++i)
+        if (m->is_dir[i]) order.push_back(i);
+    m->perm = order;
+    std::vector<int32_t> iperm(nv);
+    for (int32_t v = 0; v < nv; ++v) iperm[order[v]] = v;
+
+    // segments per colour
+    m->tables.assign(m->ncol, SegmentTable{});
+    m->table_partial_off.assign(m->ncol + 1, 0);
+    int32_t v = 0;
+    for (int c = 0; c < m->ncol; ++c) {
+        SegmentTable& t = m->tables[c];
+        t.count = 0;
+        t.total_blocks = 0;
+        while (v < m->nfree && m->colour[order[v]] == c) {
+            int W = width_for(deg(order[v]));
+            int32_t b = v;
+            while (v < m->nfree && m->colour[order[v]] == c && width_for(deg(order[v])) == W) ++v;
+            if (t.count >= kMaxSegments) return fail(m, PBNG_EINVAL, "too many segments");
+            Segment& s = t.seg[t.count++];
+            s.v_begin = b;
+            s.v_end = v;
+            s.width = W;
+            s.block_begin = t.total_blocks;
+            const int per_block = kBlock / W;
+            t.total_blocks += (v - b + per_block - 1) / per_block;
+        }
+        m->table_partial_off[c + 1] = m->table_partial_off[c] + t.total_blocks;
+    }
+    m->total_partials = m->table_partial_off[m->ncol];
+
+    // per-incidence records in internal CSR order
+    std::vector<int32_t> off(m->nfree + 1, 0);
+    for (int32_t w = 0; w < m->nfree; ++w) off[w + 1] = off[w] + deg(order[w]);
+    const size_t ninc = (size_t)off[m->nfree];
+    m->ninc = (int64_t)ninc;
+    std::vector<float4> ra(ninc), rb(ninc), rc(ninc);
+    std::vector<float2> rd(ninc);
+    for (int32_t w = 0; w < m->nfree; ++w) {
+        const int32_t i = order[w];
+        size_t s = off[w];
+        for (int32_t k = inc_off[i]; k < inc_off[i + 1]; ++k, ++s) {
+            const int32_t e = inc_tet[k];
+            const int loc = inc_loc[k];
+            const double* Be = &m->B[9 * (size_t)e];
+            double g[4][3];
+            for (int a = 0; a < 3; ++a) {
+                g[1][a] = Be[a];
+                g[2][a] = Be[3 + a];
+                g[3][a] = Be[6 + a];
+                g[0][a] = -(Be[a] + Be[3 + a] + Be[6 + a]);
+            }
+            int oth[3], n = 0;
+            for (int j = 0; j < 4; ++j)
+                if (j != loc) oth[n++] = j;
+            int32_t ids[3];
+            for (int q = 0; q < 3; ++q) ids[q] = iperm[m->tets[4 * (size_t)e + oth[q]]];
+            const double a2 = 2.0 * m->mu[e] * m->vol[e], bl = m->lam[e] * m->vol[e];
+            float4 A4, B4, C4;
+            std::memcpy(&A4.x, &ids[0], 4);
+            std::memcpy(&A4.y, &ids[1], 4);
+            std::memcpy(&A4.z, &ids[2], 4);
+            A4.w = (float)a2;
+            B4 = make_float4((float)g[oth[0]][0], (float)g[oth[0]][1], (float)g[oth[0]][2], (float)bl);
+            C4 = make_float4((float)g[oth[1]][0], (float)g[oth[1]][1], (float)g[oth[1]][2], (float)g[oth[2]][0]);
+            ra[s] = A4;
+            rb[s] = B4;
+            rc[s] = C4;
+            rd[s] = make_float2((float)g[oth[2]][1], (float)g[oth[2]][2]);
+        }
+    }
+    std::vector<float4> aux0(m->nfree), aux1(m->nfree);
+    std::vector<int32_t> comp(m->ncomp > 1 ? m->nfree : 0);
+    for (int32_t w = 0; w < m->nfree; ++w) {
+        const int32_t i = order[w];
+        const double K = m->spr_K[i];
+        float4 a0 = make_float4((float)m->fext[3 * i], (float)m->fext[3 * i + 1], (float)m->fext[3 * i + 2], (float)K);
+        float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (K > 0.0)
+            for (int a = 0; a < 3; ++a)
+                (&a1.x)[a] = (float)(m->spr_KT[3 * i + a] / K - m->X[3 * i + a]);
+        if (m->has_plane)
+            a1.w = (float)(m->pn[0] * m->X[3 * i] + m->pn[1] * m->X[3 * i + 1] + m->pn[2] * m->X[3 * i + 2] - m->pd);
+        aux0[w] = a0;
+        aux1[w] = a1;
+        if (m->ncomp > 1) comp[w] = m->comp_of[i];
+    }
+    const int32_t nd = nv - m->nfree;
+    std::vector<float4> dhi(nd), dlo(nd);
+    for (int32_t q = 0; q < nd; ++q) {
+        const int32_t i = order[m->nfree + q];
+        float h[3], l[3];
+        for (int a = 0; a < 3; ++a) {
+            const double d = m->dir_pos[3 * i + a] - m->X[3 * i + a];
+            h[a] = (float)d;
+            l[a] = (float)(d - (double)h[a]);
+        }
+        dhi[q] = make_float4(h[0], h[1], h[2], 0.f);
+        dlo[q] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+    cudaStream_t st = m->stream;
+    PBNG_CUDA(m, upload(m->d_inc_off, off, st));
+    PBNG_CUDA(m, upload(m->d_rec_a, ra, st));
+    PBNG_CUDA(m, upload(m->d_rec_b, rb, st));
+    PBNG_CUDA(m, upload(m->d_rec_c, rc, st));
+    PBNG_CUDA(m, upload(m->d_rec_d, rd, st));
+    PBNG_CUDA(m, upload(m->d_aux0, aux0, st));
+    PBNG_CUDA(m, upload(m->d_aux1, aux1, st));
+    PBNG_CUDA(m, upload(m->d_comp, comp, st));
+    PBNG_CUDA(m, upload(m->d_perm, m->perm, st));
+    PBNG_CUDA(m, upload(m->d_dir_hi, dhi, st));
+    PBNG_CUDA(m, upload(m->d_dir_lo, dlo, st));
+    for (auto& sb : m->d_state)
+        for (auto& b : sb) PBNG_CUDA(m, ensure_buf(b, sizeof(float4) * (size_t)nv));
+    PBNG_CUDA(m, ensure_buf(m->d_partial, sizeof(double) * (size_t)std::max(1, m->total_partials)));
+    PBNG_CUDA(m, ensure_buf(m->d_comp_sq, sizeof(double) * (size_t)m->ncomp));
+    PBNG_CUDA(m, ensure_buf(m->d_scalar, sizeof(double) * 4));
+    PBNG_CUDA(m, ensure_buf(m->d_err, sizeof(int32_t)));
+    PBNG_CUDA(m, cudaMemsetAsync(m->d_err.p, 0, sizeof(int32_t), st));
+
+    DeviceMesh& d = m->dm;
+    d.nv = nv;
+    d.nfree = m->nfree;
+    d.inc_off = (const int32_t*)m->d_inc_off.p;
+    d.rec_a = (const float4*)m->d_rec_a.p;
+    d.rec_b = (const float4*)m->d_rec_b.p;
+    d.rec_c = (const float4*)m->d_rec_c.p;
+    d.rec_d = (const float2*)m->d_rec_d.p;
+    d.aux0 = (const float4*)m->d_aux0.p;
+    d.aux1 = (const float4*)m->d_aux1.p;
+    d.comp = m->ncomp > 1 ? (const int32_t*)m->d_comp.p : nullptr;
+    d.pn_x = (float)m->pn[0];
+    d.pn_y = (float)m->pn[1];
+    d.pn_z = (float)m->pn[2];
+    d.k_contact = m->has_plane ? (float)m->kc : 0.0f;
+    m->dirty = false;
+    m->has_state = false;
+    return PBNG_OK;
+}
+
+State state_of(pbng_mesh* m, int slot) {
+    return State{(float4*)m->d_state[slot][0].p, (float4*)m->d_state[slot][1].p};
+}
+
+pbng_status ensure_ready(pbng_mesh* m) {
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    cudaError_t e = cudaSetDevice(m->device);
+    if (e != cudaSuccess) return cuda_fail(m, e, "cudaSetDevice");
+    if (m->dirty) return build_layout(m);
+    return PBNG_OK;
+}
+
+// FP64 squared residual norms (per component) of state `slot` -> host `out`.
+pbng_status residual_sq(pbng_mesh* m, int slot, bool compensated, double* out) {
+    cudaStream_t st = m->stream;
+    State s = state_of(m, slot);
+    const bool multi = m->ncomp > 1;
+    const int pslot = prof_begin(m, kProfResidual);
+    if (multi) PBNG_CUDA(m, cudaMemsetAsync(m->d_comp_sq.p, 0, sizeof(double) * m->ncomp, st));
+    for (int c = 0; c < m->ncol; ++c) {
+        PBNG_CUDA(m, launch_residual(m->dm, s, m->tables[c], compensated,
+                                     (double*)m->d_partial.p + m->table_partial_off[c],
+                                     multi ? (double*)m->d_comp_sq.p : nullptr, m->ncomp, nullptr, st));
+        if (m->tables[c].total_blocks > 0) m->kernel_launches++;
+    }
+    if (!multi) {
+        PBNG_CUDA(m, launch_reduce((const double*)m->d_partial.p, m->total_partials,
+                                   (double*)m->d_scalar.p, st));
+        m->kernel_launches++;
+    }
+    prof_end(m, pslot);
+    if (multi) {
+        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_comp_sq.p, sizeof(double) * m->ncomp,
+                                     cudaMemcpyDeviceToHost, st));
+    } else {
+        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_scalar.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    for (int k = 0; k < m->ncomp; ++k) out[k] = m->h_pinned[k];
+    if (m->ncol == 0)
+        for (int k = 0; k < m->ncomp; ++k) out[k] = 0.0;
+    return PBNG_OK;
+}
+
+pbng_status check_err(pbng_mesh* m) {
+    int32_t h = 0;
+    PBNG_CUDA(m, cudaMemcpyAsync(&h, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream));
+    PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (h) {
+        PBNG_CUDA(m, cudaMemsetAsync(m->d_err.p, 0, sizeof(int32_t), m->stream));
+        if (h & kErrNonSPD) return fail(m, PBNG_EDEGENERATE, "nodal Hessian not positive definite");
+        return fail(m, PBNG_EDIVERGED, "non-finite vertex update");
+    }
+    return PBNG_OK;
+}
+
+bool valid_params(const pbng_params* p) {
+    return p && p->model == 0 && p->accel >= 0 && p->accel <= 2 && p->residual_every >= 1 &&
+           (p->precision == PBNG_PREC_FP32 || p->precision == PBNG_PREC_COMPENSATED) &&
+           std::isfinite(p->omega) && std::isfinite(p->rho) && std::isfinite(p->gamma) &&
+           std::isfinite(p->step) && p->skip_tol >= 0.0;
+}
+
+// Loads u_dev (or keeps the stored iterate) and resets the history.
+pbng_status begin(pbng_mesh* m, const float* u_dev, const pbng_params* p, bool need_r0) {
+    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    if (!p->resume || !m->has_state) {
+        if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
+        PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, (const int32_t*)m->d_perm.p,
+                                 (const float4*)m->d_dir_hi.p, (const float4*)m->d_dir_lo.p,
+                                 state_of(m, 0), m->stream));
+        PBNG_CUDA(m, launch_copy_state(m->nv, state_of(m, 0), state_of(m, 1), m->stream));
+        PBNG_CUDA(m, launch_copy_state(m->nv, state_of(m, 0), state_of(m, 2), m->stream));
+        m->kernel_launches += 3;
+        m->p1_slot = 1;
+        m->p2_slot = 2;
+        m->sweep_l = 0;
+        m->omega_l = 1.0;
+        m->has_state = true;
+        m->r0.assign(m->ncomp, -1.0);
+    }
+    if (need_r0 && (m->r0.empty() || m->r0[0] < 0.0)) {
+        m->r0.assign(m->ncomp, 0.0);
+        pbng_status s = residual_sq(m, 0, comp, m->r0.data());
+        if (s) return s;
+        for (auto& r : m->r0) r = std::sqrt(r);
+    }
+    return PBNG_OK;
+}
+
+// One PBNG iteration over all colours, then the acceleration step.
+pbng_status one_sweep(pbng_mesh* m, const pbng_params* p) {
+    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    PassParams pp{(float)p->step, (float)p->skip_tol};
+    State cur = state_of(m, 0);
+    for (int c = 0; c < m->ncol; ++c) {
+        if (m->tables[c].total_blocks <= 0) continue;
+        const int slot = prof_begin(m, kProfColour);
+        PBNG_CUDA(m, launch_colour_pass(m->dm, cur, m->tables[c], pp, comp, (int32_t*)m->d_err.p, m->stream));
+        prof_end(m, slot);
+        m->kernel_launches++;
+    }
+    if (p->accel != PBNG_ACCEL_NONE) {
+        double w, g;
+        const int l = m->sweep_l;
+        if (p->accel == PBNG_ACCEL_CHEBYSHEV) {
+            // omega_{l+1} = 1 (l < 2), 2/(2 - rho^2) (l = 2), 4/(4 - rho^2 omega_l) (l > 2)
+            if (l < 2) w = 1.0;
+            else if (l == 2) w = 2.0 / (2.0 - p->rho * p->rho);
+            else w = 4.0 / (4.0 - p->rho * p->rho * m->omega_l);
+            m->omega_l = w;
+            g = p->gamma;
+        } else {
+            w = p->omega;
+            g = 1.0;
+        }
+        const int slot = prof_begin(m, kProfAccel);
+        PBNG_CUDA(m, launch_accel(m->nfree, cur, state_of(m, m->p1_slot), state_of(m, m->p2_slot),
+                                  (float)w, (float)g, comp, m->stream));
+        prof_end(m, slot);
+        if (m->nfree > 0) m->kernel_launches++;
+        std::swap(m->p1_slot, m->p2_slot);
+    }
+    m->sweep_l++;
+    return PBNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pbng_default_params(pbng_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->model = 0;
+    p->accel = PBNG_ACCEL_NONE;
+    p->omega = 1.7;
+    p->rho = 0.95;
+    p->gamma = 1.7;
+    p->step = 1.0;
+    p->skip_tol = 0.0;
+    p->residual_every = 10;
+    p->resume = 0;
+    p->precision = PBNG_PREC_COMPENSATED;
+}
+
+pbng_status pbng_create_mesh(const double* rest_xyz, int32_t nv, const int32_t* tets, int32_t ne,
+                             const double* young, const double* poisson, const int32_t* mesh_id,
+                             void* stream, pbng_mesh** out) {
+    if (!out) return PBNG_EINVAL;
+    *out = nullptr;
+    if (!rest_xyz || nv <= 0 || ne <= 0 || !tets || !young || !poisson) return PBNG_EINVAL;
+    if ((int64_t)ne * 4 > INT32_MAX) return PBNG_EINVAL;
+    pbng_mesh* m = new (std::nothrow) pbng_mesh();
+    if (!m) return PBNG_ENOMEM;
+    try {
+        if (cudaGetDevice(&m->device) != cudaSuccess) { delete m; return PBNG_ECUDA; }
+        m->stream = (cudaStream_t)stream;
+        m->nv = nv;
+        m->ne = ne;
+        m->X.assign(rest_xyz, rest_xyz + 3 * (size_t)nv);
+        m->tets.assign(tets, tets + 4 * (size_t)ne);
+        for (int32_t v : m->tets)
+            if (v < 0 || v >= nv) { delete m; return PBNG_EINVAL; }
+        m->B.resize(9 * (size_t)ne);
+        m->vol.resize(ne);
+        m->mu.resize(ne);
+        m->lam.resize(ne);
+        for (int32_t e = 0; e < ne; ++e) {
+            const int32_t* t = &m->tets[4 * (size_t)e];
+            double Dm[9], hmax = 0.0;
+            for (int c = 0; c < 3; ++c)
+                for (int a = 0; a < 3; ++a) {
+                    Dm[3 * a + c] = m->X[3 * (size_t)t[c + 1] + a] - m->X[3 * (size_t)t[0] + a];
+                    hmax = std::max(hmax, std::fabs(Dm[3 * a + c]));
+                }
+            const double D = det3(Dm);
+            if (!(std::fabs(D) / 6.0 > 1e-12 * hmax * hmax * hmax)) { delete m; return PBNG_EDEGENERATE; }
+            // rows of Dm^{-1} = columns of cof(Dm) / det
+            const double C[9] = {Dm[4] * Dm[8] - Dm[5] * Dm[7], Dm[5] * Dm[6] - Dm[3] * Dm[8],
+                                 Dm[3] * Dm[7] - Dm[4] * Dm[6], Dm[7] * Dm[2] - Dm[8] * Dm[1],
+                                 Dm[8] * Dm[0] - Dm[6] * Dm[2], Dm[6] * Dm[1] - Dm[7] * Dm[0],
+                                 Dm[1] * Dm[5] - Dm[2] * Dm[4], Dm[2] * Dm[3] - Dm[0] * Dm[5],
+                                 Dm[0] * Dm[4] - Dm[1] * Dm[3]};
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) m->B[9 * (size_t)e + 3 * a + b] = C[3 * b + a] / D;
+            m->vol[e] = std::fabs(D) / 6.0;
+            const double E = young[e], nu = poisson[e];
+            if (!(E > 0.0) || !(nu >= 0.0 && nu < 0.5)) { delete m; return PBNG_EINVAL; }
+            m->mu[e] = E / (2.0 * (1.0 + nu));                       // Eq. lame
+            m->lam[e] = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+        }
+        if (mesh_id) {
+            m->comp_of.assign(mesh_id, mesh_id + nv);
+            int32_t mx = -1;
+            for (int32_t c : m->comp_of) {
+                if (c < 0) { delete m; return PBNG_EINVAL; }
+                mx = std::max(mx, c);
+            }
+            m->ncomp = mx + 1;
+        }
+        m->is_dir.assign(nv, 0);
+        m->dir_pos.assign(3 * (size_t)nv, 0.0);
+        m->spr_K.assign(nv, 0.0);
+        m->spr_KT.assign(3 * (size_t)nv, 0.0);
+        m->fext.assign(3 * (size_t)nv, 0.0);
+        if (cudaMallocHost((void**)&m->h_pinned, sizeof(double) * (m->ncomp + 2)) != cudaSuccess) {
+            delete m;
+            return PBNG_ECUDA;
+        }
+    } catch (const std::bad_alloc&) {
+        delete m;
+        return PBNG_ENOMEM;
+    }
+    *out = m;
+    return PBNG_OK;
+}
+
+pbng_status pbng_set_constraints(pbng_mesh* m, const int32_t* dir_idx, const double* dir_xyz,
+                                 int32_t nd, const int32_t* spr_idx, const double* spr_target,
+                                 const double* spr_k, int32_t ns, const double* plane_nd,
+                                 double k_contact, const double* body_accel, const double* density) {
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    if (nd < 0 || ns < 0 || (nd > 0 && (!dir_idx || !dir_xyz)) ||
+        (ns > 0 && (!spr_idx || !spr_target || !spr_k)))
+        return fail(m, PBNG_EINVAL, "bad constraint arrays");
+    try {
+        std::fill(m->is_dir.begin(), m->is_dir.end(), 0);
+        for (int32_t q = 0; q < nd; ++q) {
+            const int32_t i = dir_idx[q];
+            if (i < 0 || i >= m->nv) return fail(m, PBNG_EINVAL, "clamped id out of range");
+            m->is_dir[i] = 1;
+            for (int a = 0; a < 3; ++a) m->dir_pos[3 * (size_t)i + a] = dir_xyz[3 * (size_t)q + a];
+        }
+        std::fill(m->spr_K.begin(), m->spr_K.end(), 0.0);
+        std::fill(m->spr_KT.begin(), m->spr_KT.end(), 0.0);
+        for (int32_t s = 0; s < ns; ++s) {
+            const int32_t i = spr_idx[s];
+            if (i < 0 || i >= m->nv || !(spr_k[s] >= 0.0)) return fail(m, PBNG_EINVAL, "bad spring");
+            m->spr_K[i] += spr_k[s];
+            for (int a = 0; a < 3; ++a) m->spr_KT[3 * (size_t)i + a] += spr_k[s] * spr_target[3 * (size_t)s + a];
+        }
+        m->has_plane = plane_nd != nullptr && k_contact > 0.0;
+        if (m->has_plane) {
+            const double n = std::sqrt(plane_nd[0] * plane_nd[0] + plane_nd[1] * plane_nd[1] + plane_nd[2] * plane_nd[2]);
+            if (!(n > 0.0)) return fail(m, PBNG_EINVAL, "zero plane normal");
+            for (int a = 0; a < 3; ++a) m->pn[a] = plane_nd[a] / n;
+            m->pd = plane_nd[3] / n;
+            m->kc = k_contact;
+        }
+        std::fill(m->fext.begin(), m->fext.end(), 0.0);
+        if (body_accel)
+            for (int32_t e = 0; e < m->ne; ++e) {
+                const double rho = density ? density[e] : 1.0;
+                for (int j = 0; j < 4; ++j)
+                    for (int a = 0; a < 3; ++a)
+                        m->fext[3 * (size_t)m->tets[4 * (size_t)e + j] + a] += rho * body_accel[a] * m->vol[e] / 4.0;
+            }
+    } catch (const std::bad_alloc&) {
+        return PBNG_ENOMEM;
+    }
+    m->dirty = true;
+    m->has_state = false;
+    return PBNG_OK;
+}
+
+pbng_status pbng_get_colouring(pbng_mesh* m, int32_t* colour_out, int32_t* ncolours) {
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (colour_out) std::copy(m->colour.begin(), m->colour.end(), colour_out);
+    if (ncolours) *ncolours = m->ncol;
+    return PBNG_OK;
+}
+
+pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_params* p,
+                       double* rel_residual_out) {
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!valid_params(p) || nsweeps < 0) return fail(m, PBNG_EINVAL, "bad parameters");
+    if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
+    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    if ((s = begin(m, u_dev, p, rel_residual_out != nullptr))) return s;
+    for (int32_t k = 0; k < nsweeps; ++k)
+        if ((s = one_sweep(m, p))) return s;
+    PBNG_CUDA(m, launch_store(m->nv, (const int32_t*)m->d_perm.p, state_of(m, 0), u_dev, m->stream));
+    m->kernel_launches++;
+    if ((s = check_err(m))) return s;
+    if (rel_residual_out) {
+        std::vector<double> sq(m->ncomp);
+        if ((s = residual_sq(m, 0, comp, sq.data()))) return s;
+        for (int k = 0; k < m->ncomp; ++k)
+            rel_residual_out[k] = std::sqrt(sq[k]) / (m->r0[k] > 0 ? m->r0[k] : 1.0);
+    }
+    return PBNG_OK;
+}
+
+pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps,
+                       const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out) {
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
+    if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
+    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    if ((s = begin(m, u_dev, p, true))) return s;
+    std::vector<double> sq(m->ncomp), rel(m->ncomp, 0.0);
+    int32_t done = 0;
+    pbng_status result = PBNG_ENOTCONVERGED;
+    auto converged = [&]() {
+        bool all = true;
+        for (int k = 0; k < m->ncomp; ++k) {
+            rel[k] = std::sqrt(sq[k]) / (m->r0[k] > 0 ? m->r0[k] : 1.0);
+            if (!std::isfinite(rel[k]) || rel[k] > 1e3) return -1;
+            if (rel[k] > rel_tol) all = false;
+        }
+        return all ? 1 : 0;
+    };
+    for (int k = 0; k < m->ncomp; ++k) sq[k] = m->r0[k] * m->r0[k];
+    int cv = converged();
+    if (cv == 1) result = PBNG_OK;
+    while (cv == 0 && done < max_sweeps) {
+        const int32_t chunk = std::min<int32_t>(p->residual_every, max_sweeps - done);
+        for (int32_t k = 0; k < chunk; ++k)
+            if ((s = one_sweep(m, p))) return s;
+        done += chunk;
+        if ((s = check_err(m))) return s;
+        if ((s = residual_sq(m, 0, comp, sq.data()))) return s;
+        cv = converged();
+        if (cv == 1) result = PBNG_OK;
+        if (cv < 0) result = PBNG_EDIVERGED;
+    }
+    PBNG_CUDA(m, launch_store(m->nv, (const int32_t*)m->d_perm.p, state_of(m, 0), u_dev, m->stream));
+    m->kernel_launches++;
+    PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
+    if (sweeps_out) *sweeps_out = done;
+    if (rel_residual_out)
+        for (int k = 0; k < m->ncomp; ++k) rel_residual_out[k] = rel[k];
+    if (result == PBNG_ENOTCONVERGED) m->err = "max_sweeps reached";
+    if (result == PBNG_EDIVERGED) m->err = "residual diverged";
+    return result;
+}
+
+pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out) {
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!u_dev || !residual_out) return fail(m, PBNG_EINVAL, "NULL argument");
+    PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, (const int32_t*)m->d_perm.p,
+                             (const float4*)m->d_dir_hi.p, (const float4*)m->d_dir_lo.p,
+                             state_of(m, 3), m->stream));
+    m->kernel_launches++;
+    std::vector<double> sq(m->ncomp);
+    if ((s = residual_sq(m, 3, true, sq.data()))) return s;
+    for (int k = 0; k < m->ncomp; ++k) residual_out[k] = std::sqrt(sq[k]);
+    return PBNG_OK;
+}
+
+pbng_status pbng_set_profiling(pbng_mesh* m, int32_t enable) {
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    PBNG_CUDA(m, prof_flush(m));
+    m->prof = enable != 0;
+    if (m->prof) {
+        for (int k = 0; k < 3; ++k) {
+            m->prof_launches[k] = 0;
+            m->prof_ms[k] = 0.0;
+        }
+        m->kernel_launches = 0;
+    }
+    return PBNG_OK;
+}
+
+pbng_status pbng_get_profile(pbng_mesh* m, pbng_profile* out) {
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!out) return fail(m, PBNG_EINVAL, "NULL profile");
+    PBNG_CUDA(m, prof_flush(m));
+    PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->colour_pass_launches = m->prof_launches[kProfColour];
+    out->colour_pass_ms = m->prof_ms[kProfColour];
+    out->accel_launches = m->prof_launches[kProfAccel];
+    out->accel_ms = m->prof_ms[kProfAccel];
+    out->residual_launches = m->prof_launches[kProfResidual];
+    out->residual_ms = m->prof_ms[kProfResidual];
+    out->kernel_launches = m->kernel_launches;
+    out->free_vertices = m->nfree;
+    out->incidences = m->ninc;
+    out->ncolours = m->ncol;
+    return PBNG_OK;
+}
+
+int32_t pbng_num_components(const pbng_mesh* m) { return m ? m->ncomp : 0; }
+
+const char* pbng_status_string(pbng_status s) {
+    switch (s) {
+        case PBNG_OK: return "ok";
+        case PBNG_EINVAL: return "invalid argument";
+        case PBNG_ENOMEM: return "out of memory";
+        case PBNG_ECUDA: return "CUDA error";
+        case PBNG_EDEGENERATE: return "degenerate element or nodal Hessian";
+        case PBNG_EDIVERGED: return "diverged";
+        case PBNG_ETIMEOUT: return "device wait timed out";
+        case PBNG_ENOTCONVERGED: return "not converged";
+    }
+    return "unknown status";
+}
+
+const char* pbng_last_error(const pbng_mesh* m) { return m ? m->err.c_str() : ""; }
+
+void pbng_destroy(pbng_mesh* m) {
+    if (!m) return;
+    cudaSetDevice(m->device);
+    if (m->stream) cudaStreamSynchronize(m->stream);
+    DevBuf* bufs[] = {&m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
+                      &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
+                      &m->d_partial, &m->d_comp_sq, &m->d_scalar, &m->d_err};
+    for (DevBuf* b : bufs) free_buf(*b);
+    for (auto& sb : m->d_state)
+        for (auto& b : sb) free_buf(b);
+    for (auto& p : m->ev_used) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : m->ev_free) cudaEventDestroy(e);
+    if (m->h_pinned) cudaFreeHost(m->h_pinned);
+    delete m;
+}
+
+}  // extern "C"

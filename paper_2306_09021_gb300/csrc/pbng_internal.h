@@ -1,0 +1,79 @@
+// Internal declarations shared by the host runtime (pbng_api.cpp) and the
+// CUDA kernels (pbng_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pbng {
+
+// A run of free vertices (internal, colour-ordered ids) that share a lane
+// group width: each vertex gets `width` consecutive lanes of one warp.
+struct Segment {
+    int32_t v_begin;
+    int32_t v_end;
+    int32_t width;        // 4, 8, 16 or 32
+    int32_t block_begin;  // first block of this segment within its launch
+};
+
+constexpr int kMaxSegments = 48;
+constexpr int kBlock = 256;
+
+struct SegmentTable {
+    int32_t count;
+    int32_t total_blocks;
+    Segment seg[kMaxSegments];
+};
+
+// Device view of a prepared mesh.  Per-incidence records are laid out in the
+// order the colour passes consume them (vertex-major CSR over the internal,
+// colour-ordered free vertices), so consecutive lanes read consecutive
+// records.
+struct DeviceMesh {
+    int32_t nv;              // all vertices (free first, then clamped)
+    int32_t nfree;
+    const int32_t* inc_off;  // [nfree + 1] CSR offsets into the records
+    const float4* rec_a;     // [ninc] other vertex ids j1, j2, j3 (int bits), a = 2 mu V
+    const float4* rec_b;     // [ninc] g_j1 (xyz), b = lambda V
+    const float4* rec_c;     // [ninc] g_j2 (xyz), g_j3.x
+    const float2* rec_d;     // [ninc] g_j3.y, g_j3.z
+    const float4* aux0;      // [nfree] f_ext (xyz), total spring stiffness K
+    const float4* aux1;      // [nfree] spring target displacement (xyz), n.X - d
+    const int32_t* comp;     // [nfree] component id, or nullptr for one component
+    float pn_x, pn_y, pn_z;  // contact plane normal (unit)
+    float k_contact;         // 0 = no plane
+};
+
+// The iterate: displacement u = x - X as a float pair hi + lo (lo is unused
+// in plain FP32 mode).  xyz used, w = 0.
+struct State {
+    float4* hi;
+    float4* lo;
+};
+
+struct PassParams {
+    float step;       // scale of the Newton step
+    float skip_tol;   // 0 = never skip
+};
+
+// Error bits written by the kernels (OR-ed into a device word).
+enum : int32_t {
+    kErrNonSPD = 1,      // det(A_i) <= 0 or non-finite
+    kErrNonFinite = 2,   // non-finite update
+};
+
+// Host launch wrappers (pbng_kernels.cu).  All enqueue on `st`.
+cudaError_t launch_colour_pass(const DeviceMesh& m, State s, const SegmentTable& t, PassParams p,
+                               bool compensated, int32_t* err, cudaStream_t st);
+cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t, bool compensated,
+                            double* block_partial, double* comp_sq, int32_t ncomp,
+                            float* r_out, cudaStream_t st);
+cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStream_t st);
+cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, float w, float g,
+                         bool compensated, cudaStream_t st);
+cudaError_t launch_load(int32_t nv, int32_t nfree, const float* u_user, const int32_t* perm,
+                        const float4* dir_hi, const float4* dir_lo, State s, cudaStream_t st);
+cudaError_t launch_store(int32_t nv, const int32_t* perm, State s, float* u_user, cudaStream_t st);
+cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st);
+
+}  // namespace pbng

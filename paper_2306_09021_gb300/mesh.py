@@ -1,0 +1,146 @@
+"""Python face of the PBNG C ABI: one ``Mesh`` per pbng_mesh handle.
+
+Host arrays go in as numpy arrays; the iterate u = x - X is a float32 CUDA
+tensor [nv, 3] owned by the caller (PyTorch provides the memory and the
+stream).  Methods map one-to-one onto pbng_* entry points.
+"""
+
+import ctypes
+
+import numpy as np
+
+from ._lib import ACCEL, PRECISION, PbngParams, PbngProfile, check, load
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def default_params(**kw):
+    """pbng_default_params, then overrides: accel ('none'|'chebyshev'|'sor'),
+    precision ('fp32'|'compensated'), omega, rho, gamma, step, skip_tol,
+    residual_every, resume."""
+    p = PbngParams()
+    load().pbng_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "accel":
+            v = ACCEL[v] if isinstance(v, str) else int(v)
+        elif k == "precision":
+            v = PRECISION[v] if isinstance(v, str) else int(v)
+        setattr(p, k, v)
+    return p
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_u(u, nv):
+    import torch
+    if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dtype == torch.float32
+            and u.is_contiguous() and tuple(u.shape) == (nv, 3)):
+        raise ValueError(f"u must be a contiguous float32 CUDA tensor of shape ({nv}, 3)")
+
+
+class Mesh:
+    """A pbng_mesh handle (pbng_create_mesh / pbng_destroy)."""
+
+    def __init__(self, X, tets, young, poisson, mesh_id=None, stream=None):
+        L = load()
+        self.X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        self.tets = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+        self.nv, self.ne = self.X.shape[0], self.tets.shape[0]
+        young = np.ascontiguousarray(np.broadcast_to(young, (self.ne,)), dtype=np.float64)
+        poisson = np.ascontiguousarray(np.broadcast_to(poisson, (self.ne,)), dtype=np.float64)
+        mid = None if mesh_id is None else np.ascontiguousarray(mesh_id, dtype=np.int32)
+        self._stream = _stream_ptr(stream)
+        h = ctypes.c_void_p()
+        st = L.pbng_create_mesh(_dptr(self.X), self.nv, _iptr(self.tets), self.ne, _dptr(young),
+                                _dptr(poisson), None if mid is None else _iptr(mid), self._stream,
+                                ctypes.byref(h))
+        check(st, "pbng_create_mesh")
+        self.h = h
+        self.ncomp = L.pbng_num_components(self.h)
+        self.dirichlet = np.zeros(0, np.int32)
+
+    @classmethod
+    def from_problem(cls, p, stream=None):
+        m = cls(p.X, p.tets, p.young, p.poisson, stream=stream)
+        m.set_constraints(p.dirichlet, p.x0[p.dirichlet], p.spr_idx, p.spr_target, p.spr_k,
+                          p.plane, p.k_contact, p.body_accel, p.density)
+        return m
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            load().pbng_destroy(h)
+            self.h = None
+
+    def set_constraints(self, dir_idx=None, dir_xyz=None, spr_idx=None, spr_target=None,
+                        spr_k=None, plane=None, k_contact=0.0, body_accel=None, density=None):
+        di = np.ascontiguousarray(np.zeros(0) if dir_idx is None else dir_idx, dtype=np.int32)
+        dx = np.ascontiguousarray(np.zeros((0, 3)) if dir_xyz is None else dir_xyz, dtype=np.float64)
+        si = np.ascontiguousarray(np.zeros(0) if spr_idx is None else spr_idx, dtype=np.int32)
+        stg = np.ascontiguousarray(np.zeros((0, 3)) if spr_target is None else spr_target, dtype=np.float64)
+        sk = np.ascontiguousarray(np.zeros(0) if spr_k is None else spr_k, dtype=np.float64)
+        pl = None if plane is None else np.ascontiguousarray(plane, dtype=np.float64)
+        ba = None if body_accel is None else np.ascontiguousarray(body_accel, dtype=np.float64)
+        de = None if density is None else np.ascontiguousarray(np.broadcast_to(density, (self.ne,)), dtype=np.float64)
+        st = load().pbng_set_constraints(
+            self.h, _iptr(di), _dptr(dx), len(di), _iptr(si), _dptr(stg), _dptr(sk), len(si),
+            None if pl is None else _dptr(pl), float(k_contact),
+            None if ba is None else _dptr(ba), None if de is None else _dptr(de))
+        check(st, "pbng_set_constraints", self.h)
+        self.dirichlet = di.copy()
+
+    def colouring(self):
+        col = np.zeros(self.nv, np.int32)
+        n = ctypes.c_int32()
+        check(load().pbng_get_colouring(self.h, _iptr(col), ctypes.byref(n)), "pbng_get_colouring", self.h)
+        return col, n.value
+
+    def sweep(self, u, nsweeps, params=None, want_residual=False):
+        """pbng_sweep in place on u; returns the relative residuals (or None)."""
+        _check_u(u, self.nv)
+        p = params if params is not None else default_params()
+        out = np.zeros(self.ncomp) if want_residual else None
+        st = load().pbng_sweep(self.h, ctypes.c_void_p(u.data_ptr()), int(nsweeps), ctypes.byref(p),
+                               None if out is None else _dptr(out))
+        check(st, "pbng_sweep", self.h)
+        return out
+
+    def solve(self, u, rel_tol, max_sweeps, params=None, raise_on_status=True):
+        """pbng_solve in place on u; returns (status, sweeps, rel_residuals)."""
+        _check_u(u, self.nv)
+        p = params if params is not None else default_params()
+        sweeps = ctypes.c_int32()
+        out = np.zeros(self.ncomp)
+        st = load().pbng_solve(self.h, ctypes.c_void_p(u.data_ptr()), float(rel_tol), int(max_sweeps),
+                               ctypes.byref(p), ctypes.byref(sweeps), _dptr(out))
+        if raise_on_status:
+            check(st, "pbng_solve", self.h)
+        return st, sweeps.value, out
+
+    def residual(self, u):
+        """pbng_residual: absolute FP64 residual norms per component."""
+        _check_u(u, self.nv)
+        out = np.zeros(self.ncomp)
+        check(load().pbng_residual(self.h, ctypes.c_void_p(u.data_ptr()), _dptr(out)), "pbng_residual", self.h)
+        return out
+
+    def set_profiling(self, enable=True):
+        """pbng_set_profiling: per-launch event timing of the library's kernels."""
+        check(load().pbng_set_profiling(self.h, 1 if enable else 0), "pbng_set_profiling", self.h)
+
+    def profile(self):
+        """pbng_get_profile as a dict."""
+        pr = PbngProfile()
+        check(load().pbng_get_profile(self.h, ctypes.byref(pr)), "pbng_get_profile", self.h)
+        return {k: getattr(pr, k) for k, _ in PbngProfile._fields_ if k != "reserved"}

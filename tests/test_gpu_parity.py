@@ -1,0 +1,231 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance: positions after a fixed number of sweeps agree to
+max_i |x_gpu - x_oracle| / max_i |x_oracle - X| <= 1e-5 in compensated
+precision (float32 element arithmetic, float32-pair iterate); colourings agree
+bit for bit.
+"""
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-5
+RES_FLOOR = 1e-5  # relative-residual target of the float32 path
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_09021_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _gpu_run(p, sweeps, **kw):
+    from paper_2306_09021_gb300 import Mesh, default_params
+    m = Mesh.from_problem(p)
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    rel = m.sweep(u, sweeps, default_params(**kw), want_residual=True)
+    return m, u.cpu().double().numpy() + p.X, rel
+
+
+def _oracle(oracle_mod, p):
+    return oracle_mod.OracleMesh.from_problem(p)
+
+
+def _pos_err(x, xr, X):
+    return np.abs(x - xr).max() / max(np.abs(xr - X).max(), 1e-300)
+
+
+ACCELS = [dict(accel="none"), dict(accel="chebyshev"), dict(accel="sor", omega=1.5)]
+
+
+@pytest.mark.parametrize("kw", ACCELS, ids=lambda k: k["accel"])
+def test_twist_block_200_sweeps(oracle_mod, kw):
+    """Unit cube 10^3 cells (1331 vertices, 5000 tets), E = 1e5, nu = 0.3,
+    bottom clamped, top lifted 30% and twisted 90 degrees; 200 sweeps."""
+    p = W.twist_block(10, 90.0, 0.3)
+    _, x, rel = _gpu_run(p, 200, **kw)
+    om = _oracle(oracle_mod, p)
+    xr, st = om.sweeps(p.x0, 200, accel=kw["accel"], omega=kw.get("omega", 1.7))
+    assert st == 0
+    err = _pos_err(x, xr, p.X)
+    rr = om.residual(xr) / om.residual(p.x0)
+    print(f"twist 10^3 {kw['accel']}: pos err {err:.2e}, rel residual gpu {rel[0]:.3e} oracle {rr:.3e}")
+    assert err <= POS_TOL
+    # float32 element arithmetic floors the relative residual near 1e-6 here;
+    # above that floor the two residuals agree.
+    assert abs(rel[0] - rr) <= 1e-3 * rr + RES_FLOOR
+
+
+def test_fp32_mode_is_close(oracle_mod):
+    p = W.twist_block(6, 90.0, 0.3)
+    _, x, _ = _gpu_run(p, 60, precision="fp32")
+    xr, _ = _oracle(oracle_mod, p).sweeps(p.x0, 60)
+    assert _pos_err(x, xr, p.X) <= 1e-4
+
+
+def _ragged_problem():
+    """Bar of 3 x 2 x 5 cells with lognormal stiffness, gravity, springs on 10%
+    of the vertices and an active contact plane; boundary vertices give every
+    lane-group width and ragged colour tails."""
+    p = W.contact_bar(3, 2, 5, 0.1, seed=7, spring_frac=0.1)
+    p.body_accel = np.array([0.0, 0.0, -9.8])
+    p.density = np.full(p.ne, 1000.0)
+    p.dirichlet = np.array([0, 1], np.int32)
+    p.plane = np.array([0.0, 0.0, 1.0, 0.01])  # n.x < 0.01 is in contact
+    return p
+
+
+@pytest.mark.parametrize("kw", ACCELS, ids=lambda k: k["accel"])
+def test_ragged_bar_with_weak_constraints(oracle_mod, kw):
+    p = _ragged_problem()
+    if kw["accel"] == "chebyshev":
+        # With the 1e8 contact penalty, gamma = 1.7 Chebyshev does not converge
+        # (the FP64 residual oscillates near 3e6 and 1e-9 input noise moves the
+        # iterate by 1e-5): no reference trajectory exists.  Check the springs
+        # and gravity part of the path under Chebyshev with the plane removed.
+        p.plane = None
+    _, x, _ = _gpu_run(p, 80, **kw)
+    xr, st = _oracle(oracle_mod, p).sweeps(p.x0, 80, accel=kw["accel"], omega=kw.get("omega", 1.7))
+    assert st == 0
+    assert _pos_err(x, xr, p.X) <= POS_TOL
+
+
+@pytest.mark.parametrize("maker", [lambda: W.twist_block(5), lambda: W.gravity_sag(7),
+                                   lambda: W.contact_bar(4, 3, 9, 0.05, spring_frac=0.05),
+                                   _ragged_problem])
+def test_colouring_matches_oracle(oracle_mod, maker):
+    from paper_2306_09021_gb300 import Mesh
+    p = maker()
+    col, n = Mesh.from_problem(p).colouring()
+    om = _oracle(oracle_mod, p)
+    assert n == om.ncolours
+    assert np.array_equal(col, om.colours())
+
+
+def test_table1_colour_counts():
+    """Table 1: 5 particle colours for the Res 16 / 32 / 64 / 128 boxes."""
+    from paper_2306_09021_gb300 import Mesh
+    from tests.golden.values import paper_values
+    pv = paper_values()
+    for res in (16, 32, 64, 128):
+        X, tets = W.box_grid(res, res, res, 1.0 / res)
+        m = Mesh(X, tets, 1e5, 0.3)
+        m.set_constraints()
+        _, n = m.colouring()
+        assert n == int(pv[f"box_res{res}_particle_colours"])
+
+
+def test_residual_matches_oracle(oracle_mod):
+    from paper_2306_09021_gb300 import Mesh
+    p = _ragged_problem()
+    m = Mesh.from_problem(p)
+    om = _oracle(oracle_mod, p)
+    rng = np.random.default_rng(3)
+    for k in range(3):
+        x = p.x0 + 0.01 * rng.standard_normal(p.x0.shape)
+        x[p.dirichlet] = p.x0[p.dirichlet]
+        u = torch.tensor(x - p.X, dtype=torch.float32, device="cuda")
+        xs = u.cpu().double().numpy() + p.X  # the float32-rounded state both sides see
+        r_gpu = m.residual(u)[0]
+        r_ora = om.residual(xs)
+        assert r_gpu == pytest.approx(r_ora, rel=1e-5)
+
+
+def test_sweep_commutes_with_rigid_motion():
+    p = W.twist_block(5, 60.0, 0.2)
+    _, x1, _ = _gpu_run(p, 20)
+    a = 0.7
+    Q = np.array([[np.cos(a), -np.sin(a), 0], [np.sin(a), np.cos(a), 0], [0, 0, 1.0]])
+    Q = Q @ np.array([[1, 0, 0], [0, np.cos(0.4), -np.sin(0.4)], [0, np.sin(0.4), np.cos(0.4)]])
+    b = np.array([0.2, -0.1, 0.3])
+    q = W.twist_block(5, 60.0, 0.2)
+    q.X = p.X @ Q.T + b
+    q.x0 = p.x0 @ Q.T + b
+    _, x2, _ = _gpu_run(q, 20)
+    assert np.abs(x2 - (x1 @ Q.T + b)).max() / np.abs(x1 - p.X).max() <= POS_TOL
+
+
+def test_solve_reaches_newton_equilibrium(oracle_mod):
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.gravity_sag(6)
+    m = Mesh.from_problem(p)
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    st, sweeps, rel = m.solve(u, RES_FLOOR, 20000, default_params(accel="chebyshev", residual_every=20),
+                              raise_on_status=False)
+    print(f"sag 6^3 chebyshev: status {st}, {sweeps} sweeps, rel residual {rel[0]:.3e}")
+    assert st == 0 and rel[0] <= RES_FLOOR
+    xn, it, _ = _oracle(oracle_mod, p).newton(p.x0, 1e-12, 60)
+    assert it >= 0
+    x = u.cpu().double().numpy() + p.X
+    assert _pos_err(x, xn, p.X) <= 1e-4
+
+
+def test_resume_is_bit_exact():
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.twist_block(6, 90.0, 0.3)
+    m = Mesh.from_problem(p)
+    u1 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    m.sweep(u1, 50, default_params(accel="chebyshev"))
+    m.sweep(u1, 50, default_params(accel="chebyshev", resume=1))
+    m2 = Mesh.from_problem(p)
+    u2 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    m2.sweep(u2, 100, default_params(accel="chebyshev"))
+    assert torch.equal(u1, u2)
+
+
+def test_full_size_gravity_sag_sampled(oracle_mod):
+    """64^3 cells (274,625 vertices, 1,310,720 tets), the benchmark's mesh and
+    launch configuration: the update of sampled vertices of every colour in one
+    GPU sweep equals the oracle's node update from the same state."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.gravity_sag(64)
+    m = Mesh.from_problem(p)
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    m.sweep(u, 5, default_params())
+    s0 = u.cpu().double().numpy() + p.X
+    m.sweep(u, 1, default_params())
+    s1 = u.cpu().double().numpy() + p.X
+    col, ncol = m.colouring()
+    om = _oracle(oracle_mod, p)
+    rng = np.random.default_rng(11)
+    for c in range(ncol):
+        ids = rng.choice(np.flatnonzero(col == c), 12, replace=False)
+        mixed = np.where((col < c)[:, None] & (col >= 0)[:, None], s1, s0)
+        for i in ids:
+            r, A = om.local_system(mixed, i)
+            d_ora = np.linalg.solve(A, r)
+            d_gpu = s1[i] - s0[i]
+            assert np.abs(d_gpu - d_ora).max() <= 2e-4 * np.abs(d_ora).max() + 1e-9
+
+
+def test_edge_cases():
+    from paper_2306_09021_gb300 import Mesh, PbngError, default_params
+    # every vertex clamped: a sweep leaves the targets in place
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1.0]])
+    tets = np.array([[0, 1, 2, 3]], np.int32)
+    m = Mesh(X, tets, 1e5, 0.3)
+    m.set_constraints(np.arange(4), X + 0.1)
+    u = torch.zeros(4, 3, device="cuda")
+    m.sweep(u, 3, default_params())
+    assert torch.allclose(u, torch.full_like(u, 0.1))
+    # one free vertex, pulled by gravity: converges
+    m.set_constraints(np.arange(3), X[:3], body_accel=[0, 0, -9.8], density=[1e3])
+    st, n, rel = m.solve(u, 1e-7, 5000, default_params())
+    assert st == 0
+    # bad inputs fail with a status, never a crash
+    with pytest.raises(PbngError):
+        Mesh(X, np.array([[0, 1, 2, 7]], np.int32), 1e5, 0.3)
+    with pytest.raises(PbngError):
+        Mesh(np.zeros((4, 3)), tets, 1e5, 0.3)  # zero-volume tet
+    with pytest.raises(PbngError):
+        m.set_constraints(np.array([9], np.int32), np.zeros((1, 3)))
+    with pytest.raises(ValueError):
+        m.sweep(torch.zeros(5, 3, device="cuda"), 1)
