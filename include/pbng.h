@@ -139,6 +139,32 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
  * (host double [ncomp]).  Does not modify u_dev. */
 pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out);
 
+/* pbng_residual without any allocation.  The paper has no counterpart: this
+ * is a service of the library for callers that must not allocate memory once
+ * their solve loop is running — for example an application whose GPU memory
+ * is entirely handed to its own pool allocator, or a real-time loop in which a
+ * cudaMalloc or cudaFree (either can synchronise the whole device) is not
+ * allowed.  It computes the same per-component FP64 residual norms as
+ * pbng_residual with the same kernels, but calls no cudaMalloc, cudaFree or
+ * other allocating routine, on the device or the host.
+ *   - Its FP64 partial sums live in one fixed array of 65,536 doubles
+ *     (512 KiB) that the library reserves on every GPU that loads it, until
+ *     the process exits.  A mesh whose residual launch needs more partial
+ *     sums (one per 256-thread block; beyond roughly 20 million incidences)
+ *     or has more than 65,536 components is rejected with PBNG_EINVAL.
+ *   - The handle's layout must exist already: make any pbng_get_colouring,
+ *     pbng_sweep, pbng_solve or pbng_residual call after the last
+ *     pbng_set_constraints first (layout building allocates); otherwise
+ *     PBNG_EINVAL.
+ *   - The first call on a device looks the array's device address up once
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call, from any handle or thread, uses the same array and leaves
+ *     its last contents there; calls whose GPU work overlaps (different
+ *     streams or threads at the same time) race and return wrong sums.
+ *   - Synchronises the handle's stream; writes residual_out (host double
+ *     [ncomp]).  u_dev as for pbng_residual. */
+pbng_status pbng_residual_noalloc(pbng_mesh* m, const float* u_dev, double* residual_out);
+
 /* Per-kernel timing on the handle's stream (tracing; Section "Coloring and
  * Parallelism" reports per-iteration runtimes).  While enabled, each colour
  * pass, acceleration and residual launch is bracketed by CUDA events.

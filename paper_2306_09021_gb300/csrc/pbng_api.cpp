@@ -747,6 +747,49 @@ pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out
     return PBNG_OK;
 }
 
+pbng_status pbng_residual_noalloc(pbng_mesh* m, const float* u_dev, double* residual_out) {
+    // Same kernels as pbng_residual; the FP64 partial sums go to the fixed
+    // scratch array of pbng_kernels.cu instead of handle buffers, and nothing
+    // (device or host) is allocated here.
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    if (!u_dev || !residual_out) return fail(m, PBNG_EINVAL, "NULL argument");
+    if (m->dirty)
+        return fail(m, PBNG_EINVAL,
+                    "layout not built: call pbng_get_colouring, pbng_sweep, pbng_solve or "
+                    "pbng_residual once after pbng_set_constraints");
+    PBNG_CUDA(m, cudaSetDevice(m->device));
+    double* scratch = nullptr;
+    PBNG_CUDA(m, noalloc_scratch(m->device, &scratch));
+    const bool multi = m->ncomp > 1;
+    const int64_t need = multi ? (int64_t)m->ncomp : (int64_t)m->total_partials + 1;
+    if (need > noalloc_scratch_capacity())
+        return fail(m, PBNG_EINVAL, "mesh needs more FP64 partial sums than the fixed 65,536-entry scratch holds");
+    cudaStream_t st = m->stream;
+    PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, (const int32_t*)m->d_perm.p,
+                             (const float4*)m->d_dir_hi.p, (const float4*)m->d_dir_lo.p,
+                             state_of(m, 3), st));
+    State s = state_of(m, 3);
+    if (multi) {
+        // per-component sums accumulate atomically: start them at zero
+        PBNG_CUDA(m, cudaMemsetAsync(scratch, 0, sizeof(double) * m->ncomp, st));
+        for (int c = 0; c < m->ncol; ++c)
+            PBNG_CUDA(m, launch_residual(m->dm, s, m->tables[c], true, scratch, scratch, m->ncomp, nullptr, st));
+        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, scratch, sizeof(double) * m->ncomp, cudaMemcpyDeviceToHost, st));
+    } else {
+        // every block of every colour writes its own partial; the sum lands after them
+        for (int c = 0; c < m->ncol; ++c)
+            PBNG_CUDA(m, launch_residual(m->dm, s, m->tables[c], true, scratch + m->table_partial_off[c],
+                                         nullptr, m->ncomp, nullptr, st));
+        PBNG_CUDA(m, launch_reduce(scratch, m->total_partials, scratch + m->total_partials, st));
+        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, scratch + m->total_partials, sizeof(double),
+                                     cudaMemcpyDeviceToHost, st));
+    }
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    for (int k = 0; k < m->ncomp; ++k) residual_out[k] = (m->ncol == 0) ? 0.0 : std::sqrt(m->h_pinned[k]);
+    return PBNG_OK;
+}
+
 pbng_status pbng_set_profiling(pbng_mesh* m, int32_t enable) {
     if (!m) return PBNG_EINVAL;
     m->err.clear();

@@ -76,4 +76,8 @@ cudaError_t launch_load(int32_t nv, int32_t nfree, const float* u_user, const in
 cudaError_t launch_store(int32_t nv, const int32_t* perm, State s, float* u_user, cudaStream_t st);
 cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st);
 
+// Fixed device scratch of the allocation-free residual (pbng_kernels.cu).
+int noalloc_scratch_capacity();
+cudaError_t noalloc_scratch(int device, double** out);
+
 }  // namespace pbng

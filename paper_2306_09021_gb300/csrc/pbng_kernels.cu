@@ -529,3 +529,40 @@ cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st) 
 }
 
 }  // namespace pbng
+
+// ---------------------------------------------------------------------------
+// Fixed scratch for the allocation-free residual (pbng_residual_noalloc).
+// One array per GPU that loads the library, kept until the process exits.
+#include <mutex>
+
+namespace pbng {
+namespace {
+
+constexpr int kNoAllocScratchDoubles = 1 << 16;  // 65,536 doubles = 512 KiB
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+double* g_noalloc_addr[kMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+int noalloc_scratch_capacity() { return kNoAllocScratchDoubles; }
+
+// Device address of the scratch array on `device`, which must be current.
+// The host-side name g_noalloc_scratch is only a stand-in; the address is
+// looked up once per device with cudaGetSymbolAddress and cached.
+cudaError_t noalloc_scratch(int device, double** out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace pbng
