@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--cells", type=int, default=64)
     ap.add_argument("--sweeps-per-step", type=int, default=10)
     ap.add_argument("--precision", choices=["compensated", "fp32"], default="compensated")
+    ap.add_argument("--kernel-path", type=int, choices=[0, 1], default=0,
+                    help="0: 1-ring layout kernels (TMA-staged), 1: CSR direct-load kernels")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-5 solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -68,6 +70,8 @@ def config_of(args, p):
         "sweeps_per_step": args.sweeps_per_step,
         "accel": "chebyshev rho=0.95 gamma=1.7",
         "precision": args.precision,
+        "kernels": ("1-ring layout, per-warp TMA bulk records + cp.async gathers" if args.kernel_path == 0
+                    else "CSR layout, direct loads"),
         "l2": "inputs larger than L2 (per-incidence records ~294 MB streamed per sweep)",
         "seed": "deterministic grid, no random draws",
     }
@@ -138,17 +142,24 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def kernel_sources_sha256():
+    """Hash of the CUDA sources that define the sweep kernels."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_09021_gb300", "csrc")
+    for name in ("pbng_element.cuh", "pbng_internal.h", "pbng_kernels.cu", "pbng_ring.cu"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def kernel_traffic():
     """Per-launch DRAM bytes of the colour pass from the committed ncu summary,
     or None when the kernel source changed since it was captured."""
     path = os.path.join(ROOT, "profiles", "colour_pass_traffic.json")
-    src = os.path.join(ROOT, "paper_2306_09021_gb300", "csrc", "pbng_kernels.cu")
     try:
         with open(path) as f:
             d = json.load(f)
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()
-        if d.get("kernel_sha256") != h:
+        if d.get("kernel_sha256") != kernel_sources_sha256():
             return None
         return d
     except (OSError, ValueError):
@@ -233,8 +244,9 @@ def main():
     u0 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
     u = u0.clone()
     S = args.sweeps_per_step
-    first = default_params(accel="chebyshev", precision=args.precision)
-    cont = default_params(accel="chebyshev", precision=args.precision, resume=1)
+    first = default_params(accel="chebyshev", precision=args.precision, kernel_path=args.kernel_path)
+    cont = default_params(accel="chebyshev", precision=args.precision, resume=1,
+                          kernel_path=args.kernel_path)
 
     # warm-up (also loads the iterate and the acceleration history)
     m.sweep(u, S, first, want_residual=True)
@@ -282,7 +294,9 @@ def main():
                 "traffic": None if tr is None else tr["dram_bytes_per_launch"],
                 "alg_bytes_per_launch": alg_bytes_launch, "avg_launch_us": per_launch_ms * 1e3,
                 "launches_timed": prof["colour_pass_launches"],
-                "colour_pass_share_of_step": prof["colour_pass_ms"] / ms}
+                "colour_pass_share_of_step": prof["colour_pass_ms"] / ms,
+                "accel_share_of_step": prof["accel_ms"] / ms,
+                "residual_share_of_step": prof["residual_ms"] / ms}
 
     # end to end through the public API with host buffers
     h_u = torch.empty_like(u, device="cpu").pin_memory()
@@ -319,7 +333,8 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             st, sweeps, relr = m.solve(uu, 1e-5, 20000,
-                                       default_params(precision=args.precision, residual_every=10, **kw),
+                                       default_params(precision=args.precision, residual_every=10,
+                                                      kernel_path=args.kernel_path, **kw),
                                        raise_on_status=False)
             torch.cuda.synchronize()
             ttr[name] = {"status": int(st), "sweeps": int(sweeps), "rel_residual": float(relr[0]),

@@ -72,12 +72,16 @@ typedef struct {
                                float32 pair (hi + lo), neighbour differences and
                                updates are formed in that pair; all element
                                arithmetic stays float32.                          */
-    int32_t reserved[4];
+    int32_t kernel_path;    /* 0: pipelined kernels (TMA-staged records, cp.async
+                               gathers) wherever every vertex of a colour has at
+                               most 256 incident tets, else direct loads;
+                               1: direct-load kernels everywhere.                 */
+    int32_t reserved[3];
 } pbng_params;
 
 /* Fills p with the paper's defaults: corotated, no acceleration, omega 1.7,
  * rho 0.95, gamma 1.7, step 1, skip_tol 0, residual_every 10, resume 0,
- * compensated precision. */
+ * compensated precision, pipelined kernels. */
 void pbng_default_params(pbng_params* p);
 
 /* Creates a mesh handle (Section "Discretization": P1 tetrahedra, per-tet

@@ -33,7 +33,8 @@ class PbngParams(ctypes.Structure):
         ("residual_every", ctypes.c_int32),
         ("resume", ctypes.c_int32),
         ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("kernel_path", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
     ]
 
 

@@ -51,11 +51,20 @@ struct pbng_mesh {
     std::vector<int32_t> colour;    // nv, -1 clamped
     std::vector<int32_t> perm;      // internal -> caller id
     std::vector<SegmentTable> tables;  // one per colour
+    std::vector<uint8_t> ring_colour;  // per colour: ring layout (else CSR, direct loads)
+    bool all_ring = true;
+    std::vector<Item> items;           // ring items, colour by colour
+    std::vector<int32_t> item_off;     // ncol + 1 offsets into items
+    int32_t nitems_ring = 0;
+    int32_t ring_partials = 0;         // residual partials of the ring launch
+    bool want_direct = false;          // params.kernel_path == 1 requested
+    bool built_direct = false;         // layout built with want_direct
     std::vector<int32_t> table_partial_off;  // residual partial offset per colour
     int32_t total_partials = 0;
 
     // device buffers
     DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
+    DevBuf d_ring_ra, d_ring_rb, d_ring_rc, d_ring_id, d_items;
     DevBuf d_dir_hi, d_dir_lo;
     DevBuf d_state[4][2];           // cur, p1, p2, tmp; hi/lo
     DevBuf d_partial, d_comp_sq, d_scalar, d_err;
@@ -218,6 +227,13 @@ int width_for(int deg) {
 }
 
 // Builds the colour-ordered layout and uploads it.
+//
+// Internal vertex order: free vertices by colour, inside a colour by lane
+// width (widest first) then caller id; clamped vertices last.  A vertex's
+// lane width W is the smallest power of two (>= 4) holding both its incident
+// tets and its 1-ring.  Colours whose vertices all have W <= 32 use the ring
+// layout (pbng_ring.cu) unless direct loads were requested; the others use
+// CSR records with direct loads (pbng_kernels.cu).
 pbng_status build_layout(pbng_mesh* m) {
     const int32_t nv = m->nv, ne = m->ne;
     // vertex -> incident (tet, local) in ascending tet order
@@ -239,15 +255,36 @@ pbng_status build_layout(pbng_mesh* m) {
         words *= 2;
         if (words > 64) return fail(m, PBNG_EINVAL, "colouring needs more than 4096 colours");
     }
-    // internal order: colour, then lane-group width (widest first), then id
+    auto deg = [&](int32_t i) { return inc_off[i + 1] - inc_off[i]; };
+    // 1-ring of each free vertex (caller ids, ascending)
+    std::vector<int32_t> ring_off(nv + 1, 0), ring;
+    {
+        std::vector<int32_t> tmp;
+        for (int32_t i = 0; i < nv; ++i) {
+            if (!m->is_dir[i]) {
+                tmp.clear();
+                for (int32_t k = inc_off[i]; k < inc_off[i + 1]; ++k)
+                    for (int j = 0; j < 4; ++j) {
+                        const int32_t w = m->tets[4 * (size_t)inc_tet[k] + j];
+                        if (w != i) tmp.push_back(w);
+                    }
+                std::sort(tmp.begin(), tmp.end());
+                tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+                ring.insert(ring.end(), tmp.begin(), tmp.end());
+            }
+            ring_off[i + 1] = (int32_t)ring.size();
+        }
+    }
+    auto ring_n = [&](int32_t i) { return ring_off[i + 1] - ring_off[i]; };
+    auto lanes = [&](int32_t i) { return width_for(std::max(deg(i), ring_n(i))); };
+
     std::vector<int32_t> order;
     order.reserve(nv);
     for (int32_t i = 0; i < nv; ++i)
         if (!m->is_dir[i]) order.push_back(i);
-    auto deg = [&](int32_t i) { return inc_off[i + 1] - inc_off[i]; };
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         if (m->colour[a] != m->colour[b]) return m->colour[a] < m->colour[b];
-        return width_for(deg(a)) > width_for(deg(b));
+        return lanes(a) > lanes(b);
     });
     m->nfree = (int32_t)order.size();
     for (int32_t i = 0; i < nv; ++i)
@@ -256,71 +293,155 @@ pbng_status build_layout(pbng_mesh* m) {
     std::vector<int32_t> iperm(nv);
     for (int32_t v = 0; v < nv; ++v) iperm[order[v]] = v;
 
-    // segments per colour
+    // segments per colour, and which colours take the ring layout
     m->tables.assign(m->ncol, SegmentTable{});
     m->table_partial_off.assign(m->ncol + 1, 0);
+    m->ring_colour.assign(m->ncol, 0);
     int32_t v = 0;
     for (int c = 0; c < m->ncol; ++c) {
         SegmentTable& t = m->tables[c];
         t.count = 0;
         t.total_blocks = 0;
+        bool fits = true;
         while (v < m->nfree && m->colour[order[v]] == c) {
-            int W = width_for(deg(order[v]));
-            int32_t b = v;
-            while (v < m->nfree && m->colour[order[v]] == c && width_for(deg(order[v])) == W) ++v;
-            if (t.count >= kMaxSegments) return fail(m, PBNG_EINVAL, "too many segments");
-            Segment& s = t.seg[t.count++];
-            s.v_begin = b;
-            s.v_end = v;
-            s.width = W;
-            s.block_begin = t.total_blocks;
+            const int W = lanes(order[v]);
+            const int32_t b = v;
+            while (v < m->nfree && m->colour[order[v]] == c && lanes(order[v]) == W) {
+                if (std::max(deg(order[v]), ring_n(order[v])) > kRingLanes) fits = false;
+                ++v;
+            }
+            if (t.count >= kMaxSegments) return fail(m, PBNG_EINVAL, "too many lane-width runs in a colour");
+            Segment& sg = t.seg[t.count++];
+            sg.v_begin = b;
+            sg.v_end = v;
+            sg.width = W;
+            sg.block_begin = t.total_blocks;
             const int per_block = kBlock / W;
             t.total_blocks += (v - b + per_block - 1) / per_block;
         }
-        m->table_partial_off[c + 1] = m->table_partial_off[c] + t.total_blocks;
+        m->ring_colour[c] = (fits && !m->want_direct) ? 1 : 0;
     }
-    m->total_partials = m->table_partial_off[m->ncol];
+    m->all_ring = true;
+    int32_t direct_partials = 0;
+    for (int c = 0; c < m->ncol; ++c) {
+        m->table_partial_off[c] = direct_partials;
+        if (!m->ring_colour[c]) {
+            m->all_ring = false;
+            direct_partials += m->tables[c].total_blocks;
+        }
+    }
+    m->table_partial_off[m->ncol] = direct_partials;
+    m->total_partials = direct_partials;
 
-    // per-incidence records in internal CSR order
+    int64_t ninc_all = 0;
+    for (int32_t w = 0; w < m->nfree; ++w) ninc_all += deg(order[w]);
+    m->ninc = ninc_all;
+
+    // CSR records for the direct-load colours (empty ranges elsewhere)
     std::vector<int32_t> off(m->nfree + 1, 0);
-    for (int32_t w = 0; w < m->nfree; ++w) off[w + 1] = off[w] + deg(order[w]);
+    for (int32_t w = 0; w < m->nfree; ++w)
+        off[w + 1] = off[w] + (m->ring_colour[m->colour[order[w]]] ? 0 : deg(order[w]));
     const size_t ninc = (size_t)off[m->nfree];
-    m->ninc = (int64_t)ninc;
     std::vector<float4> ra(ninc), rb(ninc), rc(ninc);
     std::vector<float2> rd(ninc);
+    auto grads = [&](int32_t e, double g[4][3]) {
+        const double* Be = &m->B[9 * (size_t)e];
+        for (int a = 0; a < 3; ++a) {
+            g[1][a] = Be[a];
+            g[2][a] = Be[3 + a];
+            g[3][a] = Be[6 + a];
+            g[0][a] = -(Be[a] + Be[3 + a] + Be[6 + a]);
+        }
+    };
     for (int32_t w = 0; w < m->nfree; ++w) {
         const int32_t i = order[w];
+        if (m->ring_colour[m->colour[i]]) continue;
         size_t s = off[w];
         for (int32_t k = inc_off[i]; k < inc_off[i + 1]; ++k, ++s) {
             const int32_t e = inc_tet[k];
             const int loc = inc_loc[k];
-            const double* Be = &m->B[9 * (size_t)e];
             double g[4][3];
-            for (int a = 0; a < 3; ++a) {
-                g[1][a] = Be[a];
-                g[2][a] = Be[3 + a];
-                g[3][a] = Be[6 + a];
-                g[0][a] = -(Be[a] + Be[3 + a] + Be[6 + a]);
-            }
+            grads(e, g);
             int oth[3], n = 0;
             for (int j = 0; j < 4; ++j)
                 if (j != loc) oth[n++] = j;
             int32_t ids[3];
             for (int q = 0; q < 3; ++q) ids[q] = iperm[m->tets[4 * (size_t)e + oth[q]]];
-            const double a2 = 2.0 * m->mu[e] * m->vol[e], bl = m->lam[e] * m->vol[e];
-            float4 A4, B4, C4;
+            float4 A4;
             std::memcpy(&A4.x, &ids[0], 4);
             std::memcpy(&A4.y, &ids[1], 4);
             std::memcpy(&A4.z, &ids[2], 4);
-            A4.w = (float)a2;
-            B4 = make_float4((float)g[oth[0]][0], (float)g[oth[0]][1], (float)g[oth[0]][2], (float)bl);
-            C4 = make_float4((float)g[oth[1]][0], (float)g[oth[1]][1], (float)g[oth[1]][2], (float)g[oth[2]][0]);
+            A4.w = (float)(2.0 * m->mu[e] * m->vol[e]);
             ra[s] = A4;
-            rb[s] = B4;
-            rc[s] = C4;
+            rb[s] = make_float4((float)g[oth[0]][0], (float)g[oth[0]][1], (float)g[oth[0]][2],
+                                (float)(m->lam[e] * m->vol[e]));
+            rc[s] = make_float4((float)g[oth[1]][0], (float)g[oth[1]][1], (float)g[oth[1]][2], (float)g[oth[2]][0]);
             rd[s] = make_float2((float)g[oth[2]][1], (float)g[oth[2]][2]);
         }
     }
+
+    // ring layout: per lane-width run, 32-slot aligned; W slots per vertex
+    m->items.clear();
+    m->item_off.assign(m->ncol + 1, 0);
+    std::vector<float4> qa, qb, qc;
+    std::vector<int32_t> qid;
+    for (int c = 0; c < m->ncol; ++c) {
+        if (m->ring_colour[c]) {
+            const SegmentTable& t = m->tables[c];
+            for (int k = 0; k < t.count; ++k) {
+                const Segment& sg = t.seg[k];
+                const int W = sg.width;
+                const int32_t slot_base = (int32_t)qa.size();  // a multiple of 32
+                const int32_t nslots = ((sg.v_end - sg.v_begin) * W + kRingLanes - 1) / kRingLanes * kRingLanes;
+                qa.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
+                qb.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
+                qc.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
+                qid.resize(slot_base + nslots, 0);
+                for (int32_t vv = sg.v_begin; vv < sg.v_end; ++vv) {
+                    const int32_t i = order[vv];
+                    const int32_t s0 = slot_base + (vv - sg.v_begin) * W;
+                    const int32_t* rg = &ring[ring_off[i]];
+                    const int rn = ring_n(i);
+                    for (int l = 0; l < W; ++l) qid[s0 + l] = l < rn ? iperm[rg[l]] : vv;
+                    for (int32_t k2 = inc_off[i]; k2 < inc_off[i + 1]; ++k2) {
+                        const int32_t slot = s0 + (k2 - inc_off[i]);
+                        const int32_t e = inc_tet[k2];
+                        const int loc = inc_loc[k2];
+                        double g[4][3];
+                        grads(e, g);
+                        int oth[3], n = 0;
+                        for (int j = 0; j < 4; ++j)
+                            if (j != loc) oth[n++] = j;
+                        int32_t packed = 0;
+                        for (int q = 0; q < 3; ++q) {
+                            const int32_t w = m->tets[4 * (size_t)e + oth[q]];
+                            const int32_t l = (int32_t)(std::lower_bound(rg, rg + rn, w) - rg);
+                            packed |= l << (8 * q);
+                        }
+                        float pk;
+                        std::memcpy(&pk, &packed, 4);
+                        qa[slot] = make_float4((float)g[oth[0]][0], (float)g[oth[0]][1], (float)g[oth[0]][2],
+                                               (float)(2.0 * m->mu[e] * m->vol[e]));
+                        qb[slot] = make_float4((float)g[oth[1]][0], (float)g[oth[1]][1], (float)g[oth[1]][2],
+                                               (float)(m->lam[e] * m->vol[e]));
+                        qc[slot] = make_float4((float)g[oth[2]][0], (float)g[oth[2]][1], (float)g[oth[2]][2], pk);
+                    }
+                }
+                const int per_item = kRingLanes / W;
+                for (int32_t vv = sg.v_begin; vv < sg.v_end; vv += per_item) {
+                    Item it{};
+                    it.v0 = vv;
+                    it.nv = std::min<int32_t>(per_item, sg.v_end - vv);
+                    it.w = W;
+                    it.slot0 = slot_base + (vv - sg.v_begin) * W;
+                    m->items.push_back(it);
+                }
+            }
+        }
+        m->item_off[c + 1] = (int32_t)m->items.size();
+    }
+    m->nitems_ring = (int32_t)m->items.size();
+
     std::vector<float4> aux0(m->nfree), aux1(m->nfree);
     std::vector<int32_t> comp(m->ncomp > 1 ? m->nfree : 0);
     for (int32_t w = 0; w < m->nfree; ++w) {
@@ -356,6 +477,11 @@ pbng_status build_layout(pbng_mesh* m) {
     PBNG_CUDA(m, upload(m->d_rec_b, rb, st));
     PBNG_CUDA(m, upload(m->d_rec_c, rc, st));
     PBNG_CUDA(m, upload(m->d_rec_d, rd, st));
+    PBNG_CUDA(m, upload(m->d_ring_ra, qa, st));
+    PBNG_CUDA(m, upload(m->d_ring_rb, qb, st));
+    PBNG_CUDA(m, upload(m->d_ring_rc, qc, st));
+    PBNG_CUDA(m, upload(m->d_ring_id, qid, st));
+    PBNG_CUDA(m, upload(m->d_items, m->items, st));
     PBNG_CUDA(m, upload(m->d_aux0, aux0, st));
     PBNG_CUDA(m, upload(m->d_aux1, aux1, st));
     PBNG_CUDA(m, upload(m->d_comp, comp, st));
@@ -364,7 +490,8 @@ pbng_status build_layout(pbng_mesh* m) {
     PBNG_CUDA(m, upload(m->d_dir_lo, dlo, st));
     for (auto& sb : m->d_state)
         for (auto& b : sb) PBNG_CUDA(m, ensure_buf(b, sizeof(float4) * (size_t)nv));
-    PBNG_CUDA(m, ensure_buf(m->d_partial, sizeof(double) * (size_t)std::max(1, m->total_partials)));
+    m->ring_partials = ring_warps(m->nitems_ring);
+    PBNG_CUDA(m, ensure_buf(m->d_partial, sizeof(double) * (size_t)std::max(1, m->ring_partials + m->total_partials)));
     PBNG_CUDA(m, ensure_buf(m->d_comp_sq, sizeof(double) * (size_t)m->ncomp));
     PBNG_CUDA(m, ensure_buf(m->d_scalar, sizeof(double) * 4));
     PBNG_CUDA(m, ensure_buf(m->d_err, sizeof(int32_t)));
@@ -381,10 +508,15 @@ pbng_status build_layout(pbng_mesh* m) {
     d.aux0 = (const float4*)m->d_aux0.p;
     d.aux1 = (const float4*)m->d_aux1.p;
     d.comp = m->ncomp > 1 ? (const int32_t*)m->d_comp.p : nullptr;
+    d.ring_ra = (const float4*)m->d_ring_ra.p;
+    d.ring_rb = (const float4*)m->d_ring_rb.p;
+    d.ring_rc = (const float4*)m->d_ring_rc.p;
+    d.ring_id = (const int32_t*)m->d_ring_id.p;
     d.pn_x = (float)m->pn[0];
     d.pn_y = (float)m->pn[1];
     d.pn_z = (float)m->pn[2];
     d.k_contact = m->has_plane ? (float)m->kc : 0.0f;
+    m->built_direct = m->want_direct;
     m->dirty = false;
     m->has_state = false;
     return PBNG_OK;
@@ -403,35 +535,47 @@ pbng_status ensure_ready(pbng_mesh* m) {
     return PBNG_OK;
 }
 
-// FP64 squared residual norms (per component) of state `slot` -> host `out`.
-pbng_status residual_sq(pbng_mesh* m, int slot, bool compensated, double* out) {
+// Enqueues the FP64 squared residual norms of state `s`: the ring launch
+// writes ring_partials per-warp partials at partial[0..), each direct-load
+// colour its per-block partials after them; then the sum lands in *scalar.
+// With several components the sums go to comp_sq (zeroed here) instead.
+pbng_status enqueue_residual(pbng_mesh* m, State s, bool compensated, double* partial, double* comp_sq,
+                             double* scalar) {
     cudaStream_t st = m->stream;
-    State s = state_of(m, slot);
     const bool multi = m->ncomp > 1;
-    const int pslot = prof_begin(m, kProfResidual);
-    if (multi) PBNG_CUDA(m, cudaMemsetAsync(m->d_comp_sq.p, 0, sizeof(double) * m->ncomp, st));
+    if (multi) PBNG_CUDA(m, cudaMemsetAsync(comp_sq, 0, sizeof(double) * m->ncomp, st));
+    if (m->nitems_ring > 0) {
+        PBNG_CUDA(m, launch_ring_residual(m->dm, s, (const Item*)m->d_items.p, m->nitems_ring, compensated,
+                                          partial, multi ? comp_sq : nullptr, (int32_t*)m->d_err.p, st));
+        m->kernel_launches++;
+    }
     for (int c = 0; c < m->ncol; ++c) {
+        if (m->ring_colour[c]) continue;
         PBNG_CUDA(m, launch_residual(m->dm, s, m->tables[c], compensated,
-                                     (double*)m->d_partial.p + m->table_partial_off[c],
-                                     multi ? (double*)m->d_comp_sq.p : nullptr, m->ncomp, nullptr, st));
+                                     partial + m->ring_partials + m->table_partial_off[c],
+                                     multi ? comp_sq : nullptr, m->ncomp, nullptr, st));
         if (m->tables[c].total_blocks > 0) m->kernel_launches++;
     }
     if (!multi) {
-        PBNG_CUDA(m, launch_reduce((const double*)m->d_partial.p, m->total_partials,
-                                   (double*)m->d_scalar.p, st));
+        PBNG_CUDA(m, launch_reduce(partial, m->ring_partials + m->total_partials, scalar, st));
         m->kernel_launches++;
     }
+    return PBNG_OK;
+}
+
+// FP64 squared residual norms (per component) of state `slot` -> host `out`.
+pbng_status residual_sq(pbng_mesh* m, int slot, bool compensated, double* out) {
+    cudaStream_t st = m->stream;
+    const bool multi = m->ncomp > 1;
+    const int pslot = prof_begin(m, kProfResidual);
+    pbng_status r = enqueue_residual(m, state_of(m, slot), compensated, (double*)m->d_partial.p,
+                                     (double*)m->d_comp_sq.p, (double*)m->d_scalar.p);
+    if (r) return r;
     prof_end(m, pslot);
-    if (multi) {
-        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_comp_sq.p, sizeof(double) * m->ncomp,
-                                     cudaMemcpyDeviceToHost, st));
-    } else {
-        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_scalar.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-    }
+    PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? m->d_comp_sq.p : m->d_scalar.p,
+                                 sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
     PBNG_CUDA(m, cudaStreamSynchronize(st));
-    for (int k = 0; k < m->ncomp; ++k) out[k] = m->h_pinned[k];
-    if (m->ncol == 0)
-        for (int k = 0; k < m->ncomp; ++k) out[k] = 0.0;
+    for (int k = 0; k < m->ncomp; ++k) out[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
     return PBNG_OK;
 }
 
@@ -441,17 +585,25 @@ pbng_status check_err(pbng_mesh* m) {
     PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
     if (h) {
         PBNG_CUDA(m, cudaMemsetAsync(m->d_err.p, 0, sizeof(int32_t), m->stream));
+        if (h & kErrTimeout) return fail(m, PBNG_ETIMEOUT, "asynchronous copy wait gave up");
         if (h & kErrNonSPD) return fail(m, PBNG_EDEGENERATE, "nodal Hessian not positive definite");
         return fail(m, PBNG_EDIVERGED, "non-finite vertex update");
     }
     return PBNG_OK;
 }
 
+// kernel_path 1 (direct loads everywhere) needs CSR records for every
+// colour: switching path rebuilds the layout (and drops the iterate history).
+void select_path(pbng_mesh* m, const pbng_params* p) {
+    m->want_direct = p->kernel_path == 1;
+    if (m->want_direct != m->built_direct) m->dirty = true;
+}
+
 bool valid_params(const pbng_params* p) {
     return p && p->model == 0 && p->accel >= 0 && p->accel <= 2 && p->residual_every >= 1 &&
            (p->precision == PBNG_PREC_FP32 || p->precision == PBNG_PREC_COMPENSATED) &&
            std::isfinite(p->omega) && std::isfinite(p->rho) && std::isfinite(p->gamma) &&
-           std::isfinite(p->step) && p->skip_tol >= 0.0;
+           std::isfinite(p->step) && p->skip_tol >= 0.0 && (p->kernel_path == 0 || p->kernel_path == 1);
 }
 
 // Loads u_dev (or keeps the stored iterate) and resets the history.
@@ -489,7 +641,12 @@ pbng_status one_sweep(pbng_mesh* m, const pbng_params* p) {
     for (int c = 0; c < m->ncol; ++c) {
         if (m->tables[c].total_blocks <= 0) continue;
         const int slot = prof_begin(m, kProfColour);
-        PBNG_CUDA(m, launch_colour_pass(m->dm, cur, m->tables[c], pp, comp, (int32_t*)m->d_err.p, m->stream));
+        if (m->ring_colour[c])
+            PBNG_CUDA(m, launch_ring_pass(m->dm, cur, (const Item*)m->d_items.p + m->item_off[c],
+                                          m->item_off[c + 1] - m->item_off[c], pp, comp,
+                                          (int32_t*)m->d_err.p, m->stream));
+        else
+            PBNG_CUDA(m, launch_colour_pass(m->dm, cur, m->tables[c], pp, comp, (int32_t*)m->d_err.p, m->stream));
         prof_end(m, slot);
         m->kernel_launches++;
     }
@@ -668,9 +825,11 @@ pbng_status pbng_get_colouring(pbng_mesh* m, int32_t* colour_out, int32_t* ncolo
 
 pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_params* p,
                        double* rel_residual_out) {
+    if (!m) return PBNG_EINVAL;
+    if (!valid_params(p) || nsweeps < 0) return fail(m, PBNG_EINVAL, "bad parameters");
+    select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
-    if (!valid_params(p) || nsweeps < 0) return fail(m, PBNG_EINVAL, "bad parameters");
     if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
     const bool comp = p->precision == PBNG_PREC_COMPENSATED;
     if ((s = begin(m, u_dev, p, rel_residual_out != nullptr))) return s;
@@ -690,9 +849,11 @@ pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_p
 
 pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps,
                        const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out) {
+    if (!m) return PBNG_EINVAL;
+    if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
+    select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
-    if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
     if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
     const bool comp = p->precision == PBNG_PREC_COMPENSATED;
     if ((s = begin(m, u_dev, p, true))) return s;
@@ -762,29 +923,22 @@ pbng_status pbng_residual_noalloc(pbng_mesh* m, const float* u_dev, double* resi
     double* scratch = nullptr;
     PBNG_CUDA(m, noalloc_scratch(m->device, &scratch));
     const bool multi = m->ncomp > 1;
-    const int64_t need = multi ? (int64_t)m->ncomp : (int64_t)m->total_partials + 1;
+    // partial sums (per warp of the ring launch, per block of direct-load
+    // colours) then the total, or the per-component sums
+    const int64_t nparts = (int64_t)m->ring_partials + m->total_partials;
+    const int64_t need = multi ? (int64_t)m->ncomp : nparts + 1;
     if (need > noalloc_scratch_capacity())
         return fail(m, PBNG_EINVAL, "mesh needs more FP64 partial sums than the fixed 65,536-entry scratch holds");
     cudaStream_t st = m->stream;
     PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, (const int32_t*)m->d_perm.p,
                              (const float4*)m->d_dir_hi.p, (const float4*)m->d_dir_lo.p,
                              state_of(m, 3), st));
-    State s = state_of(m, 3);
-    if (multi) {
-        // per-component sums accumulate atomically: start them at zero
-        PBNG_CUDA(m, cudaMemsetAsync(scratch, 0, sizeof(double) * m->ncomp, st));
-        for (int c = 0; c < m->ncol; ++c)
-            PBNG_CUDA(m, launch_residual(m->dm, s, m->tables[c], true, scratch, scratch, m->ncomp, nullptr, st));
-        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, scratch, sizeof(double) * m->ncomp, cudaMemcpyDeviceToHost, st));
-    } else {
-        // every block of every colour writes its own partial; the sum lands after them
-        for (int c = 0; c < m->ncol; ++c)
-            PBNG_CUDA(m, launch_residual(m->dm, s, m->tables[c], true, scratch + m->table_partial_off[c],
-                                         nullptr, m->ncomp, nullptr, st));
-        PBNG_CUDA(m, launch_reduce(scratch, m->total_partials, scratch + m->total_partials, st));
-        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, scratch + m->total_partials, sizeof(double),
-                                     cudaMemcpyDeviceToHost, st));
-    }
+    // per-component sums accumulate atomically and start at zero (the memset
+    // in enqueue_residual); every partial is written before it is summed
+    pbng_status r = enqueue_residual(m, state_of(m, 3), true, scratch, scratch, scratch + nparts);
+    if (r) return r;
+    PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? scratch : scratch + nparts,
+                                 sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
     PBNG_CUDA(m, cudaStreamSynchronize(st));
     for (int k = 0; k < m->ncomp; ++k) residual_out[k] = (m->ncol == 0) ? 0.0 : std::sqrt(m->h_pinned[k]);
     return PBNG_OK;
@@ -848,6 +1002,7 @@ void pbng_destroy(pbng_mesh* m) {
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
     DevBuf* bufs[] = {&m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
+                      &m->d_ring_ra, &m->d_ring_rb, &m->d_ring_rc, &m->d_ring_id, &m->d_items,
                       &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_partial, &m->d_comp_sq, &m->d_scalar, &m->d_err};
     for (DevBuf* b : bufs) free_buf(*b);

@@ -1,0 +1,297 @@
+// Per-element and per-vertex arithmetic of the PBNG node update, shared by
+// the direct kernels (pbng_kernels.cu) and the pipelined kernels
+// (pbng_pipeline.cu).  All of it is float32; see pbng_kernels.cu for the
+// precision scheme.
+#pragma once
+
+#include "pbng_internal.h"
+
+namespace pbng {
+namespace el {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
+
+__device__ __forceinline__ float det3(float a, float b, float c, float d, float e, float f, float g,
+                                      float h, float i) {
+    return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+}
+
+// u_j - u_i from stored pairs: (hi_j - hi_i) + (lo_j - lo_i).
+template <bool COMP>
+__device__ __forceinline__ float3 pair_diff(float4 hj, float4 lj, float3 uh, float3 ul) {
+    float3 d = make_float3(hj.x - uh.x, hj.y - uh.y, hj.z - uh.z);
+    if (COMP) {
+        d.x += lj.x - ul.x;
+        d.y += lj.y - ul.y;
+        d.z += lj.z - ul.z;
+    }
+    return d;
+}
+
+// Slow path of rotation_minus_identity for rotations beyond about 120
+// degrees: the adjugate column with the largest diagonal entry.
+static __device__ __noinline__ void adjugate_best_column(const float* M, float q00, float* q) {
+    float best = -q00;
+    int kbest = 0;
+    for (int k = 1; k < 4; ++k) {
+        int r[3], n = 0;
+        for (int i = 0; i < 4; ++i)
+            if (i != k) r[n++] = i;
+        const float dkk = det3(M[4 * r[0] + r[0]], M[4 * r[0] + r[1]], M[4 * r[0] + r[2]],
+                               M[4 * r[1] + r[0]], M[4 * r[1] + r[1]], M[4 * r[1] + r[2]],
+                               M[4 * r[2] + r[0]], M[4 * r[2] + r[1]], M[4 * r[2] + r[2]]);
+        if (-dkk > best) { best = -dkk; kbest = k; }
+    }
+    if (kbest == 0) return;
+    for (int j = 0; j < 4; ++j) {
+        // adj_jk = (-1)^{j+k} det(M without row k and column j)
+        int rr[3], cc[3], nr = 0, nc = 0;
+        for (int i = 0; i < 4; ++i) {
+            if (i != kbest) rr[nr++] = i;
+            if (i != j) cc[nc++] = i;
+        }
+        const float dm = det3(M[4 * rr[0] + cc[0]], M[4 * rr[0] + cc[1]], M[4 * rr[0] + cc[2]],
+                              M[4 * rr[1] + cc[0]], M[4 * rr[1] + cc[1]], M[4 * rr[1] + cc[2]],
+                              M[4 * rr[2] + cc[0]], M[4 * rr[2] + cc[1]], M[4 * rr[2] + cc[2]]);
+        q[j] = ((j + kbest) & 1) ? -dm : dm;
+    }
+}
+
+// Rotation part of F = I + H for the corotated energy (Section "Constitutive
+// Models", Eq. cor, with R the rotation of the polar decomposition in SO(3)).
+//
+// Method (Horn 1987, "Closed-form solution of absolute orientation using unit
+// quaternions"; the polar use follows Higham & Noferini 2016): R(q) maximises
+// tr(R^T F) over rotations, which is the SO(3) polar factor (the smallest
+// singular value takes the sign of det F).  tr(R(q)^T F) = q^T N q for a
+// traceless symmetric 4x4 N built linearly from F, so q is the eigenvector of
+// N's largest eigenvalue.  Its characteristic polynomial is
+//   p(t) = t^4 - 2|F|^2 t^2 - 8 det(F) t + |F|^4 - 4|cof F|^2,
+// whose largest root is found by Newton from the upper bound sqrt(3)|F|
+// (monotone, because p is real-rooted; the quotient uses the fast
+// approximate division, which Newton's own correction absorbs).  The
+// eigenvector is a column of adj(N - t I), which is rank one; column 0 is
+// used when it is well scaled (rotation angle up to about 120 degrees), else
+// the column with the largest diagonal entry.  N - tI is built from H, so the
+// vector part of q, and with it R - I = 2w[v]x + 2[v]x^2, keep relative
+// accuracy as H -> 0.
+__device__ __forceinline__ void rotation_minus_identity(const float* H, float n2, float c2, float J,
+                                                        float* RmI) {
+    const float k0 = n2 * n2 - 4.0f * c2;
+    const float n23 = 3.0f * n2;
+    float t = n23 * rsqrtf(n23);
+    float dp = 1.0f;
+#pragma unroll 1
+    for (int it = 0; it < 16; ++it) {
+        const float t2 = t * t;
+        const float p = ((t2 - 2.0f * n2) * t - 8.0f * J) * t + k0;
+        dp = (4.0f * t2 - 4.0f * n2) * t - 8.0f * J;
+        const float d = __fdividef(p, dp);
+        t -= d;
+        if (!(fabsf(d) > 2e-7f * t)) break;
+    }
+    const float trH = H[0] + H[4] + H[8];
+    const float m00 = (3.0f - t) + trH;
+    const float m11 = (-1.0f - t) + (H[0] - H[4] - H[8]);
+    const float m22 = (-1.0f - t) + (H[4] - H[0] - H[8]);
+    const float m33 = (-1.0f - t) + (H[8] - H[0] - H[4]);
+    const float m01 = H[7] - H[5], m02 = H[2] - H[6], m03 = H[3] - H[1];
+    const float m12 = H[1] + H[3], m13 = H[2] + H[6], m23 = H[5] + H[7];
+    // Column 0 of adj(M) = (+min00, -min01, +min02, -min03), the minors of
+    // rows 1..3.  Expand each along row 1 with the six 2x2 minors of rows 2, 3
+    // (columns a < b), which the four determinants share.
+    const float k01 = m02 * m13 - m12 * m03, k02 = m02 * m23 - m22 * m03, k03 = m02 * m33 - m23 * m03;
+    const float k12 = m12 * m23 - m22 * m13, k13 = m12 * m33 - m23 * m13, k23 = m22 * m33 - m23 * m23;
+    float q[4];
+    q[0] = m11 * k23 - m12 * k13 + m13 * k12;
+    q[1] = -(m01 * k23 - m12 * k03 + m13 * k02);
+    q[2] = m01 * k13 - m11 * k03 + m13 * k01;
+    q[3] = -(m01 * k12 - m11 * k02 + m12 * k01);
+    // adj(M) = -p'(t) q q^T, so q_0^2 = -adj_00 / p'(t).
+    if (!(-q[0] > 0.25f * dp)) {
+        const float M[16] = {m00, m01, m02, m03, m01, m11, m12, m13,
+                             m02, m12, m22, m23, m03, m13, m23, m33};
+        adjugate_best_column(M, q[0], q);
+    }
+    const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
+    if (qq > 1e-30f && qq < 3.0e38f) {
+        const float inv = rsqrtf(qq);
+        w = q[0] * inv; x = q[1] * inv; y = q[2] * inv; z = q[3] * inv;
+    }
+    // R - I = 2 w [v]x + 2 (v v^T - |v|^2 I), v = (x, y, z).
+    const float xx = x * x, yy = y * y, zz = z * z;
+    const float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
+    RmI[0] = -2.0f * (yy + zz);
+    RmI[1] = 2.0f * (xy - wz);
+    RmI[2] = 2.0f * (xz + wy);
+    RmI[3] = 2.0f * (xy + wz);
+    RmI[4] = -2.0f * (xx + zz);
+    RmI[5] = 2.0f * (yz - wx);
+    RmI[6] = 2.0f * (xz - wy);
+    RmI[7] = 2.0f * (yz + wx);
+    RmI[8] = -2.0f * (xx + yy);
+}
+
+// Contribution of one incident tetrahedron to the force r and modified
+// Hessian A (upper triangle a00 a01 a02 a11 a12 a22) of vertex i:
+//   r -= V P(F) g_i,  P = 2 mu (F - R) + lambda (J - 1) cof F
+//   A += V (2 mu |g_i|^2 I + lambda w w^T),  w = cof(F) g_i
+// with F = I + sum_{j != i} (u_j - u_i) g_j^T and g_i = -(g_j1 + g_j2 + g_j3).
+// gk = dN_jk/dX of the other three vertices, a = 2 mu V, b = lambda V,
+// dk = u_jk - u_i.
+template <bool NEED_A>
+__device__ __forceinline__ void element_math(float3 gj1, float3 gj2, float3 gj3, float a, float b,
+                                             float3 d1, float3 d2, float3 d3, float* r, float* A) {
+    const float g1[3] = {gj1.x, gj1.y, gj1.z}, g2[3] = {gj2.x, gj2.y, gj2.z}, g3[3] = {gj3.x, gj3.y, gj3.z};
+    const float dd1[3] = {d1.x, d1.y, d1.z}, dd2[3] = {d2.x, d2.y, d2.z}, dd3[3] = {d3.x, d3.y, d3.z};
+    float H[9];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) H[3 * p + q] = dd1[p] * g1[q] + dd2[p] * g2[q] + dd3[p] * g3[q];
+    const float gi[3] = {-(g1[0] + g2[0] + g3[0]), -(g1[1] + g2[1] + g3[1]), -(g1[2] + g2[2] + g3[2])};
+
+    const float F0 = 1.0f + H[0], F4 = 1.0f + H[4], F8 = 1.0f + H[8];
+    const float F1 = H[1], F2 = H[2], F3 = H[3], F5 = H[5], F6 = H[6], F7 = H[7];
+    float C[9];
+    C[0] = F4 * F8 - F5 * F7;
+    C[1] = F5 * F6 - F3 * F8;
+    C[2] = F3 * F7 - F4 * F6;
+    C[3] = F7 * F2 - F8 * F1;
+    C[4] = F8 * F0 - F6 * F2;
+    C[5] = F6 * F1 - F7 * F0;
+    C[6] = F1 * F5 - F2 * F4;
+    C[7] = F2 * F3 - F0 * F5;
+    C[8] = F0 * F4 - F1 * F3;
+    // J - 1 = tr H + (sum of principal 2x2 minors of H) + det H.
+    const float Jm1 = (H[0] + H[4] + H[8]) +
+                      (H[0] * H[4] - H[1] * H[3] + H[0] * H[8] - H[2] * H[6] + H[4] * H[8] - H[5] * H[7]) +
+                      det3(H[0], H[1], H[2], H[3], H[4], H[5], H[6], H[7], H[8]);
+    float n2 = 0.0f, c2 = 0.0f;
+    const float Fm[9] = {F0, F1, F2, F3, F4, F5, F6, F7, F8};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        n2 += Fm[k] * Fm[k];
+        c2 += C[k] * C[k];
+    }
+    float RmI[9];
+    rotation_minus_identity(H, n2, c2, 1.0f + Jm1, RmI);
+    float w[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        w[p] = C[3 * p] * gi[0] + C[3 * p + 1] * gi[1] + C[3 * p + 2] * gi[2];
+        const float fr = (H[3 * p] - RmI[3 * p]) * gi[0] + (H[3 * p + 1] - RmI[3 * p + 1]) * gi[1] +
+                         (H[3 * p + 2] - RmI[3 * p + 2]) * gi[2];
+        r[p] -= a * fr + b * Jm1 * w[p];
+    }
+    if (NEED_A) {
+        const float ag = a * (gi[0] * gi[0] + gi[1] * gi[1] + gi[2] * gi[2]);
+        A[0] += ag + b * w[0] * w[0];
+        A[1] += b * w[0] * w[1];
+        A[2] += b * w[0] * w[2];
+        A[3] += ag + b * w[1] * w[1];
+        A[4] += b * w[1] * w[2];
+        A[5] += ag + b * w[2] * w[2];
+    }
+}
+
+// Body force, weak springs and plane contact of a vertex at displacement
+// uh + ul (Section "Weak Constraints"), from its aux records
+// x0 = (f^ext, K), x1 = (spring target displacement, n.X - d):
+// r += f^ext; r -= K (u - t_u), A += K I; if s = n.X - d + n.u < 0:
+// r -= k s n, A += k n n^T.
+template <bool COMP, bool NEED_A>
+__device__ __forceinline__ void vertex_terms(const DeviceMesh& m, float4 x0, float4 x1, float3 uh,
+                                             float3 ul, float* r, float* A) {
+    r[0] += x0.x;
+    r[1] += x0.y;
+    r[2] += x0.z;
+    if (x0.w != 0.0f) {
+        float e0 = uh.x - x1.x, e1 = uh.y - x1.y, e2 = uh.z - x1.z;
+        if (COMP) { e0 += ul.x; e1 += ul.y; e2 += ul.z; }
+        r[0] -= x0.w * e0;
+        r[1] -= x0.w * e1;
+        r[2] -= x0.w * e2;
+        if (NEED_A) { A[0] += x0.w; A[3] += x0.w; A[5] += x0.w; }
+    }
+    if (m.k_contact > 0.0f) {
+        float sd = x1.w + (m.pn_x * uh.x + m.pn_y * uh.y + m.pn_z * uh.z);
+        if (COMP) sd += m.pn_x * ul.x + m.pn_y * ul.y + m.pn_z * ul.z;
+        if (sd < 0.0f) {
+            const float ks = m.k_contact * sd;
+            r[0] -= ks * m.pn_x;
+            r[1] -= ks * m.pn_y;
+            r[2] -= ks * m.pn_z;
+            if (NEED_A) {
+                A[0] += m.k_contact * m.pn_x * m.pn_x;
+                A[1] += m.k_contact * m.pn_x * m.pn_y;
+                A[2] += m.k_contact * m.pn_x * m.pn_z;
+                A[3] += m.k_contact * m.pn_y * m.pn_y;
+                A[4] += m.k_contact * m.pn_y * m.pn_z;
+                A[5] += m.k_contact * m.pn_z * m.pn_z;
+            }
+        }
+    }
+}
+
+// hi + lo += d, keeping the pair normalised (TwoSum, then Fast2Sum).
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float d) {
+    const float s = __fadd_rn(hi, d);
+    const float bp = __fadd_rn(s, -hi);
+    const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bp)), __fadd_rn(d, -bp));
+    const float t = __fadd_rn(e, lo);
+    const float h2 = __fadd_rn(s, t);
+    lo = __fadd_rn(t, -__fadd_rn(h2, -s));
+    hi = h2;
+}
+
+template <int W>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off, W);
+    return v;
+}
+
+// Eq. pbgn_dx / pbgn_update: Delta = step A^{-1} r (adjugate; A is SPD by
+// construction, Eq. mod_hess) and u_v += Delta in place.
+template <bool COMP>
+__device__ __forceinline__ void solve_and_write(State s, int v, float3 uh, float3 ul, const float* r,
+                                                const float* A, PassParams pp, int32_t* err) {
+    if (pp.skip_tol > 0.0f && r[0] * r[0] + r[1] * r[1] + r[2] * r[2] <= pp.skip_tol * pp.skip_tol) return;
+    const float c00 = A[3] * A[5] - A[4] * A[4];
+    const float c01 = A[2] * A[4] - A[1] * A[5];
+    const float c02 = A[1] * A[4] - A[2] * A[3];
+    const float c11 = A[0] * A[5] - A[2] * A[2];
+    const float c12 = A[1] * A[2] - A[0] * A[4];
+    const float c22 = A[0] * A[3] - A[1] * A[1];
+    const float det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (!(det > 0.0f) || !(det < 3.0e38f)) {
+        atomicOr(err, kErrNonSPD);
+        return;
+    }
+    const float sc = __fdividef(pp.step, det);
+    const float dx = sc * (c00 * r[0] + c01 * r[1] + c02 * r[2]);
+    const float dy = sc * (c01 * r[0] + c11 * r[1] + c12 * r[2]);
+    const float dz = sc * (c02 * r[0] + c12 * r[1] + c22 * r[2]);
+    if (!(fabsf(dx) + fabsf(dy) + fabsf(dz) < 3.0e38f)) {  // NaN or infinity
+        atomicOr(err, kErrNonFinite);
+        return;
+    }
+    if (COMP) {
+        pair_add(uh.x, ul.x, dx);
+        pair_add(uh.y, ul.y, dy);
+        pair_add(uh.z, ul.z, dz);
+        s.lo[v] = make_float4(ul.x, ul.y, ul.z, 0.f);
+    } else {
+        uh.x += dx;
+        uh.y += dy;
+        uh.z += dz;
+    }
+    s.hi[v] = make_float4(uh.x, uh.y, uh.z, 0.f);
+}
+
+}  // namespace el
+}  // namespace pbng

@@ -40,6 +40,12 @@ struct DeviceMesh {
     const float4* aux0;      // [nfree] f_ext (xyz), total spring stiffness K
     const float4* aux1;      // [nfree] spring target displacement (xyz), n.X - d
     const int32_t* comp;     // [nfree] component id, or nullptr for one component
+    // Ring layout (colours whose vertices all fit 32 lanes): one 32-slot
+    // item per warp; vertex v of a lane-width-W run owns W consecutive slots.
+    const float4* ring_ra;   // [nslots] g_j1 (xyz), a = 2 mu V
+    const float4* ring_rb;   // [nslots] g_j2 (xyz), b = lambda V
+    const float4* ring_rc;   // [nslots] g_j3 (xyz), local ring indices l1 | l2 << 8 | l3 << 16 (int bits)
+    const int32_t* ring_id;  // [nslots] internal id of the vertex's l-th 1-ring neighbour (own id when padding)
     float pn_x, pn_y, pn_z;  // contact plane normal (unit)
     float k_contact;         // 0 = no plane
 };
@@ -60,7 +66,18 @@ struct PassParams {
 enum : int32_t {
     kErrNonSPD = 1,      // det(A_i) <= 0 or non-finite
     kErrNonFinite = 2,   // non-finite update
+    kErrTimeout = 4,     // a bounded wait on an asynchronous copy gave up
 };
+
+// One warp's work item in the ring layout: 32 slots starting at slot0,
+// holding nv = 32 / w (or fewer at the end of a run) vertices v0, v0+1, ...
+struct Item {
+    int32_t v0;
+    int32_t nv;
+    int32_t w;
+    int32_t slot0;
+};
+constexpr int kRingLanes = 32;
 
 // Host launch wrappers (pbng_kernels.cu).  All enqueue on `st`.
 cudaError_t launch_colour_pass(const DeviceMesh& m, State s, const SegmentTable& t, PassParams p,
@@ -75,6 +92,17 @@ cudaError_t launch_load(int32_t nv, int32_t nfree, const float* u_user, const in
                         const float4* dir_hi, const float4* dir_lo, State s, cudaStream_t st);
 cudaError_t launch_store(int32_t nv, const int32_t* perm, State s, float* u_user, cudaStream_t st);
 cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st);
+
+// Ring-layout kernels (pbng_ring.cu): persistent warps, each streaming its
+// items with TMA bulk copies and cp.async gathers.  The residual writes one
+// FP64 partial per warp of the grid (ring_warps(nitems) of them) or, with
+// comp_sq, per-component sums.
+int ring_warps(int nitems);
+cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
+                             bool compensated, int32_t* err, cudaStream_t st);
+cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
+                                 bool compensated, double* warp_partial, double* comp_sq,
+                                 int32_t* err, cudaStream_t st);
 
 // Fixed device scratch of the allocation-free residual (pbng_kernels.cu).
 int noalloc_scratch_capacity();

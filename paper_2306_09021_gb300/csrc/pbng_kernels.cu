@@ -14,6 +14,7 @@
 // displacement differences, J - 1 from the invariants of H, and R - I of the
 // polar rotation from a quaternion whose vector part carries the rotation.
 // Residual norms are accumulated in float64.
+#include "pbng_element.cuh"
 #include "pbng_internal.h"
 
 #include <math.h>
@@ -21,252 +22,13 @@
 namespace pbng {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
+using el::kFull;
+using el::f3;
 
-__device__ __forceinline__ float3 f3(float4 v) { return make_float3(v.x, v.y, v.z); }
-
-// u_j - u_i from the stored pair: (hi_j - hi_i) + (lo_j - lo_i).
-template <bool COMP>
-__device__ __forceinline__ float3 disp_diff(const State& s, int j, float3 uh, float3 ul) {
-    const float4 h = __ldg(s.hi + j);
-    float3 d = make_float3(h.x - uh.x, h.y - uh.y, h.z - uh.z);
-    if (COMP) {
-        const float4 l = __ldg(s.lo + j);
-        d.x += l.x - ul.x;
-        d.y += l.y - ul.y;
-        d.z += l.z - ul.z;
-    }
-    return d;
-}
-
-__device__ __forceinline__ float det3(float a, float b, float c, float d, float e, float f, float g,
-                                      float h, float i) {
-    return a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
-}
-
-// Rotation part of F = I + H for the corotated energy (Section "Constitutive
-// Models", Eq. cor, with R the rotation of the polar decomposition in SO(3)).
-//
-// Method (Horn 1987, "Closed-form solution of absolute orientation using unit
-// quaternions"; the polar use follows Higham & Noferini 2016): R(q) maximises
-// tr(R^T F) over rotations, which is the SO(3) polar factor (the smallest
-// singular value takes the sign of det F).  tr(R(q)^T F) = q^T N q for a
-// traceless symmetric 4x4 N built linearly from F, so q is the eigenvector of
-// N's largest eigenvalue.  Its characteristic polynomial is
-//   p(t) = t^4 - 2|F|^2 t^2 - 8 det(F) t + |F|^4 - 4|cof F|^2,
-// whose largest root is found by Newton from the upper bound sqrt(3)|F|
-// (monotone, because p is real-rooted).  The eigenvector is a column of
-// adj(N - t I), which is rank one; column 0 is used when it is well scaled
-// (rotation angle up to about 120 degrees), else the column with the largest
-// diagonal entry.  N - I_4-shifted is built from H, so the vector part of q,
-// and with it R - I = 2w[v]x + 2[v]x^2, keep relative accuracy as H -> 0.
-__device__ __forceinline__ void rotation_minus_identity(const float* H, float n2, float c2, float J,
-                                                        float* RmI) {
-    const float k0 = n2 * n2 - 4.0f * c2;
-    float t = sqrtf(3.0f * n2);
-    float dp = 1.0f;
-#pragma unroll 1
-    for (int it = 0; it < 12; ++it) {
-        const float t2 = t * t;
-        const float p = ((t2 - 2.0f * n2) * t - 8.0f * J) * t + k0;
-        dp = (4.0f * t2 - 4.0f * n2) * t - 8.0f * J;
-        const float d = p / dp;
-        t -= d;
-        if (!(fabsf(d) > 1e-7f * t)) break;
-    }
-    const float trH = H[0] + H[4] + H[8];
-    const float m00 = (3.0f - t) + trH;
-    const float m11 = (-1.0f - t) + (H[0] - H[4] - H[8]);
-    const float m22 = (-1.0f - t) + (H[4] - H[0] - H[8]);
-    const float m33 = (-1.0f - t) + (H[8] - H[0] - H[4]);
-    const float m01 = H[7] - H[5], m02 = H[2] - H[6], m03 = H[3] - H[1];
-    const float m12 = H[1] + H[3], m13 = H[2] + H[6], m23 = H[5] + H[7];
-    // Column 0 of adj(M): (+min00, -min01, +min02, -min03).
-    float q0 = det3(m11, m12, m13, m12, m22, m23, m13, m23, m33);
-    float q1 = -det3(m01, m12, m13, m02, m22, m23, m03, m23, m33);
-    float q2 = det3(m01, m11, m13, m02, m12, m23, m03, m13, m33);
-    float q3 = -det3(m01, m11, m12, m02, m12, m22, m03, m13, m23);
-    // adj(M) = -p'(t) q q^T, so q_0^2 = -adj_00 / p'(t).
-    if (!(-q0 > 0.25f * dp)) {
-        const float M[16] = {m00, m01, m02, m03, m01, m11, m12, m13,
-                             m02, m12, m22, m23, m03, m13, m23, m33};
-        float best = -q0;
-        int kbest = 0;
-        float colk[4];
-        for (int k = 1; k < 4; ++k) {
-            // diagonal entry adj_kk = det of M without row k and column k
-            int r[3], n = 0;
-            for (int i = 0; i < 4; ++i)
-                if (i != k) r[n++] = i;
-            const float dkk = det3(M[4 * r[0] + r[0]], M[4 * r[0] + r[1]], M[4 * r[0] + r[2]],
-                                   M[4 * r[1] + r[0]], M[4 * r[1] + r[1]], M[4 * r[1] + r[2]],
-                                   M[4 * r[2] + r[0]], M[4 * r[2] + r[1]], M[4 * r[2] + r[2]]);
-            if (-dkk > best) { best = -dkk; kbest = k; }
-        }
-        if (kbest != 0) {
-            for (int j = 0; j < 4; ++j) {
-                // adj_jk = (-1)^{j+k} det(M without row k, column j)
-                int rr[3], cc[3], nr = 0, nc = 0;
-                for (int i = 0; i < 4; ++i) {
-                    if (i != kbest) rr[nr++] = i;
-                    if (i != j) cc[nc++] = i;
-                }
-                const float dm = det3(M[4 * rr[0] + cc[0]], M[4 * rr[0] + cc[1]], M[4 * rr[0] + cc[2]],
-                                      M[4 * rr[1] + cc[0]], M[4 * rr[1] + cc[1]], M[4 * rr[1] + cc[2]],
-                                      M[4 * rr[2] + cc[0]], M[4 * rr[2] + cc[1]], M[4 * rr[2] + cc[2]]);
-                colk[j] = ((j + kbest) & 1) ? -dm : dm;
-            }
-            q0 = colk[0]; q1 = colk[1]; q2 = colk[2]; q3 = colk[3];
-        }
-    }
-    const float qq = q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3;
-    float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
-    if (qq > 1e-30f && isfinite(qq)) {
-        const float inv = rsqrtf(qq);
-        w = q0 * inv; x = q1 * inv; y = q2 * inv; z = q3 * inv;
-    }
-    // R - I = 2 w [v]x + 2 (v v^T - |v|^2 I), v = (x, y, z).
-    const float xx = x * x, yy = y * y, zz = z * z;
-    const float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
-    RmI[0] = -2.0f * (yy + zz);
-    RmI[1] = 2.0f * (xy - wz);
-    RmI[2] = 2.0f * (xz + wy);
-    RmI[3] = 2.0f * (xy + wz);
-    RmI[4] = -2.0f * (xx + zz);
-    RmI[5] = 2.0f * (yz - wx);
-    RmI[6] = 2.0f * (xz - wy);
-    RmI[7] = 2.0f * (yz + wx);
-    RmI[8] = -2.0f * (xx + yy);
-}
-
-// Contribution of one incident tetrahedron (record s) to the force r and
-// modified Hessian A (upper triangle a00 a01 a02 a11 a12 a22) of vertex i:
-//   r -= V P(F) g_i,  P = 2 mu (F - R) + lambda (J - 1) cof F
-//   A += V (2 mu |g_i|^2 I + lambda w w^T),  w = cof(F) g_i
-// with F = I + sum_{j != i} (u_j - u_i) g_j^T and g_i = -(g_j1 + g_j2 + g_j3).
-template <bool COMP, bool NEED_A>
-__device__ __forceinline__ void element_term(const DeviceMesh& m, const State& s, int rec, float3 uh,
-                                             float3 ul, float* r, float* A) {
-    const float4 ra = __ldcs(m.rec_a + rec);
-    const float4 rb = __ldcs(m.rec_b + rec);
-    const float4 rc = __ldcs(m.rec_c + rec);
-    const float2 rd = __ldcs(m.rec_d + rec);
-    const float a = ra.w, b = rb.w;
-    const float3 d1 = disp_diff<COMP>(s, __float_as_int(ra.x), uh, ul);
-    const float3 d2 = disp_diff<COMP>(s, __float_as_int(ra.y), uh, ul);
-    const float3 d3 = disp_diff<COMP>(s, __float_as_int(ra.z), uh, ul);
-    const float g1[3] = {rb.x, rb.y, rb.z}, g2[3] = {rc.x, rc.y, rc.z}, g3[3] = {rc.w, rd.x, rd.y};
-    const float dd1[3] = {d1.x, d1.y, d1.z}, dd2[3] = {d2.x, d2.y, d2.z}, dd3[3] = {d3.x, d3.y, d3.z};
-    float H[9];
-#pragma unroll
-    for (int p = 0; p < 3; ++p)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) H[3 * p + q] = dd1[p] * g1[q] + dd2[p] * g2[q] + dd3[p] * g3[q];
-    const float gi[3] = {-(g1[0] + g2[0] + g3[0]), -(g1[1] + g2[1] + g3[1]), -(g1[2] + g2[2] + g3[2])};
-
-    const float F0 = 1.0f + H[0], F4 = 1.0f + H[4], F8 = 1.0f + H[8];
-    const float F1 = H[1], F2 = H[2], F3 = H[3], F5 = H[5], F6 = H[6], F7 = H[7];
-    float C[9];
-    C[0] = F4 * F8 - F5 * F7;
-    C[1] = F5 * F6 - F3 * F8;
-    C[2] = F3 * F7 - F4 * F6;
-    C[3] = F7 * F2 - F8 * F1;
-    C[4] = F8 * F0 - F6 * F2;
-    C[5] = F6 * F1 - F7 * F0;
-    C[6] = F1 * F5 - F2 * F4;
-    C[7] = F2 * F3 - F0 * F5;
-    C[8] = F0 * F4 - F1 * F3;
-    // J - 1 = tr H + (sum of principal 2x2 minors of H) + det H.
-    const float Jm1 = (H[0] + H[4] + H[8]) +
-                      (H[0] * H[4] - H[1] * H[3] + H[0] * H[8] - H[2] * H[6] + H[4] * H[8] - H[5] * H[7]) +
-                      det3(H[0], H[1], H[2], H[3], H[4], H[5], H[6], H[7], H[8]);
-    float n2 = 0.0f, c2 = 0.0f;
-    const float Fm[9] = {F0, F1, F2, F3, F4, F5, F6, F7, F8};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        n2 += Fm[k] * Fm[k];
-        c2 += C[k] * C[k];
-    }
-    float RmI[9];
-    rotation_minus_identity(H, n2, c2, 1.0f + Jm1, RmI);
-    float w[3];
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        w[p] = C[3 * p] * gi[0] + C[3 * p + 1] * gi[1] + C[3 * p + 2] * gi[2];
-        const float fr = (H[3 * p] - RmI[3 * p]) * gi[0] + (H[3 * p + 1] - RmI[3 * p + 1]) * gi[1] +
-                         (H[3 * p + 2] - RmI[3 * p + 2]) * gi[2];
-        r[p] -= a * fr + b * Jm1 * w[p];
-    }
-    if (NEED_A) {
-        const float ag = a * (gi[0] * gi[0] + gi[1] * gi[1] + gi[2] * gi[2]);
-        A[0] += ag + b * w[0] * w[0];
-        A[1] += b * w[0] * w[1];
-        A[2] += b * w[0] * w[2];
-        A[3] += ag + b * w[1] * w[1];
-        A[4] += b * w[1] * w[2];
-        A[5] += ag + b * w[2] * w[2];
-    }
-}
-
-// Weak and contact terms of vertex v (internal free id) at displacement (uh + ul):
-// springs r -= K (u - t_u), A += K I; plane contact with s = n.X - d + n.u < 0:
-// r -= k s n, A += k n n^T.
-template <bool COMP, bool NEED_A>
-__device__ __forceinline__ void vertex_terms(const DeviceMesh& m, int v, float3 uh, float3 ul,
-                                             float* r, float* A) {
-    const float4 x0 = __ldg(m.aux0 + v);
-    r[0] += x0.x;
-    r[1] += x0.y;
-    r[2] += x0.z;
-    const float4 x1 = __ldg(m.aux1 + v);
-    if (x0.w != 0.0f) {
-        float e0 = uh.x - x1.x, e1 = uh.y - x1.y, e2 = uh.z - x1.z;
-        if (COMP) { e0 += ul.x; e1 += ul.y; e2 += ul.z; }
-        r[0] -= x0.w * e0;
-        r[1] -= x0.w * e1;
-        r[2] -= x0.w * e2;
-        if (NEED_A) { A[0] += x0.w; A[3] += x0.w; A[5] += x0.w; }
-    }
-    if (m.k_contact > 0.0f) {
-        float sd = x1.w + (m.pn_x * uh.x + m.pn_y * uh.y + m.pn_z * uh.z);
-        if (COMP) sd += m.pn_x * ul.x + m.pn_y * ul.y + m.pn_z * ul.z;
-        if (sd < 0.0f) {
-            const float ks = m.k_contact * sd;
-            r[0] -= ks * m.pn_x;
-            r[1] -= ks * m.pn_y;
-            r[2] -= ks * m.pn_z;
-            if (NEED_A) {
-                A[0] += m.k_contact * m.pn_x * m.pn_x;
-                A[1] += m.k_contact * m.pn_x * m.pn_y;
-                A[2] += m.k_contact * m.pn_x * m.pn_z;
-                A[3] += m.k_contact * m.pn_y * m.pn_y;
-                A[4] += m.k_contact * m.pn_y * m.pn_z;
-                A[5] += m.k_contact * m.pn_z * m.pn_z;
-            }
-        }
-    }
-}
-
-// hi + lo += d, keeping the pair normalised (TwoSum, then Fast2Sum).
-__device__ __forceinline__ void pair_add(float& hi, float& lo, float d) {
-    const float s = __fadd_rn(hi, d);
-    const float bp = __fadd_rn(s, -hi);
-    const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bp)), __fadd_rn(d, -bp));
-    const float t = __fadd_rn(e, lo);
-    const float h2 = __fadd_rn(s, t);
-    lo = __fadd_rn(t, -__fadd_rn(h2, -s));
-    hi = h2;
-}
-
-template <int W>
-__device__ __forceinline__ float group_sum(float v) {
-#pragma unroll
-    for (int off = W / 2; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off, W);
-    return v;
-}
-
-// One vertex per W-lane group.  UPDATE: Eq. pbgn_dx / pbgn_update in place.
-// Otherwise: write the residual of the vertex (lane 0 returns |r|^2 in rr).
+// One vertex per W-lane group, direct loads from global memory (the path
+// for small launches and for vertices with more than 256 incident tets).
+// UPDATE: Eq. pbgn_dx / pbgn_update in place.  Otherwise the residual of the
+// vertex (lane 0 returns |r|^2 in rr).
 template <int W, bool COMP, bool UPDATE>
 __device__ __forceinline__ void vertex_group(const DeviceMesh& m, State s, int v, bool active,
                                              int lane, PassParams pp, int32_t* err, double* rr,
@@ -281,15 +43,27 @@ __device__ __forceinline__ void vertex_group(const DeviceMesh& m, State s, int v
     }
     float r[3] = {0.f, 0.f, 0.f};
     float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int k = b0 + lane; k < b1; k += W) element_term<COMP, UPDATE>(m, s, k, uh, ul, r, A);
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = b0 + lane; k < b1; k += W) {
+        const float4 ra = __ldcs(m.rec_a + k);
+        const float4 rb = __ldcs(m.rec_b + k);
+        const float4 rc = __ldcs(m.rec_c + k);
+        const float2 rd = __ldcs(m.rec_d + k);
+        const int j1 = __float_as_int(ra.x), j2 = __float_as_int(ra.y), j3 = __float_as_int(ra.z);
+        const float3 d1 = el::pair_diff<COMP>(__ldg(s.hi + j1), COMP ? __ldg(s.lo + j1) : zero4, uh, ul);
+        const float3 d2 = el::pair_diff<COMP>(__ldg(s.hi + j2), COMP ? __ldg(s.lo + j2) : zero4, uh, ul);
+        const float3 d3 = el::pair_diff<COMP>(__ldg(s.hi + j3), COMP ? __ldg(s.lo + j3) : zero4, uh, ul);
+        el::element_math<UPDATE>(make_float3(rb.x, rb.y, rb.z), make_float3(rc.x, rc.y, rc.z),
+                                 make_float3(rc.w, rd.x, rd.y), ra.w, rb.w, d1, d2, d3, r, A);
+    }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) r[k] = group_sum<W>(r[k]);
+    for (int k = 0; k < 3; ++k) r[k] = el::group_sum<W>(r[k]);
     if (UPDATE) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) A[k] = group_sum<W>(A[k]);
+        for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
     }
     if (!active || lane != 0) return;
-    vertex_terms<COMP, UPDATE>(m, v, uh, ul, r, A);
+    el::vertex_terms<COMP, UPDATE>(m, __ldg(m.aux0 + v), __ldg(m.aux1 + v), uh, ul, r, A);
     if (!UPDATE) {
         *rr = (double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2];
         if (r_out) {
@@ -299,38 +73,7 @@ __device__ __forceinline__ void vertex_group(const DeviceMesh& m, State s, int v
         }
         return;
     }
-    if (pp.skip_tol > 0.0f && r[0] * r[0] + r[1] * r[1] + r[2] * r[2] <= pp.skip_tol * pp.skip_tol) return;
-    // Delta = A^{-1} r by the adjugate (A symmetric positive definite).
-    const float c00 = A[3] * A[5] - A[4] * A[4];
-    const float c01 = A[2] * A[4] - A[1] * A[5];
-    const float c02 = A[1] * A[4] - A[2] * A[3];
-    const float c11 = A[0] * A[5] - A[2] * A[2];
-    const float c12 = A[1] * A[2] - A[0] * A[4];
-    const float c22 = A[0] * A[3] - A[1] * A[1];
-    const float det = A[0] * c00 + A[1] * c01 + A[2] * c02;
-    if (!(det > 0.0f) || !isfinite(det)) {
-        atomicOr(err, kErrNonSPD);
-        return;
-    }
-    const float sc = pp.step / det;
-    const float dx = sc * (c00 * r[0] + c01 * r[1] + c02 * r[2]);
-    const float dy = sc * (c01 * r[0] + c11 * r[1] + c12 * r[2]);
-    const float dz = sc * (c02 * r[0] + c12 * r[1] + c22 * r[2]);
-    if (!(isfinite(dx) && isfinite(dy) && isfinite(dz))) {
-        atomicOr(err, kErrNonFinite);
-        return;
-    }
-    if (COMP) {
-        pair_add(uh.x, ul.x, dx);
-        pair_add(uh.y, ul.y, dy);
-        pair_add(uh.z, ul.z, dz);
-        s.lo[v] = make_float4(ul.x, ul.y, ul.z, 0.f);
-    } else {
-        uh.x += dx;
-        uh.y += dy;
-        uh.z += dz;
-    }
-    s.hi[v] = make_float4(uh.x, uh.y, uh.z, 0.f);
+    el::solve_and_write<COMP>(s, v, uh, ul, r, A, pp, err);
 }
 
 __device__ __forceinline__ const Segment* find_segment(const SegmentTable& t, int block) {
@@ -426,7 +169,7 @@ __global__ void accel_kernel(int n, State cur, State p1, State p2, float w, floa
         if (COMP) { dP += XL[k] - AL[k]; dD += AL[k] - BL[k]; }
         const float inc = w * (g * dP + dD);
         float hi = B[k], lo = BL[k];
-        if (COMP) pair_add(hi, lo, inc);
+        if (COMP) el::pair_add(hi, lo, inc);
         else hi += inc;
         o[k][0] = hi;
         o[k][1] = lo;

@@ -1,0 +1,343 @@
+// Ring-layout colour pass and residual for sm_103a.
+//
+// Layout: every free vertex of a colour owns W consecutive record slots
+// (W = 4, 8, 16 or 32: the smallest power of two holding both its incident
+// tets and its 1-ring, the distinct vertices it shares a tet with).  Slot l
+// holds one incident tet (dN/dX of the other three vertices, 2 mu V,
+// lambda V, and the three vertices' positions in the 1-ring as bytes) and the
+// id of the l-th 1-ring vertex.  A warp's work item is 32 aligned slots =
+// 32 / W vertices, one W-lane group each.
+//
+// Each warp is persistent and runs its own three-stage pipeline, with no
+// block-wide barrier anywhere:
+//   * lane 0 fetches an item's three record arrays and 1-ring ids with TMA
+//     1D bulk copies (cp.async.bulk ... mbarrier::complete_tx) two items ahead;
+//   * once they land, every lane gathers the displacement pair of its 1-ring
+//     vertex (and the item's own vertices and aux data) with cp.async one item
+//     ahead, so each neighbour is read once per vertex update, not once per
+//     incident tet;
+//   * the compute forms u_j - u_i once per 1-ring vertex, passes the three a
+//     tet needs to its lane by warp shuffles, evaluates the element term
+//     (pbng_element.cuh), sums the W lanes, and the group's first lane solves
+//     and writes the vertex (Eq. pbgn_dx, Eq. pbgn_update).
+// Everything gathered by a pass belongs to other colours or to the item's own
+// vertices, which only their own group writes.
+#include "pbng_element.cuh"
+#include "pbng_internal.h"
+
+#include <stdint.h>
+
+namespace pbng {
+namespace {
+
+using el::f3;
+using el::kFull;
+
+constexpr int kWarps = kBlock / 32;
+constexpr int kRecStages = 3;
+constexpr int kGatStages = 2;
+constexpr int kItemVerts = kRingLanes / 4;
+constexpr int kCtasPerSm = 3;
+
+struct __align__(16) RecStage {
+    float4 ra[kRingLanes];
+    float4 rb[kRingLanes];
+    float4 rc[kRingLanes];
+    int32_t id[kRingLanes];
+};
+
+struct __align__(16) GatStage {
+    float4 nh[kRingLanes];   // 1-ring displacement hi
+    float4 nl[kRingLanes];   // 1-ring displacement lo
+    float4 oh[kItemVerts];   // own vertex hi
+    float4 ol[kItemVerts];   // own vertex lo
+    float4 a0[kItemVerts];   // aux0 (f_ext, K)
+    float4 a1[kItemVerts];   // aux1 (spring target, n.X - d)
+};
+
+struct __align__(16) WarpSmem {
+    RecStage rec[kRecStages];
+    GatStage gat[kGatStages];
+    Item desc[kRecStages];
+    unsigned long long bar[kRecStages];
+};
+
+constexpr int kRecBytes = 3 * kRingLanes * 16 + kRingLanes * 4;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after about two seconds of SM clock.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > 4000000000LL) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Lane 0: request the records and 1-ring ids of item `it` into stage r.
+__device__ __forceinline__ void issue_records(const DeviceMesh& m, const Item& it, WarpSmem& S, int r) {
+    S.desc[r] = it;
+    unsigned long long* bar = S.bar + r;
+    mbar_arrive_expect_tx(bar, kRecBytes);
+    bulk_g2s(S.rec[r].ra, m.ring_ra + it.slot0, kRingLanes * 16, bar);
+    bulk_g2s(S.rec[r].rb, m.ring_rb + it.slot0, kRingLanes * 16, bar);
+    bulk_g2s(S.rec[r].rc, m.ring_rc + it.slot0, kRingLanes * 16, bar);
+    bulk_g2s(S.rec[r].id, m.ring_id + it.slot0, kRingLanes * 4, bar);
+}
+
+// All lanes: gather the 1-ring displacements and own-vertex data of the item
+// in record stage r into gather stage g.
+template <bool COMP>
+__device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& s, WarpSmem& S, int r, int g,
+                                              int lane) {
+    const Item it = S.desc[r];
+    GatStage& G = S.gat[g];
+    const int id = S.rec[r].id[lane];
+    cp_async16(G.nh + lane, s.hi + id);
+    if (COMP) cp_async16(G.nl + lane, s.lo + id);
+    if (lane < it.nv) {
+        const int v = it.v0 + lane;
+        cp_async16(G.oh + lane, s.hi + v);
+        if (COMP) cp_async16(G.ol + lane, s.lo + v);
+        cp_async16(G.a0 + lane, m.aux0 + v);
+        cp_async16(G.a1 + lane, m.aux1 + v);
+    }
+}
+
+template <int W, bool COMP, bool UPDATE>
+__device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, const WarpSmem& S, int r, int g,
+                                               int lane, PassParams pp, int32_t* err, double& rr,
+                                               double* comp_sq) {
+    const Item it = S.desc[r];
+    const RecStage& R = S.rec[r];
+    const GatStage& G = S.gat[g];
+    const int j = lane / W;
+    const bool active = j < it.nv;
+    const float3 zero3 = make_float3(0.f, 0.f, 0.f);
+    float3 uh = zero3, ul = zero3, d = zero3;
+    if (active) {
+        uh = f3(G.oh[j]);
+        if (COMP) ul = f3(G.ol[j]);
+        d = el::pair_diff<COMP>(G.nh[lane], COMP ? G.nl[lane] : make_float4(0.f, 0.f, 0.f, 0.f), uh, ul);
+    }
+    const float4 ra = R.ra[lane], rb = R.rb[lane], rc = R.rc[lane];
+    const int loc = __float_as_int(rc.w);
+    const int base = lane & ~(W - 1);
+    const int s1 = base + (loc & 255), s2 = base + ((loc >> 8) & 255), s3 = base + ((loc >> 16) & 255);
+    const float3 d1 = make_float3(__shfl_sync(kFull, d.x, s1), __shfl_sync(kFull, d.y, s1), __shfl_sync(kFull, d.z, s1));
+    const float3 d2 = make_float3(__shfl_sync(kFull, d.x, s2), __shfl_sync(kFull, d.y, s2), __shfl_sync(kFull, d.z, s2));
+    const float3 d3 = make_float3(__shfl_sync(kFull, d.x, s3), __shfl_sync(kFull, d.y, s3), __shfl_sync(kFull, d.z, s3));
+    float rv[3] = {0.f, 0.f, 0.f};
+    float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    el::element_math<UPDATE>(f3(ra), f3(rb), f3(rc), ra.w, rb.w, d1, d2, d3, rv, A);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rv[k] = el::group_sum<W>(rv[k]);
+    if (UPDATE) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
+    }
+    if (!active || (lane & (W - 1)) != 0) return;
+    el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
+    const int v = it.v0 + j;
+    if (UPDATE) {
+        el::solve_and_write<COMP>(s, v, uh, ul, rv, A, pp, err);
+    } else {
+        const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];
+        if (comp_sq) atomicAdd(comp_sq + m.comp[v], q);
+        else rr += q;
+    }
+}
+
+// The lane width is uniform over an item: dispatch once per item.
+template <bool COMP, bool UPDATE>
+__device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, const WarpSmem& S, int r, int g,
+                                             int lane, PassParams pp, int32_t* err, double& rr,
+                                             double* comp_sq) {
+    switch (S.desc[r].w) {
+        case 4: compute_item_w<4, COMP, UPDATE>(m, s, S, r, g, lane, pp, err, rr, comp_sq); break;
+        case 8: compute_item_w<8, COMP, UPDATE>(m, s, S, r, g, lane, pp, err, rr, comp_sq); break;
+        case 16: compute_item_w<16, COMP, UPDATE>(m, s, S, r, g, lane, pp, err, rr, comp_sq); break;
+        default: compute_item_w<32, COMP, UPDATE>(m, s, S, r, g, lane, pp, err, rr, comp_sq); break;
+    }
+}
+
+template <bool COMP, bool UPDATE>
+__global__ void __launch_bounds__(kBlock, kCtasPerSm)
+    ring_kernel(const DeviceMesh m, State s, const Item* __restrict__ items, int nitems, PassParams pp,
+                int32_t* err, double* partial, double* comp_sq) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem& S = reinterpret_cast<WarpSmem*>(smem)[warp];
+    const int gw = (int)blockIdx.x * kWarps + warp, nw = (int)gridDim.x * kWarps;
+    const int n = gw < nitems ? (nitems - gw + nw - 1) / nw : 0;
+    double rr = 0.0;
+    int issued = 0, waited = 0;  // items whose records were requested / awaited
+    bool ok = true;
+    Item next{};                 // lane 0: next item to request, loaded one item early
+    if (n > 0) {
+        if (lane == 0) {
+            for (int i = 0; i < kRecStages; ++i) mbar_init(S.bar + i, 1);
+            fence_mbar_init();
+            issue_records(m, items[gw], S, 0);
+            if (n > 1) issue_records(m, items[gw + nw], S, 1);
+            if (n > 2) next = items[gw + 2 * nw];
+        }
+        issued = n < 2 ? n : 2;
+        __syncwarp();
+        ok = mbar_wait(S.bar + 0, 0);
+        waited = 1;
+        if (__any_sync(kFull, !ok)) goto abort;
+        issue_gathers<COMP>(m, s, S, 0, 0, lane);
+        cp_async_commit();
+        for (int k = 0; k < n; ++k) {
+            // Record stage (k+2)%3 and gather stage (k+1)%2 were last read by
+            // item k-1, finished before the previous __syncwarp.
+            if (k + 2 < n) {
+                if (lane == 0) {
+                    fence_proxy_async();
+                    issue_records(m, next, S, (k + 2) % kRecStages);
+                    if (k + 3 < n) next = items[gw + (k + 3) * nw];
+                }
+                issued = k + 3;
+            }
+            ok = true;
+            if (k + 1 < n) {
+                ok = mbar_wait(S.bar + (k + 1) % kRecStages, ((k + 1) / kRecStages) & 1);
+                waited = k + 2;
+                if (ok) issue_gathers<COMP>(m, s, S, (k + 1) % kRecStages, (k + 1) % kGatStages, lane);
+            }
+            cp_async_commit();
+            cp_async_wait<1>();  // this lane's gathers of item k have landed
+            if (__any_sync(kFull, !ok)) goto abort;
+            __syncwarp();        // ... and the other lanes'
+            compute_item<COMP, UPDATE>(m, s, S, k % kRecStages, k % kGatStages, lane, pp, err, rr, comp_sq);
+            __syncwarp();
+        }
+    }
+    if (!UPDATE && partial) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
+        if (lane == 0) partial[gw] = rr;
+    }
+    return;
+
+abort:
+    // A record copy did not complete in time: report it, let the copies this
+    // warp started finish (bounded), then leave.
+    if (lane == 0) {
+        atomicOr(err, kErrTimeout);
+        for (int k = waited; k < issued; ++k) (void)mbar_wait(S.bar + k % kRecStages, (k / kRecStages) & 1);
+        if (!UPDATE && partial) partial[gw] = 0.0;
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+        cached[dev] = nsm;
+    }
+    return cached[dev];
+}
+
+int ring_ctas(int nitems) {
+    const int want = (nitems + kWarps - 1) / kWarps;
+    const int cap = kCtasPerSm * sm_count();
+    return want < cap ? want : cap;
+}
+
+template <bool COMP, bool UPDATE>
+cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams pp,
+                        int32_t* err, double* partial, double* comp_sq, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int bytes = kWarps * (int)sizeof(WarpSmem);
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(ring_kernel<COMP, UPDATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
+    }
+    ring_kernel<COMP, UPDATE><<<ring_ctas(nitems), kBlock, bytes, st>>>(m, s, items, nitems, pp, err, partial,
+                                                                       comp_sq);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int ring_warps(int nitems) { return nitems > 0 ? ring_ctas(nitems) * kWarps : 0; }
+
+cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
+                             bool compensated, int32_t* err, cudaStream_t st) {
+    if (compensated) return launch_impl<true, true>(m, s, items, nitems, p, err, nullptr, nullptr, st);
+    return launch_impl<false, true>(m, s, items, nitems, p, err, nullptr, nullptr, st);
+}
+
+cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
+                                 bool compensated, double* warp_partial, double* comp_sq, int32_t* err,
+                                 cudaStream_t st) {
+    const PassParams pp{1.f, 0.f};
+    double* part = comp_sq ? nullptr : warp_partial;
+    if (compensated) return launch_impl<true, false>(m, s, items, nitems, pp, err, part, comp_sq, st);
+    return launch_impl<false, false>(m, s, items, nitems, pp, err, part, comp_sq, st);
+}
+
+}  // namespace pbng
