@@ -78,6 +78,21 @@ struct pbng_mesh {
     int p1_slot = 1, p2_slot = 2;
     std::vector<double> r0;
 
+    // captured chunks of sweeps (CUDA graphs), keyed by their configuration
+    struct GraphEntry {
+        int32_t K, accel, prec, with_res, p1, prof;
+        float step, skip;
+        cudaGraphExec_t exec = nullptr;
+        int64_t nkernels = 0;
+        std::vector<cudaEvent_t> ev;   // pairs around timed launches (profiled variant)
+        std::vector<int> ev_kind;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr; // private stream the graphs are captured on
+    DevBuf d_wg;                       // float2 [kMaxChunk] per-sweep acceleration weights
+    float2* h_wg = nullptr;            // pinned staging for the weights of one call
+    size_t h_wg_cap = 0;
+
     // profiling (pbng_set_profiling): event pairs per timed launch
     bool prof = false;
     struct EvPair { cudaEvent_t a, b; int kind; };
@@ -159,6 +174,16 @@ void free_buf(DevBuf& b) {
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
+}
+
+constexpr int32_t kMaxChunk = 1024;
+
+void destroy_graphs(pbng_mesh* m) {
+    for (auto& g : m->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+    }
+    m->graphs.clear();
 }
 
 cudaError_t ensure_buf(DevBuf& b, size_t bytes) {
@@ -490,6 +515,9 @@ pbng_status build_layout(pbng_mesh* m) {
     PBNG_CUDA(m, upload(m->d_dir_lo, dlo, st));
     for (auto& sb : m->d_state)
         for (auto& b : sb) PBNG_CUDA(m, ensure_buf(b, sizeof(float4) * (size_t)nv));
+    destroy_graphs(m);
+    PBNG_CUDA(m, ring_prepare());
+    PBNG_CUDA(m, ensure_buf(m->d_wg, sizeof(float2) * kMaxChunk));
     m->ring_partials = ring_warps(m->nitems_ring);
     PBNG_CUDA(m, ensure_buf(m->d_partial, sizeof(double) * (size_t)std::max(1, m->ring_partials + m->total_partials)));
     PBNG_CUDA(m, ensure_buf(m->d_comp_sq, sizeof(double) * (size_t)m->ncomp));
@@ -540,8 +568,7 @@ pbng_status ensure_ready(pbng_mesh* m) {
 // colour its per-block partials after them; then the sum lands in *scalar.
 // With several components the sums go to comp_sq (zeroed here) instead.
 pbng_status enqueue_residual(pbng_mesh* m, State s, bool compensated, double* partial, double* comp_sq,
-                             double* scalar) {
-    cudaStream_t st = m->stream;
+                             double* scalar, cudaStream_t st) {
     const bool multi = m->ncomp > 1;
     if (multi) PBNG_CUDA(m, cudaMemsetAsync(comp_sq, 0, sizeof(double) * m->ncomp, st));
     if (m->nitems_ring > 0) {
@@ -569,7 +596,7 @@ pbng_status residual_sq(pbng_mesh* m, int slot, bool compensated, double* out) {
     const bool multi = m->ncomp > 1;
     const int pslot = prof_begin(m, kProfResidual);
     pbng_status r = enqueue_residual(m, state_of(m, slot), compensated, (double*)m->d_partial.p,
-                                     (double*)m->d_comp_sq.p, (double*)m->d_scalar.p);
+                                     (double*)m->d_comp_sq.p, (double*)m->d_scalar.p, st);
     if (r) return r;
     prof_end(m, pslot);
     PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? m->d_comp_sq.p : m->d_scalar.p,
@@ -633,45 +660,148 @@ pbng_status begin(pbng_mesh* m, const float* u_dev, const pbng_params* p, bool n
     return PBNG_OK;
 }
 
-// One PBNG iteration over all colours, then the acceleration step.
-pbng_status one_sweep(pbng_mesh* m, const pbng_params* p) {
-    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
-    PassParams pp{(float)p->step, (float)p->skip_tol};
-    State cur = state_of(m, 0);
-    for (int c = 0; c < m->ncol; ++c) {
-        if (m->tables[c].total_blocks <= 0) continue;
-        const int slot = prof_begin(m, kProfColour);
-        if (m->ring_colour[c])
-            PBNG_CUDA(m, launch_ring_pass(m->dm, cur, (const Item*)m->d_items.p + m->item_off[c],
-                                          m->item_off[c + 1] - m->item_off[c], pp, comp,
-                                          (int32_t*)m->d_err.p, m->stream));
-        else
-            PBNG_CUDA(m, launch_colour_pass(m->dm, cur, m->tables[c], pp, comp, (int32_t*)m->d_err.p, m->stream));
-        prof_end(m, slot);
-        m->kernel_launches++;
-    }
-    if (p->accel != PBNG_ACCEL_NONE) {
-        double w, g;
-        const int l = m->sweep_l;
+// (w, g) of the acceleration step after each of the next K sweeps
+// (Section "Acceleration Techniques"), advancing the host copy of the sweep
+// index and of omega_l.  Chebyshev: omega_{l+1} = 1 (l < 2), 2/(2 - rho^2)
+// (l = 2), 4/(4 - rho^2 omega_l) (l > 2), g = gamma.  SOR: (omega, 1).
+void chunk_weights(pbng_mesh* m, const pbng_params* p, int32_t K, float2* out) {
+    for (int32_t k = 0; k < K; ++k) {
+        double w = 1.0, g = 1.0;
+        const int l = m->sweep_l + k;
         if (p->accel == PBNG_ACCEL_CHEBYSHEV) {
-            // omega_{l+1} = 1 (l < 2), 2/(2 - rho^2) (l = 2), 4/(4 - rho^2 omega_l) (l > 2)
             if (l < 2) w = 1.0;
             else if (l == 2) w = 2.0 / (2.0 - p->rho * p->rho);
             else w = 4.0 / (4.0 - p->rho * p->rho * m->omega_l);
             m->omega_l = w;
             g = p->gamma;
-        } else {
+        } else if (p->accel == PBNG_ACCEL_SOR) {
             w = p->omega;
-            g = 1.0;
         }
-        const int slot = prof_begin(m, kProfAccel);
-        PBNG_CUDA(m, launch_accel(m->nfree, cur, state_of(m, m->p1_slot), state_of(m, m->p2_slot),
-                                  (float)w, (float)g, comp, m->stream));
-        prof_end(m, slot);
-        if (m->nfree > 0) m->kernel_launches++;
-        std::swap(m->p1_slot, m->p2_slot);
+        out[k] = make_float2((float)w, (float)g);
     }
-    m->sweep_l++;
+    m->sweep_l += K;
+}
+
+// Enqueues K sweeps (every colour pass, then the acceleration step with the
+// weights at d_wg[k]) and, with with_res, the FP64 residual and its copy to
+// h_pinned.  Captured into a graph, or enqueued directly on the handle's
+// stream when profiling.  p1 is the slot holding x^l at the start.
+pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_res, int p1,
+                          bool prof, int64_t* nkernels, cudaStream_t st) {
+    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const PassParams pp{(float)p->step, (float)p->skip_tol};
+    const State cur = state_of(m, 0);
+    int p2 = 3 - p1;
+    // With profiling (never inside a capture) each timed launch is bracketed
+    // by a pair of pooled events.
+    int slot = -1;
+    auto mark = [&](int kind) -> pbng_status {
+        if (!prof) return PBNG_OK;
+        if (slot < 0) slot = prof_begin(m, kind);
+        else { prof_end(m, slot); slot = -1; }
+        return PBNG_OK;
+    };
+    pbng_status r;
+    for (int32_t k = 0; k < K; ++k) {
+        for (int c = 0; c < m->ncol; ++c) {
+            if (m->tables[c].total_blocks <= 0) continue;
+            if ((r = mark(kProfColour))) return r;
+            if (m->ring_colour[c])
+                PBNG_CUDA(m, launch_ring_pass(m->dm, cur, (const Item*)m->d_items.p + m->item_off[c],
+                                              m->item_off[c + 1] - m->item_off[c], pp, comp,
+                                              (int32_t*)m->d_err.p, st));
+            else
+                PBNG_CUDA(m, launch_colour_pass(m->dm, cur, m->tables[c], pp, comp, (int32_t*)m->d_err.p, st));
+            if ((r = mark(kProfColour))) return r;
+            (*nkernels)++;
+        }
+        if (p->accel != PBNG_ACCEL_NONE && m->nfree > 0) {
+            if ((r = mark(kProfAccel))) return r;
+            PBNG_CUDA(m, launch_accel(m->nfree, cur, state_of(m, p1), state_of(m, p2),
+                                      (const float2*)m->d_wg.p + k, comp, st));
+            if ((r = mark(kProfAccel))) return r;
+            (*nkernels)++;
+            std::swap(p1, p2);
+        }
+    }
+    if (with_res) {
+        const bool multi = m->ncomp > 1;
+        if ((r = mark(kProfResidual))) return r;
+        const int64_t before = m->kernel_launches;
+        if ((r = enqueue_residual(m, cur, comp, (double*)m->d_partial.p, (double*)m->d_comp_sq.p,
+                                  (double*)m->d_scalar.p, st)))
+            return r;
+        *nkernels += m->kernel_launches - before;
+        m->kernel_launches = before;
+        if ((r = mark(kProfResidual))) return r;
+        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? m->d_comp_sq.p : m->d_scalar.p,
+                                     sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
+    }
+    return PBNG_OK;
+}
+
+// Runs K <= kMaxChunk sweeps (and the residual) as one CUDA graph launch,
+// capturing the graph the first time a configuration is seen.  host_wg
+// (pinned) must stay untouched until the stream reaches this chunk.
+pbng_status run_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_res, float2* host_wg) {
+    cudaStream_t st = m->stream;
+    chunk_weights(m, p, K, host_wg);
+    PBNG_CUDA(m, cudaMemcpyAsync(m->d_wg.p, host_wg, sizeof(float2) * K, cudaMemcpyHostToDevice, st));
+    const int32_t accel = (p->accel != PBNG_ACCEL_NONE && m->nfree > 0) ? 1 : 0;
+    if (m->prof) {
+        // per-launch timing needs plain launches (captured event records
+        // cannot be timed): the same kernels, enqueued one by one
+        int64_t nk = 0;
+        pbng_status r = enqueue_chunk(m, p, K, with_res, m->p1_slot, true, &nk, st);
+        if (r) return r;
+        m->kernel_launches += nk;
+        if (accel && (K & 1)) std::swap(m->p1_slot, m->p2_slot);
+        return PBNG_OK;
+    }
+    pbng_mesh::GraphEntry* g = nullptr;
+    for (auto& e : m->graphs)
+        if (e.K == K && e.accel == accel && e.prec == p->precision && e.with_res == (int)with_res &&
+            e.p1 == m->p1_slot && e.step == (float)p->step && e.skip == (float)p->skip_tol)
+            g = &e;
+    if (!g) {
+        pbng_mesh::GraphEntry e;
+        e.K = K;
+        e.accel = accel;
+        e.prec = p->precision;
+        e.with_res = with_res;
+        e.p1 = m->p1_slot;
+        e.prof = 0;
+        e.step = (float)p->step;
+        e.skip = (float)p->skip_tol;
+        if (!m->cap_stream) PBNG_CUDA(m, cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        PBNG_CUDA(m, cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
+        pbng_status r = enqueue_chunk(m, p, K, with_res, m->p1_slot, false, &e.nkernels, m->cap_stream);
+        const cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &graph);
+        if (r) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (ce != cudaSuccess) return cuda_fail(m, ce, "cudaStreamEndCapture");
+        const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_fail(m, ie, "cudaGraphInstantiate");
+        m->graphs.push_back(std::move(e));
+        g = &m->graphs.back();
+    }
+    PBNG_CUDA(m, cudaGraphLaunch(g->exec, st));
+    m->kernel_launches += g->nkernels;
+    if (accel && (K & 1)) std::swap(m->p1_slot, m->p2_slot);
+    return PBNG_OK;
+}
+
+pbng_status ensure_wg(pbng_mesh* m, size_t n) {
+    if (m->h_wg_cap >= n) return PBNG_OK;
+    if (m->h_wg) cudaFreeHost(m->h_wg);
+    m->h_wg = nullptr;
+    m->h_wg_cap = 0;
+    PBNG_CUDA(m, cudaMallocHost((void**)&m->h_wg, sizeof(float2) * n));
+    m->h_wg_cap = n;
     return PBNG_OK;
 }
 
@@ -833,14 +963,29 @@ pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_p
     if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
     const bool comp = p->precision == PBNG_PREC_COMPENSATED;
     if ((s = begin(m, u_dev, p, rel_residual_out != nullptr))) return s;
-    for (int32_t k = 0; k < nsweeps; ++k)
-        if ((s = one_sweep(m, p))) return s;
+    // Chunks of up to residual_every sweeps, each one graph launch; the last
+    // chunk also computes the residual when it is requested.
+    if ((s = ensure_wg(m, (size_t)std::max<int32_t>(1, nsweeps)))) return s;
+    const int32_t K = std::min<int32_t>(p->residual_every, kMaxChunk);
+    bool res_done = false;
+    for (int32_t done = 0; done < nsweeps;) {
+        const int32_t chunk = std::min<int32_t>(K, nsweeps - done);
+        const bool last = done + chunk == nsweeps;
+        const bool with_res = last && rel_residual_out != nullptr;
+        if ((s = run_chunk(m, p, chunk, with_res, m->h_wg + done))) return s;
+        res_done = res_done || with_res;
+        done += chunk;
+    }
     PBNG_CUDA(m, launch_store(m->nv, (const int32_t*)m->d_perm.p, state_of(m, 0), u_dev, m->stream));
     m->kernel_launches++;
-    if ((s = check_err(m))) return s;
+    if ((s = check_err(m))) return s;  // synchronises: h_pinned holds the residual
     if (rel_residual_out) {
         std::vector<double> sq(m->ncomp);
-        if ((s = residual_sq(m, 0, comp, sq.data()))) return s;
+        if (res_done) {
+            for (int k = 0; k < m->ncomp; ++k) sq[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
+        } else if ((s = residual_sq(m, 0, comp, sq.data()))) {
+            return s;
+        }
         for (int k = 0; k < m->ncomp; ++k)
             rel_residual_out[k] = std::sqrt(sq[k]) / (m->r0[k] > 0 ? m->r0[k] : 1.0);
     }
@@ -872,13 +1017,16 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     for (int k = 0; k < m->ncomp; ++k) sq[k] = m->r0[k] * m->r0[k];
     int cv = converged();
     if (cv == 1) result = PBNG_OK;
+    const int32_t K = std::min<int32_t>(p->residual_every, kMaxChunk);
+    if ((s = ensure_wg(m, (size_t)K))) return s;
     while (cv == 0 && done < max_sweeps) {
-        const int32_t chunk = std::min<int32_t>(p->residual_every, max_sweeps - done);
-        for (int32_t k = 0; k < chunk; ++k)
-            if ((s = one_sweep(m, p))) return s;
+        // one graph launch: the chunk's sweeps and the residual (synchronised
+        // below, so the weight staging can be reused)
+        const int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
+        if ((s = run_chunk(m, p, chunk, true, m->h_wg))) return s;
         done += chunk;
         if ((s = check_err(m))) return s;
-        if ((s = residual_sq(m, 0, comp, sq.data()))) return s;
+        for (int k = 0; k < m->ncomp; ++k) sq[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
         cv = converged();
         if (cv == 1) result = PBNG_OK;
         if (cv < 0) result = PBNG_EDIVERGED;
@@ -935,7 +1083,7 @@ pbng_status pbng_residual_noalloc(pbng_mesh* m, const float* u_dev, double* resi
                              state_of(m, 3), st));
     // per-component sums accumulate atomically and start at zero (the memset
     // in enqueue_residual); every partial is written before it is summed
-    pbng_status r = enqueue_residual(m, state_of(m, 3), true, scratch, scratch, scratch + nparts);
+    pbng_status r = enqueue_residual(m, state_of(m, 3), true, scratch, scratch, scratch + nparts, st);
     if (r) return r;
     PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? scratch : scratch + nparts,
                                  sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
@@ -1013,6 +1161,10 @@ void pbng_destroy(pbng_mesh* m) {
         cudaEventDestroy(p.b);
     }
     for (auto e : m->ev_free) cudaEventDestroy(e);
+    destroy_graphs(m);
+    if (m->cap_stream) cudaStreamDestroy(m->cap_stream);
+    if (m->h_wg) cudaFreeHost(m->h_wg);
+    free_buf(m->d_wg);
     if (m->h_pinned) cudaFreeHost(m->h_pinned);
     delete m;
 }

@@ -86,7 +86,7 @@ cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t,
                             double* block_partial, double* comp_sq, int32_t ncomp,
                             float* r_out, cudaStream_t st);
 cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStream_t st);
-cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, float w, float g,
+cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, const float2* wg,
                          bool compensated, cudaStream_t st);
 cudaError_t launch_load(int32_t nv, int32_t nfree, const float* u_user, const int32_t* perm,
                         const float4* dir_hi, const float4* dir_lo, State s, cudaStream_t st);
@@ -98,6 +98,7 @@ cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st);
 // FP64 partial per warp of the grid (ring_warps(nitems) of them) or, with
 // comp_sq, per-component sums.
 int ring_warps(int nitems);
+cudaError_t ring_prepare();  // sets kernel attributes (call outside stream capture)
 cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
                              bool compensated, int32_t* err, cudaStream_t st);
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,

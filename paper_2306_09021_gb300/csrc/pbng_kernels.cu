@@ -150,12 +150,14 @@ __global__ void reduce_kernel(const double* partial, int n, double* out) {
 // Section "Acceleration Techniques", applied after a whole sweep:
 //   x^{l+1} = w (g (x_P - x^l) + x^l - x^{l-1}) + x^{l-1}
 // (Chebyshev: w = omega_{l+1}, g = gamma; SOR as printed: w = omega, g = 1).
-// cur holds x_P on entry; p1 = x^l, p2 = x^{l-1}.  Writes x^{l+1} to cur and
+// cur holds x_P on entry; p1 = x^l, p2 = x^{l-1}; (w, g) is read from device
+// memory so a captured graph serves every sweep.  Writes x^{l+1} to cur and
 // to p2 (the caller then swaps p1 and p2).
 template <bool COMP>
-__global__ void accel_kernel(int n, State cur, State p1, State p2, float w, float g) {
+__global__ void accel_kernel(int n, State cur, State p1, State p2, const float2* __restrict__ wg) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
+    const float w = wg->x, g = wg->y;
     float4 xh = cur.hi[v], ah = p1.hi[v], bh = p2.hi[v];
     float4 xl = make_float4(0.f, 0.f, 0.f, 0.f), al = xl, bl = xl;
     if (COMP) { xl = cur.lo[v]; al = p1.lo[v]; bl = p2.lo[v]; }
@@ -246,11 +248,11 @@ cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, float w, float g,
+cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, const float2* wg,
                          bool compensated, cudaStream_t st) {
     if (nfree <= 0) return cudaSuccess;
-    if (compensated) accel_kernel<true><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, w, g);
-    else accel_kernel<false><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, w, g);
+    if (compensated) accel_kernel<true><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, wg);
+    else accel_kernel<false><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, wg);
     return cudaGetLastError();
 }
 

@@ -306,16 +306,7 @@ template <bool COMP, bool UPDATE>
 cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams pp,
                         int32_t* err, double* partial, double* comp_sq, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    const int bytes = kWarps * (int)sizeof(WarpSmem);
-    static bool attr_set[64] = {false};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(ring_kernel<COMP, UPDATE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e != cudaSuccess) return e;
-        attr_set[dev] = true;
-    }
+    const int bytes = kWarps * (int)sizeof(WarpSmem);  // attribute set by ring_prepare()
     ring_kernel<COMP, UPDATE><<<ring_ctas(nitems), kBlock, bytes, st>>>(m, s, items, nitems, pp, err, partial,
                                                                        comp_sq);
     return cudaGetLastError();
@@ -324,6 +315,15 @@ cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nit
 }  // namespace
 
 int ring_warps(int nitems) { return nitems > 0 ? ring_ctas(nitems) * kWarps : 0; }
+
+cudaError_t ring_prepare() {
+    const int bytes = kWarps * (int)sizeof(WarpSmem);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(ring_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ring_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    if ((e = cudaFuncSetAttribute(ring_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
+    return cudaFuncSetAttribute(ring_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
                              bool compensated, int32_t* err, cudaStream_t st) {
