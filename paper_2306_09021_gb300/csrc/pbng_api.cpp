@@ -65,6 +65,8 @@ struct pbng_mesh {
     // device buffers
     DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
     DevBuf d_ring_ra, d_ring_rb, d_ring_rc, d_ring_id, d_items;
+    DevBuf d_active;                   // int32 [ncomp] component flags (1 = active)
+    int32_t* h_active = nullptr;       // pinned host copy
     DevBuf d_dir_hi, d_dir_lo;
     DevBuf d_state[4][2];           // cur, p1, p2, tmp; hi/lo
     DevBuf d_partial, d_comp_sq, d_scalar, d_err;
@@ -307,9 +309,14 @@ pbng_status build_layout(pbng_mesh* m) {
     order.reserve(nv);
     for (int32_t i = 0; i < nv; ++i)
         if (!m->is_dir[i]) order.push_back(i);
+    // inside a colour and lane width, group the vertices of each component so
+    // that most ring items hold a single component (and can be skipped whole
+    // once that component has converged)
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         if (m->colour[a] != m->colour[b]) return m->colour[a] < m->colour[b];
-        return lanes(a) > lanes(b);
+        if (lanes(a) != lanes(b)) return lanes(a) > lanes(b);
+        if (m->ncomp > 1 && m->comp_of[a] != m->comp_of[b]) return m->comp_of[a] < m->comp_of[b];
+        return false;
     });
     m->nfree = (int32_t)order.size();
     for (int32_t i = 0; i < nv; ++i)
@@ -459,6 +466,9 @@ pbng_status build_layout(pbng_mesh* m) {
                     it.nv = std::min<int32_t>(per_item, sg.v_end - vv);
                     it.w = W;
                     it.slot0 = slot_base + (vv - sg.v_begin) * W;
+                    it.comp = m->ncomp > 1 ? m->comp_of[order[vv]] : 0;
+                    for (int32_t q = 1; q < it.nv; ++q)
+                        if (m->ncomp > 1 && m->comp_of[order[vv + q]] != it.comp) it.comp = -1;
                     m->items.push_back(it);
                 }
             }
@@ -521,6 +531,11 @@ pbng_status build_layout(pbng_mesh* m) {
     m->ring_partials = ring_warps(m->nitems_ring);
     PBNG_CUDA(m, ensure_buf(m->d_partial, sizeof(double) * (size_t)std::max(1, m->ring_partials + m->total_partials)));
     PBNG_CUDA(m, ensure_buf(m->d_comp_sq, sizeof(double) * (size_t)m->ncomp));
+    PBNG_CUDA(m, ensure_buf(m->d_active, sizeof(int32_t) * (size_t)m->ncomp));
+    for (int32_t k = 0; k < m->ncomp; ++k) m->h_active[k] = 1;
+    PBNG_CUDA(m, cudaMemcpyAsync(m->d_active.p, m->h_active, sizeof(int32_t) * m->ncomp,
+                                 cudaMemcpyHostToDevice, st));
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
     PBNG_CUDA(m, ensure_buf(m->d_scalar, sizeof(double) * 4));
     PBNG_CUDA(m, ensure_buf(m->d_err, sizeof(int32_t)));
     PBNG_CUDA(m, cudaMemsetAsync(m->d_err.p, 0, sizeof(int32_t), st));
@@ -536,6 +551,7 @@ pbng_status build_layout(pbng_mesh* m) {
     d.aux0 = (const float4*)m->d_aux0.p;
     d.aux1 = (const float4*)m->d_aux1.p;
     d.comp = m->ncomp > 1 ? (const int32_t*)m->d_comp.p : nullptr;
+    d.comp_active = m->ncomp > 1 ? (const int32_t*)m->d_active.p : nullptr;
     d.ring_ra = (const float4*)m->d_ring_ra.p;
     d.ring_rb = (const float4*)m->d_ring_rb.p;
     d.ring_rc = (const float4*)m->d_ring_rc.p;
@@ -718,7 +734,7 @@ pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool wi
         if (p->accel != PBNG_ACCEL_NONE && m->nfree > 0) {
             if ((r = mark(kProfAccel))) return r;
             PBNG_CUDA(m, launch_accel(m->nfree, cur, state_of(m, p1), state_of(m, p2),
-                                      (const float2*)m->d_wg.p + k, comp, st));
+                                      (const float2*)m->d_wg.p + k, m->dm.comp, m->dm.comp_active, comp, st));
             if ((r = mark(kProfAccel))) return r;
             (*nkernels)++;
             std::swap(p1, p2);
@@ -884,7 +900,9 @@ pbng_status pbng_create_mesh(const double* rest_xyz, int32_t nv, const int32_t* 
         m->spr_K.assign(nv, 0.0);
         m->spr_KT.assign(3 * (size_t)nv, 0.0);
         m->fext.assign(3 * (size_t)nv, 0.0);
-        if (cudaMallocHost((void**)&m->h_pinned, sizeof(double) * (m->ncomp + 2)) != cudaSuccess) {
+        if (cudaMallocHost((void**)&m->h_pinned, sizeof(double) * (m->ncomp + 2)) != cudaSuccess ||
+            cudaMallocHost((void**)&m->h_active, sizeof(int32_t) * m->ncomp) != cudaSuccess) {
+            if (m->h_pinned) cudaFreeHost(m->h_pinned);
             delete m;
             return PBNG_ECUDA;
         }
@@ -1005,12 +1023,25 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     std::vector<double> sq(m->ncomp), rel(m->ncomp, 0.0);
     int32_t done = 0;
     pbng_status result = PBNG_ENOTCONVERGED;
+    // With several components each one stops (is frozen: neither updated,
+    // accelerated nor re-evaluated) at the first check that finds it below
+    // rel_tol, exactly as if it were solved on its own.
+    const bool freeze = m->ncomp > 1;
+    std::vector<uint8_t> frozen(m->ncomp, 0);
+    bool changed = false;
     auto converged = [&]() {
         bool all = true;
+        changed = false;
         for (int k = 0; k < m->ncomp; ++k) {
+            if (frozen[k]) continue;
             rel[k] = std::sqrt(sq[k]) / (m->r0[k] > 0 ? m->r0[k] : 1.0);
             if (!std::isfinite(rel[k]) || rel[k] > 1e3) return -1;
             if (rel[k] > rel_tol) all = false;
+            else if (freeze) {
+                frozen[k] = 1;
+                m->h_active[k] = 0;
+                changed = true;
+            }
         }
         return all ? 1 : 0;
     };
@@ -1028,11 +1059,20 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
         if ((s = check_err(m))) return s;
         for (int k = 0; k < m->ncomp; ++k) sq[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
         cv = converged();
+        if (changed && cv == 0)  // ordered before the next chunk; h_active is not touched until the next sync
+            PBNG_CUDA(m, cudaMemcpyAsync(m->d_active.p, m->h_active, sizeof(int32_t) * m->ncomp,
+                                         cudaMemcpyHostToDevice, m->stream));
         if (cv == 1) result = PBNG_OK;
         if (cv < 0) result = PBNG_EDIVERGED;
     }
     PBNG_CUDA(m, launch_store(m->nv, (const int32_t*)m->d_perm.p, state_of(m, 0), u_dev, m->stream));
     m->kernel_launches++;
+    if (freeze) {  // leave every component active for later calls
+        PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
+        for (int32_t k = 0; k < m->ncomp; ++k) m->h_active[k] = 1;
+        PBNG_CUDA(m, cudaMemcpyAsync(m->d_active.p, m->h_active, sizeof(int32_t) * m->ncomp,
+                                     cudaMemcpyHostToDevice, m->stream));
+    }
     PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
     if (sweeps_out) *sweeps_out = done;
     if (rel_residual_out)
@@ -1166,6 +1206,8 @@ void pbng_destroy(pbng_mesh* m) {
     if (m->h_wg) cudaFreeHost(m->h_wg);
     free_buf(m->d_wg);
     if (m->h_pinned) cudaFreeHost(m->h_pinned);
+    if (m->h_active) cudaFreeHost(m->h_active);
+    free_buf(m->d_active);
     delete m;
 }
 

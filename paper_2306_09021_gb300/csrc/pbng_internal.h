@@ -40,6 +40,7 @@ struct DeviceMesh {
     const float4* aux0;      // [nfree] f_ext (xyz), total spring stiffness K
     const float4* aux1;      // [nfree] spring target displacement (xyz), n.X - d
     const int32_t* comp;     // [nfree] component id, or nullptr for one component
+    const int32_t* comp_active;  // [ncomp] 0 = frozen (converged), or nullptr
     // Ring layout (colours whose vertices all fit 32 lanes): one 32-slot
     // item per warp; vertex v of a lane-width-W run owns W consecutive slots.
     const float4* ring_ra;   // [nslots] g_j1 (xyz), a = 2 mu V
@@ -76,6 +77,9 @@ struct Item {
     int32_t nv;
     int32_t w;
     int32_t slot0;
+    int32_t comp;  // component of every vertex of the item, or -1 when mixed
+    int32_t skip;  // set on the device copy: the item's component is frozen
+    int32_t pad[2];
 };
 constexpr int kRingLanes = 32;
 
@@ -87,7 +91,7 @@ cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t,
                             float* r_out, cudaStream_t st);
 cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStream_t st);
 cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, const float2* wg,
-                         bool compensated, cudaStream_t st);
+                         const int32_t* comp, const int32_t* comp_active, bool compensated, cudaStream_t st);
 cudaError_t launch_load(int32_t nv, int32_t nfree, const float* u_user, const int32_t* perm,
                         const float4* dir_hi, const float4* dir_lo, State s, cudaStream_t st);
 cudaError_t launch_store(int32_t nv, const int32_t* perm, State s, float* u_user, cudaStream_t st);

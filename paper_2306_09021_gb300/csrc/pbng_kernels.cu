@@ -73,6 +73,7 @@ __device__ __forceinline__ void vertex_group(const DeviceMesh& m, State s, int v
         }
         return;
     }
+    if (m.comp_active && !m.comp_active[m.comp[v]]) return;  // frozen (converged) component
     el::solve_and_write<COMP>(s, v, uh, ul, r, A, pp, err);
 }
 
@@ -154,9 +155,11 @@ __global__ void reduce_kernel(const double* partial, int n, double* out) {
 // memory so a captured graph serves every sweep.  Writes x^{l+1} to cur and
 // to p2 (the caller then swaps p1 and p2).
 template <bool COMP>
-__global__ void accel_kernel(int n, State cur, State p1, State p2, const float2* __restrict__ wg) {
+__global__ void accel_kernel(int n, State cur, State p1, State p2, const float2* __restrict__ wg,
+                             const int32_t* __restrict__ comp, const int32_t* __restrict__ active) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
+    if (active && !active[comp[v]]) return;  // frozen (converged) component
     const float w = wg->x, g = wg->y;
     float4 xh = cur.hi[v], ah = p1.hi[v], bh = p2.hi[v];
     float4 xl = make_float4(0.f, 0.f, 0.f, 0.f), al = xl, bl = xl;
@@ -249,10 +252,12 @@ cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStr
 }
 
 cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, const float2* wg,
-                         bool compensated, cudaStream_t st) {
+                         const int32_t* comp, const int32_t* comp_active, bool compensated, cudaStream_t st) {
     if (nfree <= 0) return cudaSuccess;
-    if (compensated) accel_kernel<true><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, wg);
-    else accel_kernel<false><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, wg);
+    if (compensated)
+        accel_kernel<true><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, wg, comp, comp_active);
+    else
+        accel_kernel<false><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, wg, comp, comp_active);
     return cudaGetLastError();
 }
 

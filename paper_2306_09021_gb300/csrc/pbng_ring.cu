@@ -125,10 +125,16 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Lane 0: request the records and 1-ring ids of item `it` into stage r.
-__device__ __forceinline__ void issue_records(const DeviceMesh& m, const Item& it, WarpSmem& S, int r) {
+// Lane 0: request the records and 1-ring ids of item `it` into stage r.  An
+// item whose whole component is frozen is marked skipped and fetches nothing.
+__device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, WarpSmem& S, int r) {
+    it.skip = (it.comp >= 0 && m.comp_active && !m.comp_active[it.comp]) ? 1 : 0;
     S.desc[r] = it;
     unsigned long long* bar = S.bar + r;
+    if (it.skip) {
+        mbar_arrive_expect_tx(bar, 0);
+        return;
+    }
     mbar_arrive_expect_tx(bar, kRecBytes);
     bulk_g2s(S.rec[r].ra, m.ring_ra + it.slot0, kRingLanes * 16, bar);
     bulk_g2s(S.rec[r].rb, m.ring_rb + it.slot0, kRingLanes * 16, bar);
@@ -142,6 +148,7 @@ template <bool COMP>
 __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& s, WarpSmem& S, int r, int g,
                                               int lane) {
     const Item it = S.desc[r];
+    if (it.skip) return;
     GatStage& G = S.gat[g];
     const int id = S.rec[r].id[lane];
     cp_async16(G.nh + lane, s.hi + id);
@@ -160,6 +167,7 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, con
                                                int lane, PassParams pp, int32_t* err, double& rr,
                                                double* comp_sq) {
     const Item it = S.desc[r];
+    if (it.skip) return;  // uniform over the warp
     const RecStage& R = S.rec[r];
     const GatStage& G = S.gat[g];
     const int j = lane / W;
@@ -191,6 +199,7 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, con
     el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
     const int v = it.v0 + j;
     if (UPDATE) {
+        if (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) return;  // frozen vertex of a mixed item
         el::solve_and_write<COMP>(s, v, uh, ul, rv, A, pp, err);
     } else {
         const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];

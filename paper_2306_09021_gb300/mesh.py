@@ -71,8 +71,8 @@ class Mesh:
         self.dirichlet = np.zeros(0, np.int32)
 
     @classmethod
-    def from_problem(cls, p, stream=None):
-        m = cls(p.X, p.tets, p.young, p.poisson, stream=stream)
+    def from_problem(cls, p, stream=None, mesh_id=None):
+        m = cls(p.X, p.tets, p.young, p.poisson, mesh_id=mesh_id, stream=stream)
         m.set_constraints(p.dirichlet, p.x0[p.dirichlet], p.spr_idx, p.spr_target, p.spr_k,
                           p.plane, p.k_contact, p.body_accel, p.density)
         return m

@@ -1,0 +1,67 @@
+"""Batched solves: many independent meshes of uneven size in one handle
+(one launch per colour across all of them), each stopping at its own
+tolerance.  Each mesh's result must equal solving it on its own."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_09021_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def test_batched_solve_equals_separate_solves():
+    from paper_2306_09021_gb300 import Mesh, default_params
+    probs = W.batched_blocks(count=5, side_lo=3, side_hi=7, seed=11)
+    batch, mid, offs = W.concat_problems(probs)
+    params = default_params(accel="chebyshev", residual_every=10)
+    m = Mesh.from_problem(batch, mesh_id=mid)
+    assert m.ncomp == len(probs)
+    u = torch.tensor(batch.x0 - batch.X, dtype=torch.float32, device="cuda")
+    st, sweeps, rel = m.solve(u, 1e-5, 20000, params)
+    assert st == 0 and np.all(rel <= 1e-5)
+    ub = u.cpu().double().numpy()
+    for k, p in enumerate(probs):
+        ms = Mesh.from_problem(p)
+        us = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+        st1, sw1, rel1 = ms.solve(us, 1e-5, 20000, params)
+        assert st1 == 0
+        part = ub[offs[k]:offs[k + 1]]
+        ref = us.cpu().double().numpy()
+        scale = np.abs(ref).max()
+        assert np.abs(part - ref).max() <= 1e-6 * scale, k
+        assert rel[k] == pytest.approx(rel1[0], rel=1e-6)
+
+
+def test_batched_colouring_is_per_mesh():
+    from paper_2306_09021_gb300 import Mesh
+    probs = W.batched_blocks(count=4, side_lo=3, side_hi=6, seed=3)
+    batch, mid, offs = W.concat_problems(probs)
+    col, n = Mesh.from_problem(batch, mesh_id=mid).colouring()
+    for k, p in enumerate(probs):
+        ck, _ = Mesh.from_problem(p).colouring()
+        assert np.array_equal(col[offs[k]:offs[k + 1]], ck)
+
+
+def test_batched_sweep_residuals_per_mesh(oracle_mod):
+    from paper_2306_09021_gb300 import Mesh, default_params
+    probs = W.batched_blocks(count=3, side_lo=3, side_hi=5, seed=5)
+    batch, mid, offs = W.concat_problems(probs)
+    m = Mesh.from_problem(batch, mesh_id=mid)
+    u = torch.tensor(batch.x0 - batch.X, dtype=torch.float32, device="cuda")
+    m.sweep(u, 15, default_params(accel="sor", omega=1.5))
+    r = m.residual(u)
+    x = u.cpu().double().numpy() + batch.X
+    for k, p in enumerate(probs):
+        om = oracle_mod.OracleMesh.from_problem(p)
+        assert r[k] == pytest.approx(om.residual(x[offs[k]:offs[k + 1]]), rel=1e-5)

@@ -17,6 +17,7 @@ from .problems import (
     batched_blocks,
     adjoint_block,
     adjoint_load_cases,
+    concat_problems,
 )
 
 __all__ = [
@@ -32,4 +33,5 @@ __all__ = [
     "batched_blocks",
     "adjoint_block",
     "adjoint_load_cases",
+    "concat_problems",
 ]

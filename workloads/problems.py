@@ -197,3 +197,33 @@ def adjoint_load_cases(p: Problem, count: int = 32, seed: int = 777,
         sz = np.sqrt(max(0.0, 1.0 - cz * cz))
         accs.append(g * np.array([sz * np.cos(phi), sz * np.sin(phi), cz]))
     return np.stack(xds), np.stack(accs)
+
+
+def concat_problems(problems: List[Problem], spacing: float = 0.0):
+    """One batch of independent meshes: vertex, tet and constraint arrays
+    concatenated with offsets, plus the component id of every vertex.
+    Returns (Problem, mesh_id, vertex_offsets).  Body forces must agree."""
+    offs = np.cumsum([0] + [p.nv for p in problems])
+    shift = lambda k: np.array([spacing * k, 0.0, 0.0])
+    X = np.vstack([p.X + shift(k) for k, p in enumerate(problems)])
+    x0 = np.vstack([p.x0 + shift(k) for k, p in enumerate(problems)])
+    tets = np.vstack([p.tets + offs[k] for k, p in enumerate(problems)]).astype(np.int32)
+    dirichlet = np.concatenate([p.dirichlet + offs[k] for k, p in enumerate(problems)]).astype(np.int32)
+    spr_idx = np.concatenate([p.spr_idx + offs[k] for k, p in enumerate(problems)]).astype(np.int32)
+    spr_target = np.vstack([p.spr_target + shift(k) for k, p in enumerate(problems)])
+    accels = {None if p.body_accel is None else tuple(p.body_accel) for p in problems}
+    if len(accels) != 1:
+        raise ValueError("problems of one batch must share the body acceleration")
+    acc = problems[0].body_accel
+    dens = None if acc is None else np.concatenate([p.density for p in problems])
+    mesh_id = np.concatenate([np.full(p.nv, k, np.int32) for k, p in enumerate(problems)])
+    batch = Problem(
+        name=f"batch_of_{len(problems)}", X=X, tets=tets,
+        young=np.concatenate([p.young for p in problems]),
+        poisson=np.concatenate([p.poisson for p in problems]),
+        dirichlet=dirichlet, x0=x0, body_accel=acc, density=dens,
+        spr_idx=spr_idx, spr_target=spr_target,
+        spr_k=np.concatenate([p.spr_k for p in problems]),
+        meta=dict(count=len(problems), offsets=offs),
+    )
+    return batch, mesh_id, offs
