@@ -72,10 +72,12 @@ typedef struct {
                                float32 pair (hi + lo), neighbour differences and
                                updates are formed in that pair; all element
                                arithmetic stays float32.                          */
-    int32_t kernel_path;    /* 0: pipelined kernels (TMA-staged records, cp.async
-                               gathers) wherever every vertex of a colour has at
-                               most 256 incident tets, else direct loads;
-                               1: direct-load kernels everywhere.                 */
+    int32_t kernel_path;    /* 0: 1-ring layout kernels (TMA-staged records,
+                               cp.async 1-ring gathers) for every colour whose
+                               vertices have at most 32 incident tets and 32
+                               1-ring vertices, CSR direct loads for the others;
+                               1: CSR direct-load kernels everywhere.  Changing it
+                               rebuilds the layout.                               */
     int32_t reserved[3];
 } pbng_params;
 
@@ -115,6 +117,18 @@ pbng_status pbng_set_constraints(pbng_mesh* m, const int32_t* dir_idx, const dou
                                  double k_contact, const double* body_accel,
                                  const double* density);
 
+/* Per-component body acceleration (for batches whose meshes carry different
+ * loads): accel host double [ncomp][3], density host double [ne] or NULL
+ * (= 1).  Replaces the body force of pbng_set_constraints; f^ext_i =
+ * sum_e rho_e a_c V_e / 4 with c the component of tet e (Section
+ * "Discretization").  Call after pbng_set_constraints. */
+pbng_status pbng_set_body_accel(pbng_mesh* m, const double* accel, const double* density);
+
+/* Replaces the per-tet material (host double [ne] each; Eq. lame for mu and
+ * lambda).  The layout is rebuilt on the next call that needs it, and the
+ * iterate history is dropped. */
+pbng_status pbng_set_material(pbng_mesh* m, const double* young, const double* poisson);
+
 /* Greedy node colouring of Section "Coloring and Parallelism": free vertices
  * in ascending id take the least colour not used by any vertex sharing a tet.
  * colour_out: host int32 [nv], -1 for clamped vertices.  ncolours: host. */
@@ -137,6 +151,32 @@ pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_p
  * or growing (> 1e3 r_0) residual. */
 pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps,
                        const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out);
+
+/* Equilibrium adjoint (sensitivities of a loss L(u) of the equilibrium with
+ * respect to per-tet log E and the clamped positions).  The paper states the
+ * forward problem (Eq. fem_qs / Eq. fem_d) and the true nodal Hessian
+ * (Eq. hess); the adjoint follows from differentiating fem_qs: with
+ * H = -d(f + f^ext)/dx over free vertices at the equilibrium u_eq,
+ *   H lambda = dL/du (free vertices),
+ *   dL/dlog E_e = -sum_{i in e, free} lambda_i . V_e P(F_e) g_i,
+ *   dL/dx_D = dL/du_D - H_DF lambda.
+ * lambda is found with the same colour-by-colour block Gauss-Seidel as the
+ * forward sweep (true Hessian applied matrix-free, 3x3 diagonal blocks
+ * solved exactly), with p->accel acceleration, until
+ * |dL/du - H lambda| <= rel_tol |dL/du| or max_sweeps.
+ *   u_eq_dev      device float [nv][3]  equilibrium displacement (input)
+ *   dLdu_dev      device float [nv][3]  dL/du (caller order; clamped rows are dL/dx_D)
+ *   dL_dlogE_dev  device float [ne]     output, caller tet order
+ *   dL_dxD_dev    device float [nd][3]  output, in the dir_idx order of
+ *                                       pbng_set_constraints (may be NULL)
+ * Requires every colour in the ring layout (vertices with at most 32
+ * incident tets and 1-ring vertices) and kernel_path 0.  H must be positive
+ * definite (a stable equilibrium); otherwise the iteration diverges
+ * (PBNG_EDIVERGED) or a diagonal block is singular (PBNG_EDEGENERATE).
+ * sweeps_out and rel_residual_out (host, may be NULL).  Synchronises. */
+pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_dev, float* dL_dlogE_dev,
+                         float* dL_dxD_dev, double rel_tol, int32_t max_sweeps, const pbng_params* p,
+                         int32_t* sweeps_out, double* rel_residual_out);
 
 /* FP64 2-norm of (f + f^ext) over free vertices at u_dev (Section "PBNG vs.
  * PBD and Limited Newton": the 2-norm of the Newton residual), per component

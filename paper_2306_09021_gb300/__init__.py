@@ -7,5 +7,7 @@ only marshals arguments to it.
 
 from ._lib import ACCEL, PRECISION, PbngError, PbngParams, load
 from .mesh import Mesh, default_params
+from .autograd import EquilibriumModel
 
-__all__ = ["ACCEL", "PRECISION", "PbngError", "PbngParams", "load", "Mesh", "default_params"]
+__all__ = ["ACCEL", "PRECISION", "PbngError", "PbngParams", "load", "Mesh", "default_params",
+           "EquilibriumModel"]

@@ -74,7 +74,10 @@ SIGNATURES = {
     "pbng_default_params": (None, [ctypes.POINTER(PbngParams)]),
     "pbng_create_mesh": (_I32, [_PD, _I32, _PI, _I32, _PD, _PD, _PI, _P, ctypes.POINTER(_P)]),
     "pbng_set_constraints": (_I32, [_P, _PI, _PD, _I32, _PI, _PD, _PD, _I32, _PD, _D, _PD, _PD]),
+    "pbng_set_material": (_I32, [_P, _PD, _PD]),
+    "pbng_set_body_accel": (_I32, [_P, _PD, _PD]),
     "pbng_get_colouring": (_I32, [_P, _PI, _PI]),
+    "pbng_adjoint": (_I32, [_P, _P, _P, _P, _P, _D, _I32, ctypes.POINTER(PbngParams), _PI, _PD]),
     "pbng_sweep": (_I32, [_P, _P, _I32, ctypes.POINTER(PbngParams), _PD]),
     "pbng_solve": (_I32, [_P, _P, _D, _I32, ctypes.POINTER(PbngParams), _PI, _PD]),
     "pbng_residual": (_I32, [_P, _P, _PD]),

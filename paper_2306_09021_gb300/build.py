@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpbng.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["pbng_kernels.cu", "pbng_ring.cu", "pbng_api.cpp"]
+SOURCES = ["pbng_kernels.cu", "pbng_ring.cu", "pbng_adjoint.cu", "pbng_api.cpp"]
 
 
 def _nvcc():

@@ -1,0 +1,392 @@
+// Equilibrium adjoint for sm_103a: H lambda = dL/du by coloured block
+// Gauss-Seidel with the true Hessian applied matrix-free, then the
+// parameter and boundary sensitivities (see pbng_adjoint in include/pbng.h).
+//
+// The true energy-density Hessian of the corotated model (Eq. cor, the
+// tensor of Eq. hess) acting on a direction dF is
+//   dP = 2 mu (dF - dR) + lambda (C : dF) C + lambda (J - 1) dC,
+// with C = cof F, dC its (bilinear) variation, and dR = R [w]x where
+// (tr S I - S) w = axial(R^T dF - dF^T R), S = R^T F (differentiating
+// F = R S with S symmetric).  For vertex i, (H lambda)_i = sum_e V_e dP(dF_e) g_i
+// with dF_e = sum_j lambda_j g_j^T, plus the weak terms.
+//
+// Vertex kernels use the ring layout of pbng_ring.cu (one warp per 32-slot
+// item, W lanes per vertex, 1-ring values exchanged by shuffles) with direct
+// loads; the gradient kernel runs one thread per tetrahedron.
+#include "pbng_element.cuh"
+#include "pbng_internal.h"
+
+namespace pbng {
+namespace {
+
+using el::f3;
+using el::kFull;
+
+struct ElemState {
+    float H[9];    // F - I
+    float C[9];    // cof F
+    float Jm1;     // det F - 1
+    float RmI[9];  // R - I
+};
+
+// F, its cofactor, J - 1 and the rotation, all from the displacement
+// differences dk = u_jk - u_i and the gradients of the other three vertices.
+__device__ __forceinline__ void elem_state(float3 d1, float3 d2, float3 d3, float3 g1, float3 g2, float3 g3,
+                                           ElemState& E) {
+    const float a1[3] = {d1.x, d1.y, d1.z}, a2[3] = {d2.x, d2.y, d2.z}, a3[3] = {d3.x, d3.y, d3.z};
+    const float b1[3] = {g1.x, g1.y, g1.z}, b2[3] = {g2.x, g2.y, g2.z}, b3[3] = {g3.x, g3.y, g3.z};
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) E.H[3 * p + q] = a1[p] * b1[q] + a2[p] * b2[q] + a3[p] * b3[q];
+    const float* H = E.H;
+    const float F0 = 1.0f + H[0], F4 = 1.0f + H[4], F8 = 1.0f + H[8];
+    const float F1 = H[1], F2 = H[2], F3 = H[3], F5 = H[5], F6 = H[6], F7 = H[7];
+    E.C[0] = F4 * F8 - F5 * F7;
+    E.C[1] = F5 * F6 - F3 * F8;
+    E.C[2] = F3 * F7 - F4 * F6;
+    E.C[3] = F7 * F2 - F8 * F1;
+    E.C[4] = F8 * F0 - F6 * F2;
+    E.C[5] = F6 * F1 - F7 * F0;
+    E.C[6] = F1 * F5 - F2 * F4;
+    E.C[7] = F2 * F3 - F0 * F5;
+    E.C[8] = F0 * F4 - F1 * F3;
+    E.Jm1 = (H[0] + H[4] + H[8]) +
+            (H[0] * H[4] - H[1] * H[3] + H[0] * H[8] - H[2] * H[6] + H[4] * H[8] - H[5] * H[7]) +
+            el::det3(H[0], H[1], H[2], H[3], H[4], H[5], H[6], H[7], H[8]);
+    const float Fm[9] = {F0, F1, F2, F3, F4, F5, F6, F7, F8};
+    float n2 = 0.f, c2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        n2 += Fm[k] * Fm[k];
+        c2 += E.C[k] * E.C[k];
+    }
+    el::rotation_minus_identity(H, n2, c2, 1.0f + E.Jm1, E.RmI);
+}
+
+// out = V dP(dF) (row-major 3x3), a = 2 mu V, b = lambda V.
+__device__ __forceinline__ void hess_action(const ElemState& E, float a, float b, const float* dF, float* out) {
+    float R[9], F[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float id = (k % 4 == 0) ? 1.0f : 0.0f;
+        R[k] = E.RmI[k] + id;
+        F[k] = E.H[k] + id;
+    }
+    float S[9], X[9];  // S = R^T F, X = R^T dF
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            S[3 * i + j] = R[i] * F[j] + R[3 + i] * F[3 + j] + R[6 + i] * F[6 + j];
+            X[3 * i + j] = R[i] * dF[j] + R[3 + i] * dF[3 + j] + R[6 + i] * dF[6 + j];
+        }
+    const float r0 = X[7] - X[5], r1 = X[2] - X[6], r2 = X[3] - X[1];
+    const float tr = S[0] + S[4] + S[8];
+    const float m00 = tr - S[0], m11 = tr - S[4], m22 = tr - S[8];
+    const float m01 = -0.5f * (S[1] + S[3]), m02 = -0.5f * (S[2] + S[6]), m12 = -0.5f * (S[5] + S[7]);
+    const float c00 = m11 * m22 - m12 * m12, c01 = m02 * m12 - m01 * m22, c02 = m01 * m12 - m02 * m11;
+    const float c11 = m00 * m22 - m02 * m02, c12 = m01 * m02 - m00 * m12, c22 = m00 * m11 - m01 * m01;
+    const float det = m00 * c00 + m01 * c01 + m02 * c02;
+    float w0 = 0.f, w1 = 0.f, w2 = 0.f;
+    if (fabsf(det) > 1e-30f) {
+        const float inv = 1.0f / det;
+        w0 = inv * (c00 * r0 + c01 * r1 + c02 * r2);
+        w1 = inv * (c01 * r0 + c11 * r1 + c12 * r2);
+        w2 = inv * (c02 * r0 + c12 * r1 + c22 * r2);
+    }
+    // dR = R [w]x
+    float dR[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float ri0 = R[3 * i], ri1 = R[3 * i + 1], ri2 = R[3 * i + 2];
+        dR[3 * i] = ri1 * w2 - ri2 * w1;
+        dR[3 * i + 1] = ri2 * w0 - ri0 * w2;
+        dR[3 * i + 2] = ri0 * w1 - ri1 * w0;
+    }
+    // dC: row i of C is (row i+1) x (row i+2) of F
+    float dC[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int p = 3 * ((i + 1) % 3), q = 3 * ((i + 2) % 3);
+        dC[3 * i] = (dF[p + 1] * F[q + 2] - dF[p + 2] * F[q + 1]) + (F[p + 1] * dF[q + 2] - F[p + 2] * dF[q + 1]);
+        dC[3 * i + 1] = (dF[p + 2] * F[q] - dF[p] * F[q + 2]) + (F[p + 2] * dF[q] - F[p] * dF[q + 2]);
+        dC[3 * i + 2] = (dF[p] * F[q + 1] - dF[p + 1] * F[q]) + (F[p] * dF[q + 1] - F[p + 1] * dF[q]);
+    }
+    float CdF = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) CdF += E.C[k] * dF[k];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) out[k] = a * (dF[k] - dR[k]) + b * (CdF * E.C[k] + E.Jm1 * dC[k]);
+}
+
+__device__ __forceinline__ float3 mat_g(const float* M, float3 g) {
+    return make_float3(M[0] * g.x + M[1] * g.y + M[2] * g.z, M[3] * g.x + M[4] * g.y + M[5] * g.z,
+                       M[6] * g.x + M[7] * g.y + M[8] * g.z);
+}
+
+enum { kDiag = 0, kSweep = 1, kResid = 2 };
+
+template <int W, int MODE>
+__device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, float4* lam, const float4* gv,
+                                         float4* diag, const Item& it, int lane, int32_t* err, double& rr) {
+    const int j = lane / W;
+    const bool active = j < it.nv;
+    const int v = it.v0 + j;
+    const int slot = it.slot0 + lane;
+    const float3 z3 = make_float3(0.f, 0.f, 0.f);
+    float3 uh = z3, ul = z3, li = z3, du = z3, dl = z3;
+    if (active) {
+        uh = f3(u.hi[v]);
+        ul = f3(u.lo[v]);
+        li = f3(lam[v]);
+        const int id = m.ring_id[slot];
+        du = el::pair_diff<true>(u.hi[id], u.lo[id], uh, ul);
+        if (MODE != kDiag) {
+            const float3 lj = f3(lam[id]);
+            dl = make_float3(lj.x - li.x, lj.y - li.y, lj.z - li.z);
+        }
+    }
+    const float4 ra = m.ring_ra[slot], rb = m.ring_rb[slot], rc = m.ring_rc[slot];
+    const int loc = __float_as_int(rc.w);
+    const int base = lane & ~(W - 1);
+    const int s[3] = {base + (loc & 255), base + ((loc >> 8) & 255), base + ((loc >> 16) & 255)};
+    float3 d[3], e[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d[k] = make_float3(__shfl_sync(kFull, du.x, s[k]), __shfl_sync(kFull, du.y, s[k]), __shfl_sync(kFull, du.z, s[k]));
+        e[k] = make_float3(__shfl_sync(kFull, dl.x, s[k]), __shfl_sync(kFull, dl.y, s[k]), __shfl_sync(kFull, dl.z, s[k]));
+    }
+    const float3 g1 = f3(ra), g2 = f3(rb), g3 = f3(rc);
+    const float3 gi = make_float3(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+    ElemState E;
+    elem_state(d[0], d[1], d[2], g1, g2, g3, E);
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float out[9];
+    if (MODE == kDiag) {
+        const float gg[3] = {gi.x, gi.y, gi.z};
+        float col[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float dF[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            dF[3 * c] = gg[0];
+            dF[3 * c + 1] = gg[1];
+            dF[3 * c + 2] = gg[2];
+            hess_action(E, ra.w, rb.w, dF, out);
+            const float3 h = mat_g(out, gi);
+            col[c][0] = h.x;
+            col[c][1] = h.y;
+            col[c][2] = h.z;
+        }
+        acc[0] = col[0][0];
+        acc[1] = col[1][0];
+        acc[2] = col[2][0];
+        acc[3] = col[1][1];
+        acc[4] = col[2][1];
+        acc[5] = col[2][2];
+    } else {
+        const float dF[9] = {e[0].x * g1.x + e[1].x * g2.x + e[2].x * g3.x, e[0].x * g1.y + e[1].x * g2.y + e[2].x * g3.y,
+                             e[0].x * g1.z + e[1].x * g2.z + e[2].x * g3.z, e[0].y * g1.x + e[1].y * g2.x + e[2].y * g3.x,
+                             e[0].y * g1.y + e[1].y * g2.y + e[2].y * g3.y, e[0].y * g1.z + e[1].y * g2.z + e[2].y * g3.z,
+                             e[0].z * g1.x + e[1].z * g2.x + e[2].z * g3.x, e[0].z * g1.y + e[1].z * g2.y + e[2].z * g3.y,
+                             e[0].z * g1.z + e[1].z * g2.z + e[2].z * g3.z};
+        hess_action(E, ra.w, rb.w, dF, out);
+        const float3 h = mat_g(out, gi);
+        acc[0] = h.x;
+        acc[1] = h.y;
+        acc[2] = h.z;
+    }
+    constexpr int NA = (MODE == kDiag) ? 6 : 3;
+#pragma unroll
+    for (int k = 0; k < NA; ++k) acc[k] = el::group_sum<W>(acc[k]);
+    if (!active || (lane & (W - 1)) != 0) return;
+    // weak terms: springs K I, active plane contact k n n^T
+    const float4 x0 = m.aux0[v], x1 = m.aux1[v];
+    const float K = x0.w;
+    bool contact = false;
+    if (m.k_contact > 0.0f) {
+        const float sd = x1.w + (m.pn_x * (uh.x + ul.x) + m.pn_y * (uh.y + ul.y) + m.pn_z * (uh.z + ul.z));
+        contact = sd < 0.0f;
+    }
+    const float kc = contact ? m.k_contact : 0.0f;
+    const float n[3] = {m.pn_x, m.pn_y, m.pn_z};
+    if (MODE == kDiag) {
+        acc[0] += K + kc * n[0] * n[0];
+        acc[1] += kc * n[0] * n[1];
+        acc[2] += kc * n[0] * n[2];
+        acc[3] += K + kc * n[1] * n[1];
+        acc[4] += kc * n[1] * n[2];
+        acc[5] += K + kc * n[2] * n[2];
+        diag[2 * v] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        diag[2 * v + 1] = make_float4(acc[4], acc[5], 0.f, 0.f);
+        return;
+    }
+    const float nl = kc * (n[0] * li.x + n[1] * li.y + n[2] * li.z);
+    const float4 gvv = gv[v];
+    const float r0 = gvv.x - (acc[0] + K * li.x + nl * n[0]);
+    const float r1 = gvv.y - (acc[1] + K * li.y + nl * n[1]);
+    const float r2 = gvv.z - (acc[2] + K * li.z + nl * n[2]);
+    if (MODE == kResid) {
+        rr += (double)r0 * r0 + (double)r1 * r1 + (double)r2 * r2;
+        return;
+    }
+    const float4 D0 = diag[2 * v], D1 = diag[2 * v + 1];
+    const float A[6] = {D0.x, D0.y, D0.z, D0.w, D1.x, D1.y};
+    const float c00 = A[3] * A[5] - A[4] * A[4], c01 = A[2] * A[4] - A[1] * A[5], c02 = A[1] * A[4] - A[2] * A[3];
+    const float c11 = A[0] * A[5] - A[2] * A[2], c12 = A[1] * A[2] - A[0] * A[4], c22 = A[0] * A[3] - A[1] * A[1];
+    const float det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (!(det > 0.0f) || !(det < 3.0e38f)) {
+        atomicOr(err, kErrNonSPD);
+        return;
+    }
+    const float inv = 1.0f / det;
+    lam[v] = make_float4(li.x + inv * (c00 * r0 + c01 * r1 + c02 * r2), li.y + inv * (c01 * r0 + c11 * r1 + c12 * r2),
+                         li.z + inv * (c02 * r0 + c12 * r1 + c22 * r2), 0.f);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) adjoint_vertex_kernel(const DeviceMesh m, State u, float4* lam,
+                                                                const float4* gv, float4* diag,
+                                                                const Item* __restrict__ items, int nitems,
+                                                                int32_t* err, double* partial) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+    double rr = 0.0;
+    if (gw < nitems) {
+        const Item it = items[gw];
+        switch (it.w) {
+            case 4: adj_item<4, MODE>(m, u, lam, gv, diag, it, lane, err, rr); break;
+            case 8: adj_item<8, MODE>(m, u, lam, gv, diag, it, lane, err, rr); break;
+            case 16: adj_item<16, MODE>(m, u, lam, gv, diag, it, lane, err, rr); break;
+            default: adj_item<32, MODE>(m, u, lam, gv, diag, it, lane, err, rr); break;
+        }
+    }
+    if (MODE == kResid) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
+        if (lane == 0) partial[gw] = rr;
+    }
+}
+
+// One thread per tet: dL/dlog E_e = -sum_{j free} lambda_j . (V P g_j), and,
+// for tets touching clamped vertices, (H_DF lambda)_d += V dP(dF) g_d with
+// dF = sum_j lambda_j g_j^T (lambda = 0 at clamped vertices).
+__global__ void adjoint_tet_kernel(int ne, int nfree, const int4* __restrict__ tv, const float4* __restrict__ tb,
+                                   State u, const float4* __restrict__ lam, float* dLdlogE, float* hdl) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int4 t = tv[e];
+    const int ids[4] = {t.x, t.y, t.z, t.w};
+    const float4 B0 = tb[3 * e], B1 = tb[3 * e + 1], B2 = tb[3 * e + 2];
+    const float a = B0.w, b = B1.w;
+    float3 g[4];
+    g[1] = f3(B0);
+    g[2] = f3(B1);
+    g[3] = f3(B2);
+    g[0] = make_float3(-(g[1].x + g[2].x + g[3].x), -(g[1].y + g[2].y + g[3].y), -(g[1].z + g[2].z + g[3].z));
+    const float3 u0h = f3(u.hi[ids[0]]), u0l = f3(u.lo[ids[0]]);
+    float3 d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = el::pair_diff<true>(u.hi[ids[k + 1]], u.lo[ids[k + 1]], u0h, u0l);
+    ElemState E;
+    elem_state(d[0], d[1], d[2], g[1], g[2], g[3], E);
+    float VP[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) VP[k] = a * (E.H[k] - E.RmI[k]) + b * E.Jm1 * E.C[k];
+    float3 L[4];
+    float grad = 0.f;
+    bool touches = false;
+#pragma unroll
+    for (int jv = 0; jv < 4; ++jv) {
+        if (ids[jv] < nfree) {
+            L[jv] = f3(lam[ids[jv]]);
+            const float3 pg = mat_g(VP, g[jv]);
+            grad -= L[jv].x * pg.x + L[jv].y * pg.y + L[jv].z * pg.z;
+        } else {
+            L[jv] = make_float3(0.f, 0.f, 0.f);
+            touches = true;
+        }
+    }
+    dLdlogE[e] = grad;
+    if (!touches) return;
+    float dF[9];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const float lp[4] = {p == 0 ? L[0].x : (p == 1 ? L[0].y : L[0].z), p == 0 ? L[1].x : (p == 1 ? L[1].y : L[1].z),
+                             p == 0 ? L[2].x : (p == 1 ? L[2].y : L[2].z), p == 0 ? L[3].x : (p == 1 ? L[3].y : L[3].z)};
+        dF[3 * p] = lp[0] * g[0].x + lp[1] * g[1].x + lp[2] * g[2].x + lp[3] * g[3].x;
+        dF[3 * p + 1] = lp[0] * g[0].y + lp[1] * g[1].y + lp[2] * g[2].y + lp[3] * g[3].y;
+        dF[3 * p + 2] = lp[0] * g[0].z + lp[1] * g[1].z + lp[2] * g[2].z + lp[3] * g[3].z;
+    }
+    float out[9];
+    hess_action(E, a, b, dF, out);
+#pragma unroll
+    for (int jv = 0; jv < 4; ++jv)
+        if (ids[jv] >= nfree) {
+            const float3 h = mat_g(out, g[jv]);
+            atomicAdd(hdl + 4 * ids[jv], h.x);
+            atomicAdd(hdl + 4 * ids[jv] + 1, h.y);
+            atomicAdd(hdl + 4 * ids[jv] + 2, h.z);
+        }
+}
+
+// gvec[w] = dL/du of internal free vertex w (caller layout in).
+__global__ void gather_rhs_kernel(int nfree, const int32_t* perm, const float* dLdu, float4* gv) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nfree) return;
+    const int o = perm[w];
+    gv[w] = make_float4(dLdu[3 * o], dLdu[3 * o + 1], dLdu[3 * o + 2], 0.f);
+}
+
+// dL/dx_D[q] = dL/du(clamped vertex) - (H_DF lambda)(that vertex).
+__global__ void clamped_grad_kernel(int nd, const int32_t* dq_internal, const int32_t* dq_caller,
+                                    const float* dLdu, const float* hdl, float* out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nd) return;
+    const int w = dq_internal[q], o = dq_caller[q];
+    out[3 * q] = dLdu[3 * o] - hdl[4 * w];
+    out[3 * q + 1] = dLdu[3 * o + 1] - hdl[4 * w + 1];
+    out[3 * q + 2] = dLdu[3 * o + 2] - hdl[4 * w + 2];
+}
+
+inline int nblocks(int n, int b) { return (n + b - 1) / b; }
+
+}  // namespace
+
+int adjoint_warps(int nitems) { return nblocks(nitems, kBlock / 32) * (kBlock / 32); }
+
+cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4* lam, const float4* gv,
+                                  float4* diag, const Item* items, int nitems, int32_t* err, double* partial,
+                                  cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int grid = nblocks(nitems, kBlock / 32);
+    if (mode == kDiag)
+        adjoint_vertex_kernel<kDiag><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, items, nitems, err, partial);
+    else if (mode == kSweep)
+        adjoint_vertex_kernel<kSweep><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, items, nitems, err, partial);
+    else
+        adjoint_vertex_kernel<kResid><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, items, nitems, err, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_tets(int ne, int nfree, const int4* tv, const float4* tb, State u, const float4* lam,
+                                float* dLdlogE, float* hdl, cudaStream_t st) {
+    if (ne <= 0) return cudaSuccess;
+    adjoint_tet_kernel<<<nblocks(ne, 128), 128, 0, st>>>(ne, nfree, tv, tb, u, lam, dLdlogE, hdl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rhs(int nfree, const int32_t* perm, const float* dLdu, float4* gv, cudaStream_t st) {
+    if (nfree <= 0) return cudaSuccess;
+    gather_rhs_kernel<<<nblocks(nfree, 256), 256, 0, st>>>(nfree, perm, dLdu, gv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_clamped_grad(int nd, const int32_t* dq_internal, const int32_t* dq_caller, const float* dLdu,
+                                const float* hdl, float* out, cudaStream_t st) {
+    if (nd <= 0) return cudaSuccess;
+    clamped_grad_kernel<<<nblocks(nd, 256), 256, 0, st>>>(nd, dq_internal, dq_caller, dLdu, hdl, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pbng

@@ -66,6 +66,10 @@ struct pbng_mesh {
     DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
     DevBuf d_ring_ra, d_ring_rb, d_ring_rc, d_ring_id, d_items;
     DevBuf d_active;                   // int32 [ncomp] component flags (1 = active)
+    // adjoint (built on first use after each layout)
+    DevBuf d_lam[3], d_gv, d_diag, d_hdl, d_tv, d_tb, d_dq_int, d_dq_caller, d_adj_partial;
+    bool adj_ready = false;
+    std::vector<int32_t> dir_list;     // clamped ids in pbng_set_constraints order
     int32_t* h_active = nullptr;       // pinned host copy
     DevBuf d_dir_hi, d_dir_lo;
     DevBuf d_state[4][2];           // cur, p1, p2, tmp; hi/lo
@@ -561,6 +565,7 @@ pbng_status build_layout(pbng_mesh* m) {
     d.pn_z = (float)m->pn[2];
     d.k_contact = m->has_plane ? (float)m->kc : 0.0f;
     m->built_direct = m->want_direct;
+    m->adj_ready = false;
     m->dirty = false;
     m->has_state = false;
     return PBNG_OK;
@@ -925,6 +930,7 @@ pbng_status pbng_set_constraints(pbng_mesh* m, const int32_t* dir_idx, const dou
         return fail(m, PBNG_EINVAL, "bad constraint arrays");
     try {
         std::fill(m->is_dir.begin(), m->is_dir.end(), 0);
+        m->dir_list.assign(dir_idx, dir_idx + nd);
         for (int32_t q = 0; q < nd; ++q) {
             const int32_t i = dir_idx[q];
             if (i < 0 || i >= m->nv) return fail(m, PBNG_EINVAL, "clamped id out of range");
@@ -957,6 +963,40 @@ pbng_status pbng_set_constraints(pbng_mesh* m, const int32_t* dir_idx, const dou
             }
     } catch (const std::bad_alloc&) {
         return PBNG_ENOMEM;
+    }
+    m->dirty = true;
+    m->has_state = false;
+    return PBNG_OK;
+}
+
+pbng_status pbng_set_body_accel(pbng_mesh* m, const double* accel, const double* density) {
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    if (!accel) return fail(m, PBNG_EINVAL, "NULL acceleration");
+    std::fill(m->fext.begin(), m->fext.end(), 0.0);
+    for (int32_t e = 0; e < m->ne; ++e) {
+        const int32_t* t = &m->tets[4 * (size_t)e];
+        const int32_t c = m->ncomp > 1 ? m->comp_of[t[0]] : 0;
+        const double rho = density ? density[e] : 1.0;
+        for (int j = 0; j < 4; ++j)
+            for (int a = 0; a < 3; ++a)
+                m->fext[3 * (size_t)t[j] + a] += rho * accel[3 * c + a] * m->vol[e] / 4.0;
+    }
+    m->dirty = true;
+    m->has_state = false;
+    return PBNG_OK;
+}
+
+pbng_status pbng_set_material(pbng_mesh* m, const double* young, const double* poisson) {
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    if (!young || !poisson) return fail(m, PBNG_EINVAL, "NULL material array");
+    for (int32_t e = 0; e < m->ne; ++e)
+        if (!(young[e] > 0.0) || !(poisson[e] >= 0.0 && poisson[e] < 0.5))
+            return fail(m, PBNG_EINVAL, "Young's modulus must be > 0 and 0 <= nu < 0.5");
+    for (int32_t e = 0; e < m->ne; ++e) {
+        m->mu[e] = young[e] / (2.0 * (1.0 + poisson[e]));                              // Eq. lame
+        m->lam[e] = young[e] * poisson[e] / ((1.0 + poisson[e]) * (1.0 - 2.0 * poisson[e]));
     }
     m->dirty = true;
     m->has_state = false;
@@ -1082,6 +1122,148 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     return result;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Per-tet data and buffers of the adjoint (once per layout).
+pbng_status adjoint_setup(pbng_mesh* m) {
+    if (m->adj_ready) return PBNG_OK;
+    cudaStream_t st = m->stream;
+    std::vector<int32_t> iperm(m->nv);
+    for (int32_t w = 0; w < m->nv; ++w) iperm[m->perm[w]] = w;
+    std::vector<int4> tv(m->ne);
+    std::vector<float4> tb(3 * (size_t)m->ne);
+    for (int32_t e = 0; e < m->ne; ++e) {
+        const int32_t* t = &m->tets[4 * (size_t)e];
+        tv[e] = make_int4(iperm[t[0]], iperm[t[1]], iperm[t[2]], iperm[t[3]]);
+        const double* B = &m->B[9 * (size_t)e];
+        tb[3 * (size_t)e] = make_float4((float)B[0], (float)B[1], (float)B[2], (float)(2.0 * m->mu[e] * m->vol[e]));
+        tb[3 * (size_t)e + 1] = make_float4((float)B[3], (float)B[4], (float)B[5], (float)(m->lam[e] * m->vol[e]));
+        tb[3 * (size_t)e + 2] = make_float4((float)B[6], (float)B[7], (float)B[8], 0.f);
+    }
+    const int32_t nd = (int32_t)m->dir_list.size();
+    std::vector<int32_t> dq_int(nd), dq_caller(m->dir_list);
+    for (int32_t q = 0; q < nd; ++q) dq_int[q] = iperm[m->dir_list[q]];
+    PBNG_CUDA(m, upload(m->d_tv, tv, st));
+    PBNG_CUDA(m, upload(m->d_tb, tb, st));
+    PBNG_CUDA(m, upload(m->d_dq_int, dq_int, st));
+    PBNG_CUDA(m, upload(m->d_dq_caller, dq_caller, st));
+    for (auto& b : m->d_lam) PBNG_CUDA(m, ensure_buf(b, sizeof(float4) * (size_t)m->nv));
+    PBNG_CUDA(m, ensure_buf(m->d_gv, sizeof(float4) * (size_t)std::max(1, m->nfree)));
+    PBNG_CUDA(m, ensure_buf(m->d_diag, 2 * sizeof(float4) * (size_t)std::max(1, m->nfree)));
+    PBNG_CUDA(m, ensure_buf(m->d_hdl, sizeof(float4) * (size_t)m->nv));
+    PBNG_CUDA(m, ensure_buf(m->d_adj_partial, sizeof(double) * (size_t)std::max(1, adjoint_warps(m->nitems_ring))));
+    m->adj_ready = true;
+    return PBNG_OK;
+}
+
+// FP64 |dL/du - H lambda|^2 -> host.
+pbng_status adjoint_resid(pbng_mesh* m, State u, float4* lam, double* out) {
+    cudaStream_t st = m->stream;
+    PBNG_CUDA(m, launch_adjoint_vertex(kAdjResid, m->dm, u, lam, (const float4*)m->d_gv.p, (float4*)m->d_diag.p,
+                                       (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
+                                       (double*)m->d_adj_partial.p, st));
+    PBNG_CUDA(m, launch_reduce((const double*)m->d_adj_partial.p, adjoint_warps(m->nitems_ring),
+                               (double*)m->d_scalar.p, st));
+    m->kernel_launches += 2;
+    PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_scalar.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    *out = m->h_pinned[0];
+    return PBNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_dev, float* dL_dlogE_dev,
+                         float* dL_dxD_dev, double rel_tol, int32_t max_sweeps, const pbng_params* p,
+                         int32_t* sweeps_out, double* rel_residual_out) {
+    if (!m) return PBNG_EINVAL;
+    if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
+    if (!u_eq_dev || !dLdu_dev || !dL_dlogE_dev) return fail(m, PBNG_EINVAL, "NULL argument");
+    if (p->kernel_path != 0) return fail(m, PBNG_EINVAL, "the adjoint runs on the ring layout (kernel_path 0)");
+    select_path(m, p);
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!m->all_ring) return fail(m, PBNG_EINVAL, "the adjoint needs every colour in the ring layout");
+    if ((s = adjoint_setup(m))) return s;
+    cudaStream_t st = m->stream;
+    // u_eq -> state slot 3 (clamped vertices at their targets)
+    PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_eq_dev, (const int32_t*)m->d_perm.p, (const float4*)m->d_dir_hi.p,
+                             (const float4*)m->d_dir_lo.p, state_of(m, 3), st));
+    PBNG_CUDA(m, launch_gather_rhs(m->nfree, (const int32_t*)m->d_perm.p, dLdu_dev, (float4*)m->d_gv.p, st));
+    for (auto& b : m->d_lam) PBNG_CUDA(m, cudaMemsetAsync(b.p, 0, sizeof(float4) * (size_t)m->nv, st));
+    const State u = state_of(m, 3);
+    float4* lam = (float4*)m->d_lam[0].p;
+    PBNG_CUDA(m, launch_adjoint_vertex(kAdjDiag, m->dm, u, lam, (const float4*)m->d_gv.p, (float4*)m->d_diag.p,
+                                       (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p, nullptr, st));
+    m->kernel_launches += 3;
+    double g2 = 0.0, r2 = 0.0;
+    if ((s = adjoint_resid(m, u, lam, &g2))) return s;  // lambda = 0: |dL/du|^2
+    // Gauss-Seidel sweeps with the forward's acceleration, on a local sweep
+    // index so the forward iterate's history is left alone
+    const int32_t saved_l = m->sweep_l;
+    const double saved_om = m->omega_l;
+    m->sweep_l = 0;
+    m->omega_l = 1.0;
+    int p1 = 1, p2 = 2;
+    int32_t done = 0;
+    double rel = g2 > 0.0 ? 1.0 : 0.0;
+    pbng_status result = PBNG_ENOTCONVERGED;
+    const int32_t K = std::min<int32_t>(p->residual_every, kMaxChunk);
+    if ((s = ensure_wg(m, (size_t)K))) return s;
+    while (g2 > 0.0 && done < max_sweeps) {
+        const int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
+        chunk_weights(m, p, chunk, m->h_wg);
+        PBNG_CUDA(m, cudaMemcpyAsync(m->d_wg.p, m->h_wg, sizeof(float2) * chunk, cudaMemcpyHostToDevice, st));
+        for (int32_t k = 0; k < chunk; ++k) {
+            for (int c = 0; c < m->ncol; ++c)
+                PBNG_CUDA(m, launch_adjoint_vertex(kAdjSweep, m->dm, u, lam, (const float4*)m->d_gv.p,
+                                                   (float4*)m->d_diag.p, (const Item*)m->d_items.p + m->item_off[c],
+                                                   m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
+                                                   nullptr, st));
+            m->kernel_launches += m->ncol;
+            if (p->accel != PBNG_ACCEL_NONE && m->nfree > 0) {
+                const State lc{lam, lam}, l1{(float4*)m->d_lam[p1].p, (float4*)m->d_lam[p1].p},
+                    l2{(float4*)m->d_lam[p2].p, (float4*)m->d_lam[p2].p};
+                PBNG_CUDA(m, launch_accel(m->nfree, lc, l1, l2, (const float2*)m->d_wg.p + k, nullptr, nullptr,
+                                          false, st));
+                m->kernel_launches++;
+                std::swap(p1, p2);
+            }
+        }
+        done += chunk;
+        if ((s = check_err(m))) break;
+        if ((s = adjoint_resid(m, u, lam, &r2))) break;
+        rel = std::sqrt(r2 / g2);
+        if (!std::isfinite(rel) || rel > 1e3) { result = PBNG_EDIVERGED; break; }
+        if (rel <= rel_tol) { result = PBNG_OK; break; }
+    }
+    m->sweep_l = saved_l;
+    m->omega_l = saved_om;
+    if (s) return s;
+    if (g2 == 0.0) result = PBNG_OK;
+    // sensitivities
+    PBNG_CUDA(m, cudaMemsetAsync(m->d_hdl.p, 0, sizeof(float4) * (size_t)m->nv, st));
+    PBNG_CUDA(m, launch_adjoint_tets(m->ne, m->nfree, (const int4*)m->d_tv.p, (const float4*)m->d_tb.p, u, lam,
+                                     dL_dlogE_dev, (float*)m->d_hdl.p, st));
+    m->kernel_launches++;
+    if (dL_dxD_dev) {
+        PBNG_CUDA(m, launch_clamped_grad((int32_t)m->dir_list.size(), (const int32_t*)m->d_dq_int.p,
+                                         (const int32_t*)m->d_dq_caller.p, dLdu_dev, (const float*)m->d_hdl.p,
+                                         dL_dxD_dev, st));
+        m->kernel_launches++;
+    }
+    if ((s = check_err(m))) return s;
+    if (sweeps_out) *sweeps_out = done;
+    if (rel_residual_out) *rel_residual_out = rel;
+    if (result == PBNG_ENOTCONVERGED) m->err = "max_sweeps reached";
+    if (result == PBNG_EDIVERGED) m->err = "adjoint iteration diverged";
+    return result;
+}
+
 pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out) {
     pbng_status s = ensure_ready(m);
     if (s) return s;
@@ -1189,7 +1371,9 @@ void pbng_destroy(pbng_mesh* m) {
     if (!m) return;
     cudaSetDevice(m->device);
     if (m->stream) cudaStreamSynchronize(m->stream);
-    DevBuf* bufs[] = {&m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
+    DevBuf* bufs[] = {&m->d_lam[0], &m->d_lam[1], &m->d_lam[2], &m->d_gv, &m->d_diag, &m->d_hdl, &m->d_tv,
+                      &m->d_tb, &m->d_dq_int, &m->d_dq_caller, &m->d_adj_partial,
+                      &m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
                       &m->d_ring_ra, &m->d_ring_rb, &m->d_ring_rc, &m->d_ring_id, &m->d_items,
                       &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_partial, &m->d_comp_sq, &m->d_scalar, &m->d_err};

@@ -109,6 +109,21 @@ cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items
                                  bool compensated, double* warp_partial, double* comp_sq,
                                  int32_t* err, cudaStream_t st);
 
+// Equilibrium adjoint (pbng_adjoint.cu).  Vertex kernels: one warp per
+// ring item; mode 0 computes the 3x3 diagonal blocks of H, mode 1 is one
+// Gauss-Seidel pass over the given items (one colour), mode 2 writes one FP64
+// partial of |dL/du - H lambda|^2 per warp (adjoint_warps(nitems) of them).
+enum { kAdjDiag = 0, kAdjSweep = 1, kAdjResid = 2 };
+int adjoint_warps(int nitems);
+cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4* lam, const float4* gv,
+                                  float4* diag, const Item* items, int nitems, int32_t* err, double* partial,
+                                  cudaStream_t st);
+cudaError_t launch_adjoint_tets(int ne, int nfree, const int4* tv, const float4* tb, State u, const float4* lam,
+                                float* dLdlogE, float* hdl, cudaStream_t st);
+cudaError_t launch_gather_rhs(int nfree, const int32_t* perm, const float* dLdu, float4* gv, cudaStream_t st);
+cudaError_t launch_clamped_grad(int nd, const int32_t* dq_internal, const int32_t* dq_caller, const float* dLdu,
+                                const float* hdl, float* out, cudaStream_t st);
+
 // Fixed device scratch of the allocation-free residual (pbng_kernels.cu).
 int noalloc_scratch_capacity();
 cudaError_t noalloc_scratch(int device, double** out);

@@ -100,6 +100,40 @@ class Mesh:
         check(st, "pbng_set_constraints", self.h)
         self.dirichlet = di.copy()
 
+    def set_body_accel(self, accel, density=None):
+        """pbng_set_body_accel: accel [ncomp, 3] (host), density [ne] or None."""
+        acc = np.ascontiguousarray(accel, dtype=np.float64).reshape(-1, 3)
+        if acc.shape[0] != self.ncomp:
+            raise ValueError("one acceleration per component")
+        de = None if density is None else np.ascontiguousarray(np.broadcast_to(density, (self.ne,)), dtype=np.float64)
+        check(load().pbng_set_body_accel(self.h, _dptr(acc), None if de is None else _dptr(de)),
+              "pbng_set_body_accel", self.h)
+
+    def set_material(self, young, poisson):
+        """pbng_set_material (per-tet E and nu, host arrays)."""
+        young = np.ascontiguousarray(np.broadcast_to(young, (self.ne,)), dtype=np.float64)
+        poisson = np.ascontiguousarray(np.broadcast_to(poisson, (self.ne,)), dtype=np.float64)
+        check(load().pbng_set_material(self.h, _dptr(young), _dptr(poisson)), "pbng_set_material", self.h)
+
+    def adjoint(self, u_eq, dLdu, rel_tol=1e-6, max_sweeps=100000, params=None, raise_on_status=True):
+        """pbng_adjoint: returns (status, dL/dlogE [ne], dL/dx_D [nd, 3], sweeps, rel residual)."""
+        import torch
+        _check_u(u_eq, self.nv)
+        _check_u(dLdu, self.nv)
+        p = params if params is not None else default_params()
+        dE = torch.empty(self.ne, dtype=torch.float32, device=u_eq.device)
+        dD = torch.empty((max(1, len(self.dirichlet)), 3), dtype=torch.float32, device=u_eq.device)
+        sweeps = ctypes.c_int32()
+        rel = ctypes.c_double()
+        st = load().pbng_adjoint(self.h, ctypes.c_void_p(u_eq.data_ptr()), ctypes.c_void_p(dLdu.data_ptr()),
+                                 ctypes.c_void_p(dE.data_ptr()),
+                                 ctypes.c_void_p(dD.data_ptr()) if len(self.dirichlet) else None,
+                                 float(rel_tol), int(max_sweeps), ctypes.byref(p), ctypes.byref(sweeps),
+                                 ctypes.byref(rel))
+        if raise_on_status:
+            check(st, "pbng_adjoint", self.h)
+        return st, dE, dD[:len(self.dirichlet)], sweeps.value, rel.value
+
     def colouring(self):
         col = np.zeros(self.nv, np.int32)
         n = ctypes.c_int32()

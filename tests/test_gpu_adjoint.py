@@ -1,0 +1,75 @@
+"""The coloured Gauss-Seidel adjoint (pbng_adjoint) against the oracle's
+dense adjoint (itself pinned by finite differences of the loss)."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ADJ_TOL = 1e-3  # relative, float32 adjoint vs FP64 dense adjoint
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_09021_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _loaded(n=4):
+    p = W.adjoint_block(n)
+    xd, acc = W.adjoint_load_cases(p, count=1, seed=9)
+    p.x0 = p.X.copy()
+    p.x0[p.dirichlet] = xd[0]
+    p.body_accel = acc[0]
+    return p
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("n,accel", [(3, "none"), (4, "chebyshev"), (5, "sor")])
+def test_adjoint_matches_dense_oracle(oracle_mod, n, accel):
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = _loaded(n)
+    om = oracle_mod.OracleMesh.from_problem(p)
+    xeq, it, _ = om.newton(p.x0, 1e-12, 60)
+    assert it >= 0
+    top = np.isclose(p.X[:, 2], 1.0)
+    rng = np.random.default_rng(n)
+    target = xeq + 0.01 * rng.standard_normal(xeq.shape)
+    dLdx = np.where(top[:, None], 2.0 * (xeq - target), 0.0)
+    dLdx[p.dirichlet] = 0.05 * rng.standard_normal((len(p.dirichlet), 3))  # direct boundary term
+    dE_ref, dD_ref = om.adjoint(xeq, dLdx)
+
+    m = Mesh.from_problem(p)
+    u = torch.tensor(xeq - p.X, dtype=torch.float32, device="cuda")
+    g = torch.tensor(dLdx, dtype=torch.float32, device="cuda")
+    kw = dict(accel=accel)
+    if accel == "sor":
+        kw["omega"] = 1.5
+    st, dE, dD, sweeps, rel = m.adjoint(u, g, rel_tol=1e-6, max_sweeps=20000, params=default_params(**kw),
+                                        raise_on_status=False)
+    print(f"adjoint {n}^3 {accel}: status {st}, {sweeps} sweeps, rel residual {rel:.2e}")
+    assert st == 0 or (st == 7 and rel <= 1e-5), (st, sweeps, rel)
+    dE = dE.cpu().double().numpy()
+    dD = dD.cpu().double().numpy()
+    assert _rel(dE, dE_ref) <= ADJ_TOL
+    # dir_idx order of pbng_set_constraints is the ascending clamped ids, as in the oracle
+    assert _rel(dD, dD_ref) <= ADJ_TOL
+
+
+def test_adjoint_zero_rhs_gives_zero():
+    from paper_2306_09021_gb300 import Mesh
+    p = _loaded(3)
+    m = Mesh.from_problem(p)
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    st, dE, dD, sweeps, rel = m.adjoint(u, torch.zeros_like(u))
+    assert st == 0 and sweeps == 0
+    assert torch.count_nonzero(dE) == 0 and torch.count_nonzero(dD) == 0
