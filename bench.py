@@ -47,9 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["sag64", "twist10", "bar", "batched"], default="sag64",
+    ap.add_argument("--config", choices=["sag64", "twist10", "bar", "batched", "adjoint"], default="sag64",
                     help="sag64: 64^3 gravity-sag cube (default); twist10: 10^3 twisted block; "
-                         "bar: 40x40x200 bar with springs and contact; batched: 256 uneven blocks")
+                         "bar: 40x40x200 bar with springs and contact; batched: 256 uneven blocks; "
+                         "adjoint: 32 load cases of a 48^3 cube, forward + adjoint")
     ap.add_argument("--cells", type=int, default=64, help="cube cells per side for sag64")
     ap.add_argument("--sweeps-per-step", type=int, default=10)
     ap.add_argument("--precision", choices=["compensated", "fp32"], default="compensated")
@@ -71,6 +72,20 @@ def workload(args):
         p = W.contact_bar()
         return p, None, ("bar 40x40x200 cells (337,881 verts, 1.6M tets), lognormal E (ln 1e5, 0.5), "
                          "nu=0.4, 2% verts on k=1e4 springs, z=0 plane contact k_n=1e8"), dict(accel="sor", omega=1.5)
+    if args.config == "adjoint":
+        base = W.adjoint_block(48)
+        xds, accs = W.adjoint_load_cases(base, count=32)
+        cases = []
+        for c in range(32):
+            q = W.adjoint_block(48)
+            q.x0 = q.X.copy()
+            q.x0[q.dirichlet] = xds[c]
+            cases.append(q)
+        p, mid, _ = W.concat_problems(cases)
+        p.meta["case_accel"] = accs
+        return p, mid, ("32 load cases of a 48^3 cube (552,960 tets each; 3.76M verts, 17.7M tets), "
+                        "bottom clamped to seeded rigid motions, seeded gravity directions, nu=0.3; "
+                        "forward solve and adjoint of |x_top - target|^2"), dict(accel="sor", omega=1.5)
     if args.config == "batched":
         probs = W.batched_blocks()
         p, mid, _ = W.concat_problems(probs)
@@ -149,6 +164,17 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (the slowest rank's time); x itself
+    without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def measured_peaks():
@@ -259,6 +285,8 @@ def main():
     p, mesh_id, desc, acc = workload(args)
     stream = torch.cuda.current_stream()
     m = Mesh.from_problem(p, stream=stream, mesh_id=mesh_id)
+    if "case_accel" in p.meta:
+        m.set_body_accel(p.meta["case_accel"], p.density)
     u0 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
     u = u0.clone()
     S = args.sweeps_per_step
@@ -291,11 +319,7 @@ def main():
     barrier()
     launches = m.profile()["kernel_launches"]
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     updates_per_rank = p.n_free * S * args.steps
     value = updates_per_rank * world / (ms * 1e-3)
 
@@ -350,11 +374,7 @@ def main():
         h_out.copy_(u, non_blocking=True)
         torch.cuda.synchronize()
         h_u, h_out = h_out, h_u
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
     e2e = {"value": p.n_free * S * e2e_steps * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(u.numel() * 4), "d2h_bytes_per_step": int(u.numel() * 4 + 8),
            "api": "Mesh.sweep (pbng_sweep, resume=0) with pinned host u copied in and out"}
@@ -368,18 +388,35 @@ def main():
                 "sag64": [("chebyshev", dict(accel="chebyshev"), 1e-5), ("sor", dict(accel="sor", omega=1.5), 1e-5),
                           ("chebyshev_to_1e-4", dict(accel="chebyshev"), 1e-4)],
                 "bar": [("plain", {}, 1e-5), ("sor", dict(accel="sor", omega=1.5), 1e-5)],
-                "batched": [("chebyshev", dict(accel="chebyshev"), 1e-5), ("plain", {}, 1e-5)]}[args.config]
+                "batched": [("chebyshev", dict(accel="chebyshev"), 1e-5), ("plain", {}, 1e-5)],
+                "adjoint": [("sor", dict(accel="sor", omega=1.5), 1e-5)]}[args.config]
+        max_sw = 4000 if args.config == "adjoint" else 20000
         for name, kw, tol in runs:
             uu = u0.clone()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            st, sweeps, relr = m.solve(uu, tol, 20000,
+            st, sweeps, relr = m.solve(uu, tol, max_sw,
                                        default_params(precision=args.precision, residual_every=10,
                                                       kernel_path=args.kernel_path, **kw),
                                        raise_on_status=False)
             torch.cuda.synchronize()
             ttr[name] = {"tol": tol, "status": int(st), "sweeps": int(sweeps),
                          "max_rel_residual": float(np.max(relr)), "ms": 1e3 * (time.perf_counter() - t0)}
+            u_eq = uu
+        if args.config == "adjoint":
+            # dL/du of |x_top - target|^2 (target 1 cm below the rest top face)
+            top = np.isclose(p.X[:, 2], 1.0)
+            tgt = p.X + np.array([0.0, 0.0, -0.01])
+            x_eq = u_eq.double().cpu().numpy() + p.X
+            g = np.where(top[:, None], 2.0 * (x_eq - tgt), 0.0)
+            gd = torch.tensor(g, dtype=torch.float32, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, dE, dD, asw, arel = m.adjoint(u_eq, gd, 1e-5, 4000, default_params(accel="sor", omega=1.5),
+                                             raise_on_status=False)
+            torch.cuda.synchronize()
+            ttr["adjoint_sor"] = {"tol": 1e-5, "status": int(st), "sweeps": int(asw), "rel_residual": float(arel),
+                                  "ms": 1e3 * (time.perf_counter() - t0)}
 
     if rank != 0:
         if dist is not None:

@@ -83,7 +83,7 @@ typedef struct {
 
 /* Fills p with the paper's defaults: corotated, no acceleration, omega 1.7,
  * rho 0.95, gamma 1.7, step 1, skip_tol 0, residual_every 10, resume 0,
- * compensated precision, pipelined kernels. */
+ * compensated precision, kernel_path 0. */
 void pbng_default_params(pbng_params* p);
 
 /* Creates a mesh handle (Section "Discretization": P1 tetrahedra, per-tet
@@ -177,6 +177,17 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
 pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_dev, float* dL_dlogE_dev,
                          float* dL_dxD_dev, double rel_tol, int32_t max_sweeps, const pbng_params* p,
                          int32_t* sweeps_out, double* rel_residual_out);
+
+/* Checkpoint of the iteration: the iterate (float32 pairs), the two previous
+ * iterates used by the acceleration, the sweep index, omega_l and r_0.
+ * pbng_get_state with buf == NULL writes the size needed to *bytes;
+ * otherwise it copies the state into buf (host, *bytes large enough) and
+ * sets *bytes.  pbng_set_state restores it into a handle built from the same
+ * mesh and constraints (same layout; PBNG_EINVAL otherwise); the next
+ * pbng_sweep / pbng_solve with resume = 1 then continues bit for bit as if
+ * the iteration had never stopped.  Both synchronise. */
+pbng_status pbng_get_state(pbng_mesh* m, void* buf, size_t* bytes);
+pbng_status pbng_set_state(pbng_mesh* m, const void* buf, size_t bytes);
 
 /* FP64 2-norm of (f + f^ext) over free vertices at u_dev (Section "PBNG vs.
  * PBD and Limited Newton": the 2-norm of the Newton residual), per component

@@ -81,6 +81,8 @@ SIGNATURES = {
     "pbng_sweep": (_I32, [_P, _P, _I32, ctypes.POINTER(PbngParams), _PD]),
     "pbng_solve": (_I32, [_P, _P, _D, _I32, ctypes.POINTER(PbngParams), _PI, _PD]),
     "pbng_residual": (_I32, [_P, _P, _PD]),
+    "pbng_get_state": (_I32, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),
+    "pbng_set_state": (_I32, [_P, _P, ctypes.c_size_t]),
     "pbng_residual_noalloc": (_I32, [_P, _P, _PD]),
     "pbng_set_profiling": (_I32, [_P, _I32]),
     "pbng_get_profile": (_I32, [_P, ctypes.POINTER(PbngProfile)]),

@@ -1264,6 +1264,90 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     return result;
 }
 
+namespace {
+struct StateHeader {
+    uint64_t magic;     // "PBNGSTA1"
+    int64_t nv, nfree, ncol, ncomp;
+    int64_t sweep_l, p1_slot, has_state;
+    double omega_l;
+    uint64_t perm_hash;
+};
+constexpr uint64_t kStateMagic = 0x31415453474e4250ull;
+
+uint64_t perm_hash(const std::vector<int32_t>& perm) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the internal order
+    for (int32_t v : perm) {
+        h ^= (uint64_t)(uint32_t)v;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+}  // namespace
+
+pbng_status pbng_get_state(pbng_mesh* m, void* buf, size_t* bytes) {
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!bytes) return fail(m, PBNG_EINVAL, "NULL size");
+    const size_t arr = sizeof(float4) * (size_t)m->nv;
+    const size_t need = sizeof(StateHeader) + sizeof(double) * m->ncomp + 6 * arr;
+    if (!buf) {
+        *bytes = need;
+        return PBNG_OK;
+    }
+    if (*bytes < need) return fail(m, PBNG_EINVAL, "state buffer too small");
+    StateHeader h{kStateMagic, m->nv, m->nfree, m->ncol, m->ncomp, m->sweep_l, m->p1_slot, m->has_state ? 1 : 0,
+                  m->omega_l, perm_hash(m->perm)};
+    char* out = static_cast<char*>(buf);
+    std::memcpy(out, &h, sizeof(h));
+    out += sizeof(h);
+    for (int k = 0; k < m->ncomp; ++k) {
+        const double r = (k < (int)m->r0.size()) ? m->r0[k] : -1.0;
+        std::memcpy(out, &r, sizeof(double));
+        out += sizeof(double);
+    }
+    const int slots[3] = {0, m->p1_slot, m->p2_slot};
+    for (int sl : slots)
+        for (int hl = 0; hl < 2; ++hl) {
+            PBNG_CUDA(m, cudaMemcpyAsync(out, m->d_state[sl][hl].p, arr, cudaMemcpyDeviceToHost, m->stream));
+            out += arr;
+        }
+    PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
+    *bytes = need;
+    return PBNG_OK;
+}
+
+pbng_status pbng_set_state(pbng_mesh* m, const void* buf, size_t bytes) {
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!buf || bytes < sizeof(StateHeader)) return fail(m, PBNG_EINVAL, "bad state buffer");
+    StateHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    const size_t arr = sizeof(float4) * (size_t)m->nv;
+    if (h.magic != kStateMagic || h.nv != m->nv || h.nfree != m->nfree || h.ncol != m->ncol ||
+        h.ncomp != m->ncomp || h.perm_hash != perm_hash(m->perm) || (h.p1_slot != 1 && h.p1_slot != 2) ||
+        bytes < sizeof(StateHeader) + sizeof(double) * m->ncomp + 6 * arr)
+        return fail(m, PBNG_EINVAL, "state does not belong to this mesh layout");
+    const char* in = static_cast<const char*>(buf) + sizeof(h);
+    m->r0.assign(m->ncomp, -1.0);
+    for (int k = 0; k < m->ncomp; ++k) {
+        std::memcpy(&m->r0[k], in, sizeof(double));
+        in += sizeof(double);
+    }
+    m->sweep_l = (int32_t)h.sweep_l;
+    m->omega_l = h.omega_l;
+    m->p1_slot = (int)h.p1_slot;
+    m->p2_slot = 3 - m->p1_slot;
+    m->has_state = h.has_state != 0;
+    const int slots[3] = {0, m->p1_slot, m->p2_slot};
+    for (int sl : slots)
+        for (int hl = 0; hl < 2; ++hl) {
+            PBNG_CUDA(m, cudaMemcpyAsync(m->d_state[sl][hl].p, in, arr, cudaMemcpyHostToDevice, m->stream));
+            in += arr;
+        }
+    PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
+    return PBNG_OK;
+}
+
 pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out) {
     pbng_status s = ensure_ready(m);
     if (s) return s;

@@ -169,6 +169,19 @@ class Mesh:
         check(load().pbng_residual(self.h, ctypes.c_void_p(u.data_ptr()), _dptr(out)), "pbng_residual", self.h)
         return out
 
+    def get_state(self):
+        """pbng_get_state: the iteration checkpoint as bytes."""
+        n = ctypes.c_size_t()
+        check(load().pbng_get_state(self.h, None, ctypes.byref(n)), "pbng_get_state", self.h)
+        buf = ctypes.create_string_buffer(n.value)
+        check(load().pbng_get_state(self.h, buf, ctypes.byref(n)), "pbng_get_state", self.h)
+        return buf.raw[:n.value]
+
+    def set_state(self, blob):
+        """pbng_set_state: restore a checkpoint taken on an identical mesh."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        check(load().pbng_set_state(self.h, buf, len(blob)), "pbng_set_state", self.h)
+
     def set_profiling(self, enable=True):
         """pbng_set_profiling: per-launch event timing of the library's kernels."""
         check(load().pbng_set_profiling(self.h, 1 if enable else 0), "pbng_set_profiling", self.h)

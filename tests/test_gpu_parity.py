@@ -250,3 +250,26 @@ def test_pipelined_equals_direct(maker):
     assert (out[0][0] - out[1][0]).abs().max().item() <= 1e-6 * scale
     assert out[0][1][0] == pytest.approx(out[1][1][0], rel=1e-3, abs=1e-7)
     assert out[0][2][0] == pytest.approx(out[1][2][0], rel=1e-3, abs=1e-7 * out[1][2][0] + 1e-12)
+
+
+def test_checkpoint_across_handles_is_bit_exact():
+    """100 sweeps == 50 sweeps, checkpoint, restore in a new handle, 50 more."""
+    from paper_2306_09021_gb300 import Mesh, PbngError, default_params
+    p = W.twist_block(6, 90.0, 0.3)
+    params = default_params(accel="chebyshev")
+    m1 = Mesh.from_problem(p)
+    u1 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    m1.sweep(u1, 100, params)
+    m2 = Mesh.from_problem(p)
+    u2 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    m2.sweep(u2, 50, params)
+    blob = m2.get_state()
+    del m2
+    m3 = Mesh.from_problem(p)
+    m3.set_state(blob)
+    u3 = torch.zeros_like(u2)
+    m3.sweep(u3, 50, default_params(accel="chebyshev", resume=1))
+    assert torch.equal(u1, u3)
+    other = Mesh.from_problem(W.twist_block(5))
+    with pytest.raises(PbngError):
+        other.set_state(blob)
