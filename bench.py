@@ -58,6 +58,8 @@ def parse():
                     help="0: 1-ring layout kernels (TMA-staged), 1: CSR direct-load kernels")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-5 solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default colour-pass schedule instead of pbng_autotune's choice")
     return ap.parse_args()
 
 
@@ -210,7 +212,7 @@ def kernel_traffic():
         return None
 
 
-def cpu_baseline(p, acc, sweeps_budget_s=15.0, max_sweeps=12):
+def cpu_baseline(p, acc, sweeps_budget_s=12.0, max_sweeps=400):
     """The FP64 oracle, as it stands, on this host's cores: a bounded number of
     sweeps of the same mesh with the same acceleration."""
     import oracle
@@ -293,6 +295,10 @@ def main():
     first = default_params(precision=args.precision, kernel_path=args.kernel_path, **acc)
     cont = default_params(precision=args.precision, resume=1, kernel_path=args.kernel_path, **acc)
 
+    sched = None
+    if not args.no_autotune and args.kernel_path == 0:
+        sched = m.autotune(u, reps=10, params=first)   # before warm-up; not timed
+
     # warm-up (also loads the iterate and the acceleration history)
     m.sweep(u, S, first, want_residual=True)
     for _ in range(max(0, args.warmup - 1)):
@@ -346,7 +352,8 @@ def main():
     alg_bytes_launch = alg_bytes_sweep / max(1, prof["ncolours"])
     achieved = alg_bytes_launch / (per_launch_ms * 1e-3) / 1e9
     tr = kernel_traffic()
-    roofline = {"kernel": "colour_pass_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+    roofline = {"kernel": "ring_kernel<UPDATE=true> (colour pass)" if args.kernel_path == 0 else "colour_pass_kernel",
+                "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tr is None else tr["dram_bytes_per_launch"],
                 "alg_bytes_per_launch": alg_bytes_launch, "avg_launch_us": per_launch_ms * 1e3,
@@ -425,7 +432,8 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": config_of(args, p, desc, acc), "clocks": clk, "roofline": roofline, "e2e": e2e,
+           "config": dict(config_of(args, p, desc, acc), schedule=sched), "clocks": clk, "roofline": roofline,
+           "e2e": e2e,
            "gpu_launches": int(launches),
            "rel_residual_end": None if rel is None else float(rel[0]),
            "time_to_rel_residual": ttr}

@@ -243,6 +243,52 @@ pbng_status pbng_set_profiling(pbng_mesh* m, int32_t enable);
 /* Synchronises the stream and returns the counters. */
 pbng_status pbng_get_profile(pbng_mesh* m, pbng_profile* out);
 
+/* Launch schedules of the 1-ring colour passes (kernel_path 0).  The paper
+ * runs each colour as one parallel loop (Section "Coloring and
+ * Parallelism"); here each colour is one launch of a persistent grid whose
+ * warps stream 32-slot work items, and two knobs decide how:
+ *   ctas_per_sm  1..PBNG_MAX_CTAS_PER_SM CTAs (8 warps each) per SM
+ *   blocked      0: warp w takes items w, w + nwarps, ... (strided);
+ *                1: warp w takes one contiguous run of items (blocked)
+ * The vertex updates of one colour are independent, so every schedule gives
+ * a bit-identical iterate; only the time differs.  Colours laid out for
+ * direct loads (vertices with more than 32 incident tets or 1-ring vertices,
+ * or kernel_path 1) have no schedule and report ctas_per_sm = 0. */
+#define PBNG_MAX_COLOURS 64
+#define PBNG_MAX_CTAS_PER_SM 3
+typedef struct {
+    int32_t ncolours;                          /* of the current layout       */
+    int32_t ctas_per_sm[PBNG_MAX_COLOURS];     /* per colour; 0 = not a ring colour */
+    int32_t blocked[PBNG_MAX_COLOURS];
+    double default_ms_per_sweep;   /* pbng_autotune: colour passes of one sweep
+                                      with the default schedule (3, strided)   */
+    double tuned_ms_per_sweep;     /* ... with the schedule it chose           */
+    int32_t candidates;            /* schedules timed per colour               */
+    int32_t reserved;
+} pbng_schedule;
+
+/* Sets the schedule of every ring colour from s->ctas_per_sm[c] (clamped to
+ * 1..PBNG_MAX_CTAS_PER_SM) and s->blocked[c] for c < min(s->ncolours,
+ * ncolours of the layout).  Builds the layout if needed (p selects
+ * kernel_path; NULL = defaults).  Captured sweep graphs are dropped and
+ * re-captured on next use.  The schedule survives layout rebuilds that keep
+ * the colour count. */
+pbng_status pbng_set_schedule(pbng_mesh* m, const pbng_params* p, const pbng_schedule* s);
+/* Current schedule (ms fields = 0 unless set by pbng_autotune). */
+pbng_status pbng_get_schedule(pbng_mesh* m, pbng_schedule* out);
+
+/* Autotuner: times every schedule (ctas_per_sm x {strided, blocked}) of every
+ * ring colour over `reps` sweeps each, on a scratch copy of u_dev (the
+ * caller's u_dev, the handle's iterate and its acceleration history are not
+ * touched) and keeps the fastest per colour (the default unless another is
+ * at least 2 % faster).  The candidates alternate: each of the `reps` rounds
+ * runs every candidate once over all colours, each colour pass bracketed by
+ * CUDA events on the handle's stream.  out (may be NULL) receives the chosen
+ * schedule and the summed colour-pass time per sweep of the default and of
+ * the chosen schedules from the same rounds.  Synchronises; reps in 1..1000. */
+pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p, int32_t reps,
+                          pbng_schedule* out);
+
 /* Number of independent components (1 unless mesh_id was given). */
 int32_t pbng_num_components(const pbng_mesh* m);
 

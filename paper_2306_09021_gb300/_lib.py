@@ -54,6 +54,22 @@ class PbngProfile(ctypes.Structure):
     ]
 
 
+MAX_COLOURS = 64      # PBNG_MAX_COLOURS
+MAX_CTAS_PER_SM = 3   # PBNG_MAX_CTAS_PER_SM
+
+
+class PbngSchedule(ctypes.Structure):
+    _fields_ = [
+        ("ncolours", ctypes.c_int32),
+        ("ctas_per_sm", ctypes.c_int32 * MAX_COLOURS),
+        ("blocked", ctypes.c_int32 * MAX_COLOURS),
+        ("default_ms_per_sweep", ctypes.c_double),
+        ("tuned_ms_per_sweep", ctypes.c_double),
+        ("candidates", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
 class PbngError(RuntimeError):
     def __init__(self, status, where, detail=""):
         self.status = status
@@ -86,6 +102,9 @@ SIGNATURES = {
     "pbng_residual_noalloc": (_I32, [_P, _P, _PD]),
     "pbng_set_profiling": (_I32, [_P, _I32]),
     "pbng_get_profile": (_I32, [_P, ctypes.POINTER(PbngProfile)]),
+    "pbng_set_schedule": (_I32, [_P, ctypes.POINTER(PbngParams), ctypes.POINTER(PbngSchedule)]),
+    "pbng_get_schedule": (_I32, [_P, ctypes.POINTER(PbngSchedule)]),
+    "pbng_autotune": (_I32, [_P, _P, ctypes.POINTER(PbngParams), _I32, ctypes.POINTER(PbngSchedule)]),
     "pbng_num_components": (_I32, [_P]),
     "pbng_status_string": (ctypes.c_char_p, [_I32]),
     "pbng_last_error": (ctypes.c_char_p, [_P]),

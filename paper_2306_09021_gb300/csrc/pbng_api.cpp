@@ -61,6 +61,9 @@ struct pbng_mesh {
     bool built_direct = false;         // layout built with want_direct
     std::vector<int32_t> table_partial_off;  // residual partial offset per colour
     int32_t total_partials = 0;
+    std::vector<RingSched> sched;      // per colour launch schedule of the ring passes
+    double tune_default_ms = 0.0, tune_ms = 0.0;
+    int32_t tune_cands = 0;
 
     // device buffers
     DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
@@ -356,6 +359,11 @@ pbng_status build_layout(pbng_mesh* m) {
             t.total_blocks += (v - b + per_block - 1) / per_block;
         }
         m->ring_colour[c] = (fits && !m->want_direct) ? 1 : 0;
+    }
+    if ((int)m->sched.size() != m->ncol) {
+        m->sched.assign(m->ncol, RingSched{ring_max_ctas_per_sm(), 0});
+        m->tune_default_ms = m->tune_ms = 0.0;
+        m->tune_cands = 0;
     }
     m->all_ring = true;
     int32_t direct_partials = 0;
@@ -729,7 +737,7 @@ pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool wi
             if ((r = mark(kProfColour))) return r;
             if (m->ring_colour[c])
                 PBNG_CUDA(m, launch_ring_pass(m->dm, cur, (const Item*)m->d_items.p + m->item_off[c],
-                                              m->item_off[c + 1] - m->item_off[c], pp, comp,
+                                              m->item_off[c + 1] - m->item_off[c], pp, comp, m->sched[c],
                                               (int32_t*)m->d_err.p, st));
             else
                 PBNG_CUDA(m, launch_colour_pass(m->dm, cur, m->tables[c], pp, comp, (int32_t*)m->d_err.p, st));
@@ -797,7 +805,11 @@ pbng_status run_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_r
         if (!m->cap_stream) PBNG_CUDA(m, cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         PBNG_CUDA(m, cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
-        pbng_status r = enqueue_chunk(m, p, K, with_res, m->p1_slot, false, &e.nkernels, m->cap_stream);
+        pbng_status r;
+        {
+            PdlScope pdl(true);  // each kernel of the chunk may start while its predecessor drains
+            r = enqueue_chunk(m, p, K, with_res, m->p1_slot, false, &e.nkernels, m->cap_stream);
+        }
         const cudaError_t ce = cudaStreamEndCapture(m->cap_stream, &graph);
         if (r) {
             if (graph) cudaGraphDestroy(graph);
@@ -1431,6 +1443,139 @@ pbng_status pbng_get_profile(pbng_mesh* m, pbng_profile* out) {
     out->incidences = m->ninc;
     out->ncolours = m->ncol;
     return PBNG_OK;
+}
+
+pbng_status pbng_get_schedule(pbng_mesh* m, pbng_schedule* out) {
+    if (!m || !out) return PBNG_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->ncolours = m->ncol;
+    for (int c = 0; c < std::min<int>(m->ncol, PBNG_MAX_COLOURS); ++c) {
+        const bool ring = c < (int)m->ring_colour.size() && m->ring_colour[c];
+        out->ctas_per_sm[c] = ring ? m->sched[c].ctas_per_sm : 0;
+        out->blocked[c] = ring ? m->sched[c].blocked : 0;
+    }
+    out->default_ms_per_sweep = m->tune_default_ms;
+    out->tuned_ms_per_sweep = m->tune_ms;
+    out->candidates = m->tune_cands;
+    return PBNG_OK;
+}
+
+pbng_status pbng_set_schedule(pbng_mesh* m, const pbng_params* p, const pbng_schedule* s) {
+    if (!m || !s) return PBNG_EINVAL;
+    pbng_params dp;
+    if (!p) {
+        pbng_default_params(&dp);
+        p = &dp;
+    }
+    if (!valid_params(p)) return fail(m, PBNG_EINVAL, "invalid pbng_params");
+    select_path(m, p);
+    pbng_status r = ensure_ready(m);
+    if (r) return r;
+    const int cap = ring_max_ctas_per_sm();
+    for (int c = 0; c < std::min<int>(std::min(s->ncolours, m->ncol), PBNG_MAX_COLOURS); ++c) {
+        m->sched[c].ctas_per_sm = std::max(1, std::min(cap, (int)s->ctas_per_sm[c]));
+        m->sched[c].blocked = s->blocked[c] ? 1 : 0;
+    }
+    m->tune_default_ms = m->tune_ms = 0.0;
+    m->tune_cands = 0;
+    destroy_graphs(m);
+    return PBNG_OK;
+}
+
+// Times every schedule of every ring colour on a scratch copy of u_dev.  One
+// timed "round" runs each candidate once over all colours (every colour pass
+// of a sweep with that candidate), so the candidates alternate in time and
+// share the clock and cache conditions; reps rounds are summed.
+pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p, int32_t reps,
+                          pbng_schedule* out) {
+    if (!m) return PBNG_EINVAL;
+    pbng_params dp;
+    if (!p) {
+        pbng_default_params(&dp);
+        p = &dp;
+    }
+    if (!valid_params(p) || reps < 1 || reps > 1000 || !u_dev) return fail(m, PBNG_EINVAL, "bad autotune arguments");
+    select_path(m, p);
+    pbng_status r = ensure_ready(m);
+    if (r) return r;
+    cudaStream_t st = m->stream;
+    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const PassParams pp{(float)p->step, (float)p->skip_tol};
+    const State scratch = state_of(m, 3);
+    const int cap = ring_max_ctas_per_sm();
+    std::vector<RingSched> cands{{cap, 0}};   // the default first
+    for (int cps = 1; cps <= cap; ++cps)
+        for (int b = 0; b < 2; ++b)
+            if (!(cps == cap && b == 0)) cands.push_back({cps, b});
+    const int nc = (int)cands.size(), ncol = m->ncol;
+    auto pass = [&](int c, RingSched sc) -> pbng_status {
+        if (m->ring_colour[c])
+            PBNG_CUDA(m, launch_ring_pass(m->dm, scratch, (const Item*)m->d_items.p + m->item_off[c],
+                                          m->item_off[c + 1] - m->item_off[c], pp, comp, sc,
+                                          (int32_t*)m->d_err.p, st));
+        else
+            PBNG_CUDA(m, launch_colour_pass(m->dm, scratch, m->tables[c], pp, comp, (int32_t*)m->d_err.p, st));
+        m->kernel_launches++;
+        return PBNG_OK;
+    };
+    PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, (const int32_t*)m->d_perm.p, (const float4*)m->d_dir_hi.p,
+                             (const float4*)m->d_dir_lo.p, scratch, st));
+    m->kernel_launches++;
+    for (int w = 0; w < 2; ++w)  // warm-up sweeps
+        for (int c = 0; c < ncol; ++c)
+            if (m->tables[c].total_blocks > 0 && (r = pass(c, cands[0]))) return r;
+    std::vector<double> t((size_t)ncol * nc, 0.0);
+    std::vector<cudaEvent_t> ev((size_t)2 * ncol * nc, nullptr);
+    pbng_status res = PBNG_OK;
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            res = fail(m, PBNG_ECUDA, "cudaEventCreate");
+            break;
+        }
+    for (int k = 0; k < reps && res == PBNG_OK; ++k) {
+        for (int ci = 0; ci < nc && res == PBNG_OK; ++ci)
+            for (int c = 0; c < ncol && res == PBNG_OK; ++c) {
+                if (m->tables[c].total_blocks <= 0) continue;
+                cudaEvent_t* e = &ev[2 * ((size_t)ci * ncol + c)];
+                if (cudaEventRecord(e[0], st) != cudaSuccess) res = fail(m, PBNG_ECUDA, "cudaEventRecord");
+                if (res == PBNG_OK) res = pass(c, m->ring_colour[c] ? cands[ci] : cands[0]);
+                if (res == PBNG_OK && cudaEventRecord(e[1], st) != cudaSuccess)
+                    res = fail(m, PBNG_ECUDA, "cudaEventRecord");
+            }
+        if (res == PBNG_OK && cudaStreamSynchronize(st) != cudaSuccess) res = fail(m, PBNG_ECUDA, "synchronize");
+        for (int ci = 0; ci < nc && res == PBNG_OK; ++ci)
+            for (int c = 0; c < ncol; ++c) {
+                if (m->tables[c].total_blocks <= 0) continue;
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, ev[2 * ((size_t)ci * ncol + c)], ev[2 * ((size_t)ci * ncol + c) + 1]) !=
+                    cudaSuccess) {
+                    res = fail(m, PBNG_ECUDA, "cudaEventElapsedTime");
+                    break;
+                }
+                t[(size_t)c * nc + ci] += ms;
+            }
+    }
+    for (auto& e : ev)
+        if (e) cudaEventDestroy(e);
+    if (res) return res;
+    if ((r = check_err(m))) return r;
+    double t_def = 0.0, t_new = 0.0;
+    for (int c = 0; c < ncol; ++c) {
+        int best = 0;
+        if (m->ring_colour[c])
+            for (int ci = 1; ci < nc; ++ci)
+                if (t[(size_t)c * nc + ci] < t[(size_t)c * nc + best]) best = ci;
+        if (t[(size_t)c * nc + best] > 0.98 * t[(size_t)c * nc]) best = 0;
+        m->sched[c] = cands[best];
+        t_def += t[(size_t)c * nc];
+        t_new += t[(size_t)c * nc + best];
+    }
+    destroy_graphs(m);
+    m->tune_default_ms = t_def / reps;
+    m->tune_ms = t_new / reps;
+    m->tune_cands = nc;
+    return out ? pbng_get_schedule(m, out) : PBNG_OK;
 }
 
 int32_t pbng_num_components(const pbng_mesh* m) { return m ? m->ncomp : 0; }

@@ -84,6 +84,20 @@ struct Item {
 constexpr int kRingLanes = 32;
 
 // Host launch wrappers (pbng_kernels.cu).  All enqueue on `st`.
+// Programmatic dependent launch for the sweep kernels (colour passes,
+// acceleration, residual): on while a chunk of sweeps is captured into a
+// graph, off for plain launches (timed per launch with events) and for
+// everything else.  Per host thread; PdlScope restores the previous value.
+void set_pdl(bool on);
+bool pdl_enabled();
+struct PdlScope {
+    bool old;
+    explicit PdlScope(bool on) : old(pdl_enabled()) { set_pdl(on); }
+    ~PdlScope() { set_pdl(old); }
+    PdlScope(const PdlScope&) = delete;
+    PdlScope& operator=(const PdlScope&) = delete;
+};
+
 cudaError_t launch_colour_pass(const DeviceMesh& m, State s, const SegmentTable& t, PassParams p,
                                bool compensated, int32_t* err, cudaStream_t st);
 cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t, bool compensated,
@@ -101,10 +115,17 @@ cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st);
 // items with TMA bulk copies and cp.async gathers.  The residual writes one
 // FP64 partial per warp of the grid (ring_warps(nitems) of them) or, with
 // comp_sq, per-component sums.
+// A colour pass's launch schedule: CTAs per SM of the persistent grid
+// (1..ring_max_ctas_per_sm()) and the item order (0 strided, 1 blocked).
+struct RingSched {
+    int ctas_per_sm;
+    int blocked;
+};
 int ring_warps(int nitems);
+int ring_max_ctas_per_sm();
 cudaError_t ring_prepare();  // sets kernel attributes (call outside stream capture)
 cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
-                             bool compensated, int32_t* err, cudaStream_t st);
+                             bool compensated, RingSched sc, int32_t* err, cudaStream_t st);
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
                                  bool compensated, double* warp_partial, double* comp_sq,
                                  int32_t* err, cudaStream_t st);

@@ -16,6 +16,7 @@
 // Residual norms are accumulated in float64.
 #include "pbng_element.cuh"
 #include "pbng_internal.h"
+#include "pbng_launch.cuh"
 
 #include <math.h>
 
@@ -103,6 +104,8 @@ template <bool COMP>
 __global__ void __launch_bounds__(kBlock) colour_pass_kernel(const DeviceMesh m, State s,
                                                              const SegmentTable t, PassParams pp,
                                                              int32_t* err) {
+    pdl_release();
+    pdl_wait();
     const Segment* sg = find_segment(t, blockIdx.x);
     dispatch<COMP, true>(m, s, sg, pp, err, nullptr, nullptr);
 }
@@ -113,6 +116,8 @@ template <bool COMP>
 __global__ void __launch_bounds__(kBlock) residual_kernel(const DeviceMesh m, State s,
                                                           const SegmentTable t, double* partial,
                                                           double* comp_sq, float* r_out) {
+    pdl_release();
+    pdl_wait();
     const Segment* sg = find_segment(t, blockIdx.x);
     double rr = 0.0;
     dispatch<COMP, false>(m, s, sg, PassParams{1.f, 0.f}, nullptr, &rr, r_out);
@@ -136,6 +141,8 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(const DeviceMesh m, St
 }
 
 __global__ void reduce_kernel(const double* partial, int n, double* out) {
+    pdl_release();
+    pdl_wait();
     __shared__ double sh[1024];
     double acc = 0.0;
     for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partial[k];
@@ -157,6 +164,8 @@ __global__ void reduce_kernel(const double* partial, int n, double* out) {
 template <bool COMP>
 __global__ void accel_kernel(int n, State cur, State p1, State p2, const float2* __restrict__ wg,
                              const int32_t* __restrict__ comp, const int32_t* __restrict__ active) {
+    pdl_release();
+    pdl_wait();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= n) return;
     if (active && !active[comp[v]]) return;  // frozen (converged) component
@@ -224,14 +233,18 @@ __global__ void copy_state_kernel(int n, State a, State b) {
 
 inline int blocks_for(int n, int b) { return (n + b - 1) / b; }
 
+thread_local bool g_pdl = false;
+
 }  // namespace
+
+void set_pdl(bool on) { g_pdl = on; }
+bool pdl_enabled() { return g_pdl; }
 
 cudaError_t launch_colour_pass(const DeviceMesh& m, State s, const SegmentTable& t, PassParams p,
                                bool compensated, int32_t* err, cudaStream_t st) {
     if (t.total_blocks <= 0) return cudaSuccess;
-    if (compensated) colour_pass_kernel<true><<<t.total_blocks, kBlock, 0, st>>>(m, s, t, p, err);
-    else colour_pass_kernel<false><<<t.total_blocks, kBlock, 0, st>>>(m, s, t, p, err);
-    return cudaGetLastError();
+    if (compensated) return launch_kernel(colour_pass_kernel<true>, t.total_blocks, kBlock, 0, st, m, s, t, p, err);
+    return launch_kernel(colour_pass_kernel<false>, t.total_blocks, kBlock, 0, st, m, s, t, p, err);
 }
 
 cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t, bool compensated,
@@ -240,25 +253,24 @@ cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t,
     (void)ncomp;  // comp_sq is zeroed by the caller once per residual evaluation
     if (t.total_blocks <= 0) return cudaSuccess;
     if (compensated)
-        residual_kernel<true><<<t.total_blocks, kBlock, 0, st>>>(m, s, t, block_partial, comp_sq, r_out);
-    else
-        residual_kernel<false><<<t.total_blocks, kBlock, 0, st>>>(m, s, t, block_partial, comp_sq, r_out);
-    return cudaGetLastError();
+        return launch_kernel(residual_kernel<true>, t.total_blocks, kBlock, 0, st, m, s, t, block_partial, comp_sq,
+                             r_out);
+    return launch_kernel(residual_kernel<false>, t.total_blocks, kBlock, 0, st, m, s, t, block_partial, comp_sq,
+                         r_out);
 }
 
 cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStream_t st) {
-    reduce_kernel<<<1, 1024, 0, st>>>(partial, n, out);
-    return cudaGetLastError();
+    return launch_kernel(reduce_kernel, 1, 1024, 0, st, partial, (int)n, out);
 }
 
 cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, const float2* wg,
                          const int32_t* comp, const int32_t* comp_active, bool compensated, cudaStream_t st) {
     if (nfree <= 0) return cudaSuccess;
     if (compensated)
-        accel_kernel<true><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, wg, comp, comp_active);
-    else
-        accel_kernel<false><<<blocks_for(nfree, 256), 256, 0, st>>>(nfree, cur, p1, p2, wg, comp, comp_active);
-    return cudaGetLastError();
+        return launch_kernel(accel_kernel<true>, blocks_for(nfree, 256), 256, 0, st, (int)nfree, cur, p1, p2, wg, comp,
+                             comp_active);
+    return launch_kernel(accel_kernel<false>, blocks_for(nfree, 256), 256, 0, st, (int)nfree, cur, p1, p2, wg, comp,
+                         comp_active);
 }
 
 cudaError_t launch_load(int32_t nv, int32_t nfree, const float* u_user, const int32_t* perm,

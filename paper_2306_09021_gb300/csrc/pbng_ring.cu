@@ -18,12 +18,18 @@
 //     incident tet;
 //   * the compute forms u_j - u_i once per 1-ring vertex, passes the three a
 //     tet needs to its lane by warp shuffles, evaluates the element term
-//     (pbng_element.cuh), sums the W lanes, and the group's first lane solves
-//     and writes the vertex (Eq. pbgn_dx, Eq. pbgn_update).
+//     (pbng_element.cuh), sums the W lanes and adds the vertex terms; the
+//     group's first lane queues the vertex's force and Hessian;
+//   * when the warp's queue is nearly full (and at the end) all 32 lanes
+//     solve and write one queued vertex each (Eq. pbgn_dx, Eq. pbgn_update),
+//     instead of one lane per W-lane group solving while the others idle.
 // Everything gathered by a pass belongs to other colours or to the item's own
-// vertices, which only their own group writes.
+// vertices, which only their own group writes; the vertices of one colour
+// share no tet, so deferring their writes to the end of a queue changes
+// nothing that another update of the same pass reads.
 #include "pbng_element.cuh"
 #include "pbng_internal.h"
+#include "pbng_launch.cuh"
 
 #include <stdint.h>
 
@@ -38,6 +44,7 @@ constexpr int kRecStages = 3;
 constexpr int kGatStages = 2;
 constexpr int kItemVerts = kRingLanes / 4;
 constexpr int kCtasPerSm = 3;
+constexpr int kQueue = 32;   // deferred vertex updates per warp
 
 struct __align__(16) RecStage {
     float4 ra[kRingLanes];
@@ -55,9 +62,18 @@ struct __align__(16) GatStage {
     float4 a1[kItemVerts];   // aux1 (spring target, n.X - d)
 };
 
+// Force r (3) and modified Hessian A (6, upper triangle) of queued vertices,
+// structure of arrays so the flush reads without bank conflicts; v = -1 marks
+// a frozen vertex that is not written.
+struct __align__(16) UpdQueue {
+    float val[9][kQueue];
+    int32_t v[kQueue];
+};
+
 struct __align__(16) WarpSmem {
     RecStage rec[kRecStages];
     GatStage gat[kGatStages];
+    UpdQueue q;
     Item desc[kRecStages];
     unsigned long long bar[kRecStages];
 };
@@ -163,9 +179,8 @@ __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& 
 }
 
 template <int W, bool COMP, bool UPDATE>
-__device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, const WarpSmem& S, int r, int g,
-                                               int lane, PassParams pp, int32_t* err, double& rr,
-                                               double* comp_sq) {
+__device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, WarpSmem& S, int r, int g,
+                                               int lane, int qn, double& rr, double* comp_sq) {
     const Item it = S.desc[r];
     if (it.skip) return;  // uniform over the warp
     const RecStage& R = S.rec[r];
@@ -199,8 +214,13 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, con
     el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
     const int v = it.v0 + j;
     if (UPDATE) {
-        if (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) return;  // frozen vertex of a mixed item
-        el::solve_and_write<COMP>(s, v, uh, ul, rv, A, pp, err);
+        const int e = qn + j;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) S.q.val[k][e] = rv[k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) S.q.val[3 + k][e] = A[k];
+        // a frozen vertex of a mixed item is not written
+        S.q.v[e] = (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) ? -1 : v;
     } else {
         const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];
         if (comp_sq) atomicAdd(comp_sq + m.comp[v], q);
@@ -210,27 +230,65 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, con
 
 // The lane width is uniform over an item: dispatch once per item.
 template <bool COMP, bool UPDATE>
-__device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, const WarpSmem& S, int r, int g,
-                                             int lane, PassParams pp, int32_t* err, double& rr,
-                                             double* comp_sq) {
+__device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, WarpSmem& S, int r, int g,
+                                             int lane, int qn, double& rr, double* comp_sq) {
     switch (S.desc[r].w) {
-        case 4: compute_item_w<4, COMP, UPDATE>(m, s, S, r, g, lane, pp, err, rr, comp_sq); break;
-        case 8: compute_item_w<8, COMP, UPDATE>(m, s, S, r, g, lane, pp, err, rr, comp_sq); break;
-        case 16: compute_item_w<16, COMP, UPDATE>(m, s, S, r, g, lane, pp, err, rr, comp_sq); break;
-        default: compute_item_w<32, COMP, UPDATE>(m, s, S, r, g, lane, pp, err, rr, comp_sq); break;
+        case 4: compute_item_w<4, COMP, UPDATE>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
+        case 8: compute_item_w<8, COMP, UPDATE>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
+        case 16: compute_item_w<16, COMP, UPDATE>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
+        default: compute_item_w<32, COMP, UPDATE>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
     }
 }
 
+// All lanes: solve and write the qn queued vertices, one per lane.  The own
+// displacement is read again here; no other update of the pass writes it.
+template <bool COMP>
+__device__ __forceinline__ void flush_queue(State s, const WarpSmem& S, int qn, int lane, PassParams pp,
+                                            int32_t* err) {
+    __syncwarp();
+    if (lane < qn) {
+        const int v = S.q.v[lane];
+        if (v >= 0) {
+            float rv[3], A[6];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) rv[k] = S.q.val[k][lane];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) A[k] = S.q.val[3 + k][lane];
+            const float3 uh = f3(s.hi[v]);
+            const float3 ul = COMP ? f3(s.lo[v]) : make_float3(0.f, 0.f, 0.f);
+            el::solve_and_write<COMP>(s, v, uh, ul, rv, A, pp, err);
+        }
+    }
+    __syncwarp();
+}
+
+// Item order of a pass: strided (warp gw takes items gw, gw + nw, ...) or
+// blocked (warp gw takes a contiguous run of ceil(nitems / nw) items).  The
+// order only decides which warp updates which vertices of one colour; the
+// updates of a colour are independent, so the iterate is the same.
 template <bool COMP, bool UPDATE>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm)
     ring_kernel(const DeviceMesh m, State s, const Item* __restrict__ items, int nitems, PassParams pp,
-                int32_t* err, double* partial, double* comp_sq) {
+                int32_t* err, double* partial, double* comp_sq, int blocked) {
     extern __shared__ __align__(128) unsigned char smem[];
+    pdl_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem& S = reinterpret_cast<WarpSmem*>(smem)[warp];
     const int gw = (int)blockIdx.x * kWarps + warp, nw = (int)gridDim.x * kWarps;
-    const int n = gw < nitems ? (nitems - gw + nw - 1) / nw : 0;
+    int n, first, stride;
+    if (blocked) {
+        const int per = (nitems + nw - 1) / nw;
+        first = gw * per;
+        stride = 1;
+        n = nitems - first < per ? nitems - first : per;
+        if (n < 0) n = 0;
+    } else {
+        first = gw;
+        stride = nw;
+        n = gw < nitems ? (nitems - gw + nw - 1) / nw : 0;
+    }
     double rr = 0.0;
+    int qn = 0;                  // queued vertex updates (warp-uniform)
     int issued = 0, waited = 0;  // items whose records were requested / awaited
     bool ok = true;
     Item next{};                 // lane 0: next item to request, loaded one item early
@@ -238,12 +296,15 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         if (lane == 0) {
             for (int i = 0; i < kRecStages; ++i) mbar_init(S.bar + i, 1);
             fence_mbar_init();
-            issue_records(m, items[gw], S, 0);
-            if (n > 1) issue_records(m, items[gw + nw], S, 1);
-            if (n > 2) next = items[gw + 2 * nw];
+            issue_records(m, items[first], S, 0);
+            if (n > 1) issue_records(m, items[first + stride], S, 1);
+            if (n > 2) next = items[first + 2 * stride];
         }
         issued = n < 2 ? n : 2;
         __syncwarp();
+        // Records, items and component flags are written by no kernel; the
+        // iterate read from here on is written by the previous kernel.
+        pdl_wait();
         ok = mbar_wait(S.bar + 0, 0);
         waited = 1;
         if (__any_sync(kFull, !ok)) goto abort;
@@ -256,7 +317,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
                 if (lane == 0) {
                     fence_proxy_async();
                     issue_records(m, next, S, (k + 2) % kRecStages);
-                    if (k + 3 < n) next = items[gw + (k + 3) * nw];
+                    if (k + 3 < n) next = items[first + (k + 3) * stride];
                 }
                 issued = k + 3;
             }
@@ -270,11 +331,20 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
             cp_async_wait<1>();  // this lane's gathers of item k have landed
             if (__any_sync(kFull, !ok)) goto abort;
             __syncwarp();        // ... and the other lanes'
-            compute_item<COMP, UPDATE>(m, s, S, k % kRecStages, k % kGatStages, lane, pp, err, rr, comp_sq);
+            compute_item<COMP, UPDATE>(m, s, S, k % kRecStages, k % kGatStages, lane, qn, rr, comp_sq);
+            if (UPDATE) {
+                const Item& it = S.desc[k % kRecStages];
+                if (!it.skip) qn += it.nv;
+                if (qn > kQueue - kItemVerts || (k + 1 == n && qn > 0)) {
+                    flush_queue<COMP>(s, S, qn, lane, pp, err);
+                    qn = 0;
+                }
+            }
             __syncwarp();
         }
     }
     if (!UPDATE && partial) {
+        if (n == 0) pdl_wait();  // idle warp: order its write after the predecessor
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
         if (lane == 0) partial[gw] = rr;
@@ -305,48 +375,57 @@ int sm_count() {
     return cached[dev];
 }
 
-int ring_ctas(int nitems) {
+int ring_ctas(int nitems, int ctas_per_sm) {
     const int want = (nitems + kWarps - 1) / kWarps;
-    const int cap = kCtasPerSm * sm_count();
+    const int cps = ctas_per_sm < 1 ? 1 : (ctas_per_sm > kCtasPerSm ? kCtasPerSm : ctas_per_sm);
+    const int cap = cps * sm_count();
     return want < cap ? want : cap;
 }
 
 template <bool COMP, bool UPDATE>
 cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams pp,
-                        int32_t* err, double* partial, double* comp_sq, cudaStream_t st) {
+                        int32_t* err, double* partial, double* comp_sq, RingSched sc, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const int bytes = kWarps * (int)sizeof(WarpSmem);  // attribute set by ring_prepare()
-    ring_kernel<COMP, UPDATE><<<ring_ctas(nitems), kBlock, bytes, st>>>(m, s, items, nitems, pp, err, partial,
-                                                                       comp_sq);
-    return cudaGetLastError();
+    return launch_kernel(ring_kernel<COMP, UPDATE>, ring_ctas(nitems, sc.ctas_per_sm), kBlock, bytes, st, m, s, items,
+                         nitems, pp, err, partial, comp_sq, sc.blocked);
 }
 
 }  // namespace
 
-int ring_warps(int nitems) { return nitems > 0 ? ring_ctas(nitems) * kWarps : 0; }
+int ring_warps(int nitems) { return nitems > 0 ? ring_ctas(nitems, kCtasPerSm) * kWarps : 0; }
+
+int ring_max_ctas_per_sm() { return kCtasPerSm; }
 
 cudaError_t ring_prepare() {
+    // Three CTAs of 8 warps with their per-warp stages and queues need almost
+    // all of an SM's shared memory: ask for the largest carveout.
     const int bytes = kWarps * (int)sizeof(WarpSmem);
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(ring_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-    if ((e = cudaFuncSetAttribute(ring_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-    if ((e = cudaFuncSetAttribute(ring_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))) return e;
-    return cudaFuncSetAttribute(ring_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const void* fns[4] = {(const void*)ring_kernel<true, true>, (const void*)ring_kernel<false, true>,
+                          (const void*)ring_kernel<true, false>, (const void*)ring_kernel<false, false>};
+    for (const void* f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
-                             bool compensated, int32_t* err, cudaStream_t st) {
-    if (compensated) return launch_impl<true, true>(m, s, items, nitems, p, err, nullptr, nullptr, st);
-    return launch_impl<false, true>(m, s, items, nitems, p, err, nullptr, nullptr, st);
+                             bool compensated, RingSched sc, int32_t* err, cudaStream_t st) {
+    if (compensated) return launch_impl<true, true>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
+    return launch_impl<false, true>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
 }
 
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
                                  bool compensated, double* warp_partial, double* comp_sq, int32_t* err,
                                  cudaStream_t st) {
     const PassParams pp{1.f, 0.f};
+    const RingSched sc{kCtasPerSm, 0};  // ring_warps() partials
     double* part = comp_sq ? nullptr : warp_partial;
-    if (compensated) return launch_impl<true, false>(m, s, items, nitems, pp, err, part, comp_sq, st);
-    return launch_impl<false, false>(m, s, items, nitems, pp, err, part, comp_sq, st);
+    if (compensated) return launch_impl<true, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
+    return launch_impl<false, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
 }
 
 }  // namespace pbng

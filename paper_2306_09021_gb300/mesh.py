@@ -9,7 +9,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import ACCEL, PRECISION, PbngParams, PbngProfile, check, load
+from ._lib import ACCEL, PRECISION, PbngParams, PbngProfile, PbngSchedule, check, load
 
 
 def _dptr(a):
@@ -181,6 +181,38 @@ class Mesh:
         """pbng_set_state: restore a checkpoint taken on an identical mesh."""
         buf = ctypes.create_string_buffer(bytes(blob), len(blob))
         check(load().pbng_set_state(self.h, buf, len(blob)), "pbng_set_state", self.h)
+
+    @staticmethod
+    def _schedule_dict(s):
+        n = min(s.ncolours, len(s.ctas_per_sm))
+        return {"ncolours": s.ncolours, "ctas_per_sm": list(s.ctas_per_sm[:n]), "blocked": list(s.blocked[:n]),
+                "default_ms_per_sweep": s.default_ms_per_sweep, "tuned_ms_per_sweep": s.tuned_ms_per_sweep,
+                "candidates": s.candidates}
+
+    def schedule(self):
+        """pbng_get_schedule as a dict (per-colour ctas_per_sm and blocked)."""
+        s = PbngSchedule()
+        check(load().pbng_get_schedule(self.h, ctypes.byref(s)), "pbng_get_schedule", self.h)
+        return self._schedule_dict(s)
+
+    def set_schedule(self, ctas_per_sm, blocked, params=None):
+        """pbng_set_schedule from per-colour lists."""
+        s = PbngSchedule()
+        s.ncolours = len(ctas_per_sm)
+        for c, (a, b) in enumerate(zip(ctas_per_sm, blocked)):
+            s.ctas_per_sm[c] = int(a)
+            s.blocked[c] = int(b)
+        p = params if params is not None else default_params()
+        check(load().pbng_set_schedule(self.h, ctypes.byref(p), ctypes.byref(s)), "pbng_set_schedule", self.h)
+
+    def autotune(self, u, reps=10, params=None):
+        """pbng_autotune on a scratch copy of u; returns the chosen schedule."""
+        _check_u(u, self.nv)
+        s = PbngSchedule()
+        p = params if params is not None else default_params()
+        check(load().pbng_autotune(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.byref(p), int(reps),
+                                   ctypes.byref(s)), "pbng_autotune", self.h)
+        return self._schedule_dict(s)
 
     def set_profiling(self, enable=True):
         """pbng_set_profiling: per-launch event timing of the library's kernels."""
