@@ -59,7 +59,10 @@ typedef struct {
     int32_t model;          /* 0 = fixed corotated (Eq. cor); no other model yet  */
     int32_t accel;          /* PBNG_ACCEL_*                                        */
     double omega;           /* SOR weight (Section "Acceleration Techniques": 1.7) */
-    double rho;             /* Chebyshev spectral estimate (0.95)                  */
+    double rho;             /* Chebyshev spectral estimate (0.95).  rho <= 0 with
+                               PBNG_ACCEL_CHEBYSHEV: pbng_solve estimates it from
+                               its FP64 residual checks (pbng_get_solve_info);
+                               pbng_sweep rejects it.                              */
     double gamma;           /* Chebyshev relaxation (1.7)                          */
     double step;            /* scale of the Newton step of Eq. pbgn_dx (1.0)       */
     double skip_tol;        /* skip nodes with |r_i| <= skip_tol; 0 = never skip   */
@@ -288,6 +291,27 @@ pbng_status pbng_get_schedule(pbng_mesh* m, pbng_schedule* out);
  * the chosen schedules from the same rounds.  Synchronises; reps in 1..1000. */
 pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p, int32_t reps,
                           pbng_schedule* out);
+
+/* What the last pbng_solve ran with.  With automatic rho (Chebyshev,
+ * rho <= 0) pbng_solve first runs max(30, 3 residual_every) plain sweeps,
+ * takes the per-sweep contraction q = (r_b / r_a)^(1 / (b - a)) of the
+ * slowest active component between the residual check a at or after a third
+ * of them and the last one b, sets rho = clamp(1 - 2 (1 - q), 0.5, 0.98) and
+ * restarts the Chebyshev schedule (omega_1 = omega_2 = 1, x^{-1} = x^0) at
+ * the current iterate.  The Chebyshev weights assume the iteration's error
+ * modes decay with real factors up to rho; colour-ordered Gauss-Seidel on
+ * more than two colours does not guarantee that, and a rho at the measured
+ * rate itself can diverge, hence the factor 2 and the cap.  A residual check
+ * whose worst component exceeds 4x the best seen since the last (re)start
+ * doubles 1 - rho and restarts the schedule; after 4 such back-offs the
+ * remaining sweeps are plain.  The estimate is not kept across calls. */
+typedef struct {
+    double rho;              /* Chebyshev rho in use at the end (0: none)     */
+    double plain_rate;       /* automatic rho: measured q; else 0              */
+    int32_t estimate_sweeps; /* automatic rho: plain sweeps before Chebyshev   */
+    int32_t restarts;        /* automatic rho: divergence back-offs            */
+} pbng_solve_info;
+pbng_status pbng_get_solve_info(const pbng_mesh* m, pbng_solve_info* out);
 
 /* Number of independent components (1 unless mesh_id was given). */
 int32_t pbng_num_components(const pbng_mesh* m);

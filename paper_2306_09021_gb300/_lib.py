@@ -70,6 +70,15 @@ class PbngSchedule(ctypes.Structure):
     ]
 
 
+class PbngSolveInfo(ctypes.Structure):
+    _fields_ = [
+        ("rho", ctypes.c_double),
+        ("plain_rate", ctypes.c_double),
+        ("estimate_sweeps", ctypes.c_int32),
+        ("restarts", ctypes.c_int32),
+    ]
+
+
 class PbngError(RuntimeError):
     def __init__(self, status, where, detail=""):
         self.status = status
@@ -105,6 +114,7 @@ SIGNATURES = {
     "pbng_set_schedule": (_I32, [_P, ctypes.POINTER(PbngParams), ctypes.POINTER(PbngSchedule)]),
     "pbng_get_schedule": (_I32, [_P, ctypes.POINTER(PbngSchedule)]),
     "pbng_autotune": (_I32, [_P, _P, ctypes.POINTER(PbngParams), _I32, ctypes.POINTER(PbngSchedule)]),
+    "pbng_get_solve_info": (_I32, [_P, ctypes.POINTER(PbngSolveInfo)]),
     "pbng_num_components": (_I32, [_P]),
     "pbng_status_string": (ctypes.c_char_p, [_I32]),
     "pbng_last_error": (ctypes.c_char_p, [_P]),

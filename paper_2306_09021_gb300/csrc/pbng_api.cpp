@@ -61,6 +61,7 @@ struct pbng_mesh {
     bool built_direct = false;         // layout built with want_direct
     std::vector<int32_t> table_partial_off;  // residual partial offset per colour
     int32_t total_partials = 0;
+    pbng_solve_info info{};            // of the last pbng_solve
     std::vector<RingSched> sched;      // per colour launch schedule of the ring passes
     double tune_default_ms = 0.0, tune_ms = 0.0;
     int32_t tune_cands = 0;
@@ -1027,6 +1028,8 @@ pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_p
                        double* rel_residual_out) {
     if (!m) return PBNG_EINVAL;
     if (!valid_params(p) || nsweeps < 0) return fail(m, PBNG_EINVAL, "bad parameters");
+    if (p->accel == PBNG_ACCEL_CHEBYSHEV && !(p->rho > 0.0))
+        return fail(m, PBNG_EINVAL, "automatic rho (rho <= 0) needs the residual checks of pbng_solve");
     select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
@@ -1102,11 +1105,45 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     if (cv == 1) result = PBNG_OK;
     const int32_t K = std::min<int32_t>(p->residual_every, kMaxChunk);
     if ((s = ensure_wg(m, (size_t)K))) return s;
+    // Chebyshev with rho <= 0: rho from the FP64 residuals.  Plain sweeps
+    // first; from the residual ratio over the last two thirds of them, the
+    // per-sweep contraction q of the slowest active component; then
+    // rho = clamp(1 - 2 (1 - q), 0.5, 0.98) and the Chebyshev schedule
+    // restarts at the current iterate.  A check whose worst residual exceeds
+    // 4x the best one seen since the last (re)start backs rho off
+    // (1 - rho doubles) and restarts; after kMaxBackoffs the sweeps go plain.
+    pbng_params cp = *p;
+    const bool auto_rho = p->accel == PBNG_ACCEL_CHEBYSHEV && !(p->rho > 0.0);
+    const int32_t est_sweeps = std::max<int32_t>(30, 3 * K);
+    constexpr int kMaxBackoffs = 4;
+    int phase = auto_rho ? 0 : 1;
+    int32_t mark_done = -1;
+    std::vector<double> mark_rel(m->ncomp, 0.0);
+    double best = 0.0;
+    m->info = pbng_solve_info{};
+    m->info.rho = (p->accel == PBNG_ACCEL_CHEBYSHEV && !auto_rho) ? p->rho : 0.0;
+    if (auto_rho) cp.accel = PBNG_ACCEL_NONE;
+    auto restart_history = [&]() -> pbng_status {
+        PBNG_CUDA(m, launch_copy_state(m->nv, state_of(m, 0), state_of(m, m->p1_slot), m->stream));
+        PBNG_CUDA(m, launch_copy_state(m->nv, state_of(m, 0), state_of(m, m->p2_slot), m->stream));
+        m->kernel_launches += 2;
+        m->sweep_l = 0;
+        m->omega_l = 1.0;
+        best = 0.0;
+        return PBNG_OK;
+    };
+    auto worst_active = [&]() {
+        double w = 0.0;
+        for (int k = 0; k < m->ncomp; ++k)
+            if (!frozen[k]) w = std::max(w, rel[k]);
+        return w;
+    };
     while (cv == 0 && done < max_sweeps) {
         // one graph launch: the chunk's sweeps and the residual (synchronised
         // below, so the weight staging can be reused)
-        const int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
-        if ((s = run_chunk(m, p, chunk, true, m->h_wg))) return s;
+        int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
+        if (phase == 0) chunk = std::min<int32_t>(chunk, est_sweeps - done);
+        if ((s = run_chunk(m, &cp, chunk, true, m->h_wg))) return s;
         done += chunk;
         if ((s = check_err(m))) return s;
         for (int k = 0; k < m->ncomp; ++k) sq[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
@@ -1116,6 +1153,35 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
                                          cudaMemcpyHostToDevice, m->stream));
         if (cv == 1) result = PBNG_OK;
         if (cv < 0) result = PBNG_EDIVERGED;
+        if (cv != 0 || !auto_rho) continue;
+        if (phase == 0) {
+            if (mark_done < 0 && 3 * done >= est_sweeps) {
+                mark_done = done;
+                mark_rel = rel;
+            } else if (done >= est_sweeps && mark_done >= 0 && done > mark_done) {
+                double q = 0.0;
+                for (int k = 0; k < m->ncomp; ++k)
+                    if (!frozen[k] && mark_rel[k] > 0.0 && rel[k] > 0.0)
+                        q = std::max(q, std::pow(rel[k] / mark_rel[k], 1.0 / (done - mark_done)));
+                if (!(q < 1.0)) q = 0.9999;
+                cp.accel = PBNG_ACCEL_CHEBYSHEV;
+                cp.rho = std::min(0.98, std::max(0.5, 1.0 - 2.0 * (1.0 - q)));
+                m->info.plain_rate = q;
+                m->info.estimate_sweeps = done;
+                m->info.rho = cp.rho;
+                phase = 1;
+                if ((s = restart_history())) return s;
+            }
+        } else if (cp.accel == PBNG_ACCEL_CHEBYSHEV) {
+            const double w = worst_active();
+            if (best == 0.0 || w < best) best = w;
+            else if (w > 4.0 * best) {
+                if (++m->info.restarts > kMaxBackoffs) cp.accel = PBNG_ACCEL_NONE;
+                else cp.rho = std::max(0.5, 1.0 - 2.0 * (1.0 - cp.rho));
+                m->info.rho = cp.accel == PBNG_ACCEL_CHEBYSHEV ? cp.rho : 0.0;
+                if ((s = restart_history())) return s;
+            }
+        }
     }
     PBNG_CUDA(m, launch_store(m->nv, (const int32_t*)m->d_perm.p, state_of(m, 0), u_dev, m->stream));
     m->kernel_launches++;
@@ -1576,6 +1642,12 @@ pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p
     m->tune_ms = t_new / reps;
     m->tune_cands = nc;
     return out ? pbng_get_schedule(m, out) : PBNG_OK;
+}
+
+pbng_status pbng_get_solve_info(const pbng_mesh* m, pbng_solve_info* out) {
+    if (!m || !out) return PBNG_EINVAL;
+    *out = m->info;
+    return PBNG_OK;
 }
 
 int32_t pbng_num_components(const pbng_mesh* m) { return m ? m->ncomp : 0; }

@@ -9,7 +9,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import ACCEL, PRECISION, PbngParams, PbngProfile, PbngSchedule, check, load
+from ._lib import ACCEL, PRECISION, PbngParams, PbngProfile, PbngSchedule, PbngSolveInfo, check, load
 
 
 def _dptr(a):
@@ -161,6 +161,12 @@ class Mesh:
         if raise_on_status:
             check(st, "pbng_solve", self.h)
         return st, sweeps.value, out
+
+    def solve_info(self):
+        """pbng_get_solve_info of the last solve as a dict."""
+        i = PbngSolveInfo()
+        check(load().pbng_get_solve_info(self.h, ctypes.byref(i)), "pbng_get_solve_info", self.h)
+        return {k: getattr(i, k) for k, _ in PbngSolveInfo._fields_}
 
     def residual(self, u):
         """pbng_residual: absolute FP64 residual norms per component."""
