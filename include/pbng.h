@@ -54,9 +54,26 @@ typedef struct pbng_mesh pbng_mesh;   /* opaque, library-owned */
 
 enum { PBNG_ACCEL_NONE = 0, PBNG_ACCEL_CHEBYSHEV = 1, PBNG_ACCEL_SOR = 2 };
 enum { PBNG_PREC_FP32 = 0, PBNG_PREC_COMPENSATED = 1 };
+/* Constitutive models (Section "Constitutive Models"), mu and lambda from
+ * Eq. lame:
+ *   PBNG_MODEL_COROTATED   Eq. cor, mu |F - R|^2 + (lambda/2)(J - 1)^2
+ *   PBNG_MODEL_NEOHOOKEAN  Eq. nh, (mu/2)|F|^2 + (lambda_hat/2)(J - 1 - mu/lambda_hat)^2,
+ *                          lambda_hat = mu + lambda
+ *   PBNG_MODEL_STABLE_NEOHOOKEAN  Eq. snh read with lambda' on its volume
+ *                          term: (mu'/2)(|F|^2 - 3) + (lambda'/2)(J - alpha)^2
+ *                          - (mu'/2) log(1 + |F|^2), alpha = 1 + 3mu'/(4lambda'),
+ *                          mu' = 4mu/3, lambda' = lambda + 5mu/6, so that its
+ *                          Hessian at F = I is linear elasticity's (Section
+ *                          "Lame Coefficients"). */
+enum { PBNG_MODEL_COROTATED = 0, PBNG_MODEL_NEOHOOKEAN = 1, PBNG_MODEL_STABLE_NEOHOOKEAN = 2 };
 
 typedef struct {
-    int32_t model;          /* 0 = fixed corotated (Eq. cor); no other model yet  */
+    int32_t model;          /* PBNG_MODEL_*: the energy density of Section
+                               "Constitutive Models".  The nodal Hessian is
+                               Eq. mod_hess_dens for every model.  The handle
+                               keeps the model of its last sweep / solve /
+                               autotune; pbng_residual uses it.  pbng_adjoint
+                               supports PBNG_MODEL_COROTATED only.               */
     int32_t accel;          /* PBNG_ACCEL_*                                        */
     double omega;           /* SOR weight (Section "Acceleration Techniques": 1.7) */
     double rho;             /* Chebyshev spectral estimate (0.95).  rho <= 0 with

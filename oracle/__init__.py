@@ -46,9 +46,10 @@ def lib():
             "ora_lame": (None, [ctypes.c_double, ctypes.c_double, _D, _D]),
             "ora_svd3": (ctypes.c_int, [_D, _D, _D, _D]),
             "ora_polar": (None, [_D, _D, _D]),
-            "ora_psi": (ctypes.c_double, [_D, ctypes.c_double, ctypes.c_double]),
-            "ora_pk1": (None, [_D, ctypes.c_double, ctypes.c_double, _D]),
-            "ora_dpk1": (None, [_D, _D, ctypes.c_double, ctypes.c_double, _D]),
+            "ora_psi": (ctypes.c_double, [_D, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+            "ora_pk1": (None, [_D, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]),
+            "ora_dpk1": (None, [_D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]),
+            "ora_set_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
             "ora_cofactor": (None, [_D, _D]),
             "ora_modified_density_hessian": (None, [_D, ctypes.c_double, ctypes.c_double, _D]),
             "ora_create": (ctypes.c_void_p, [ctypes.c_int, _D, ctypes.c_int, _I, _D, _D, _U8,
@@ -110,22 +111,29 @@ def polar(F):
     return R, sh
 
 
-def psi(F, mu, lam):
+MODELS = {"corotated": 0, "neohookean": 1, "stable_neohookean": 2}
+
+
+def _model(model):
+    return MODELS[model] if isinstance(model, str) else int(model)
+
+
+def psi(F, mu, lam, model=0):
     F = _f64(F, (3, 3))
-    return lib().ora_psi(_d(F), mu, lam)
+    return lib().ora_psi(_d(F), mu, lam, _model(model))
 
 
-def pk1(F, mu, lam):
+def pk1(F, mu, lam, model=0):
     F = _f64(F, (3, 3))
     P = np.zeros((3, 3))
-    lib().ora_pk1(_d(F), mu, lam, _d(P))
+    lib().ora_pk1(_d(F), mu, lam, _model(model), _d(P))
     return P
 
 
-def dpk1(F, dF, mu, lam):
+def dpk1(F, dF, mu, lam, model=0):
     F, dF = _f64(F, (3, 3)), _f64(dF, (3, 3))
     dP = np.zeros((3, 3))
-    lib().ora_dpk1(_d(F), _d(dF), mu, lam, _d(dP))
+    lib().ora_dpk1(_d(F), _d(dF), mu, lam, _model(model), _d(dP))
     return dP
 
 
@@ -177,9 +185,16 @@ class OracleMesh:
             raise ValueError(f"oracle mesh rejected (status {st_code.value})")
 
     @classmethod
-    def from_problem(cls, p):
-        return cls(p.X, p.tets, p.young, p.poisson, p.dirichlet_mask(), p.body_accel,
-                   p.density, p.spr_idx, p.spr_target, p.spr_k, p.plane, p.k_contact)
+    def from_problem(cls, p, model=0):
+        m = cls(p.X, p.tets, p.young, p.poisson, p.dirichlet_mask(), p.body_accel,
+                p.density, p.spr_idx, p.spr_target, p.spr_k, p.plane, p.k_contact)
+        m.set_model(model)
+        return m
+
+    def set_model(self, model):
+        """Constitutive model: 0 / 'corotated', 1 / 'neohookean', 2 / 'stable_neohookean'."""
+        if lib().ora_set_model(self.h, _model(model)) != 0:
+            raise ValueError(f"unknown model {model!r}")
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -214,27 +214,111 @@ void polar(const double* F, double* R, double* shat) {
     if (shat) { shat[0] = s[0]; shat[1] = s[1]; shat[2] = sg * s[2]; }
 }
 
-double psi(const double* F, double mu, double lam) {
-    double R[9];
+// Models of Section "Constitutive Models": 0 corotated (Eq. cor), 1
+// Neo-Hookean in the Macklin-Mueller form (Eq. nh, lambda_hat = mu + lambda),
+// 2 stable Neo-Hookean (Eq. snh).  The printed Eq. snh has no lambda on its
+// volume term; it is read as Smith et al.'s (lambda/2)(J - alpha)^2 with
+// alpha = 1 + 3 mu'/(4 lambda'), and, as Section "Lame Coefficients"
+// requires of a model set from Lame coefficients, its Hessian at F = I is
+// made equal to linear elasticity's by Smith et al.'s mu' = 4 mu / 3,
+// lambda' = lambda + 5 mu / 6.
+enum { kCorotated = 0, kNeoHookean = 1, kStableNeoHookean = 2 };
+
+void snh_params(double mu, double lam, double* mus, double* lams, double* alpha) {
+    *mus = 4.0 * mu / 3.0;
+    *lams = lam + 5.0 * mu / 6.0;
+    *alpha = 1.0 + 3.0 * (*mus) / (4.0 * (*lams));
+}
+
+double frob2(const double* F) {
+    double n2 = 0.0;
+    for (int i = 0; i < 9; ++i) n2 += F[i] * F[i];
+    return n2;
+}
+
+double psi(const double* F, double mu, double lam, int model) {
+    const double J = det3(F);
+    if (model == kNeoHookean) {  // Eq. nh
+        const double lh = mu + lam, c = J - 1.0 - mu / lh;
+        return 0.5 * mu * frob2(F) + 0.5 * lh * c * c;
+    }
+    if (model == kStableNeoHookean) {  // Eq. snh
+        double mus, lams, alpha;
+        snh_params(mu, lam, &mus, &lams, &alpha);
+        const double ic = frob2(F);
+        return 0.5 * mus * (ic - 3.0) + 0.5 * lams * (J - alpha) * (J - alpha) - 0.5 * mus * std::log(1.0 + ic);
+    }
+    double R[9];  // Eq. cor
     polar(F, R, nullptr);
     double n2 = 0.0;
     for (int i = 0; i < 9; ++i) n2 += (F[i] - R[i]) * (F[i] - R[i]);
-    double J = det3(F);
     return mu * n2 + 0.5 * lam * (J - 1.0) * (J - 1.0);
 }
 
-void pk1(const double* F, double mu, double lam, double* P) {
-    double R[9], C[9];
-    polar(F, R, nullptr);
+// P = dPsi/dF.  With C = cof F = dJ/dF:
+//   corotated  2 mu (F - R) + lambda (J - 1) C
+//   NH         mu F + lambda_hat (J - 1 - mu / lambda_hat) C
+//   SNH        mu' (1 - 1 / (1 + |F|^2)) F + lambda' (J - alpha) C
+void pk1(const double* F, double mu, double lam, int model, double* P) {
+    double C[9];
     cof3(F, C);
-    double J = det3(F);
+    const double J = det3(F);
+    if (model == kNeoHookean) {
+        const double lh = mu + lam, k = lh * (J - 1.0 - mu / lh);
+        for (int i = 0; i < 9; ++i) P[i] = mu * F[i] + k * C[i];
+        return;
+    }
+    if (model == kStableNeoHookean) {
+        double mus, lams, alpha;
+        snh_params(mu, lam, &mus, &lams, &alpha);
+        const double s = mus * (1.0 - 1.0 / (1.0 + frob2(F))), k = lams * (J - alpha);
+        for (int i = 0; i < 9; ++i) P[i] = s * F[i] + k * C[i];
+        return;
+    }
+    double R[9];
+    polar(F, R, nullptr);
     for (int i = 0; i < 9; ++i) P[i] = 2.0 * mu * (F[i] - R[i]) + lam * (J - 1.0) * C[i];
 }
 
-// dP = 2mu(dF - dR) + lam (C:dF) C + lam (J-1) dC, with dR = R [w]_x where
-// (tr S I - S) w = axial(R^T dF - dF^T R), S = R^T F, and dC the bilinear
-// part of the quadratic map F -> cof F.
-void dpk1(const double* F, const double* dF, double mu, double lam, double* dP) {
+// The bilinear part dC of F -> cof F in direction dF: cof(F + dF) - cof F - cof dF.
+void dcof3(const double* F, const double* dF, double* dC) {
+    double Fp[9], Cp[9], C[9], Cd[9];
+    for (int i = 0; i < 9; ++i) Fp[i] = F[i] + dF[i];
+    cof3(Fp, Cp);
+    cof3(F, C);
+    cof3(dF, Cd);
+    for (int i = 0; i < 9; ++i) dC[i] = Cp[i] - C[i] - Cd[i];
+}
+
+// dP = (d^2 Psi / dF^2) : dF (the density Hessian of Eq. hess).
+//   corotated  2mu(dF - dR) + lam (C:dF) C + lam (J-1) dC, dR = R [w]_x with
+//              (tr S I - S) w = axial(R^T dF - dF^T R), S = R^T F
+//   NH         mu dF + lambda_hat (C:dF) C + lambda_hat (J - 1 - mu/lambda_hat) dC
+//   SNH        mu' (1 - 1/(1+|F|^2)) dF + mu' 2 (F:dF) / (1+|F|^2)^2 F
+//              + lambda' (C:dF) C + lambda' (J - alpha) dC
+void dpk1(const double* F, const double* dF, double mu, double lam, int model, double* dP) {
+    if (model == kNeoHookean || model == kStableNeoHookean) {
+        double C[9], dC[9];
+        cof3(F, C);
+        dcof3(F, dF, dC);
+        const double J = det3(F);
+        double CdF = 0.0, FdF = 0.0;
+        for (int i = 0; i < 9; ++i) {
+            CdF += C[i] * dF[i];
+            FdF += F[i] * dF[i];
+        }
+        if (model == kNeoHookean) {
+            const double lh = mu + lam, k = lh * (J - 1.0 - mu / lh);
+            for (int i = 0; i < 9; ++i) dP[i] = mu * dF[i] + lh * CdF * C[i] + k * dC[i];
+        } else {
+            double mus, lams, alpha;
+            snh_params(mu, lam, &mus, &lams, &alpha);
+            const double q = 1.0 + frob2(F);
+            const double s = mus * (1.0 - 1.0 / q), t = mus * 2.0 * FdF / (q * q), k = lams * (J - alpha);
+            for (int i = 0; i < 9; ++i) dP[i] = s * dF[i] + t * F[i] + lams * CdF * C[i] + k * dC[i];
+        }
+        return;
+    }
     double R[9], S[9], RtdF[9];
     polar(F, R, nullptr);
     mat_mul_tn(R, F, S);
@@ -277,6 +361,7 @@ struct Mesh {
     std::vector<double> spr_t, spr_k;
     bool has_plane = false;
     double pn[3] = {0, 0, 1}, pd = 0.0, kc = 0.0;
+    int model = kCorotated;                // Section "Constitutive Models"
     std::vector<int> colour;               // nv, -1 clamped
     std::vector<std::vector<int>> by_colour;
 };
@@ -336,7 +421,7 @@ void local_system(const Mesh& m, const double* x, int i, double* r, double* A) {
         int e = m.inc_tet[k];
         double F[9], P[9], C[9], g[3], Pg[3], w[3];
         deformation_gradient(m, x, e, F);
-        pk1(F, m.mu[e], m.lam[e], P);
+        pk1(F, m.mu[e], m.lam[e], m.model, P);
         cof3(F, C);
         grad(m, e, m.inc_loc[k], g);
         mat_vec(P, g, Pg);
@@ -398,7 +483,7 @@ double energy(const Mesh& m, const double* x) {
     for (int e = 0; e < m.ne; ++e) {
         double F[9];
         deformation_gradient(m, x, e, F);
-        E += m.vol[e] * psi(F, m.mu[e], m.lam[e]);
+        E += m.vol[e] * psi(F, m.mu[e], m.lam[e], m.model);
     }
     for (int i = 0; i < m.nv; ++i) {
         const double* xi = &x[3 * (size_t)i];
@@ -433,7 +518,7 @@ void hessian_dense(const Mesh& m, const double* x, std::vector<double>& H) {
             for (int b = 0; b < 3; ++b) {
                 double dF[9] = {0}, dP[9];
                 for (int c = 0; c < 3; ++c) dF[3 * b + c] = g[jb][c];
-                dpk1(F, dF, m.mu[e], m.lam[e], dP);
+                dpk1(F, dF, m.mu[e], m.lam[e], m.model, dP);
                 int col = 3 * m.tets[4 * (size_t)e + jb] + b;
                 for (int ja = 0; ja < 4; ++ja) {
                     double v[3];
@@ -477,10 +562,10 @@ void ora_lame(double E, double nu, double* mu, double* lam) {
 
 int ora_svd3(const double* F, double* U, double* s, double* V) { return svd3(F, U, s, V); }
 void ora_polar(const double* F, double* R, double* shat) { polar(F, R, shat); }
-double ora_psi(const double* F, double mu, double lam) { return psi(F, mu, lam); }
-void ora_pk1(const double* F, double mu, double lam, double* P) { pk1(F, mu, lam, P); }
-void ora_dpk1(const double* F, const double* dF, double mu, double lam, double* dP) {
-    dpk1(F, dF, mu, lam, dP);
+double ora_psi(const double* F, double mu, double lam, int model) { return psi(F, mu, lam, model); }
+void ora_pk1(const double* F, double mu, double lam, int model, double* P) { pk1(F, mu, lam, model, P); }
+void ora_dpk1(const double* F, const double* dF, double mu, double lam, int model, double* dP) {
+    dpk1(F, dF, mu, lam, model, dP);
 }
 void ora_cofactor(const double* F, double* C) { cof3(F, C); }
 
@@ -581,6 +666,12 @@ void* ora_create(int nv, const double* X, int ne, const int* tets, const double*
 }
 
 void ora_destroy(void* h) { delete static_cast<Mesh*>(h); }
+
+int ora_set_model(void* h, int model) {
+    if (model < kCorotated || model > kStableNeoHookean) return 1;
+    static_cast<Mesh*>(h)->model = model;
+    return 0;
+}
 
 int ora_num_colours(const void* h) { return (int)static_cast<const Mesh*>(h)->by_colour.size(); }
 
@@ -735,7 +826,7 @@ int ora_adjoint_dense(const void* h, const double* x, const double* dLdx, double
     for (int e = 0; e < m.ne; ++e) {
         double F[9], P[9], s = 0.0;
         deformation_gradient(m, x, e, F);
-        pk1(F, m.mu[e], m.lam[e], P);
+        pk1(F, m.mu[e], m.lam[e], m.model, P);
         for (int j = 0; j < 4; ++j) {
             int v = m.tets[4 * (size_t)e + j];
             if (m.dir[v]) continue;

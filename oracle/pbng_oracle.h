@@ -30,12 +30,16 @@ int ora_svd3(const double* F, double* U, double* s, double* V);
  * takes the sign of det F.  shat (may be NULL) receives the signed values. */
 void ora_polar(const double* F, double* R, double* shat);
 
-/* Fixed-corotated energy density, Eq. (cor). */
-double ora_psi(const double* F, double mu, double lam);
-/* First Piola-Kirchhoff stress P = dPsi/dF = 2mu(F-R) + lam(J-1) cof F. */
-void ora_pk1(const double* F, double mu, double lam, double* P);
-/* True energy-density Hessian applied to dF (used by the Newton oracle). */
-void ora_dpk1(const double* F, const double* dF, double mu, double lam, double* dP);
+/* Energy density of model 0 fixed corotated (Eq. cor), 1 Neo-Hookean
+ * (Eq. nh, lambda_hat = mu + lambda) or 2 stable Neo-Hookean (Eq. snh, with
+ * lambda on its volume term and Smith et al.'s mu' = 4mu/3,
+ * lambda' = lambda + 5mu/6, alpha = 1 + 3mu'/(4lambda')); mu, lambda are the
+ * Lame parameters of Eq. lame. */
+double ora_psi(const double* F, double mu, double lam, int model);
+/* First Piola-Kirchhoff stress P = dPsi/dF of the model. */
+void ora_pk1(const double* F, double mu, double lam, int model, double* P);
+/* True energy-density Hessian of the model applied to dF (Newton, adjoint). */
+void ora_dpk1(const double* F, const double* dF, double mu, double lam, int model, double* dP);
 /* Modified density Hessian, Eq. (mod_hess_dens):
  * C[(a*3+g)*9 + (b*3+d)] = 2mu d_ab d_gd + lam cof(F)_ag cof(F)_bd. */
 void ora_modified_density_hessian(const double* F, double mu, double lam, double* C81);
@@ -55,6 +59,10 @@ void* ora_create(int nv, const double* X, int ne, const int* tets,
                  int ns, const int* spr_idx, const double* spr_t, const double* spr_k,
                  const double* plane, double k_contact, int* status);
 void ora_destroy(void* h);
+/* Constitutive model of the mesh (0, 1, 2 as for ora_psi; default 0).  The
+ * modified Hessian of Eq. mod_hess_dens is the same for every model.
+ * Returns nonzero for an unknown model. */
+int ora_set_model(void* h, int model);
 
 /* Greedy node colouring of Section "Coloring and Parallelism". */
 int ora_num_colours(const void* h);

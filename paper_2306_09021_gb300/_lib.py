@@ -19,6 +19,7 @@ STATUS_NAMES = {
 
 ACCEL = {"none": 0, "chebyshev": 1, "sor": 2}
 PRECISION = {"fp32": 0, "compensated": 1}
+MODEL = {"corotated": 0, "neohookean": 1, "stable_neohookean": 2}
 
 
 class PbngParams(ctypes.Structure):

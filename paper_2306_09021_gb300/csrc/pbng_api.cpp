@@ -58,6 +58,7 @@ struct pbng_mesh {
     int32_t nitems_ring = 0;
     int32_t ring_partials = 0;         // residual partials of the ring launch
     bool want_direct = false;          // params.kernel_path == 1 requested
+    int model = 0;                     // constitutive model of the last sweep / solve (residuals use it)
     bool built_direct = false;         // layout built with want_direct
     std::vector<int32_t> table_partial_off;  // residual partial offset per colour
     int32_t total_partials = 0;
@@ -90,7 +91,7 @@ struct pbng_mesh {
 
     // captured chunks of sweeps (CUDA graphs), keyed by their configuration
     struct GraphEntry {
-        int32_t K, accel, prec, with_res, p1, prof;
+        int32_t K, accel, prec, with_res, p1, prof, model;
         float step, skip;
         cudaGraphExec_t exec = nullptr;
         int64_t nkernels = 0;
@@ -603,14 +604,14 @@ pbng_status enqueue_residual(pbng_mesh* m, State s, bool compensated, double* pa
     if (multi) PBNG_CUDA(m, cudaMemsetAsync(comp_sq, 0, sizeof(double) * m->ncomp, st));
     if (m->nitems_ring > 0) {
         PBNG_CUDA(m, launch_ring_residual(m->dm, s, (const Item*)m->d_items.p, m->nitems_ring, compensated,
-                                          partial, multi ? comp_sq : nullptr, (int32_t*)m->d_err.p, st));
+                                          partial, multi ? comp_sq : nullptr, m->model, (int32_t*)m->d_err.p, st));
         m->kernel_launches++;
     }
     for (int c = 0; c < m->ncol; ++c) {
         if (m->ring_colour[c]) continue;
         PBNG_CUDA(m, launch_residual(m->dm, s, m->tables[c], compensated,
                                      partial + m->ring_partials + m->table_partial_off[c],
-                                     multi ? comp_sq : nullptr, m->ncomp, nullptr, st));
+                                     multi ? comp_sq : nullptr, m->ncomp, nullptr, m->model, st));
         if (m->tables[c].total_blocks > 0) m->kernel_launches++;
     }
     if (!multi) {
@@ -652,12 +653,13 @@ pbng_status check_err(pbng_mesh* m) {
 // kernel_path 1 (direct loads everywhere) needs CSR records for every
 // colour: switching path rebuilds the layout (and drops the iterate history).
 void select_path(pbng_mesh* m, const pbng_params* p) {
+    m->model = p->model;
     m->want_direct = p->kernel_path == 1;
     if (m->want_direct != m->built_direct) m->dirty = true;
 }
 
 bool valid_params(const pbng_params* p) {
-    return p && p->model == 0 && p->accel >= 0 && p->accel <= 2 && p->residual_every >= 1 &&
+    return p && p->model >= 0 && p->model <= 2 && p->accel >= 0 && p->accel <= 2 && p->residual_every >= 1 &&
            (p->precision == PBNG_PREC_FP32 || p->precision == PBNG_PREC_COMPENSATED) &&
            std::isfinite(p->omega) && std::isfinite(p->rho) && std::isfinite(p->gamma) &&
            std::isfinite(p->step) && p->skip_tol >= 0.0 && (p->kernel_path == 0 || p->kernel_path == 1);
@@ -719,7 +721,7 @@ void chunk_weights(pbng_mesh* m, const pbng_params* p, int32_t K, float2* out) {
 pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_res, int p1,
                           bool prof, int64_t* nkernels, cudaStream_t st) {
     const bool comp = p->precision == PBNG_PREC_COMPENSATED;
-    const PassParams pp{(float)p->step, (float)p->skip_tol};
+    const PassParams pp{(float)p->step, (float)p->skip_tol, p->model};
     const State cur = state_of(m, 0);
     int p2 = 3 - p1;
     // With profiling (never inside a capture) each timed launch is bracketed
@@ -791,7 +793,7 @@ pbng_status run_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_r
     pbng_mesh::GraphEntry* g = nullptr;
     for (auto& e : m->graphs)
         if (e.K == K && e.accel == accel && e.prec == p->precision && e.with_res == (int)with_res &&
-            e.p1 == m->p1_slot && e.step == (float)p->step && e.skip == (float)p->skip_tol)
+            e.p1 == m->p1_slot && e.step == (float)p->step && e.skip == (float)p->skip_tol && e.model == p->model)
             g = &e;
     if (!g) {
         pbng_mesh::GraphEntry e;
@@ -803,6 +805,7 @@ pbng_status run_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_r
         e.prof = 0;
         e.step = (float)p->step;
         e.skip = (float)p->skip_tol;
+        e.model = p->model;
         if (!m->cap_stream) PBNG_CUDA(m, cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         PBNG_CUDA(m, cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1262,6 +1265,7 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
     if (!u_eq_dev || !dLdu_dev || !dL_dlogE_dev) return fail(m, PBNG_EINVAL, "NULL argument");
     if (p->kernel_path != 0) return fail(m, PBNG_EINVAL, "the adjoint runs on the ring layout (kernel_path 0)");
+    if (p->model != 0) return fail(m, PBNG_EINVAL, "the adjoint supports the corotated model (model 0) only");
     select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
@@ -1566,7 +1570,7 @@ pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p
     if (r) return r;
     cudaStream_t st = m->stream;
     const bool comp = p->precision == PBNG_PREC_COMPENSATED;
-    const PassParams pp{(float)p->step, (float)p->skip_tol};
+    const PassParams pp{(float)p->step, (float)p->skip_tol, p->model};
     const State scratch = state_of(m, 3);
     const int cap = ring_max_ctas_per_sm();
     std::vector<RingSched> cands{{cap, 0}};   // the default first

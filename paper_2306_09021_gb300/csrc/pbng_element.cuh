@@ -1,7 +1,7 @@
 // Per-element and per-vertex arithmetic of the PBNG node update, shared by
-// the direct kernels (pbng_kernels.cu) and the pipelined kernels
-// (pbng_pipeline.cu).  All of it is float32; see pbng_kernels.cu for the
-// precision scheme.
+// the direct kernels (pbng_kernels.cu), the ring-layout kernels
+// (pbng_ring.cu) and the adjoint (pbng_adjoint.cu).  All of it is float32,
+// formed relative to the rest state so that nothing cancels as F -> I.
 #pragma once
 
 #include "pbng_internal.h"
@@ -137,14 +137,29 @@ __device__ __forceinline__ void rotation_minus_identity(const float* H, float n2
 
 // Contribution of one incident tetrahedron to the force r and modified
 // Hessian A (upper triangle a00 a01 a02 a11 a12 a22) of vertex i:
-//   r -= V P(F) g_i,  P = 2 mu (F - R) + lambda (J - 1) cof F
-//   A += V (2 mu |g_i|^2 I + lambda w w^T),  w = cof(F) g_i
+//   r -= V P(F) g_i,  A += V (2 mu |g_i|^2 I + lambda w w^T),  w = cof(F) g_i
 // with F = I + sum_{j != i} (u_j - u_i) g_j^T and g_i = -(g_j1 + g_j2 + g_j3).
+// A is Eq. mod_hess_dens for every model (Section "Lame Coefficients").
 // gk = dN_jk/dX of the other three vertices, a = 2 mu V, b = lambda V,
-// dk = u_jk - u_i.
-template <bool NEED_A>
-__device__ __forceinline__ void element_math(float3 gj1, float3 gj2, float3 gj3, float a, float b,
-                                             float3 d1, float3 d2, float3 d3, float* r, float* A) {
+// dk = u_jk - u_i.  P (Section "Constitutive Models"), with C = cof F and
+// H = F - I:
+//   kCorotated (Eq. cor)  V P g = a (H - (R - I)) g + b (J - 1) w
+//   kNeoHookean (Eq. nh, lambda_hat = mu + lambda):
+//     P = mu (F - C) + lambda_hat (J - 1) C,
+//     V P g = (a/2) (F - C) g + (a/2 + b) (J - 1) w
+//   kStableNeoHookean (Eq. snh with lambda on the volume term and the Lame
+//     reparametrisation mu' = 4 mu / 3, lambda' = lambda + 5 mu / 6,
+//     alpha = 1 + 3 mu' / (4 lambda') that makes its Hessian at F = I the
+//     linear-elasticity one):
+//     P = (3 mu'/4) (F - C) + mu' (I_C - 3) / (4 (1 + I_C)) F + lambda' (J - 1) C,
+//     V P g = (a/2) (F - C) g + (a/6) (I_C - 3) / (1 + I_C) F g + (b + 5a/12) (J - 1) w
+// where F - C = H + H^T - tr(H) I - cof(H) and I_C - 3 = 2 tr H + |H|^2 are
+// formed from H, so the Neo-Hookean stresses keep relative accuracy at rest.
+enum { kCorotated = 0, kNeoHookean = 1, kStableNeoHookean = 2 };
+
+template <bool NEED_A, int MODEL>
+__device__ __forceinline__ void element_math_m(float3 gj1, float3 gj2, float3 gj3, float a, float b,
+                                               float3 d1, float3 d2, float3 d3, float* r, float* A) {
     const float g1[3] = {gj1.x, gj1.y, gj1.z}, g2[3] = {gj2.x, gj2.y, gj2.z}, g3[3] = {gj3.x, gj3.y, gj3.z};
     const float dd1[3] = {d1.x, d1.y, d1.z}, dd2[3] = {d2.x, d2.y, d2.z}, dd3[3] = {d3.x, d3.y, d3.z};
     float H[9];
@@ -167,25 +182,63 @@ __device__ __forceinline__ void element_math(float3 gj1, float3 gj2, float3 gj3,
     C[7] = F2 * F3 - F0 * F5;
     C[8] = F0 * F4 - F1 * F3;
     // J - 1 = tr H + (sum of principal 2x2 minors of H) + det H.
-    const float Jm1 = (H[0] + H[4] + H[8]) +
-                      (H[0] * H[4] - H[1] * H[3] + H[0] * H[8] - H[2] * H[6] + H[4] * H[8] - H[5] * H[7]) +
+    const float trH = H[0] + H[4] + H[8];
+    const float Jm1 = trH + (H[0] * H[4] - H[1] * H[3] + H[0] * H[8] - H[2] * H[6] + H[4] * H[8] - H[5] * H[7]) +
                       det3(H[0], H[1], H[2], H[3], H[4], H[5], H[6], H[7], H[8]);
-    float n2 = 0.0f, c2 = 0.0f;
-    const float Fm[9] = {F0, F1, F2, F3, F4, F5, F6, F7, F8};
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        n2 += Fm[k] * Fm[k];
-        c2 += C[k] * C[k];
-    }
-    float RmI[9];
-    rotation_minus_identity(H, n2, c2, 1.0f + Jm1, RmI);
     float w[3];
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-        w[p] = C[3 * p] * gi[0] + C[3 * p + 1] * gi[1] + C[3 * p + 2] * gi[2];
-        const float fr = (H[3 * p] - RmI[3 * p]) * gi[0] + (H[3 * p + 1] - RmI[3 * p + 1]) * gi[1] +
-                         (H[3 * p + 2] - RmI[3 * p + 2]) * gi[2];
-        r[p] -= a * fr + b * Jm1 * w[p];
+    for (int p = 0; p < 3; ++p) w[p] = C[3 * p] * gi[0] + C[3 * p + 1] * gi[1] + C[3 * p + 2] * gi[2];
+    if (MODEL == kCorotated) {
+        float n2 = 0.0f, c2 = 0.0f;
+        const float Fm[9] = {F0, F1, F2, F3, F4, F5, F6, F7, F8};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            n2 += Fm[k] * Fm[k];
+            c2 += C[k] * C[k];
+        }
+        float RmI[9];
+        rotation_minus_identity(H, n2, c2, 1.0f + Jm1, RmI);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const float fr = (H[3 * p] - RmI[3 * p]) * gi[0] + (H[3 * p + 1] - RmI[3 * p + 1]) * gi[1] +
+                             (H[3 * p + 2] - RmI[3 * p + 2]) * gi[2];
+            r[p] -= a * fr + b * Jm1 * w[p];
+        }
+    } else {
+        // cof(H), then F - C = H + H^T - tr(H) I - cof(H)
+        float K[9];
+        K[0] = H[4] * H[8] - H[5] * H[7];
+        K[1] = H[5] * H[6] - H[3] * H[8];
+        K[2] = H[3] * H[7] - H[4] * H[6];
+        K[3] = H[7] * H[2] - H[8] * H[1];
+        K[4] = H[8] * H[0] - H[6] * H[2];
+        K[5] = H[6] * H[1] - H[7] * H[0];
+        K[6] = H[1] * H[5] - H[2] * H[4];
+        K[7] = H[2] * H[3] - H[0] * H[5];
+        K[8] = H[0] * H[4] - H[1] * H[3];
+        const float ha = 0.5f * a;
+        float qs = 0.0f, kv = ha + b;
+        if (MODEL == kStableNeoHookean) {
+            float hh = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) hh += H[k] * H[k];
+            const float ic3 = 2.0f * trH + hh;                  // I_C - 3
+            qs = (a * (1.0f / 6.0f)) * __fdividef(ic3, 4.0f + ic3);
+            kv = b + a * (5.0f / 12.0f);
+        }
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            float fc = 0.0f, hg = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const float fmc = H[3 * p + q] + H[3 * q + p] - (p == q ? trH : 0.0f) - K[3 * p + q];
+                fc += fmc * gi[q];
+                hg += H[3 * p + q] * gi[q];
+            }
+            float t = ha * fc + kv * Jm1 * w[p];
+            if (MODEL == kStableNeoHookean) t += qs * (gi[p] + hg);
+            r[p] -= t;
+        }
     }
     if (NEED_A) {
         const float ag = a * (gi[0] * gi[0] + gi[1] * gi[1] + gi[2] * gi[2]);
@@ -196,6 +249,18 @@ __device__ __forceinline__ void element_math(float3 gj1, float3 gj2, float3 gj3,
         A[4] += b * w[1] * w[2];
         A[5] += ag + b * w[2] * w[2];
     }
+}
+
+// The model is uniform over a launch (PassParams::model): one branch per call.
+template <bool NEED_A>
+__device__ __forceinline__ void element_math(int model, float3 gj1, float3 gj2, float3 gj3, float a, float b,
+                                             float3 d1, float3 d2, float3 d3, float* r, float* A) {
+    if (model == kNeoHookean)
+        element_math_m<NEED_A, kNeoHookean>(gj1, gj2, gj3, a, b, d1, d2, d3, r, A);
+    else if (model == kStableNeoHookean)
+        element_math_m<NEED_A, kStableNeoHookean>(gj1, gj2, gj3, a, b, d1, d2, d3, r, A);
+    else
+        element_math_m<NEED_A, kCorotated>(gj1, gj2, gj3, a, b, d1, d2, d3, r, A);
 }
 
 // Body force, weak springs and plane contact of a vertex at displacement

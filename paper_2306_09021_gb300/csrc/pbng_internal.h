@@ -61,6 +61,7 @@ struct State {
 struct PassParams {
     float step;       // scale of the Newton step
     float skip_tol;   // 0 = never skip
+    int model;        // constitutive model: 0 corotated, 1 Neo-Hookean, 2 stable Neo-Hookean
 };
 
 // Error bits written by the kernels (OR-ed into a device word).
@@ -102,7 +103,7 @@ cudaError_t launch_colour_pass(const DeviceMesh& m, State s, const SegmentTable&
                                bool compensated, int32_t* err, cudaStream_t st);
 cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t, bool compensated,
                             double* block_partial, double* comp_sq, int32_t ncomp,
-                            float* r_out, cudaStream_t st);
+                            float* r_out, int model, cudaStream_t st);
 cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStream_t st);
 cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, const float2* wg,
                          const int32_t* comp, const int32_t* comp_active, bool compensated, cudaStream_t st);
@@ -127,7 +128,7 @@ cudaError_t ring_prepare();  // sets kernel attributes (call outside stream capt
 cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
                              bool compensated, RingSched sc, int32_t* err, cudaStream_t st);
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
-                                 bool compensated, double* warp_partial, double* comp_sq,
+                                 bool compensated, double* warp_partial, double* comp_sq, int model,
                                  int32_t* err, cudaStream_t st);
 
 // Equilibrium adjoint (pbng_adjoint.cu).  Vertex kernels: one warp per

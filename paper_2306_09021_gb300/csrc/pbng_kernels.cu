@@ -54,7 +54,7 @@ __device__ __forceinline__ void vertex_group(const DeviceMesh& m, State s, int v
         const float3 d1 = el::pair_diff<COMP>(__ldg(s.hi + j1), COMP ? __ldg(s.lo + j1) : zero4, uh, ul);
         const float3 d2 = el::pair_diff<COMP>(__ldg(s.hi + j2), COMP ? __ldg(s.lo + j2) : zero4, uh, ul);
         const float3 d3 = el::pair_diff<COMP>(__ldg(s.hi + j3), COMP ? __ldg(s.lo + j3) : zero4, uh, ul);
-        el::element_math<UPDATE>(make_float3(rb.x, rb.y, rb.z), make_float3(rc.x, rc.y, rc.z),
+        el::element_math<UPDATE>(pp.model, make_float3(rb.x, rb.y, rb.z), make_float3(rc.x, rc.y, rc.z),
                                  make_float3(rc.w, rd.x, rd.y), ra.w, rb.w, d1, d2, d3, r, A);
     }
 #pragma unroll
@@ -115,12 +115,12 @@ __global__ void __launch_bounds__(kBlock) colour_pass_kernel(const DeviceMesh m,
 template <bool COMP>
 __global__ void __launch_bounds__(kBlock) residual_kernel(const DeviceMesh m, State s,
                                                           const SegmentTable t, double* partial,
-                                                          double* comp_sq, float* r_out) {
+                                                          double* comp_sq, float* r_out, int model) {
     pdl_release();
     pdl_wait();
     const Segment* sg = find_segment(t, blockIdx.x);
     double rr = 0.0;
-    dispatch<COMP, false>(m, s, sg, PassParams{1.f, 0.f}, nullptr, &rr, r_out);
+    dispatch<COMP, false>(m, s, sg, PassParams{1.f, 0.f, model}, nullptr, &rr, r_out);
     if (comp_sq) {
         const int tid = (blockIdx.x - sg->block_begin) * kBlock + threadIdx.x;
         const int v = sg->v_begin + tid / sg->width;
@@ -248,15 +248,15 @@ cudaError_t launch_colour_pass(const DeviceMesh& m, State s, const SegmentTable&
 }
 
 cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t, bool compensated,
-                            double* block_partial, double* comp_sq, int32_t ncomp, float* r_out,
+                            double* block_partial, double* comp_sq, int32_t ncomp, float* r_out, int model,
                             cudaStream_t st) {
     (void)ncomp;  // comp_sq is zeroed by the caller once per residual evaluation
     if (t.total_blocks <= 0) return cudaSuccess;
     if (compensated)
         return launch_kernel(residual_kernel<true>, t.total_blocks, kBlock, 0, st, m, s, t, block_partial, comp_sq,
-                             r_out);
+                             r_out, model);
     return launch_kernel(residual_kernel<false>, t.total_blocks, kBlock, 0, st, m, s, t, block_partial, comp_sq,
-                         r_out);
+                         r_out, model);
 }
 
 cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStream_t st) {

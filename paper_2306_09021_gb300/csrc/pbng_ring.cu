@@ -180,7 +180,7 @@ __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& 
 
 template <int W, bool COMP, bool UPDATE>
 __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, WarpSmem& S, int r, int g,
-                                               int lane, int qn, double& rr, double* comp_sq) {
+                                               int lane, int qn, int model, double& rr, double* comp_sq) {
     const Item it = S.desc[r];
     if (it.skip) return;  // uniform over the warp
     const RecStage& R = S.rec[r];
@@ -203,7 +203,7 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
     const float3 d3 = make_float3(__shfl_sync(kFull, d.x, s3), __shfl_sync(kFull, d.y, s3), __shfl_sync(kFull, d.z, s3));
     float rv[3] = {0.f, 0.f, 0.f};
     float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    el::element_math<UPDATE>(f3(ra), f3(rb), f3(rc), ra.w, rb.w, d1, d2, d3, rv, A);
+    el::element_math<UPDATE>(model, f3(ra), f3(rb), f3(rc), ra.w, rb.w, d1, d2, d3, rv, A);
 #pragma unroll
     for (int k = 0; k < 3; ++k) rv[k] = el::group_sum<W>(rv[k]);
     if (UPDATE) {
@@ -231,12 +231,12 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
 // The lane width is uniform over an item: dispatch once per item.
 template <bool COMP, bool UPDATE>
 __device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, WarpSmem& S, int r, int g,
-                                             int lane, int qn, double& rr, double* comp_sq) {
+                                             int lane, int qn, int model, double& rr, double* comp_sq) {
     switch (S.desc[r].w) {
-        case 4: compute_item_w<4, COMP, UPDATE>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
-        case 8: compute_item_w<8, COMP, UPDATE>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
-        case 16: compute_item_w<16, COMP, UPDATE>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
-        default: compute_item_w<32, COMP, UPDATE>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
+        case 4: compute_item_w<4, COMP, UPDATE>(m, s, S, r, g, lane, qn, model, rr, comp_sq); break;
+        case 8: compute_item_w<8, COMP, UPDATE>(m, s, S, r, g, lane, qn, model, rr, comp_sq); break;
+        case 16: compute_item_w<16, COMP, UPDATE>(m, s, S, r, g, lane, qn, model, rr, comp_sq); break;
+        default: compute_item_w<32, COMP, UPDATE>(m, s, S, r, g, lane, qn, model, rr, comp_sq); break;
     }
 }
 
@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
             cp_async_wait<1>();  // this lane's gathers of item k have landed
             if (__any_sync(kFull, !ok)) goto abort;
             __syncwarp();        // ... and the other lanes'
-            compute_item<COMP, UPDATE>(m, s, S, k % kRecStages, k % kGatStages, lane, qn, rr, comp_sq);
+            compute_item<COMP, UPDATE>(m, s, S, k % kRecStages, k % kGatStages, lane, qn, pp.model, rr, comp_sq);
             if (UPDATE) {
                 const Item& it = S.desc[k % kRecStages];
                 if (!it.skip) qn += it.nv;
@@ -419,9 +419,9 @@ cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, in
 }
 
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
-                                 bool compensated, double* warp_partial, double* comp_sq, int32_t* err,
+                                 bool compensated, double* warp_partial, double* comp_sq, int model, int32_t* err,
                                  cudaStream_t st) {
-    const PassParams pp{1.f, 0.f};
+    const PassParams pp{1.f, 0.f, model};
     const RingSched sc{kCtasPerSm, 0};  // ring_warps() partials
     double* part = comp_sq ? nullptr : warp_partial;
     if (compensated) return launch_impl<true, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);

@@ -9,7 +9,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import ACCEL, PRECISION, PbngParams, PbngProfile, PbngSchedule, PbngSolveInfo, check, load
+from ._lib import ACCEL, MODEL, PRECISION, PbngParams, PbngProfile, PbngSchedule, PbngSolveInfo, check, load
 
 
 def _dptr(a):
@@ -21,9 +21,10 @@ def _iptr(a):
 
 
 def default_params(**kw):
-    """pbng_default_params, then overrides: accel ('none'|'chebyshev'|'sor'),
-    precision ('fp32'|'compensated'), omega, rho, gamma, step, skip_tol,
-    residual_every, resume."""
+    """pbng_default_params, then overrides: model ('corotated'|'neohookean'|
+    'stable_neohookean'), accel ('none'|'chebyshev'|'sor'), precision
+    ('fp32'|'compensated'), omega, rho, gamma, step, skip_tol, residual_every,
+    resume, kernel_path."""
     p = PbngParams()
     load().pbng_default_params(ctypes.byref(p))
     for k, v in kw.items():
@@ -31,6 +32,8 @@ def default_params(**kw):
             v = ACCEL[v] if isinstance(v, str) else int(v)
         elif k == "precision":
             v = PRECISION[v] if isinstance(v, str) else int(v)
+        elif k == "model":
+            v = MODEL[v] if isinstance(v, str) else int(v)
         setattr(p, k, v)
     return p
 

@@ -1,0 +1,113 @@
+"""GPU parity of the Neo-Hookean (Eq. nh) and stable Neo-Hookean (Eq. snh)
+sweeps against the FP64 oracle of the same model, through the C ABI."""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MODELS = ["neohookean", "stable_neohookean"]
+RES_FLOOR = 1e-5  # relative-residual target of the float32 path
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_09021_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+
+
+def _u0(p):
+    return torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+
+
+@pytest.mark.parametrize("model", MODELS)
+@pytest.mark.parametrize("accel", ["none", "chebyshev", "sor"])
+def test_twist_block_200_sweeps(model, accel):
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.twist_block(10, 90.0, 0.3)
+    kw = dict(accel=accel, omega=1.5) if accel == "sor" else dict(accel=accel)
+    m = Mesh.from_problem(p)
+    u = _u0(p)
+    rel = m.sweep(u, 200, default_params(model=model, **kw), want_residual=True)
+    om = oracle.OracleMesh.from_problem(p, model=model)
+    x_ora, st = om.sweeps(p.x0, 200, **kw)
+    assert st == 0
+    x_gpu = u.cpu().double().numpy() + p.X
+    err = np.abs(x_gpu - x_ora).max() / np.abs(x_ora - p.X).max()
+    assert err <= 1e-5, err
+    rr = om.residual(x_ora) / om.residual(p.x0)
+    assert abs(rel[0] - rr) <= 1e-3 * rr + RES_FLOOR
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_residual_uses_the_model_of_the_last_sweep(model):
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.gravity_sag(6)
+    m = Mesh.from_problem(p)
+    u = _u0(p)
+    m.sweep(u, 15, default_params(model=model))
+    x = u.cpu().double().numpy() + p.X
+    r_gpu = m.residual(u)[0]
+    r_ora = oracle.OracleMesh.from_problem(p, model=model).residual(x)
+    r_cor = oracle.OracleMesh.from_problem(p).residual(x)
+    assert abs(r_gpu - r_ora) <= 1e-4 * r_ora + 1e-6 * oracle.OracleMesh.from_problem(p).residual(p.x0)
+    assert abs(r_cor - r_ora) > 1e-2 * r_ora   # the models really differ here
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_solve_reaches_newton_equilibrium_of_the_model(model):
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.twist_block(3, 90.0, 0.3)
+    om = oracle.OracleMesh.from_problem(p, model=model)
+    xn, it, _ = om.newton(p.x0, 1e-13, 60)
+    assert it >= 0
+    m = Mesh.from_problem(p)
+    u = _u0(p)
+    st, sweeps, rel = m.solve(u, RES_FLOOR, 20000, default_params(model=model, accel="chebyshev"))
+    assert st == 0 and rel[0] <= RES_FLOOR
+    x_gpu = u.cpu().double().numpy() + p.X
+    assert np.abs(x_gpu - xn).max() <= 1e-4 * np.abs(xn - p.X).max()
+
+
+@pytest.mark.parametrize("model", MODELS)
+def test_ragged_bar_with_weak_constraints(model):
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.contact_bar(3, 4, 7, h=0.1, k_contact=1e6)
+    p.body_accel = np.array([0.0, 0.0, -9.8])
+    p.density = np.full(p.ne, 1000.0)
+    m = Mesh.from_problem(p)
+    u = _u0(p)
+    m.sweep(u, 60, default_params(model=model))
+    x_ora, st = oracle.OracleMesh.from_problem(p, model=model).sweeps(p.x0, 60)
+    assert st == 0
+    x_gpu = u.cpu().double().numpy() + p.X
+    assert np.abs(x_gpu - x_ora).max() / np.abs(x_ora - p.X).max() <= 1e-5
+
+
+def test_direct_and_ring_paths_agree_for_each_model():
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.twist_block(6, 60.0, 0.2)
+    for model in MODELS:
+        out = []
+        for path in (0, 1):
+            m = Mesh.from_problem(p)
+            u = _u0(p)
+            m.sweep(u, 30, default_params(model=model, accel="chebyshev", kernel_path=path))
+            out.append(u.cpu().double().numpy())
+        assert np.abs(out[0] - out[1]).max() <= 1e-6 * np.abs(out[0]).max()
+
+
+def test_adjoint_rejects_other_models():
+    from paper_2306_09021_gb300 import Mesh, PbngError, default_params
+    p = W.twist_block(3, 30.0, 0.1)
+    m = Mesh.from_problem(p)
+    u = _u0(p)
+    with pytest.raises(PbngError):
+        m.adjoint(u, torch.zeros_like(u), 1e-6, 10, default_params(model="neohookean"))

@@ -175,13 +175,17 @@ def adjoint_block(n: int = 48, young: float = 1e5, poisson: float = 0.3) -> Prob
 
 
 def adjoint_load_cases(p: Problem, count: int = 32, seed: int = 777,
-                       max_rot_deg: float = 5.0, max_trans: float = 0.02, g: float = 9.8):
+                       max_rot_deg: float = 5.0, max_trans: float = 0.02, g: float = 9.8,
+                       full_body: bool = False):
     """Seeded load cases for ``adjoint_block``: per case a rigid motion of the
     clamped face (rotation angle <= max_rot_deg about a random axis through
     the face centre, translation <= max_trans) and a gravity direction in the
-    lower hemisphere.  Returns (x_D [count, nd, 3], body_accel [count, 3])."""
+    lower hemisphere.  Returns (x [count, nd, 3], body_accel [count, 3]);
+    with full_body the rigid motion is applied to every vertex (x [count,
+    nv, 3]), the boundary map extended to the whole block as an initial
+    guess."""
     u = uniform01(seed, 9 * count).reshape(count, 9)
-    Xd = p.X[p.dirichlet]
+    Xd = p.X if full_body else p.X[p.dirichlet]
     centre = np.array([0.5, 0.5, 0.0])
     xds, accs = [], []
     for c in range(count):
