@@ -198,6 +198,38 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
                          float* dL_dxD_dev, double rel_tol, int32_t max_sweeps, const pbng_params* p,
                          int32_t* sweeps_out, double* rel_residual_out);
 
+/* Backward Euler (Section "Position-Based Dynamics", Eq. fem_be): with
+ * dt > 0 each free vertex gains the inertial term -m_ii (x_i - xhat_i) / dt^2
+ * in its force and m_ii / dt^2 on the diagonal of its nodal Hessian, i.e. a
+ * zero-rest-length spring of stiffness m_ii / dt^2 to the inertial target
+ * xhat = 2 x^n - x^{n-1}; PBNG then minimises the incremental potential of one
+ * time step.  The mass is lumped: m_ii = sum_e density_e V_e / 4 (the
+ * integral of R^0 N_i for P1 tets).
+ *   density  host double [ne], > 0 (required when dt > 0)
+ * dt <= 0 returns the handle to quasistatics.  The layout is rebuilt on the
+ * next call; until pbng_step sets it, xhat is the rest position. */
+pbng_status pbng_set_inertia(pbng_mesh* m, double dt, const double* density);
+
+/* One backward-Euler time step (needs pbng_set_inertia with dt > 0).
+ *   u_dev       device float [nv][3]: u^n on entry, u^{n+1} on return
+ *   u_prev_dev  device float [nv][3]: u^{n-1} on entry, u^n on return
+ * A kernel sets xhat = 2 u^n - u^{n-1} and the initial guess
+ * xhat + dt^2 f^ext_i / m_ii (the predictor the paper describes for PBD;
+ * the initial guess only changes the first iterates), then the step runs
+ * as pbng_solve(rel_tol, max_sweeps = nsweeps) when rel_tol > 0, else as
+ * nsweeps sweeps of pbng_sweep; resume is ignored (every step starts a
+ * fresh acceleration history).  Clamped vertices take their current targets
+ * (pbng_set_dirichlet_targets).  sweeps_out and rel_residual_out (host, per
+ * component) may be NULL. */
+pbng_status pbng_step(pbng_mesh* m, float* u_dev, float* u_prev_dev, int32_t nsweeps, double rel_tol,
+                      const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out);
+
+/* New targets for the clamped vertices of the last pbng_set_constraints
+ * (host double [nd][3], in its dir_idx order) without rebuilding the layout:
+ * for animated boundaries.  They apply when the iterate is next loaded (a
+ * call with resume = 0, or pbng_step).  Synchronises. */
+pbng_status pbng_set_dirichlet_targets(pbng_mesh* m, const double* dir_xyz);
+
 /* Checkpoint of the iteration: the iterate (float32 pairs), the two previous
  * iterates used by the acceleration, the sweep index, omega_l and r_0.
  * pbng_get_state with buf == NULL writes the size needed to *bytes;

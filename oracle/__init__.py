@@ -50,6 +50,8 @@ def lib():
             "ora_pk1": (None, [_D, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]),
             "ora_dpk1": (None, [_D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]),
             "ora_set_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+            "ora_set_inertia": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _D, _D]),
+            "ora_lumped_mass": (None, [ctypes.c_void_p, _D]),
             "ora_cofactor": (None, [_D, _D]),
             "ora_modified_density_hessian": (None, [_D, ctypes.c_double, ctypes.c_double, _D]),
             "ora_create": (ctypes.c_void_p, [ctypes.c_int, _D, ctypes.c_int, _I, _D, _D, _U8,
@@ -190,6 +192,20 @@ class OracleMesh:
                 p.density, p.spr_idx, p.spr_target, p.spr_k, p.plane, p.k_contact)
         m.set_model(model)
         return m
+
+    def set_inertia(self, dt, density, xhat):
+        """Backward Euler (Eq. fem_be) with inertial target xhat = 2 x^n - x^{n-1};
+        dt <= 0 returns to quasistatics."""
+        dens = _f64(np.broadcast_to(density, (self.ne,)))
+        xh = _f64(xhat, (-1, 3))
+        self._inertia_keep = (dens, xh)
+        if lib().ora_set_inertia(self.h, float(dt), _d(dens), _d(xh)) != 0:
+            raise ValueError("bad inertia arguments")
+
+    def lumped_mass(self):
+        out = np.zeros(self.nv)
+        lib().ora_lumped_mass(self.h, _d(out))
+        return out
 
     def set_model(self, model):
         """Constitutive model: 0 / 'corotated', 1 / 'neohookean', 2 / 'stable_neohookean'."""

@@ -362,6 +362,10 @@ struct Mesh {
     bool has_plane = false;
     double pn[3] = {0, 0, 1}, pd = 0.0, kc = 0.0;
     int model = kCorotated;                // Section "Constitutive Models"
+    // Backward Euler (Eq. fem_be): lumped masses m_ii and 1/dt^2 (0 = quasistatic),
+    // and the inertial target xhat = 2 x^n - x^{n-1}.
+    std::vector<double> mass, xhat;
+    double inv_dt2 = 0.0;
     std::vector<int> colour;               // nv, -1 clamped
     std::vector<std::vector<int>> by_colour;
 };
@@ -453,6 +457,15 @@ void local_system(const Mesh& m, const double* x, int i, double* r, double* A) {
             }
         }
     }
+    // Eq. fem_be moved to the right-hand side: -m_ii (x_i - xhat_i) / dt^2,
+    // whose derivative adds m_ii / dt^2 to the diagonal of A.
+    if (m.inv_dt2 > 0.0) {
+        const double k = m.mass[i] * m.inv_dt2;
+        for (int a = 0; a < 3; ++a) {
+            r[a] -= k * (x[3 * (size_t)i + a] - m.xhat[3 * (size_t)i + a]);
+            A[4 * a] += k;
+        }
+    }
 }
 
 // Eq. pbgn_update / pbgn_dx: one modified-Newton step from Delta = 0.
@@ -501,6 +514,14 @@ double energy(const Mesh& m, const double* x) {
             if (sd < 0.0) E += 0.5 * m.kc * sd * sd;
         }
         for (int a = 0; a < 3; ++a) E -= m.fext[3 * (size_t)i + a] * xi[a];
+        if (m.inv_dt2 > 0.0 && !m.dir[i]) {  // incremental potential of Eq. fem_be
+            double d2 = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                const double d = xi[a] - m.xhat[3 * (size_t)i + a];
+                d2 += d * d;
+            }
+            E += 0.5 * m.mass[i] * m.inv_dt2 * d2;
+        }
     }
     return E;
 }
@@ -530,6 +551,8 @@ void hessian_dense(const Mesh& m, const double* x, std::vector<double>& H) {
     }
     for (int i = 0; i < m.nv; ++i) {
         const double* xi = &x[3 * (size_t)i];
+        if (m.inv_dt2 > 0.0 && !m.dir[i])
+            for (int a = 0; a < 3; ++a) H[(size_t)(3 * i + a) * n + 3 * i + a] += m.mass[i] * m.inv_dt2;
         for (int k = m.spr_off[i]; k < m.spr_off[i + 1]; ++k)
             for (int a = 0; a < 3; ++a) H[(size_t)(3 * i + a) * n + 3 * i + a] += m.spr_k[m.spr_list[k]];
         if (m.has_plane) {
@@ -666,6 +689,28 @@ void* ora_create(int nv, const double* X, int ne, const int* tets, const double*
 }
 
 void ora_destroy(void* h) { delete static_cast<Mesh*>(h); }
+
+// Backward Euler of Eq. fem_be with the lumped mass m_ii = sum_e rho_e V_e / 4
+// (the integral of R^0 N_i for P1 tets).  dt <= 0 returns to quasistatics.
+int ora_set_inertia(void* h, double dt, const double* density, const double* xhat) {
+    Mesh& m = *static_cast<Mesh*>(h);
+    if (!(dt > 0.0)) {
+        m.inv_dt2 = 0.0;
+        return 0;
+    }
+    if (!density || !xhat) return 1;
+    m.mass.assign(m.nv, 0.0);
+    for (int e = 0; e < m.ne; ++e)
+        for (int j = 0; j < 4; ++j) m.mass[m.tets[4 * (size_t)e + j]] += density[e] * m.vol[e] / 4.0;
+    m.xhat.assign(xhat, xhat + 3 * (size_t)m.nv);
+    m.inv_dt2 = 1.0 / (dt * dt);
+    return 0;
+}
+
+void ora_lumped_mass(const void* h, double* out) {
+    const Mesh& m = *static_cast<const Mesh*>(h);
+    for (int i = 0; i < m.nv; ++i) out[i] = m.mass.empty() ? 0.0 : m.mass[i];
+}
 
 int ora_set_model(void* h, int model) {
     if (model < kCorotated || model > kStableNeoHookean) return 1;

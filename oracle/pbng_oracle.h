@@ -63,6 +63,15 @@ void ora_destroy(void* h);
  * modified Hessian of Eq. mod_hess_dens is the same for every model.
  * Returns nonzero for an unknown model. */
 int ora_set_model(void* h, int model);
+/* Backward Euler (Eq. fem_be): with dt > 0 every free vertex gets the
+ * inertial term -m_ii (x_i - xhat_i) / dt^2 in its force, m_ii / dt^2 on the
+ * diagonal of its Hessian and (m_ii / 2 dt^2)|x_i - xhat_i|^2 in the energy,
+ * with the lumped mass m_ii = sum_e density_e V_e / 4.  xhat (absolute
+ * [nv][3]) is the inertial target 2 x^n - x^{n-1}.  dt <= 0 turns it off.
+ * Returns nonzero on a NULL array. */
+int ora_set_inertia(void* h, double dt, const double* density, const double* xhat);
+/* The lumped masses of the last ora_set_inertia (0 before). */
+void ora_lumped_mass(const void* h, double* out);
 
 /* Greedy node colouring of Section "Coloring and Parallelism". */
 int ora_num_colours(const void* h);

@@ -116,6 +116,9 @@ SIGNATURES = {
     "pbng_get_schedule": (_I32, [_P, ctypes.POINTER(PbngSchedule)]),
     "pbng_autotune": (_I32, [_P, _P, ctypes.POINTER(PbngParams), _I32, ctypes.POINTER(PbngSchedule)]),
     "pbng_get_solve_info": (_I32, [_P, ctypes.POINTER(PbngSolveInfo)]),
+    "pbng_set_inertia": (_I32, [_P, _D, _PD]),
+    "pbng_step": (_I32, [_P, _P, _P, _I32, _D, ctypes.POINTER(PbngParams), _PI, _PD]),
+    "pbng_set_dirichlet_targets": (_I32, [_P, _PD]),
     "pbng_num_components": (_I32, [_P]),
     "pbng_status_string": (ctypes.c_char_p, [_I32]),
     "pbng_last_error": (ctypes.c_char_p, [_P]),

@@ -59,6 +59,10 @@ struct pbng_mesh {
     int32_t ring_partials = 0;         // residual partials of the ring launch
     bool want_direct = false;          // params.kernel_path == 1 requested
     int model = 0;                     // constitutive model of the last sweep / solve (residuals use it)
+    // backward Euler (pbng_set_inertia): dt > 0 and lumped masses, caller order
+    double be_dt = 0.0;
+    std::vector<double> be_mass;
+    DevBuf d_aux_base0, d_aux_base1, d_be_k;  // aux without inertia, m_v / dt^2 (internal order)
     bool built_direct = false;         // layout built with want_direct
     std::vector<int32_t> table_partial_off;  // residual partial offset per colour
     int32_t total_partials = 0;
@@ -507,6 +511,23 @@ pbng_status build_layout(pbng_mesh* m) {
         aux1[w] = a1;
         if (m->ncomp > 1) comp[w] = m->comp_of[i];
     }
+    // Backward Euler: the inertia is a zero-rest spring of stiffness
+    // m_i / dt^2 to the inertial target, which pbng_step sets; until then the
+    // target is the rest position.
+    std::vector<float4> base0, base1;
+    std::vector<float> bek;
+    if (m->be_dt > 0.0) {
+        base0 = aux0;
+        base1 = aux1;
+        bek.resize(m->nfree);
+        for (int32_t w = 0; w < m->nfree; ++w) {
+            const double k = m->be_mass[order[w]] / (m->be_dt * m->be_dt);
+            const double Ks = aux0[w].w, K = Ks + k;
+            bek[w] = (float)k;
+            aux0[w].w = (float)K;
+            for (int a = 0; a < 3; ++a) (&aux1[w].x)[a] = (float)(Ks * (&base1[w].x)[a] / K);
+        }
+    }
     const int32_t nd = nv - m->nfree;
     std::vector<float4> dhi(nd), dlo(nd);
     for (int32_t q = 0; q < nd; ++q) {
@@ -533,6 +554,11 @@ pbng_status build_layout(pbng_mesh* m) {
     PBNG_CUDA(m, upload(m->d_items, m->items, st));
     PBNG_CUDA(m, upload(m->d_aux0, aux0, st));
     PBNG_CUDA(m, upload(m->d_aux1, aux1, st));
+    if (m->be_dt > 0.0) {
+        PBNG_CUDA(m, upload(m->d_aux_base0, base0, st));
+        PBNG_CUDA(m, upload(m->d_aux_base1, base1, st));
+        PBNG_CUDA(m, upload(m->d_be_k, bek, st));
+    }
     PBNG_CUDA(m, upload(m->d_comp, comp, st));
     PBNG_CUDA(m, upload(m->d_perm, m->perm, st));
     PBNG_CUDA(m, upload(m->d_dir_hi, dhi, st));
@@ -1019,6 +1045,58 @@ pbng_status pbng_set_material(pbng_mesh* m, const double* young, const double* p
     return PBNG_OK;
 }
 
+pbng_status pbng_set_inertia(pbng_mesh* m, double dt, const double* density) {
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    if (!(dt > 0.0)) {
+        if (m->be_dt > 0.0) m->dirty = true;
+        m->be_dt = 0.0;
+        return PBNG_OK;
+    }
+    if (!density || !std::isfinite(dt)) return fail(m, PBNG_EINVAL, "backward Euler needs dt > 0 and densities");
+    for (int32_t e = 0; e < m->ne; ++e)
+        if (!(density[e] > 0.0)) return fail(m, PBNG_EINVAL, "densities must be > 0");
+    try {
+        m->be_mass.assign(m->nv, 0.0);  // m_ii = sum_e rho_e V_e / 4 (Eq. fem_be, P1)
+        for (int32_t e = 0; e < m->ne; ++e)
+            for (int j = 0; j < 4; ++j) m->be_mass[m->tets[4 * (size_t)e + j]] += density[e] * m->vol[e] / 4.0;
+    } catch (const std::bad_alloc&) {
+        return PBNG_ENOMEM;
+    }
+    m->be_dt = dt;
+    m->dirty = true;
+    m->has_state = false;
+    return PBNG_OK;
+}
+
+pbng_status pbng_set_dirichlet_targets(pbng_mesh* m, const double* dir_xyz) {
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    if (!dir_xyz && !m->dir_list.empty()) return fail(m, PBNG_EINVAL, "NULL targets");
+    for (size_t q = 0; q < m->dir_list.size(); ++q)
+        for (int a = 0; a < 3; ++a) m->dir_pos[3 * (size_t)m->dir_list[q] + a] = dir_xyz[3 * q + a];
+    if (m->dirty) return PBNG_OK;  // the next layout build uploads them
+    cudaError_t e = cudaSetDevice(m->device);
+    if (e != cudaSuccess) return cuda_fail(m, e, "cudaSetDevice");
+    const int32_t nd = m->nv - m->nfree;
+    std::vector<float4> dhi(nd), dlo(nd);
+    for (int32_t q = 0; q < nd; ++q) {
+        const int32_t i = m->perm[m->nfree + q];
+        float h[3], l[3];
+        for (int a = 0; a < 3; ++a) {
+            const double d = m->dir_pos[3 * (size_t)i + a] - m->X[3 * (size_t)i + a];
+            h[a] = (float)d;
+            l[a] = (float)(d - (double)h[a]);
+        }
+        dhi[q] = make_float4(h[0], h[1], h[2], 0.f);
+        dlo[q] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+    PBNG_CUDA(m, upload(m->d_dir_hi, dhi, m->stream));
+    PBNG_CUDA(m, upload(m->d_dir_lo, dlo, m->stream));
+    PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
+    return PBNG_OK;
+}
+
 pbng_status pbng_get_colouring(pbng_mesh* m, int32_t* colour_out, int32_t* ncolours) {
     pbng_status s = ensure_ready(m);
     if (s) return s;
@@ -1201,6 +1279,27 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     if (result == PBNG_ENOTCONVERGED) m->err = "max_sweeps reached";
     if (result == PBNG_EDIVERGED) m->err = "residual diverged";
     return result;
+}
+
+pbng_status pbng_step(pbng_mesh* m, float* u_dev, float* u_prev_dev, int32_t nsweeps, double rel_tol,
+                      const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out) {
+    if (!m) return PBNG_EINVAL;
+    if (!valid_params(p) || nsweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
+    if (!(m->be_dt > 0.0)) return fail(m, PBNG_EINVAL, "pbng_step needs pbng_set_inertia(dt > 0) first");
+    if (!u_dev || !u_prev_dev) return fail(m, PBNG_EINVAL, "NULL displacement array");
+    select_path(m, p);
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    PBNG_CUDA(m, launch_inertia(m->nv, m->nfree, (const int32_t*)m->d_perm.p, u_dev, u_prev_dev,
+                                (const float4*)m->d_aux_base0.p, (const float4*)m->d_aux_base1.p,
+                                (const float*)m->d_be_k.p, (float4*)m->d_aux0.p, (float4*)m->d_aux1.p, m->stream));
+    m->kernel_launches++;
+    pbng_params q = *p;
+    q.resume = 0;
+    if (rel_tol > 0.0) return pbng_solve(m, u_dev, rel_tol, nsweeps, &q, sweeps_out, rel_residual_out);
+    s = pbng_sweep(m, u_dev, nsweeps, &q, rel_residual_out);
+    if (s == PBNG_OK && sweeps_out) *sweeps_out = nsweeps;
+    return s;
 }
 
 }  // extern "C"
@@ -1681,6 +1780,7 @@ void pbng_destroy(pbng_mesh* m) {
                       &m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
                       &m->d_ring_ra, &m->d_ring_rb, &m->d_ring_rc, &m->d_ring_id, &m->d_items,
                       &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
+                      &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k,
                       &m->d_partial, &m->d_comp_sq, &m->d_scalar, &m->d_err};
     for (DevBuf* b : bufs) free_buf(*b);
     for (auto& sb : m->d_state)

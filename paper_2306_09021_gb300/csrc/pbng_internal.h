@@ -111,6 +111,14 @@ cudaError_t launch_load(int32_t nv, int32_t nfree, const float* u_user, const in
                         const float4* dir_hi, const float4* dir_lo, State s, cudaStream_t st);
 cudaError_t launch_store(int32_t nv, const int32_t* perm, State s, float* u_user, cudaStream_t st);
 cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st);
+// Backward-Euler step setup (Eq. fem_be): for free vertex v (internal order)
+// with caller id o = perm[v], uhat = 2 u[o] - u_prev[o]; the inertia acts as
+// a zero-rest spring of stiffness k_v = m_v / dt^2 to uhat, merged with the
+// vertex's own springs into aux; u[o] becomes the predictor
+// uhat + f_ext / k_v and u_prev[o] the old u[o] (every vertex).
+cudaError_t launch_inertia(int32_t nv, int32_t nfree, const int32_t* perm, float* u, float* u_prev,
+                           const float4* base0, const float4* base1, const float* k, float4* aux0, float4* aux1,
+                           cudaStream_t st);
 
 // Ring-layout kernels (pbng_ring.cu): persistent warps, each streaming its
 // items with TMA bulk copies and cp.async gathers.  The residual writes one

@@ -284,6 +284,41 @@ cudaError_t launch_store(int32_t nv, const int32_t* perm, State s, float* u_user
     return cudaGetLastError();
 }
 
+__global__ void inertia_kernel(int nv, int nfree, const int32_t* __restrict__ perm, float* u, float* u_prev,
+                               const float4* __restrict__ base0, const float4* __restrict__ base1,
+                               const float* __restrict__ k, float4* aux0, float4* aux1) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int o = perm[v];
+    const float un[3] = {u[3 * o], u[3 * o + 1], u[3 * o + 2]};
+    if (v < nfree) {
+        const float4 b0 = base0[v], b1 = base1[v];
+        const float kv = k[v], K = b0.w + kv;
+        float t[3], g[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float uhat = 2.0f * un[a] - u_prev[3 * o + a];
+            const float ts = (&b1.x)[a], fe = (&b0.x)[a];
+            t[a] = K > 0.0f ? __fdividef(b0.w * ts + kv * uhat, K) : ts;
+            g[a] = kv > 0.0f ? uhat + __fdividef(fe, kv) : un[a];
+        }
+        aux0[v] = make_float4(b0.x, b0.y, b0.z, K);
+        aux1[v] = make_float4(t[0], t[1], t[2], b1.w);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[3 * o + a] = g[a];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u_prev[3 * o + a] = un[a];
+}
+
+cudaError_t launch_inertia(int32_t nv, int32_t nfree, const int32_t* perm, float* u, float* u_prev,
+                           const float4* base0, const float4* base1, const float* k, float4* aux0, float4* aux1,
+                           cudaStream_t st) {
+    if (nv <= 0) return cudaSuccess;
+    inertia_kernel<<<blocks_for(nv, 256), 256, 0, st>>>(nv, nfree, perm, u, u_prev, base0, base1, k, aux0, aux1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     copy_state_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, src, dst);

@@ -165,6 +165,33 @@ class Mesh:
             check(st, "pbng_solve", self.h)
         return st, sweeps.value, out
 
+    def set_inertia(self, dt, density=None):
+        """pbng_set_inertia: backward Euler with lumped masses (dt <= 0: quasistatic)."""
+        de = None if density is None else np.ascontiguousarray(np.broadcast_to(density, (self.ne,)), dtype=np.float64)
+        check(load().pbng_set_inertia(self.h, float(dt), None if de is None else _dptr(de)), "pbng_set_inertia",
+              self.h)
+
+    def step(self, u, u_prev, nsweeps, params=None, rel_tol=0.0, raise_on_status=True):
+        """pbng_step: one backward-Euler step in place (u: u^n -> u^{n+1},
+        u_prev: u^{n-1} -> u^n).  Returns (status, sweeps, rel_residuals)."""
+        _check_u(u, self.nv)
+        _check_u(u_prev, self.nv)
+        p = params if params is not None else default_params()
+        sweeps = ctypes.c_int32()
+        out = np.zeros(self.ncomp)
+        st = load().pbng_step(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(u_prev.data_ptr()),
+                              int(nsweeps), float(rel_tol), ctypes.byref(p), ctypes.byref(sweeps), _dptr(out))
+        if raise_on_status:
+            check(st, "pbng_step", self.h)
+        return st, sweeps.value, out
+
+    def set_dirichlet_targets(self, dir_xyz):
+        """pbng_set_dirichlet_targets (positions in the order of set_constraints' dir_idx)."""
+        dx = np.ascontiguousarray(dir_xyz, dtype=np.float64).reshape(-1, 3)
+        if dx.shape[0] != len(self.dirichlet):
+            raise ValueError("one target per clamped vertex")
+        check(load().pbng_set_dirichlet_targets(self.h, _dptr(dx)), "pbng_set_dirichlet_targets", self.h)
+
     def solve_info(self):
         """pbng_get_solve_info of the last solve as a dict."""
         i = PbngSolveInfo()
