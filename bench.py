@@ -420,6 +420,16 @@ def main():
                 ttr[name]["solve_info"] = m.solve_info()
             if u_eq is None or float(np.max(relr)) < best_rel:
                 u_eq, best_rel = uu, float(np.max(relr))
+        if args.config in ("twist10", "sag64") and args.model == "corotated" and args.kernel_path == 0:
+            # Newton's method with CG on the true Hessian, on the same GPU
+            for name, tol in (("newton_cg", 1e-5), ("newton_cg_to_1e-4", 1e-4)):
+                uu = u0.clone()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, info = m.newton_cg(uu, tol, max_newton=40, max_cg=4000, cg_tol=0.1,
+                                       params=default_params(precision=args.precision), raise_on_status=False)
+                torch.cuda.synchronize()
+                ttr[name] = dict(tol=tol, status=int(st), ms=1e3 * (time.perf_counter() - t0), **info)
         if args.config in ("batched", "adjoint"):
             # the same meshes solved one handle at a time (handles built
             # before the clock starts), Chebyshev with the paper's rho

@@ -230,6 +230,40 @@ pbng_status pbng_step(pbng_mesh* m, float* u_dev, float* u_prev_dev, int32_t nsw
  * call with resume = 0, or pbng_step).  Synchronises. */
 pbng_status pbng_set_dirichlet_targets(pbng_mesh* m, const double* dir_xyz);
 
+/* Force and Hessian of the discrete energy (corotated, kernel_path 0; p may
+ * be NULL for the defaults), for Krylov or optimisation methods around PBNG.
+ * pbng_force: f_out_dev (device float [nv][3]) = f(u) + f^ext on free
+ *   vertices (the force of Eq. fem_qs with the weak terms; zero rows at
+ *   clamped vertices).
+ * pbng_hessian_apply: hp_out_dev = H p on free vertices, H = -d(f + f^ext)/du
+ *   the true Hessian (Eq. hess, with dR of the polar factor) at u, p_dev a
+ *   direction (rows of clamped vertices ignored; zero rows on output).
+ * All arrays device float [nv][3] in caller order.  Synchronise. */
+pbng_status pbng_force(pbng_mesh* m, const float* u_dev, const pbng_params* p, float* f_out_dev);
+pbng_status pbng_hessian_apply(pbng_mesh* m, const float* u_dev, const float* p_dev, const pbng_params* p,
+                               float* hp_out_dev);
+
+/* Newton-CG reference solver on the same GPU (the paper compares PBNG with
+ * Newton's method; Section "PBNG vs. PBD and Limited Newton"): each Newton
+ * iteration solves H dx = f + f^ext with block-Jacobi preconditioned CG on the
+ * true Hessian (pbng_hessian_apply), stopping at |r_cg| <= cg_tol |f + f^ext|,
+ * after max_cg iterations or at the first direction of non-positive
+ * curvature; a backtracking line search halves the step until the residual
+ * norm decreases; if none is accepted, the preconditioned residual is tried
+ * once.  Stops at |f + f^ext| <= rel_tol r_0 (global 2-norm over all
+ * components, r_0 at u_dev) or max_newton iterations (PBNG_ENOTCONVERGED).
+ * Corotated model and kernel_path 0 only.  u_dev in / out.  info may be NULL.
+ * The acceleration history of the handle is reset.  Synchronises. */
+typedef struct {
+    int32_t newton_iterations;
+    int32_t cg_iterations;          /* summed over Newton iterations            */
+    int32_t line_search_halvings;
+    int32_t fallbacks;              /* steps along the preconditioned residual  */
+    double rel_residual;            /* |f + f^ext| / r_0 at the end              */
+} pbng_newton_info;
+pbng_status pbng_newton_cg(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_newton, int32_t max_cg,
+                           double cg_tol, const pbng_params* p, pbng_newton_info* info);
+
 /* Checkpoint of the iteration: the iterate (float32 pairs), the two previous
  * iterates used by the acceleration, the sweep index, omega_l and r_0.
  * pbng_get_state with buf == NULL writes the size needed to *bytes;

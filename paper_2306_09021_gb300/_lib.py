@@ -80,6 +80,16 @@ class PbngSolveInfo(ctypes.Structure):
     ]
 
 
+class PbngNewtonInfo(ctypes.Structure):
+    _fields_ = [
+        ("newton_iterations", ctypes.c_int32),
+        ("cg_iterations", ctypes.c_int32),
+        ("line_search_halvings", ctypes.c_int32),
+        ("fallbacks", ctypes.c_int32),
+        ("rel_residual", ctypes.c_double),
+    ]
+
+
 class PbngError(RuntimeError):
     def __init__(self, status, where, detail=""):
         self.status = status
@@ -119,6 +129,10 @@ SIGNATURES = {
     "pbng_set_inertia": (_I32, [_P, _D, _PD]),
     "pbng_step": (_I32, [_P, _P, _P, _I32, _D, ctypes.POINTER(PbngParams), _PI, _PD]),
     "pbng_set_dirichlet_targets": (_I32, [_P, _PD]),
+    "pbng_force": (_I32, [_P, _P, ctypes.POINTER(PbngParams), _P]),
+    "pbng_hessian_apply": (_I32, [_P, _P, _P, ctypes.POINTER(PbngParams), _P]),
+    "pbng_newton_cg": (_I32, [_P, _P, _D, _I32, _I32, _D, ctypes.POINTER(PbngParams),
+                              ctypes.POINTER(PbngNewtonInfo)]),
     "pbng_num_components": (_I32, [_P]),
     "pbng_status_string": (ctypes.c_char_p, [_I32]),
     "pbng_last_error": (ctypes.c_char_p, [_P]),

@@ -125,11 +125,17 @@ __device__ __forceinline__ float3 mat_g(const float* M, float3 g) {
                        M[6] * g.x + M[7] * g.y + M[8] * g.z);
 }
 
-enum { kDiag = 0, kSweep = 1, kResid = 2 };
+// kDiag: 3x3 diagonal blocks of H; kSweep: one block Gauss-Seidel pass;
+// kResid: |gv - H lam|^2 per warp; kForce: r = f + f^ext at u into out, the
+// SPD modified blocks A_i of Eq. mod_hess into diag, |r|^2 per warp;
+// kApply: out = H lam (lam = a direction, zero at clamped vertices),
+// lam . H lam per warp.
+enum { kDiag = 0, kSweep = 1, kResid = 2, kForce = 3, kApply = 4 };
 
 template <int W, int MODE>
 __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, float4* lam, const float4* gv,
-                                         float4* diag, const Item& it, int lane, int32_t* err, double& rr) {
+                                         float4* diag, float4* out4, const Item& it, int lane, int32_t* err,
+                                         double& rr) {
     const int j = lane / W;
     const bool active = j < it.nv;
     const int v = it.v0 + j;
@@ -139,10 +145,10 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
     if (active) {
         uh = f3(u.hi[v]);
         ul = f3(u.lo[v]);
-        li = f3(lam[v]);
+        if (MODE != kForce) li = f3(lam[v]);
         const int id = m.ring_id[slot];
         du = el::pair_diff<true>(u.hi[id], u.lo[id], uh, ul);
-        if (MODE != kDiag) {
+        if (MODE != kDiag && MODE != kForce) {
             const float3 lj = f3(lam[id]);
             dl = make_float3(lj.x - li.x, lj.y - li.y, lj.z - li.z);
         }
@@ -161,9 +167,27 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
     const float3 gi = make_float3(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
     ElemState E;
     elem_state(d[0], d[1], d[2], g1, g2, g3, E);
-    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float out[9];
-    if (MODE == kDiag) {
+    if (MODE == kForce) {
+        // -V P g_i (Eq. cor) and V (2 mu |g_i|^2 I + lambda w w^T), w = cof(F) g_i
+        const float3 w = mat_g(E.C, gi);
+        float HR[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) HR[k] = E.H[k] - E.RmI[k];
+        const float3 fr = mat_g(HR, gi);
+        const float a = ra.w, b = rb.w;
+        acc[0] = -(a * fr.x + b * E.Jm1 * w.x);
+        acc[1] = -(a * fr.y + b * E.Jm1 * w.y);
+        acc[2] = -(a * fr.z + b * E.Jm1 * w.z);
+        const float ag = a * (gi.x * gi.x + gi.y * gi.y + gi.z * gi.z);
+        acc[3] = ag + b * w.x * w.x;
+        acc[4] = b * w.x * w.y;
+        acc[5] = b * w.x * w.z;
+        acc[6] = ag + b * w.y * w.y;
+        acc[7] = b * w.y * w.z;
+        acc[8] = ag + b * w.z * w.z;
+    } else if (MODE == kDiag) {
         const float gg[3] = {gi.x, gi.y, gi.z};
         float col[3][3];
 #pragma unroll
@@ -196,10 +220,20 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
         acc[1] = h.y;
         acc[2] = h.z;
     }
-    constexpr int NA = (MODE == kDiag) ? 6 : 3;
+    constexpr int NA = (MODE == kForce) ? 9 : ((MODE == kDiag) ? 6 : 3);
 #pragma unroll
     for (int k = 0; k < NA; ++k) acc[k] = el::group_sum<W>(acc[k]);
     if (!active || (lane & (W - 1)) != 0) return;
+    if (MODE == kForce) {
+        float r[3] = {acc[0], acc[1], acc[2]};
+        float A[6] = {acc[3], acc[4], acc[5], acc[6], acc[7], acc[8]};
+        el::vertex_terms<true, true>(m, m.aux0[v], m.aux1[v], uh, ul, r, A);
+        out4[v] = make_float4(r[0], r[1], r[2], 0.f);
+        diag[2 * v] = make_float4(A[0], A[1], A[2], A[3]);
+        diag[2 * v + 1] = make_float4(A[4], A[5], 0.f, 0.f);
+        rr += (double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2];
+        return;
+    }
     // weak terms: springs K I, active plane contact k n n^T
     const float4 x0 = m.aux0[v], x1 = m.aux1[v];
     const float K = x0.w;
@@ -222,6 +256,13 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
         return;
     }
     const float nl = kc * (n[0] * li.x + n[1] * li.y + n[2] * li.z);
+    if (MODE == kApply) {
+        const float h0 = acc[0] + K * li.x + nl * n[0], h1 = acc[1] + K * li.y + nl * n[1],
+                    h2 = acc[2] + K * li.z + nl * n[2];
+        out4[v] = make_float4(h0, h1, h2, 0.f);
+        rr += (double)li.x * h0 + (double)li.y * h1 + (double)li.z * h2;
+        return;
+    }
     const float4 gvv = gv[v];
     const float r0 = gvv.x - (acc[0] + K * li.x + nl * n[0]);
     const float r1 = gvv.y - (acc[1] + K * li.y + nl * n[1]);
@@ -246,7 +287,7 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
 
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) adjoint_vertex_kernel(const DeviceMesh m, State u, float4* lam,
-                                                                const float4* gv, float4* diag,
+                                                                const float4* gv, float4* diag, float4* out4,
                                                                 const Item* __restrict__ items, int nitems,
                                                                 int32_t* err, double* partial) {
     const int lane = threadIdx.x & 31;
@@ -255,13 +296,13 @@ __global__ void __launch_bounds__(kBlock) adjoint_vertex_kernel(const DeviceMesh
     if (gw < nitems) {
         const Item it = items[gw];
         switch (it.w) {
-            case 4: adj_item<4, MODE>(m, u, lam, gv, diag, it, lane, err, rr); break;
-            case 8: adj_item<8, MODE>(m, u, lam, gv, diag, it, lane, err, rr); break;
-            case 16: adj_item<16, MODE>(m, u, lam, gv, diag, it, lane, err, rr); break;
-            default: adj_item<32, MODE>(m, u, lam, gv, diag, it, lane, err, rr); break;
+            case 4: adj_item<4, MODE>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
+            case 8: adj_item<8, MODE>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
+            case 16: adj_item<16, MODE>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
+            default: adj_item<32, MODE>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
         }
     }
-    if (MODE == kResid) {
+    if (MODE == kResid || MODE == kForce || MODE == kApply) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
         if (lane == 0) partial[gw] = rr;
@@ -351,21 +392,187 @@ __global__ void clamped_grad_kernel(int nd, const int32_t* dq_internal, const in
 
 inline int nblocks(int n, int b) { return (n + b - 1) / b; }
 
+// ---- preconditioned conjugate gradients on H x = r (free vertices) --------
+// Scalars live on the device: sc[0] = r.z, sc[1] = p.Hp, sc[2] = new r.z,
+// sc[3] = |r|^2.  A direction with p.Hp <= 0 (H not positive definite along
+// it) sets *flag and freezes every later update (truncated CG).
+
+// z = A^{-1} r for the SPD 3x3 block A (upper triangle in two float4).
+__device__ __forceinline__ float3 block_solve(float4 D0, float4 D1, float3 r) {
+    const float A[6] = {D0.x, D0.y, D0.z, D0.w, D1.x, D1.y};
+    const float c00 = A[3] * A[5] - A[4] * A[4], c01 = A[2] * A[4] - A[1] * A[5], c02 = A[1] * A[4] - A[2] * A[3];
+    const float c11 = A[0] * A[5] - A[2] * A[2], c12 = A[1] * A[2] - A[0] * A[4], c22 = A[0] * A[3] - A[1] * A[1];
+    const float det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    const float inv = det > 0.0f ? 1.0f / det : 0.0f;
+    return make_float3(inv * (c00 * r.x + c01 * r.y + c02 * r.z), inv * (c01 * r.x + c11 * r.y + c12 * r.z),
+                       inv * (c02 * r.x + c12 * r.y + c22 * r.z));
+}
+
+// One FP64 partial per block, summed in a fixed order.  Ends with a barrier
+// so that a second call in the same kernel cannot overwrite ws while thread 0
+// still reads it.
+__device__ __forceinline__ void block_partial(double v, double* partial) {
+    __shared__ double ws[kBlock / 32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kBlock / 32; ++k) t += ws[k];
+        partial[blockIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBlock) cg_init_kernel(int n, const float4* r, const float4* diag, float4* x,
+                                                         float4* z, float4* p, double* partial) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    double rz = 0.0;
+    if (v < n) {
+        const float3 rv = f3(r[v]);
+        const float3 zv = block_solve(diag[2 * v], diag[2 * v + 1], rv);
+        x[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        z[v] = make_float4(zv.x, zv.y, zv.z, 0.f);
+        p[v] = z[v];
+        rz = (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z;
+    }
+    block_partial(rz, partial);
+}
+
+__global__ void __launch_bounds__(kBlock) cg_update_kernel(int n, const double* sc, float4* x, float4* r,
+                                                           const float4* p, const float4* q, const float4* diag,
+                                                           float4* z, double* part_rz, double* part_rr,
+                                                           int32_t* flag) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const double pq = sc[1];
+    const bool stop = *flag != 0 || !(pq > 0.0);
+    double rz = 0.0, rr = 0.0;
+    if (!stop && v < n) {
+        const float alpha = (float)(sc[0] / pq);
+        const float4 xv = x[v], pv = p[v], qv = q[v];
+        float3 rv = f3(r[v]);
+        x[v] = make_float4(xv.x + alpha * pv.x, xv.y + alpha * pv.y, xv.z + alpha * pv.z, 0.f);
+        rv = make_float3(rv.x - alpha * qv.x, rv.y - alpha * qv.y, rv.z - alpha * qv.z);
+        r[v] = make_float4(rv.x, rv.y, rv.z, 0.f);
+        const float3 zv = block_solve(diag[2 * v], diag[2 * v + 1], rv);
+        z[v] = make_float4(zv.x, zv.y, zv.z, 0.f);
+        rz = (double)rv.x * zv.x + (double)rv.y * zv.y + (double)rv.z * zv.z;
+        rr = (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z;
+    }
+    if (stop && v == 0 && *flag == 0) atomicOr(flag, 1);
+    block_partial(rz, part_rz);
+    block_partial(rr, part_rr);
+}
+
+__global__ void __launch_bounds__(kBlock) cg_dir_kernel(int n, const double* sc, const float4* z, float4* p,
+                                                        const int32_t* flag) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n || *flag) return;
+    const float beta = (float)(sc[2] / sc[0]);
+    const float4 zv = z[v], pv = p[v];
+    p[v] = make_float4(zv.x + beta * pv.x, zv.y + beta * pv.y, zv.z + beta * pv.z, 0.f);
+}
+
+__global__ void cg_shift_kernel(double* sc, const int32_t* flag) {
+    if (!*flag) sc[0] = sc[2];
+}
+
+// dst = src + s x on free vertices (compensated pairs); clamped vertices copied.
+__global__ void newton_axpy_kernel(int nv, int nfree, State src, const float4* x, float s, State dst) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    float4 h = src.hi[v], l = src.lo[v];
+    if (v < nfree) {
+        const float4 xv = x[v];
+        el::pair_add(h.x, l.x, s * xv.x);
+        el::pair_add(h.y, l.y, s * xv.y);
+        el::pair_add(h.z, l.z, s * xv.z);
+    }
+    dst.hi[v] = h;
+    dst.lo[v] = l;
+}
+
+// Internal float4 vector (free rows, zero elsewhere) <-> caller float [nv][3].
+__global__ void gather_vec_kernel(int nv, int nfree, const int32_t* perm, const float* in, float4* out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int o = perm[v];
+    out[v] = v < nfree ? make_float4(in[3 * o], in[3 * o + 1], in[3 * o + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void scatter_vec_kernel(int nv, int nfree, const int32_t* perm, const float4* in, float* out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int o = perm[v];
+    const float4 a = v < nfree ? in[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+    out[3 * o] = a.x;
+    out[3 * o + 1] = a.y;
+    out[3 * o + 2] = a.z;
+}
+
 }  // namespace
 
 int adjoint_warps(int nitems) { return nblocks(nitems, kBlock / 32) * (kBlock / 32); }
 
 cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4* lam, const float4* gv,
                                   float4* diag, const Item* items, int nitems, int32_t* err, double* partial,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, float4* out) {
     if (nitems <= 0) return cudaSuccess;
     const int grid = nblocks(nitems, kBlock / 32);
     if (mode == kDiag)
-        adjoint_vertex_kernel<kDiag><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, items, nitems, err, partial);
+        adjoint_vertex_kernel<kDiag><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
     else if (mode == kSweep)
-        adjoint_vertex_kernel<kSweep><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, items, nitems, err, partial);
+        adjoint_vertex_kernel<kSweep><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
+    else if (mode == kResid)
+        adjoint_vertex_kernel<kResid><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
+    else if (mode == kForce)
+        adjoint_vertex_kernel<kForce><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
     else
-        adjoint_vertex_kernel<kResid><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, items, nitems, err, partial);
+        adjoint_vertex_kernel<kApply><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
+    return cudaGetLastError();
+}
+
+int vec_blocks(int n) { return nblocks(n, kBlock); }
+
+cudaError_t launch_cg_init(int n, const float4* r, const float4* diag, float4* x, float4* z, float4* p,
+                           double* partial, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cg_init_kernel<<<nblocks(n, kBlock), kBlock, 0, st>>>(n, r, diag, x, z, p, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(int n, const double* sc, float4* x, float4* r, const float4* p, const float4* q,
+                             const float4* diag, float4* z, double* part_rz, double* part_rr, int32_t* flag,
+                             cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cg_update_kernel<<<nblocks(n, kBlock), kBlock, 0, st>>>(n, sc, x, r, p, q, diag, z, part_rz, part_rr, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_dir(int n, const double* sc, const float4* z, float4* p, const int32_t* flag, double* sc_rw,
+                          cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cg_dir_kernel<<<nblocks(n, kBlock), kBlock, 0, st>>>(n, sc, z, p, flag);
+    cg_shift_kernel<<<1, 1, 0, st>>>(sc_rw, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_newton_axpy(int nv, int nfree, State src, const float4* x, float s, State dst, cudaStream_t st) {
+    if (nv <= 0) return cudaSuccess;
+    newton_axpy_kernel<<<nblocks(nv, 256), 256, 0, st>>>(nv, nfree, src, x, s, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_vec(int nv, int nfree, const int32_t* perm, const float* in, float4* out, cudaStream_t st) {
+    if (nv <= 0) return cudaSuccess;
+    gather_vec_kernel<<<nblocks(nv, 256), 256, 0, st>>>(nv, nfree, perm, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_vec(int nv, int nfree, const int32_t* perm, const float4* in, float* out, cudaStream_t st) {
+    if (nv <= 0) return cudaSuccess;
+    scatter_vec_kernel<<<nblocks(nv, 256), 256, 0, st>>>(nv, nfree, perm, in, out);
     return cudaGetLastError();
 }
 

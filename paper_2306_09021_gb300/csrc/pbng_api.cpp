@@ -77,6 +77,9 @@ struct pbng_mesh {
     DevBuf d_active;                   // int32 [ncomp] component flags (1 = active)
     // adjoint (built on first use after each layout)
     DevBuf d_lam[3], d_gv, d_diag, d_hdl, d_tv, d_tb, d_dq_int, d_dq_caller, d_adj_partial;
+    // Newton-CG (pbng_newton_cg, pbng_force, pbng_hessian_apply): r, x, z, p, q
+    DevBuf d_nw[5], d_nw_part[2], d_nw_sc, d_nw_flag;
+    double* h_nw = nullptr;            // pinned: sc[3], flag
     bool adj_ready = false;
     std::vector<int32_t> dir_list;     // clamped ids in pbng_set_constraints order
     int32_t* h_active = nullptr;       // pinned host copy
@@ -1355,6 +1358,51 @@ pbng_status adjoint_resid(pbng_mesh* m, State u, float4* lam, double* out) {
 
 }  // namespace
 
+namespace {
+
+// Buffers of the Newton-CG solver and of pbng_force / pbng_hessian_apply.
+pbng_status newton_setup(pbng_mesh* m) {
+    pbng_status s = adjoint_setup(m);
+    if (s) return s;
+    for (auto& b : m->d_nw) PBNG_CUDA(m, ensure_buf(b, sizeof(float4) * (size_t)m->nv));
+    const size_t np = (size_t)std::max(1, std::max(vec_blocks(m->nfree), adjoint_warps(m->nitems_ring)));
+    for (auto& b : m->d_nw_part) PBNG_CUDA(m, ensure_buf(b, sizeof(double) * np));
+    PBNG_CUDA(m, ensure_buf(m->d_nw_sc, sizeof(double) * 4));
+    PBNG_CUDA(m, ensure_buf(m->d_nw_flag, sizeof(int32_t)));
+    if (!m->h_nw) PBNG_CUDA(m, cudaMallocHost((void**)&m->h_nw, sizeof(double) * 2));
+    return PBNG_OK;
+}
+
+// Checks shared by the Newton-CG entry points: corotated, ring layout.
+pbng_status newton_ready(pbng_mesh* m, const pbng_params* p) {
+    if (!valid_params(p)) return fail(m, PBNG_EINVAL, "bad parameters");
+    if (p->kernel_path != 0 || p->model != 0)
+        return fail(m, PBNG_EINVAL, "Newton-CG runs the corotated model on the ring layout (model 0, kernel_path 0)");
+    select_path(m, p);
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!m->all_ring) return fail(m, PBNG_EINVAL, "Newton-CG needs every colour in the ring layout");
+    return newton_setup(m);
+}
+
+// r = f + f^ext at state u into d_nw[0], the SPD blocks into d_diag; FP64 |r|^2 -> *rr.
+pbng_status newton_force(pbng_mesh* m, State u, double* rr) {
+    cudaStream_t st = m->stream;
+    float4* r = (float4*)m->d_nw[0].p;
+    PBNG_CUDA(m, launch_adjoint_vertex(kAdjForce, m->dm, u, nullptr, nullptr, (float4*)m->d_diag.p,
+                                       (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
+                                       (double*)m->d_nw_part[0].p, st, r));
+    PBNG_CUDA(m, launch_reduce((const double*)m->d_nw_part[0].p, adjoint_warps(m->nitems_ring),
+                               (double*)m->d_scalar.p, st));
+    m->kernel_launches += 2;
+    PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_scalar.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    *rr = m->h_pinned[0];
+    return check_err(m);
+}
+
+}  // namespace
+
 extern "C" {
 
 pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_dev, float* dL_dlogE_dev,
@@ -1442,6 +1490,176 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     if (rel_residual_out) *rel_residual_out = rel;
     if (result == PBNG_ENOTCONVERGED) m->err = "max_sweeps reached";
     if (result == PBNG_EDIVERGED) m->err = "adjoint iteration diverged";
+    return result;
+}
+
+pbng_status pbng_force(pbng_mesh* m, const float* u_dev, const pbng_params* p, float* f_out_dev) {
+    if (!m) return PBNG_EINVAL;
+    pbng_params dp;
+    if (!p) {
+        pbng_default_params(&dp);
+        p = &dp;
+    }
+    if (!u_dev || !f_out_dev) return fail(m, PBNG_EINVAL, "NULL argument");
+    pbng_status s = newton_ready(m, p);
+    if (s) return s;
+    cudaStream_t st = m->stream;
+    PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, (const int32_t*)m->d_perm.p, (const float4*)m->d_dir_hi.p,
+                             (const float4*)m->d_dir_lo.p, state_of(m, 3), st));
+    double rr = 0.0;
+    if ((s = newton_force(m, state_of(m, 3), &rr))) return s;
+    PBNG_CUDA(m, launch_scatter_vec(m->nv, m->nfree, (const int32_t*)m->d_perm.p, (const float4*)m->d_nw[0].p,
+                                    f_out_dev, st));
+    m->kernel_launches += 2;
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    return PBNG_OK;
+}
+
+pbng_status pbng_hessian_apply(pbng_mesh* m, const float* u_dev, const float* p_dev, const pbng_params* p,
+                               float* hp_out_dev) {
+    if (!m) return PBNG_EINVAL;
+    pbng_params dp;
+    if (!p) {
+        pbng_default_params(&dp);
+        p = &dp;
+    }
+    if (!u_dev || !p_dev || !hp_out_dev) return fail(m, PBNG_EINVAL, "NULL argument");
+    pbng_status s = newton_ready(m, p);
+    if (s) return s;
+    cudaStream_t st = m->stream;
+    const int32_t* perm = (const int32_t*)m->d_perm.p;
+    PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, perm, (const float4*)m->d_dir_hi.p,
+                             (const float4*)m->d_dir_lo.p, state_of(m, 3), st));
+    PBNG_CUDA(m, launch_gather_vec(m->nv, m->nfree, perm, p_dev, (float4*)m->d_nw[3].p, st));
+    PBNG_CUDA(m, launch_adjoint_vertex(kAdjApply, m->dm, state_of(m, 3), (float4*)m->d_nw[3].p, nullptr,
+                                       (float4*)m->d_diag.p, (const Item*)m->d_items.p, m->nitems_ring,
+                                       (int32_t*)m->d_err.p, (double*)m->d_nw_part[0].p, st, (float4*)m->d_nw[4].p));
+    PBNG_CUDA(m, launch_scatter_vec(m->nv, m->nfree, perm, (const float4*)m->d_nw[4].p, hp_out_dev, st));
+    m->kernel_launches += 4;
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    return check_err(m);
+}
+
+// Newton's method on f(u) + f^ext = 0 with the true Hessian (Eq. hess) and a
+// block-Jacobi preconditioned CG inner solve, truncated at the first
+// direction of non-positive curvature; a backtracking line search halves the
+// step until |r| decreases by the factor (1 - 1e-4 s).  If no step along the
+// CG direction is accepted, the preconditioned residual D^{-1} r (the
+// Jacobi counterpart of one PBNG sweep) is tried instead.
+pbng_status pbng_newton_cg(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_newton, int32_t max_cg,
+                           double cg_tol, const pbng_params* p, pbng_newton_info* info) {
+    if (!m) return PBNG_EINVAL;
+    if (!p || !u_dev || !(rel_tol >= 0.0) || max_newton < 0 || max_cg < 1 || !(cg_tol > 0.0 && cg_tol < 1.0))
+        return fail(m, PBNG_EINVAL, "bad Newton-CG arguments");
+    pbng_status s = newton_ready(m, p);
+    if (s) return s;
+    pbng_params q = *p;
+    q.resume = 0;
+    if ((s = begin(m, u_dev, &q, true))) return s;
+    cudaStream_t st = m->stream;
+    const int n = m->nfree;
+    const State u0 = state_of(m, 0), ut = state_of(m, 3);
+    float4* r = (float4*)m->d_nw[0].p;
+    float4* x = (float4*)m->d_nw[1].p;
+    float4* z = (float4*)m->d_nw[2].p;
+    float4* pd = (float4*)m->d_nw[3].p;
+    float4* hq = (float4*)m->d_nw[4].p;
+    double* sc = (double*)m->d_nw_sc.p;
+    int32_t* flag = (int32_t*)m->d_nw_flag.p;
+    double* part0 = (double*)m->d_nw_part[0].p;
+    double* part1 = (double*)m->d_nw_part[1].p;
+    const float4* diag = (const float4*)m->d_diag.p;
+    pbng_newton_info nfo{};
+    double r0 = 0.0;
+    for (double v : m->r0) r0 += v * v;
+    r0 = std::sqrt(r0);
+    if (!(r0 > 0.0)) r0 = 1.0;
+    double rr = 0.0;
+    if ((s = newton_force(m, u0, &rr))) return s;
+    double rel = std::sqrt(rr) / r0;
+    pbng_status result = PBNG_ENOTCONVERGED;
+    auto line_search = [&](bool* accepted) -> pbng_status {
+        *accepted = false;
+        double sl = 1.0;
+        for (int t = 0; t < 12 && !*accepted; ++t, sl *= 0.5) {
+            PBNG_CUDA(m, launch_newton_axpy(m->nv, n, u0, x, (float)sl, ut, st));
+            m->kernel_launches++;
+            double rt = 0.0;
+            pbng_status e = newton_force(m, ut, &rt);
+            if (e) return e;
+            if (std::isfinite(rt) && std::sqrt(rt) < (1.0 - 1e-4 * sl) * std::sqrt(rr)) {
+                PBNG_CUDA(m, launch_copy_state(m->nv, ut, u0, st));
+                m->kernel_launches++;
+                rr = rt;
+                *accepted = true;
+            } else {
+                ++nfo.line_search_halvings;
+            }
+        }
+        return PBNG_OK;
+    };
+    while (rel > rel_tol && nfo.newton_iterations < max_newton) {
+        PBNG_CUDA(m, cudaMemsetAsync(pd, 0, sizeof(float4) * (size_t)m->nv, st));
+        PBNG_CUDA(m, cudaMemsetAsync(flag, 0, sizeof(int32_t), st));
+        PBNG_CUDA(m, launch_cg_init(n, r, diag, x, z, pd, part0, st));
+        PBNG_CUDA(m, launch_reduce(part0, vec_blocks(n), sc, st));
+        m->kernel_launches += 2;
+        const double bnorm = std::sqrt(rr);
+        int k = 0;
+        while (k < max_cg) {
+            PBNG_CUDA(m, launch_adjoint_vertex(kAdjApply, m->dm, u0, pd, nullptr, (float4*)m->d_diag.p,
+                                               (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
+                                               part1, st, hq));
+            PBNG_CUDA(m, launch_reduce(part1, adjoint_warps(m->nitems_ring), sc + 1, st));
+            PBNG_CUDA(m, launch_cg_update(n, sc, x, r, pd, hq, diag, z, part0, part1, flag, st));
+            PBNG_CUDA(m, launch_reduce(part0, vec_blocks(n), sc + 2, st));
+            PBNG_CUDA(m, launch_reduce(part1, vec_blocks(n), sc + 3, st));
+            PBNG_CUDA(m, launch_cg_dir(n, sc, z, pd, flag, sc, st));
+            m->kernel_launches += 7;
+            ++k;
+            if (k % 8 == 0 || k == max_cg) {
+                PBNG_CUDA(m, cudaMemcpyAsync(m->h_nw, sc + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+                PBNG_CUDA(m, cudaMemcpyAsync(m->h_nw + 1, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                PBNG_CUDA(m, cudaStreamSynchronize(st));
+                int32_t f = 0;
+                std::memcpy(&f, m->h_nw + 1, sizeof(int32_t));
+                if (f || std::sqrt(m->h_nw[0]) <= cg_tol * bnorm) break;
+            }
+        }
+        nfo.cg_iterations += k;
+        if ((s = check_err(m))) return s;
+        bool ok = false;
+        if ((s = line_search(&ok))) return s;
+        if (!ok) {  // fall back to the preconditioned residual at u0 (recomputed: r was overwritten)
+            if ((s = newton_force(m, u0, &rr))) return s;
+            PBNG_CUDA(m, launch_cg_init(n, r, diag, x, z, pd, part0, st));
+            PBNG_CUDA(m, cudaMemcpyAsync(x, z, sizeof(float4) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+            m->kernel_launches++;
+            ++nfo.fallbacks;
+            if ((s = line_search(&ok))) return s;
+            if (!ok) {
+                // newton_force(ut) ran last: restore r and the blocks at u0
+                if ((s = newton_force(m, u0, &rr))) return s;
+                ++nfo.newton_iterations;
+                m->err = "line search failed";
+                break;
+            }
+        }
+        ++nfo.newton_iterations;
+        rel = std::sqrt(rr) / r0;
+        if (!std::isfinite(rel)) {
+            result = PBNG_EDIVERGED;
+            break;
+        }
+    }
+    if (rel <= rel_tol) result = PBNG_OK;
+    PBNG_CUDA(m, launch_store(m->nv, (const int32_t*)m->d_perm.p, u0, u_dev, st));
+    m->kernel_launches++;
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    m->has_state = false;  // the acceleration history does not describe this iterate
+    nfo.rel_residual = rel;
+    if (info) *info = nfo;
+    if (result == PBNG_ENOTCONVERGED && m->err.empty()) m->err = "max Newton iterations reached";
     return result;
 }
 
@@ -1781,6 +1999,8 @@ void pbng_destroy(pbng_mesh* m) {
                       &m->d_ring_ra, &m->d_ring_rb, &m->d_ring_rc, &m->d_ring_id, &m->d_items,
                       &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k,
+                      &m->d_nw[0], &m->d_nw[1], &m->d_nw[2], &m->d_nw[3], &m->d_nw[4], &m->d_nw_part[0],
+                      &m->d_nw_part[1], &m->d_nw_sc, &m->d_nw_flag,
                       &m->d_partial, &m->d_comp_sq, &m->d_scalar, &m->d_err};
     for (DevBuf* b : bufs) free_buf(*b);
     for (auto& sb : m->d_state)
@@ -1796,6 +2016,7 @@ void pbng_destroy(pbng_mesh* m) {
     free_buf(m->d_wg);
     if (m->h_pinned) cudaFreeHost(m->h_pinned);
     if (m->h_active) cudaFreeHost(m->h_active);
+    if (m->h_nw) cudaFreeHost(m->h_nw);
     free_buf(m->d_active);
     delete m;
 }

@@ -143,11 +143,28 @@ cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items
 // ring item; mode 0 computes the 3x3 diagonal blocks of H, mode 1 is one
 // Gauss-Seidel pass over the given items (one colour), mode 2 writes one FP64
 // partial of |dL/du - H lambda|^2 per warp (adjoint_warps(nitems) of them).
-enum { kAdjDiag = 0, kAdjSweep = 1, kAdjResid = 2 };
+// Mode 3 writes r = f + f^ext at u to out and the SPD blocks of Eq. mod_hess
+// to diag; mode 4 writes out = H lam (lam zero at clamped vertices); both
+// write one FP64 partial per warp (|r|^2, lam . H lam).
+enum { kAdjDiag = 0, kAdjSweep = 1, kAdjResid = 2, kAdjForce = 3, kAdjApply = 4 };
 int adjoint_warps(int nitems);
 cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4* lam, const float4* gv,
                                   float4* diag, const Item* items, int nitems, int32_t* err, double* partial,
-                                  cudaStream_t st);
+                                  cudaStream_t st, float4* out = nullptr);
+// Preconditioned conjugate gradients on the free rows (pbng_adjoint.cu): the
+// scalars stay on the device in sc[0..3] = (r.z, p.Hp, new r.z, |r|^2); one
+// FP64 partial per kBlock threads (vec_blocks(n) of them).
+int vec_blocks(int n);
+cudaError_t launch_cg_init(int n, const float4* r, const float4* diag, float4* x, float4* z, float4* p,
+                           double* partial, cudaStream_t st);
+cudaError_t launch_cg_update(int n, const double* sc, float4* x, float4* r, const float4* p, const float4* q,
+                             const float4* diag, float4* z, double* part_rz, double* part_rr, int32_t* flag,
+                             cudaStream_t st);
+cudaError_t launch_cg_dir(int n, const double* sc, const float4* z, float4* p, const int32_t* flag, double* sc_rw,
+                          cudaStream_t st);
+cudaError_t launch_newton_axpy(int nv, int nfree, State src, const float4* x, float s, State dst, cudaStream_t st);
+cudaError_t launch_gather_vec(int nv, int nfree, const int32_t* perm, const float* in, float4* out, cudaStream_t st);
+cudaError_t launch_scatter_vec(int nv, int nfree, const int32_t* perm, const float4* in, float* out, cudaStream_t st);
 cudaError_t launch_adjoint_tets(int ne, int nfree, const int4* tv, const float4* tb, State u, const float4* lam,
                                 float* dLdlogE, float* hdl, cudaStream_t st);
 cudaError_t launch_gather_rhs(int nfree, const int32_t* perm, const float* dLdu, float4* gv, cudaStream_t st);

@@ -9,7 +9,8 @@ import ctypes
 
 import numpy as np
 
-from ._lib import ACCEL, MODEL, PRECISION, PbngParams, PbngProfile, PbngSchedule, PbngSolveInfo, check, load
+from ._lib import (ACCEL, MODEL, PRECISION, PbngNewtonInfo, PbngParams, PbngProfile, PbngSchedule, PbngSolveInfo,
+                   check, load)
 
 
 def _dptr(a):
@@ -191,6 +192,39 @@ class Mesh:
         if dx.shape[0] != len(self.dirichlet):
             raise ValueError("one target per clamped vertex")
         check(load().pbng_set_dirichlet_targets(self.h, _dptr(dx)), "pbng_set_dirichlet_targets", self.h)
+
+    def force(self, u, params=None):
+        """pbng_force: f(u) + f^ext as a float32 CUDA tensor [nv, 3] (zero at clamped rows)."""
+        import torch
+        _check_u(u, self.nv)
+        out = torch.empty_like(u)
+        p = params if params is not None else default_params()
+        check(load().pbng_force(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.byref(p),
+                                ctypes.c_void_p(out.data_ptr())), "pbng_force", self.h)
+        return out
+
+    def hessian_apply(self, u, direction, params=None):
+        """pbng_hessian_apply: H(u) direction on free rows (zero at clamped rows)."""
+        import torch
+        _check_u(u, self.nv)
+        _check_u(direction, self.nv)
+        out = torch.empty_like(u)
+        p = params if params is not None else default_params()
+        check(load().pbng_hessian_apply(self.h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(direction.data_ptr()),
+                                        ctypes.byref(p), ctypes.c_void_p(out.data_ptr())),
+              "pbng_hessian_apply", self.h)
+        return out
+
+    def newton_cg(self, u, rel_tol, max_newton=50, max_cg=1000, cg_tol=0.1, params=None, raise_on_status=True):
+        """pbng_newton_cg in place on u; returns (status, info dict)."""
+        _check_u(u, self.nv)
+        p = params if params is not None else default_params()
+        info = PbngNewtonInfo()
+        st = load().pbng_newton_cg(self.h, ctypes.c_void_p(u.data_ptr()), float(rel_tol), int(max_newton),
+                                   int(max_cg), float(cg_tol), ctypes.byref(p), ctypes.byref(info))
+        if raise_on_status:
+            check(st, "pbng_newton_cg", self.h)
+        return st, {k: getattr(info, k) for k, _ in PbngNewtonInfo._fields_}
 
     def solve_info(self):
         """pbng_get_solve_info of the last solve as a dict."""
