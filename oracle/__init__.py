@@ -52,6 +52,8 @@ def lib():
             "ora_set_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
             "ora_set_inertia": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _D, _D]),
             "ora_lumped_mass": (None, [ctypes.c_void_p, _D]),
+            "ora_set_weak_constraints": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _I, _D, _D, _D, _D,
+                                                        ctypes.c_int]),
             "ora_cofactor": (None, [_D, _D]),
             "ora_modified_density_hessian": (None, [_D, ctypes.c_double, ctypes.c_double, _D]),
             "ora_create": (ctypes.c_void_p, [ctypes.c_int, _D, ctypes.c_int, _I, _D, _D, _U8,
@@ -201,6 +203,20 @@ class OracleMesh:
         self._inertia_keep = (dens, xh)
         if lib().ora_set_inertia(self.h, float(dt), _d(dens), _d(xh)) != 0:
             raise ValueError("bad inertia arguments")
+
+    def set_weak_constraints(self, idx, w, kn, kt, normal, recolour=False):
+        """General weak constraints: idx, w [nc, 8] (side 0 = columns 0..3,
+        side 1 = 4..7, idx -1 unused), kn, kt [nc], normal [nc, 3]."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 8)
+        nc = idx.shape[0]
+        w = _f64(w, (nc, 8)) if nc else np.zeros((0, 8))
+        kn = _f64(np.broadcast_to(kn, (nc,))) if nc else np.zeros(0)
+        kt = _f64(np.broadcast_to(kt, (nc,))) if nc else np.zeros(0)
+        nrm = _f64(np.broadcast_to(normal, (nc, 3))) if nc else np.zeros((0, 3))
+        self._wc_keep = (idx, w, kn, kt, nrm)
+        if lib().ora_set_weak_constraints(self.h, nc, idx.ctypes.data_as(_I), _d(w), _d(kn), _d(kt), _d(nrm),
+                                          1 if recolour else 0) != 0:
+            raise ValueError("bad weak constraints")
 
     def lumped_mass(self):
         out = np.zeros(self.nv)

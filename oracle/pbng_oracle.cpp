@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 #include <set>
+#include <array>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -366,6 +367,15 @@ struct Mesh {
     // and the inertial target xhat = 2 x^n - x^{n-1}.
     std::vector<double> mass, xhat;
     double inv_dt2 = 0.0;
+    // General weak constraints of Section "Weak Constraints":
+    // C_c(y) = sum_j (w0_cj - w1_cj) y_j, energy (1/2) C^T K_c C,
+    // K_c = k_tau I + (k_n - k_tau) n n^T.  wc_v / wc_b hold each constraint's
+    // vertices and coefficients w0 - w1 (duplicates merged); vert_wc lists the
+    // constraints of every vertex.
+    std::vector<std::vector<int>> wc_v;
+    std::vector<std::vector<double>> wc_b;
+    std::vector<std::array<double, 9>> wc_K;
+    std::vector<std::vector<int>> vert_wc;
     std::vector<int> colour;               // nv, -1 clamped
     std::vector<std::vector<int>> by_colour;
 };
@@ -396,24 +406,72 @@ void deformation_gradient(const Mesh& m, const double* x, int e, double* F) {
 // takes the least colour absent from the used-colour sets S_c of every
 // element (and multi-node weak constraint; none here) it belongs to, then
 // registers that colour in each of those sets.
-void colour_nodes(Mesh& m) {
-    std::vector<std::set<int>> S(m.ne);
-    m.colour.assign(m.nv, -1);
+void group_by_colour(Mesh& m) {
     int ncol = 0;
+    for (int i = 0; i < m.nv; ++i) ncol = std::max(ncol, m.colour[i] + 1);
+    m.by_colour.assign(ncol, {});
+    for (int i = 0; i < m.nv; ++i)
+        if (m.colour[i] >= 0) m.by_colour[m.colour[i]].push_back(i);
+}
+
+void colour_nodes(Mesh& m) {
+    // S_e for tets (first ne sets) and for multi-node weak constraints.
+    std::vector<std::set<int>> S(m.ne + m.wc_v.size());
+    m.colour.assign(m.nv, -1);
     for (int i = 0; i < m.nv; ++i) {
         if (m.dir[i]) continue;
         std::set<int> used;
         for (int k = m.inc_off[i]; k < m.inc_off[i + 1]; ++k)
             used.insert(S[m.inc_tet[k]].begin(), S[m.inc_tet[k]].end());
+        for (int c : m.vert_wc[i]) used.insert(S[m.ne + c].begin(), S[m.ne + c].end());
         int c = 0;
         while (used.count(c)) ++c;
         m.colour[i] = c;
         for (int k = m.inc_off[i]; k < m.inc_off[i + 1]; ++k) S[m.inc_tet[k]].insert(c);
-        ncol = std::max(ncol, c + 1);
+        for (int cc : m.vert_wc[i]) S[m.ne + cc].insert(c);
     }
-    m.by_colour.assign(ncol, {});
-    for (int i = 0; i < m.nv; ++i)
-        if (m.colour[i] >= 0) m.by_colour[m.colour[i]].push_back(i);
+    group_by_colour(m);
+}
+
+// Section "Collision Coloring": only nodes incident to weak constraints are
+// revisited (ascending id); each keeps its previous colour unless a node it
+// shares a tet or a constraint with already uses it, else takes the least
+// colour none of them uses.  Nodes of unchanged constraints keep their
+// colours, so visiting all constraint nodes recolours exactly those of the
+// new ones.
+void recolour_constraint_nodes(Mesh& m) {
+    for (int i = 0; i < m.nv; ++i) {
+        if (m.dir[i] || m.vert_wc[i].empty()) continue;
+        std::set<int> used;
+        for (int k = m.inc_off[i]; k < m.inc_off[i + 1]; ++k) {
+            const int e = m.inc_tet[k];
+            for (int j = 0; j < 4; ++j) {
+                const int v = m.tets[4 * (size_t)e + j];
+                if (v != i && m.colour[v] >= 0) used.insert(m.colour[v]);
+            }
+        }
+        for (int c : m.vert_wc[i])
+            for (int v : m.wc_v[c])
+                if (v != i && m.colour[v] >= 0) used.insert(m.colour[v]);
+        if (m.colour[i] >= 0 && !used.count(m.colour[i])) continue;
+        int c = 0;
+        while (used.count(c)) ++c;
+        m.colour[i] = c;
+    }
+    group_by_colour(m);
+}
+
+// C_c(x) and the force / Hessian contributions of constraint c on node i.
+void wc_value(const Mesh& m, int c, const double* x, double* C) {
+    C[0] = C[1] = C[2] = 0.0;
+    for (size_t k = 0; k < m.wc_v[c].size(); ++k)
+        for (int a = 0; a < 3; ++a) C[a] += m.wc_b[c][k] * x[3 * (size_t)m.wc_v[c][k] + a];
+}
+
+double wc_coeff(const Mesh& m, int c, int i) {
+    for (size_t k = 0; k < m.wc_v[c].size(); ++k)
+        if (m.wc_v[c][k] == i) return m.wc_b[c][k];
+    return 0.0;
 }
 
 // Right-hand side and modified Hessian of node i (Eq. pbgn_dx with the force
@@ -455,6 +513,18 @@ void local_system(const Mesh& m, const double* x, int i, double* r, double* A) {
                 r[a] -= m.kc * sd * m.pn[a];
                 for (int b = 0; b < 3; ++b) A[3 * a + b] += m.kc * m.pn[a] * m.pn[b];
             }
+        }
+    }
+    // General weak constraints: -dE/dx_i = -b_i K C, and b_i^2 K on A
+    // (the second term of Eq. mod_hess).
+    for (int c : m.vert_wc[i]) {
+        double C[3];
+        wc_value(m, c, x, C);
+        const double b = wc_coeff(m, c, i);
+        const double* K = m.wc_K[c].data();
+        for (int a = 0; a < 3; ++a) {
+            r[a] -= b * (K[3 * a] * C[0] + K[3 * a + 1] * C[1] + K[3 * a + 2] * C[2]);
+            for (int bb = 0; bb < 3; ++bb) A[3 * a + bb] += b * b * K[3 * a + bb];
         }
     }
     // Eq. fem_be moved to the right-hand side: -m_ii (x_i - xhat_i) / dt^2,
@@ -523,6 +593,13 @@ double energy(const Mesh& m, const double* x) {
             E += 0.5 * m.mass[i] * m.inv_dt2 * d2;
         }
     }
+    for (size_t c = 0; c < m.wc_v.size(); ++c) {  // (1/2) C^T K C
+        double C[3];
+        wc_value(m, (int)c, x, C);
+        const double* K = m.wc_K[c].data();
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) E += 0.5 * C[a] * K[3 * a + b] * C[b];
+    }
     return E;
 }
 
@@ -549,6 +626,15 @@ void hessian_dense(const Mesh& m, const double* x, std::vector<double>& H) {
                 }
             }
     }
+    for (size_t c = 0; c < m.wc_v.size(); ++c)
+        for (size_t p = 0; p < m.wc_v[c].size(); ++p)
+            for (size_t q = 0; q < m.wc_v[c].size(); ++q) {
+                const int vi = m.wc_v[c][p], vj = m.wc_v[c][q];
+                const double bb = m.wc_b[c][p] * m.wc_b[c][q];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        H[(size_t)(3 * vi + a) * n + 3 * vj + b] += bb * m.wc_K[c][3 * a + b];
+            }
     for (int i = 0; i < m.nv; ++i) {
         const double* xi = &x[3 * (size_t)i];
         if (m.inv_dt2 > 0.0 && !m.dir[i])
@@ -683,6 +769,7 @@ void* ora_create(int nv, const double* X, int ne, const int* tets, const double*
         m->pd = plane[3];
         m->kc = k_contact;
     }
+    m->vert_wc.assign(nv, {});
     colour_nodes(*m);
     *status = 0;
     return m;
@@ -710,6 +797,56 @@ int ora_set_inertia(void* h, double dt, const double* density, const double* xha
 void ora_lumped_mass(const void* h, double* out) {
     const Mesh& m = *static_cast<const Mesh*>(h);
     for (int i = 0; i < m.nv; ++i) out[i] = m.mass.empty() ? 0.0 : m.mass[i];
+}
+
+// General weak constraints (Section "Weak Constraints").  Constraint c has
+// up to 4 nodes per side: idx[8c + k] (-1 = unused), weights w[8c + k] >= 0
+// with k < 4 on side 0 and k >= 4 on side 1, each used side summing to one;
+// stiffness K_c = kt I + (kn - kt) n n^T with |n| = 1.  recolour = 0 colours
+// every node again greedily; 1 keeps the current colours and revisits the
+// constraint nodes (Section "Collision Coloring").  Returns nonzero on bad
+// input.
+int ora_set_weak_constraints(void* h, int nc, const int* idx, const double* w, const double* kn, const double* kt,
+                             const double* nrm, int recolour) {
+    Mesh& m = *static_cast<Mesh*>(h);
+    std::vector<std::vector<int>> cv(nc);
+    std::vector<std::vector<double>> cb(nc);
+    std::vector<std::array<double, 9>> cK(nc);
+    for (int c = 0; c < nc; ++c) {
+        double sum[2] = {0.0, 0.0};
+        for (int k = 0; k < 8; ++k) {
+            const int v = idx[8 * c + k];
+            const double wk = w[8 * c + k];
+            if (v < 0) continue;
+            if (v >= m.nv || !(wk >= 0.0)) return 1;
+            sum[k / 4] += wk;
+            const double coef = k < 4 ? wk : -wk;
+            size_t p = 0;
+            while (p < cv[c].size() && cv[c][p] != v) ++p;
+            if (p == cv[c].size()) {
+                cv[c].push_back(v);
+                cb[c].push_back(coef);
+            } else {
+                cb[c][p] += coef;
+            }
+        }
+        if (std::fabs(sum[0] - 1.0) > 1e-9 || std::fabs(sum[1] - 1.0) > 1e-9) return 1;
+        const double* n = &nrm[3 * c];
+        const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(nn > 0.0) || !(kn[c] >= 0.0) || !(kt[c] >= 0.0)) return 1;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                cK[c][3 * a + b] = (a == b ? kt[c] : 0.0) + (kn[c] - kt[c]) * n[a] * n[b] / (nn * nn);
+    }
+    m.wc_v = std::move(cv);
+    m.wc_b = std::move(cb);
+    m.wc_K = std::move(cK);
+    m.vert_wc.assign(m.nv, {});
+    for (int c = 0; c < nc; ++c)
+        for (int v : m.wc_v[c]) m.vert_wc[v].push_back(c);
+    if (recolour) recolour_constraint_nodes(m);
+    else colour_nodes(m);
+    return 0;
 }
 
 int ora_set_model(void* h, int model) {

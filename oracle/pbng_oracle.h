@@ -70,6 +70,16 @@ int ora_set_model(void* h, int model);
  * [nv][3]) is the inertial target 2 x^n - x^{n-1}.  dt <= 0 turns it off.
  * Returns nonzero on a NULL array. */
 int ora_set_inertia(void* h, double dt, const double* density, const double* xhat);
+/* General weak constraints (Section "Weak Constraints"):
+ * C_c(y) = sum_j w0_cj y_j - sum_j w1_cj y_j, energy (1/2) C_c^T K_c C_c with
+ * K_c = kt_c I + (kn_c - kt_c) n_c n_c^T.  Constraint c lists up to four
+ * nodes per side in idx[8c .. 8c+3] (side 0) and idx[8c+4 .. 8c+7] (side 1),
+ * -1 = unused, with non-negative weights w summing to one per side.  The
+ * colouring treats each constraint like an element; recolour = 1 keeps the
+ * current colours and revisits only the constraint nodes (Section
+ * "Collision Coloring"), 0 colours every node again.  Nonzero on bad input. */
+int ora_set_weak_constraints(void* h, int nc, const int* idx, const double* w, const double* kn, const double* kt,
+                             const double* nrm, int recolour);
 /* The lumped masses of the last ora_set_inertia (0 before). */
 void ora_lumped_mass(const void* h, double* out);
 

@@ -18,6 +18,7 @@ from .problems import (
     adjoint_block,
     adjoint_load_cases,
     concat_problems,
+    two_blocks_hanging,
 )
 
 __all__ = [
@@ -34,4 +35,5 @@ __all__ = [
     "adjoint_block",
     "adjoint_load_cases",
     "concat_problems",
+    "two_blocks_hanging",
 ]

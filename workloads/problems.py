@@ -231,3 +231,52 @@ def concat_problems(problems: List[Problem], spacing: float = 0.0):
         meta=dict(count=len(problems), offsets=offs),
     )
     return batch, mesh_id, offs
+
+
+def two_blocks_hanging(n_top: int = 4, n_bottom: int = 3, young: float = 1000.0, poisson: float = 0.3,
+                       density: float = 10.0, k: float = 1e8, g: float = 9.8) -> Problem:
+    """Two unit cubes stacked in z (the "Varying Stiffness" example): the top
+    one (z in [1, 2], n_top cells, top face clamped) holds the bottom one
+    (z in [0, 1], n_bottom cells, free) through zero-rest-length weak
+    constraints, one per vertex of the bottom block's top face, to the point
+    of the top block's bottom face at the same position.  That point is
+    interpolated with the barycentric weights of a top-block tet with a face
+    on z = 1 containing it.  Gravity -g in z, density and E as in the paper's
+    example; k_n = k_tau = k.  The constraints are in meta["weak"] as
+    (idx [nc, 8], w [nc, 8], kn [nc], kt [nc], normal [nc, 3])."""
+    Xa, ta = box_grid(n_top, n_top, n_top, 1.0 / n_top)
+    Xa = Xa + np.array([0.0, 0.0, 1.0])
+    Xb, tb = box_grid(n_bottom, n_bottom, n_bottom, 1.0 / n_bottom)
+    na = Xa.shape[0]
+    X = np.vstack([Xa, Xb])
+    tets = np.vstack([ta, tb + na]).astype(np.int32)
+    dirichlet = np.flatnonzero(np.isclose(X[:, 2], 2.0)).astype(np.int32)
+    bottom_faces = [t for t in ta if np.isclose(Xa[t, 2], 1.0).sum() == 3]
+    idx, w = [], []
+    for v in np.flatnonzero(np.isclose(Xb[:, 2], 1.0)):
+        P = Xb[v]
+        for t in bottom_faces:
+            T = Xa[t]
+            M = np.column_stack([T[1] - T[0], T[2] - T[0], T[3] - T[0]])
+            l123 = np.linalg.solve(M, P - T[0])
+            lam = np.concatenate([[1.0 - l123.sum()], l123])
+            if lam.min() >= -1e-12:
+                lam = np.clip(lam, 0.0, None)
+                lam /= lam.sum()
+                idx.append([na + v, -1, -1, -1] + [int(i) for i in t])
+                w.append([1.0, 0.0, 0.0, 0.0] + list(lam))
+                break
+        else:
+            raise RuntimeError("no top-block tet contains a binding point")
+    nc = len(idx)
+    ne = tets.shape[0]
+    p = Problem(
+        name=f"two_blocks_{n_top}_{n_bottom}", X=X, tets=tets,
+        young=np.full(ne, young), poisson=np.full(ne, poisson),
+        dirichlet=dirichlet, x0=X.copy(),
+        body_accel=np.array([0.0, 0.0, -g]), density=np.full(ne, density),
+        meta=dict(cells=(n_top, n_bottom)),
+    )
+    p.meta["weak"] = (np.array(idx, np.int32), np.array(w), np.full(nc, k), np.full(nc, k),
+                      np.tile([0.0, 0.0, 1.0], (nc, 1)))
+    return p
