@@ -198,6 +198,29 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
                          float* dL_dxD_dev, double rel_tol, int32_t max_sweeps, const pbng_params* p,
                          int32_t* sweeps_out, double* rel_residual_out);
 
+/* General weak constraints (Section "Weak Constraints"): constraint c adds
+ * (1/2) C_c^T K_c C_c to the energy, C_c(y) = sum_j w0_cj y_j - sum_j w1_cj y_j
+ * joining two interpolated points (zero rest length), and
+ * K_c = k_tau I + (k_n - k_tau) n n^T (n normalised here).
+ *   idx     host int32 [nc][8]: side 0 in columns 0..3, side 1 in 4..7,
+ *           -1 = unused (a vertex may appear on both sides)
+ *   w       host double [nc][8]: weights >= 0, each side summing to one
+ *   kn, kt  host double [nc] >= 0;  normal  host double [nc][3], nonzero
+ * Each node update adds -beta K_c C_c to its force and beta^2 K_c to its
+ * nodal Hessian (beta = w0 - w1 at the node; Eq. mod_hess).  The colouring
+ * treats each constraint like an element (its free vertices get distinct
+ * colours).  recolour = 0 colours the mesh again from scratch; 1 keeps the
+ * current colours and revisits only the constraint vertices (Section
+ * "Collision Coloring": a vertex keeps its colour unless a neighbour through
+ * a tet or a constraint uses it, else takes the least unused colour), so
+ * adding constraints to a coloured mesh recolours only their vertices.
+ * The layout is rebuilt on the next call (pbng_get_profile reports the
+ * colouring and layout times).  nc = 0 removes all constraints.  A
+ * constraint may not join two batch components.  pbng_adjoint and
+ * pbng_newton_cg reject meshes with such constraints. */
+pbng_status pbng_set_weak_constraints(pbng_mesh* m, int32_t nc, const int32_t* idx, const double* w,
+                                      const double* kn, const double* kt, const double* normal, int32_t recolour);
+
 /* Backward Euler (Section "Position-Based Dynamics", Eq. fem_be): with
  * dt > 0 each free vertex gains the inertial term -m_ii (x_i - xhat_i) / dt^2
  * in its force and m_ii / dt^2 on the diagonal of its nodal Hessian, i.e. a
@@ -322,6 +345,8 @@ typedef struct {
     int64_t incidences;           /* (free vertex, incident tet) pairs        */
     int32_t ncolours;
     int32_t reserved;
+    double colour_ms;             /* host time of the last colouring (or recolouring) */
+    double layout_ms;             /* host time of the last layout build, colouring included */
 } pbng_profile;
 
 /* enable = 1 starts (and zeroes) the counters, 0 stops timing. */

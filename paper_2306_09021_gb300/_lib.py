@@ -52,6 +52,8 @@ class PbngProfile(ctypes.Structure):
         ("incidences", ctypes.c_int64),
         ("ncolours", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("colour_ms", ctypes.c_double),
+        ("layout_ms", ctypes.c_double),
     ]
 
 
@@ -127,6 +129,7 @@ SIGNATURES = {
     "pbng_autotune": (_I32, [_P, _P, ctypes.POINTER(PbngParams), _I32, ctypes.POINTER(PbngSchedule)]),
     "pbng_get_solve_info": (_I32, [_P, ctypes.POINTER(PbngSolveInfo)]),
     "pbng_set_inertia": (_I32, [_P, _D, _PD]),
+    "pbng_set_weak_constraints": (_I32, [_P, _I32, _PI, _PD, _PD, _PD, _PD, _I32]),
     "pbng_step": (_I32, [_P, _P, _P, _I32, _D, ctypes.POINTER(PbngParams), _PI, _PD]),
     "pbng_set_dirichlet_targets": (_I32, [_P, _PD]),
     "pbng_force": (_I32, [_P, _P, ctypes.POINTER(PbngParams), _P]),

@@ -13,6 +13,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <array>
+#include <chrono>
 #include <vector>
 
 using namespace pbng;
@@ -44,6 +46,12 @@ struct pbng_mesh {
     bool has_plane = false;
     double pn[3] = {0, 0, 1}, pd = 0.0, kc = 0.0;
     std::vector<double> fext;       // 3 nv
+    // general weak constraints (pbng_set_weak_constraints), caller ids
+    std::vector<std::vector<int32_t>> wc_v;
+    std::vector<std::vector<double>> wc_b;
+    std::vector<std::array<double, 6>> wc_k;
+    bool wc_incremental = false;       // next layout: keep colours, revisit constraint vertices
+    double colour_ms = 0.0, layout_ms = 0.0;
 
     // layout
     bool dirty = true;
@@ -63,6 +71,7 @@ struct pbng_mesh {
     double be_dt = 0.0;
     std::vector<double> be_mass;
     DevBuf d_aux_base0, d_aux_base1, d_be_k;  // aux without inertia, m_v / dt^2 (internal order)
+    DevBuf d_wc_off, d_wc_list, d_wc_v, d_wc_b, d_wc_k, d_wc_c0;
     bool built_direct = false;         // layout built with want_direct
     std::vector<int32_t> table_partial_off;  // residual partial offset per colour
     int32_t total_partials = 0;
@@ -232,9 +241,9 @@ double det3(const double* F) {
 // registered yet, then register it in each of those elements.  Element
 // colour sets are bit masks of `words` 64-bit words.
 bool greedy_colour(const pbng_mesh& m, const std::vector<int32_t>& inc_off,
-                   const std::vector<int32_t>& inc_tet, int words, std::vector<int32_t>& colour,
+                   const std::vector<int32_t>& inc_tet, int32_t nelem, int words, std::vector<int32_t>& colour,
                    int32_t& ncol) {
-    std::vector<uint64_t> used((size_t)m.ne * words, 0);
+    std::vector<uint64_t> used((size_t)nelem * words, 0);
     std::vector<uint64_t> acc(words);
     colour.assign(m.nv, -1);
     ncol = 0;
@@ -260,6 +269,33 @@ bool greedy_colour(const pbng_mesh& m, const std::vector<int32_t>& inc_off,
             used[(size_t)inc_tet[k] * words + (c >> 6)] |= 1ull << (c & 63);
     }
     return true;
+}
+
+// Section "Collision Coloring": starting from the current colours, every
+// free vertex of a weak constraint (ascending id) keeps its colour unless a
+// vertex it shares a tet or a constraint with uses it, else takes the least
+// colour none of them uses.  Vertices of constraints that were already there
+// keep their colours, so only those of new constraints change.
+void recolour_constraint_vertices(const pbng_mesh& m, const std::vector<int32_t>& inc_off,
+                                  const std::vector<int32_t>& inc_tet, const std::vector<int32_t>& vwc_off,
+                                  const std::vector<int32_t>& vwc, std::vector<int32_t>& colour, int32_t& ncol) {
+    std::vector<uint8_t> used;
+    for (int32_t i = 0; i < m.nv; ++i) {
+        if (m.is_dir[i] || vwc_off[i + 1] == vwc_off[i]) continue;
+        used.assign((size_t)ncol + 1, 0);
+        auto mark = [&](int32_t v) {
+            if (v != i && colour[v] >= 0) used[colour[v]] = 1;
+        };
+        for (int32_t k = inc_off[i]; k < inc_off[i + 1]; ++k)
+            for (int j = 0; j < 4; ++j) mark(m.tets[4 * (size_t)inc_tet[k] + j]);
+        for (int32_t k = vwc_off[i]; k < vwc_off[i + 1]; ++k)
+            for (int32_t v : m.wc_v[vwc[k]]) mark(v);
+        if (colour[i] >= 0 && !used[colour[i]]) continue;
+        int32_t c = 0;
+        while (used[c]) ++c;
+        colour[i] = c;
+        ncol = std::max(ncol, c + 1);
+    }
 }
 
 int width_for(int deg) {
@@ -293,11 +329,47 @@ pbng_status build_layout(pbng_mesh* m) {
                 fill[v]++;
             }
     }
-    int words = 1;
-    while (!greedy_colour(*m, inc_off, inc_tet, words, m->colour, m->ncol)) {
-        words *= 2;
-        if (words > 64) return fail(m, PBNG_EINVAL, "colouring needs more than 4096 colours");
+    const auto t_start = std::chrono::steady_clock::now();
+    // vertex -> weak constraints
+    const int32_t nwc = (int32_t)m->wc_v.size();
+    std::vector<int32_t> vwc_off(nv + 1, 0), vwc;
+    for (const auto& c : m->wc_v)
+        for (int32_t v : c) vwc_off[v + 1]++;
+    for (int32_t i = 0; i < nv; ++i) vwc_off[i + 1] += vwc_off[i];
+    vwc.resize(vwc_off[nv]);
+    {
+        std::vector<int32_t> fill(vwc_off.begin(), vwc_off.end() - 1);
+        for (int32_t c = 0; c < nwc; ++c)
+            for (int32_t v : m->wc_v[c]) vwc[fill[v]++] = c;
     }
+    bool incremental = m->wc_incremental && (int32_t)m->colour.size() == nv;
+    if (incremental)
+        for (int32_t i = 0; i < nv && incremental; ++i) incremental = m->is_dir[i] || m->colour[i] >= 0;
+    if (incremental) {
+        int32_t ncol = 0;
+        for (int32_t i = 0; i < nv; ++i) {
+            if (m->is_dir[i]) m->colour[i] = -1;
+            ncol = std::max(ncol, m->colour[i] + 1);
+        }
+        recolour_constraint_vertices(*m, inc_off, inc_tet, vwc_off, vwc, m->colour, ncol);
+        m->ncol = ncol;
+    } else {
+        // tets and weak constraints are the elements of the greedy colouring
+        std::vector<int32_t> ce_off(nv + 1, 0), ce;
+        ce.reserve(inc_tet.size() + vwc.size());
+        for (int32_t i = 0; i < nv; ++i) {
+            ce.insert(ce.end(), inc_tet.begin() + inc_off[i], inc_tet.begin() + inc_off[i + 1]);
+            for (int32_t k = vwc_off[i]; k < vwc_off[i + 1]; ++k) ce.push_back(ne + vwc[k]);
+            ce_off[i + 1] = (int32_t)ce.size();
+        }
+        int words = 1;
+        while (!greedy_colour(*m, ce_off, ce, ne + nwc, words, m->colour, m->ncol)) {
+            words *= 2;
+            if (words > 64) return fail(m, PBNG_EINVAL, "colouring needs more than 4096 colours");
+        }
+    }
+    m->wc_incremental = false;
+    m->colour_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     auto deg = [&](int32_t i) { return inc_off[i + 1] - inc_off[i]; };
     // 1-ring of each free vertex (caller ids, ascending)
     std::vector<int32_t> ring_off(nv + 1, 0), ring;
@@ -562,6 +634,49 @@ pbng_status build_layout(pbng_mesh* m) {
         PBNG_CUDA(m, upload(m->d_aux_base1, base1, st));
         PBNG_CUDA(m, upload(m->d_be_k, bek, st));
     }
+    if (nwc > 0) {
+        // constraint tables in internal ids; per free vertex, its constraints
+        std::vector<int32_t> iperm(nv);
+        for (int32_t w = 0; w < nv; ++w) iperm[order[w]] = w;
+        std::vector<int32_t> cv(8 * (size_t)nwc, -1);
+        std::vector<float> cb(8 * (size_t)nwc, 0.f), ck(6 * (size_t)nwc);
+        std::vector<float4> c0(2 * (size_t)nwc);
+        for (int32_t c = 0; c < nwc; ++c) {
+            double C0[3] = {0.0, 0.0, 0.0};
+            for (size_t q = 0; q < m->wc_v[c].size(); ++q) {
+                const int32_t v = m->wc_v[c][q];
+                cv[8 * (size_t)c + q] = iperm[v];
+                cb[8 * (size_t)c + q] = (float)m->wc_b[c][q];
+                for (int a = 0; a < 3; ++a) C0[a] += m->wc_b[c][q] * m->X[3 * (size_t)v + a];
+            }
+            for (int k = 0; k < 6; ++k) ck[6 * (size_t)c + k] = (float)m->wc_k[c][k];
+            const float h0 = (float)C0[0], h1 = (float)C0[1], h2 = (float)C0[2];
+            c0[2 * (size_t)c] = make_float4(h0, h1, h2, 0.f);
+            c0[2 * (size_t)c + 1] = make_float4((float)(C0[0] - h0), (float)(C0[1] - h1), (float)(C0[2] - h2), 0.f);
+        }
+        std::vector<int32_t> woff(m->nfree + 1, 0);
+        std::vector<int2> wlist;
+        for (int32_t w = 0; w < m->nfree; ++w) {
+            const int32_t i = order[w];
+            for (int32_t k = vwc_off[i]; k < vwc_off[i + 1]; ++k) {
+                const int32_t c = vwc[k];
+                double b = 0.0;
+                for (size_t q = 0; q < m->wc_v[c].size(); ++q)
+                    if (m->wc_v[c][q] == i) b = m->wc_b[c][q];
+                const float bf = (float)b;
+                int32_t bits;
+                std::memcpy(&bits, &bf, sizeof(bits));
+                wlist.push_back(make_int2(c, bits));
+            }
+            woff[w + 1] = (int32_t)wlist.size();
+        }
+        PBNG_CUDA(m, upload(m->d_wc_off, woff, st));
+        PBNG_CUDA(m, upload(m->d_wc_list, wlist, st));
+        PBNG_CUDA(m, upload(m->d_wc_v, cv, st));
+        PBNG_CUDA(m, upload(m->d_wc_b, cb, st));
+        PBNG_CUDA(m, upload(m->d_wc_k, ck, st));
+        PBNG_CUDA(m, upload(m->d_wc_c0, c0, st));
+    }
     PBNG_CUDA(m, upload(m->d_comp, comp, st));
     PBNG_CUDA(m, upload(m->d_perm, m->perm, st));
     PBNG_CUDA(m, upload(m->d_dir_hi, dhi, st));
@@ -603,6 +718,14 @@ pbng_status build_layout(pbng_mesh* m) {
     d.pn_y = (float)m->pn[1];
     d.pn_z = (float)m->pn[2];
     d.k_contact = m->has_plane ? (float)m->kc : 0.0f;
+    const bool has_wc = !m->wc_v.empty();
+    d.wc_off = has_wc ? (const int32_t*)m->d_wc_off.p : nullptr;
+    d.wc_list = has_wc ? (const int2*)m->d_wc_list.p : nullptr;
+    d.wc_v = has_wc ? (const int32_t*)m->d_wc_v.p : nullptr;
+    d.wc_b = has_wc ? (const float*)m->d_wc_b.p : nullptr;
+    d.wc_k = has_wc ? (const float*)m->d_wc_k.p : nullptr;
+    d.wc_c0 = has_wc ? (const float4*)m->d_wc_c0.p : nullptr;
+    m->layout_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     m->built_direct = m->want_direct;
     m->adj_ready = false;
     m->dirty = false;
@@ -1048,6 +1171,61 @@ pbng_status pbng_set_material(pbng_mesh* m, const double* young, const double* p
     return PBNG_OK;
 }
 
+pbng_status pbng_set_weak_constraints(pbng_mesh* m, int32_t nc, const int32_t* idx, const double* w,
+                                      const double* kn, const double* kt, const double* normal, int32_t recolour) {
+    if (!m) return PBNG_EINVAL;
+    m->err.clear();
+    if (nc < 0 || (nc > 0 && (!idx || !w || !kn || !kt || !normal)))
+        return fail(m, PBNG_EINVAL, "bad weak-constraint arrays");
+    std::vector<std::vector<int32_t>> cv(nc);
+    std::vector<std::vector<double>> cb(nc);
+    std::vector<std::array<double, 6>> ck(nc);
+    try {
+        for (int32_t c = 0; c < nc; ++c) {
+            double sum[2] = {0.0, 0.0};
+            for (int k = 0; k < 8; ++k) {
+                const int32_t v = idx[8 * (size_t)c + k];
+                const double wk = w[8 * (size_t)c + k];
+                if (v < 0) continue;
+                if (v >= m->nv || !(wk >= 0.0)) return fail(m, PBNG_EINVAL, "bad weak-constraint vertex or weight");
+                sum[k / 4] += wk;
+                const double coef = k < 4 ? wk : -wk;
+                size_t q = 0;
+                while (q < cv[c].size() && cv[c][q] != v) ++q;
+                if (q == cv[c].size()) {
+                    cv[c].push_back(v);
+                    cb[c].push_back(coef);
+                } else {
+                    cb[c][q] += coef;
+                }
+            }
+            if (std::fabs(sum[0] - 1.0) > 1e-9 || std::fabs(sum[1] - 1.0) > 1e-9)
+                return fail(m, PBNG_EINVAL, "the weights of each side must sum to one");
+            if (m->ncomp > 1)
+                for (int32_t v : cv[c])
+                    if (m->comp_of[v] != m->comp_of[cv[c][0]])
+                        return fail(m, PBNG_EINVAL, "a weak constraint joins two components");
+            const double* n = normal + 3 * (size_t)c;
+            const double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+            if (!(nn > 0.0) || !(kn[c] >= 0.0) || !(kt[c] >= 0.0))
+                return fail(m, PBNG_EINVAL, "bad weak-constraint stiffness or normal");
+            // K = k_tau I + (k_n - k_tau) n n^T, upper triangle 00 01 02 11 12 22
+            const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+            for (int k = 0; k < 6; ++k)
+                ck[c][k] = (ia[k] == ib[k] ? kt[c] : 0.0) + (kn[c] - kt[c]) * n[ia[k]] * n[ib[k]] / nn;
+        }
+    } catch (const std::bad_alloc&) {
+        return PBNG_ENOMEM;
+    }
+    m->wc_v = std::move(cv);
+    m->wc_b = std::move(cb);
+    m->wc_k = std::move(ck);
+    m->wc_incremental = recolour != 0;
+    m->dirty = true;
+    m->has_state = false;
+    return PBNG_OK;
+}
+
 pbng_status pbng_set_inertia(pbng_mesh* m, double dt, const double* density) {
     if (!m) return PBNG_EINVAL;
     m->err.clear();
@@ -1382,6 +1560,7 @@ pbng_status newton_ready(pbng_mesh* m, const pbng_params* p) {
     pbng_status s = ensure_ready(m);
     if (s) return s;
     if (!m->all_ring) return fail(m, PBNG_EINVAL, "Newton-CG needs every colour in the ring layout");
+    if (!m->wc_v.empty()) return fail(m, PBNG_EINVAL, "Newton-CG does not support two-sided weak constraints");
     return newton_setup(m);
 }
 
@@ -1417,6 +1596,7 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     pbng_status s = ensure_ready(m);
     if (s) return s;
     if (!m->all_ring) return fail(m, PBNG_EINVAL, "the adjoint needs every colour in the ring layout");
+    if (!m->wc_v.empty()) return fail(m, PBNG_EINVAL, "the adjoint does not support two-sided weak constraints");
     if ((s = adjoint_setup(m))) return s;
     cudaStream_t st = m->stream;
     // u_eq -> state slot 3 (clamped vertices at their targets)
@@ -1829,6 +2009,8 @@ pbng_status pbng_get_profile(pbng_mesh* m, pbng_profile* out) {
     out->free_vertices = m->nfree;
     out->incidences = m->ninc;
     out->ncolours = m->ncol;
+    out->colour_ms = m->colour_ms;
+    out->layout_ms = m->layout_ms;
     return PBNG_OK;
 }
 
@@ -1998,7 +2180,8 @@ void pbng_destroy(pbng_mesh* m) {
                       &m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
                       &m->d_ring_ra, &m->d_ring_rb, &m->d_ring_rc, &m->d_ring_id, &m->d_items,
                       &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
-                      &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k,
+                      &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k, &m->d_wc_off, &m->d_wc_list, &m->d_wc_v,
+                      &m->d_wc_b, &m->d_wc_k, &m->d_wc_c0,
                       &m->d_nw[0], &m->d_nw[1], &m->d_nw[2], &m->d_nw[3], &m->d_nw[4], &m->d_nw_part[0],
                       &m->d_nw_part[1], &m->d_nw_sc, &m->d_nw_flag,
                       &m->d_partial, &m->d_comp_sq, &m->d_scalar, &m->d_err};

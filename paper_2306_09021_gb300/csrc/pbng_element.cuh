@@ -302,6 +302,65 @@ __device__ __forceinline__ void vertex_terms(const DeviceMesh& m, float4 x0, flo
     }
 }
 
+// General weak constraints of Section "Weak Constraints" on free vertex v:
+// for each constraint c with own coefficient beta (w0 - w1 at v),
+// C = C0 + sum_q b_q u_q, r -= beta K C and A += beta^2 K (the second term
+// of Eq. mod_hess).  The other vertices of c have other colours, so none of
+// them is written by the pass that updates v.
+// C is small next to the displacements it is formed from (a stiff binding
+// holds its two points together), so it is accumulated without rounding
+// loss: each b_q u_q as an exact product pair (FMA), summed with TwoSum, on
+// top of the float-pair rest value C0.
+__device__ __forceinline__ void acc_exact(float& s, float& c, float b, float u) {
+    const float p = b * u;
+    const float pe = __fmaf_rn(b, u, -p);  // b u - p exactly
+    const float t = __fadd_rn(s, p);
+    const float bp = __fadd_rn(t, -s);
+    c += __fadd_rn(__fadd_rn(s, -__fadd_rn(t, -bp)), __fadd_rn(p, -bp)) + pe;
+    s = t;
+}
+
+template <bool COMP, bool NEED_A>
+__device__ __forceinline__ void weak_terms(const DeviceMesh& m, const State& s, int v, float* r, float* A) {
+    if (!m.wc_off) return;
+    const int k1 = m.wc_off[v + 1];
+    for (int k = m.wc_off[v]; k < k1; ++k) {
+        const int2 e = m.wc_list[k];
+        const int c = e.x;
+        const float beta = __int_as_float(e.y);
+        const float4 c0 = m.wc_c0[2 * c], c0l = m.wc_c0[2 * c + 1];
+        float S[3] = {c0.x, c0.y, c0.z}, E[3] = {c0l.x, c0l.y, c0l.z};
+        for (int q = 0; q < 8; ++q) {
+            const int j = m.wc_v[8 * c + q];
+            if (j < 0) break;
+            const float bq = m.wc_b[8 * c + q];
+            const float4 h = s.hi[j];
+            acc_exact(S[0], E[0], bq, h.x);
+            acc_exact(S[1], E[1], bq, h.y);
+            acc_exact(S[2], E[2], bq, h.z);
+            if (COMP) {
+                const float4 l = s.lo[j];
+                E[0] += bq * l.x;
+                E[1] += bq * l.y;
+                E[2] += bq * l.z;
+            }
+        }
+        const float C[3] = {S[0] + E[0], S[1] + E[1], S[2] + E[2]};
+        const float* K = m.wc_k + 6 * c;
+        const float KC0 = K[0] * C[0] + K[1] * C[1] + K[2] * C[2];
+        const float KC1 = K[1] * C[0] + K[3] * C[1] + K[4] * C[2];
+        const float KC2 = K[2] * C[0] + K[4] * C[1] + K[5] * C[2];
+        r[0] -= beta * KC0;
+        r[1] -= beta * KC1;
+        r[2] -= beta * KC2;
+        if (NEED_A) {
+            const float b2 = beta * beta;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) A[t] += b2 * K[t];
+        }
+    }
+}
+
 // hi + lo += d, keeping the pair normalised (TwoSum, then Fast2Sum).
 __device__ __forceinline__ void pair_add(float& hi, float& lo, float d) {
     const float s = __fadd_rn(hi, d);

@@ -49,6 +49,18 @@ struct DeviceMesh {
     const int32_t* ring_id;  // [nslots] internal id of the vertex's l-th 1-ring neighbour (own id when padding)
     float pn_x, pn_y, pn_z;  // contact plane normal (unit)
     float k_contact;         // 0 = no plane
+    // General weak constraints (nullptr when there are none): constraint c
+    // couples up to 8 vertices wc_v[8c + q] (internal ids, -1 unused) with
+    // coefficients wc_b[8c + q] = w0 - w1; C = C0 + sum_q b_q u_q with the
+    // rest value C0 = sum_q b_q X_q as a float pair wc_c0[2c] + wc_c0[2c + 1];
+    // stiffness upper triangle wc_k[6c ..].  Free vertex v owns entries
+    // wc_off[v] .. wc_off[v + 1] of wc_list = (constraint, own coefficient bits).
+    const int32_t* wc_off;
+    const int2* wc_list;
+    const int32_t* wc_v;
+    const float* wc_b;
+    const float* wc_k;
+    const float4* wc_c0;
 };
 
 // The iterate: displacement u = x - X as a float pair hi + lo (lo is unused

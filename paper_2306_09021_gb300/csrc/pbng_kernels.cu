@@ -65,6 +65,7 @@ __device__ __forceinline__ void vertex_group(const DeviceMesh& m, State s, int v
     }
     if (!active || lane != 0) return;
     el::vertex_terms<COMP, UPDATE>(m, __ldg(m.aux0 + v), __ldg(m.aux1 + v), uh, ul, r, A);
+    el::weak_terms<COMP, UPDATE>(m, s, v, r, A);
     if (!UPDATE) {
         *rr = (double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2];
         if (r_out) {

@@ -222,6 +222,7 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
         // a frozen vertex of a mixed item is not written
         S.q.v[e] = (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) ? -1 : v;
     } else {
+        el::weak_terms<COMP, false>(m, s, v, rv, A);
         const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];
         if (comp_sq) atomicAdd(comp_sq + m.comp[v], q);
         else rr += q;
@@ -243,8 +244,8 @@ __device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, WarpS
 // All lanes: solve and write the qn queued vertices, one per lane.  The own
 // displacement is read again here; no other update of the pass writes it.
 template <bool COMP>
-__device__ __forceinline__ void flush_queue(State s, const WarpSmem& S, int qn, int lane, PassParams pp,
-                                            int32_t* err) {
+__device__ __forceinline__ void flush_queue(const DeviceMesh& m, State s, const WarpSmem& S, int qn, int lane,
+                                            PassParams pp, int32_t* err) {
     __syncwarp();
     if (lane < qn) {
         const int v = S.q.v[lane];
@@ -256,6 +257,7 @@ __device__ __forceinline__ void flush_queue(State s, const WarpSmem& S, int qn, 
             for (int k = 0; k < 6; ++k) A[k] = S.q.val[3 + k][lane];
             const float3 uh = f3(s.hi[v]);
             const float3 ul = COMP ? f3(s.lo[v]) : make_float3(0.f, 0.f, 0.f);
+            el::weak_terms<COMP, true>(m, s, v, rv, A);
             el::solve_and_write<COMP>(s, v, uh, ul, rv, A, pp, err);
         }
     }
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
                 const Item& it = S.desc[k % kRecStages];
                 if (!it.skip) qn += it.nv;
                 if (qn > kQueue - kItemVerts || (k + 1 == n && qn > 0)) {
-                    flush_queue<COMP>(s, S, qn, lane, pp, err);
+                    flush_queue<COMP>(m, s, S, qn, lane, pp, err);
                     qn = 0;
                 }
             }

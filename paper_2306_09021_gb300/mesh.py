@@ -166,6 +166,18 @@ class Mesh:
             check(st, "pbng_solve", self.h)
         return st, sweeps.value, out
 
+    def set_weak_constraints(self, idx, w, kn, kt, normal, recolour=False):
+        """pbng_set_weak_constraints: idx, w [nc, 8] (side 0 = columns 0..3,
+        side 1 = 4..7, idx -1 unused), kn, kt [nc], normal [nc, 3]."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32).reshape(-1, 8)
+        nc = idx.shape[0]
+        w = np.ascontiguousarray(w, dtype=np.float64).reshape(nc, 8)
+        kn = np.ascontiguousarray(np.broadcast_to(kn, (nc,)), dtype=np.float64)
+        kt = np.ascontiguousarray(np.broadcast_to(kt, (nc,)), dtype=np.float64)
+        nrm = np.ascontiguousarray(np.broadcast_to(normal, (nc, 3)), dtype=np.float64)
+        check(load().pbng_set_weak_constraints(self.h, nc, _iptr(idx), _dptr(w), _dptr(kn), _dptr(kt), _dptr(nrm),
+                                               1 if recolour else 0), "pbng_set_weak_constraints", self.h)
+
     def set_inertia(self, dt, density=None):
         """pbng_set_inertia: backward Euler with lumped masses (dt <= 0: quasistatic)."""
         de = None if density is None else np.ascontiguousarray(np.broadcast_to(density, (self.ne,)), dtype=np.float64)
