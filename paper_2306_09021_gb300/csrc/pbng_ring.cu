@@ -160,7 +160,7 @@ __device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, Warp
 
 // All lanes: gather the 1-ring displacements and own-vertex data of the item
 // in record stage r into gather stage g.
-template <bool COMP>
+template <bool COMP, bool UPDATE>
 __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& s, WarpSmem& S, int r, int g,
                                               int lane) {
     const Item it = S.desc[r];
@@ -173,14 +173,72 @@ __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& 
         const int v = it.v0 + lane;
         cp_async16(G.oh + lane, s.hi + v);
         if (COMP) cp_async16(G.ol + lane, s.lo + v);
-        cp_async16(G.a0 + lane, m.aux0 + v);
-        cp_async16(G.a1 + lane, m.aux1 + v);
+        if (!UPDATE) {  // update passes add the vertex terms when the queue is flushed
+            cp_async16(G.a0 + lane, m.aux0 + v);
+            cp_async16(G.a1 + lane, m.aux1 + v);
+        }
     }
 }
 
-template <int W, bool COMP, bool UPDATE>
+// Reduce-scatter of a lane's 9 values (r, then A's upper triangle) over its
+// W-lane group: log2(W) steps with offsets W/2 .. 1.  A step on N values keeps
+// the first ceil(N/2) (lane bit clear) or the rest, zero-padded (bit set), and
+// adds the partner's copy of the kept half, so after the last step a lane
+// holds finished sums: one for W = 32 and 16, two for W = 8, three for W = 4
+// (a step on one value is a plain pairwise sum).  Compared with nine
+// separate W-lane sums this takes 12 shuffles instead of 45 for W = 32.
+template <int N>
+__device__ __forceinline__ void halve(float* v, int off, bool hi) {
+    constexpr int h = (N + 1) / 2;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+        const float lo_v = v[k];
+        const float hi_v = (h + k < N) ? v[h + k] : 0.0f;
+        const float keep = hi ? hi_v : lo_v;
+        const float send = hi ? lo_v : hi_v;
+        v[k] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+}
+
+template <int N, int OFF>
+__device__ __forceinline__ void butterfly(float* v, int lane) {
+    if constexpr (OFF > 0) {
+        if constexpr (N == 1) {
+            v[0] += __shfl_xor_sync(kFull, v[0], OFF);
+        } else {
+            halve<N>(v, OFF, (lane & OFF) != 0);
+        }
+        butterfly<(N == 1 ? 1 : (N + 1) / 2), OFF / 2>(v, lane);
+    }
+}
+
+// Index (0..8) of the sum a lane holds in final slot k, or -1 for padding.
+template <int N, int OFF>
+__device__ __forceinline__ int butterfly_index(int lane, int k) {
+    if constexpr (OFF == 0) {
+        return k < N ? k : -1;
+    } else if constexpr (N == 1) {
+        return butterfly_index<1, OFF / 2>(lane, k);
+    } else {
+        constexpr int h = (N + 1) / 2;
+        const int p = butterfly_index<h, OFF / 2>(lane, k);
+        if (p < 0) return -1;
+        const int q = ((lane & OFF) ? h : 0) + p;
+        return q < N ? q : -1;
+    }
+}
+
+// Final slots per lane, and whether a lane writes them (for W = 32 the last
+// step is a plain sum, so lanes 2i and 2i + 1 hold the same value).
+template <int W>
+struct ButterflyShape {
+    static constexpr int slots = W >= 16 ? 1 : (W == 8 ? 2 : 3);
+    static __device__ __forceinline__ bool writer(int lane) { return W == 32 ? (lane & 1) == 0 : true; }
+};
+
+template <int W, bool COMP, bool UPDATE, int MODEL>
 __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, WarpSmem& S, int r, int g,
-                                               int lane, int qn, int model, double& rr, double* comp_sq) {
+                                               int lane, int qn, double& rr, double* comp_sq) {
     const Item it = S.desc[r];
     if (it.skip) return;  // uniform over the warp
     const RecStage& R = S.rec[r];
@@ -203,25 +261,32 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
     const float3 d3 = make_float3(__shfl_sync(kFull, d.x, s3), __shfl_sync(kFull, d.y, s3), __shfl_sync(kFull, d.z, s3));
     float rv[3] = {0.f, 0.f, 0.f};
     float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    el::element_math<UPDATE>(model, f3(ra), f3(rb), f3(rc), ra.w, rb.w, d1, d2, d3, rv, A);
+    el::element_math_m<UPDATE, MODEL>(f3(ra), f3(rb), f3(rc), ra.w, rb.w, d1, d2, d3, rv, A);
+    if (UPDATE) {
+        // the element sums of the group's vertex go straight into the queue
+        // from the lanes that hold them; the vertex terms are added at flush
+        float val[9] = {rv[0], rv[1], rv[2], A[0], A[1], A[2], A[3], A[4], A[5]};
+        butterfly<9, W / 2>(val, lane);
+        const int e = qn + j;
+        if (active && ButterflyShape<W>::writer(lane)) {
+#pragma unroll
+            for (int k = 0; k < ButterflyShape<W>::slots; ++k) {
+                const int idx = butterfly_index<9, W / 2>(lane, k);
+                if (idx >= 0) S.q.val[idx][e] = val[k];
+            }
+        }
+        if (!active || (lane & (W - 1)) != 0) return;
+        const int v = it.v0 + j;
+        // a frozen vertex of a mixed item is not written
+        S.q.v[e] = (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) ? -1 : v;
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 3; ++k) rv[k] = el::group_sum<W>(rv[k]);
-    if (UPDATE) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
-    }
     if (!active || (lane & (W - 1)) != 0) return;
     el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
     const int v = it.v0 + j;
-    if (UPDATE) {
-        const int e = qn + j;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) S.q.val[k][e] = rv[k];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) S.q.val[3 + k][e] = A[k];
-        // a frozen vertex of a mixed item is not written
-        S.q.v[e] = (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) ? -1 : v;
-    } else {
+    {
         el::weak_terms<COMP, false>(m, s, v, rv, A);
         const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];
         if (comp_sq) atomicAdd(comp_sq + m.comp[v], q);
@@ -230,14 +295,14 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
 }
 
 // The lane width is uniform over an item: dispatch once per item.
-template <bool COMP, bool UPDATE>
+template <bool COMP, bool UPDATE, int MODEL>
 __device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, WarpSmem& S, int r, int g,
-                                             int lane, int qn, int model, double& rr, double* comp_sq) {
+                                             int lane, int qn, double& rr, double* comp_sq) {
     switch (S.desc[r].w) {
-        case 4: compute_item_w<4, COMP, UPDATE>(m, s, S, r, g, lane, qn, model, rr, comp_sq); break;
-        case 8: compute_item_w<8, COMP, UPDATE>(m, s, S, r, g, lane, qn, model, rr, comp_sq); break;
-        case 16: compute_item_w<16, COMP, UPDATE>(m, s, S, r, g, lane, qn, model, rr, comp_sq); break;
-        default: compute_item_w<32, COMP, UPDATE>(m, s, S, r, g, lane, qn, model, rr, comp_sq); break;
+        case 4: compute_item_w<4, COMP, UPDATE, MODEL>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
+        case 8: compute_item_w<8, COMP, UPDATE, MODEL>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
+        case 16: compute_item_w<16, COMP, UPDATE, MODEL>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
+        default: compute_item_w<32, COMP, UPDATE, MODEL>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
     }
 }
 
@@ -257,6 +322,7 @@ __device__ __forceinline__ void flush_queue(const DeviceMesh& m, State s, const 
             for (int k = 0; k < 6; ++k) A[k] = S.q.val[3 + k][lane];
             const float3 uh = f3(s.hi[v]);
             const float3 ul = COMP ? f3(s.lo[v]) : make_float3(0.f, 0.f, 0.f);
+            el::vertex_terms<COMP, true>(m, m.aux0[v], m.aux1[v], uh, ul, rv, A);
             el::weak_terms<COMP, true>(m, s, v, rv, A);
             el::solve_and_write<COMP>(s, v, uh, ul, rv, A, pp, err);
         }
@@ -268,7 +334,7 @@ __device__ __forceinline__ void flush_queue(const DeviceMesh& m, State s, const 
 // blocked (warp gw takes a contiguous run of ceil(nitems / nw) items).  The
 // order only decides which warp updates which vertices of one colour; the
 // updates of a colour are independent, so the iterate is the same.
-template <bool COMP, bool UPDATE>
+template <bool COMP, bool UPDATE, int MODEL>
 __global__ void __launch_bounds__(kBlock, kCtasPerSm)
     ring_kernel(const DeviceMesh m, State s, const Item* __restrict__ items, int nitems, PassParams pp,
                 int32_t* err, double* partial, double* comp_sq, int blocked) {
@@ -310,7 +376,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         ok = mbar_wait(S.bar + 0, 0);
         waited = 1;
         if (__any_sync(kFull, !ok)) goto abort;
-        issue_gathers<COMP>(m, s, S, 0, 0, lane);
+        issue_gathers<COMP, UPDATE>(m, s, S, 0, 0, lane);
         cp_async_commit();
         for (int k = 0; k < n; ++k) {
             // Record stage (k+2)%3 and gather stage (k+1)%2 were last read by
@@ -327,13 +393,13 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
             if (k + 1 < n) {
                 ok = mbar_wait(S.bar + (k + 1) % kRecStages, ((k + 1) / kRecStages) & 1);
                 waited = k + 2;
-                if (ok) issue_gathers<COMP>(m, s, S, (k + 1) % kRecStages, (k + 1) % kGatStages, lane);
+                if (ok) issue_gathers<COMP, UPDATE>(m, s, S, (k + 1) % kRecStages, (k + 1) % kGatStages, lane);
             }
             cp_async_commit();
             cp_async_wait<1>();  // this lane's gathers of item k have landed
             if (__any_sync(kFull, !ok)) goto abort;
             __syncwarp();        // ... and the other lanes'
-            compute_item<COMP, UPDATE>(m, s, S, k % kRecStages, k % kGatStages, lane, qn, pp.model, rr, comp_sq);
+            compute_item<COMP, UPDATE, MODEL>(m, s, S, k % kRecStages, k % kGatStages, lane, qn, rr, comp_sq);
             if (UPDATE) {
                 const Item& it = S.desc[k % kRecStages];
                 if (!it.skip) qn += it.nv;
@@ -389,8 +455,15 @@ cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nit
                         int32_t* err, double* partial, double* comp_sq, RingSched sc, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const int bytes = kWarps * (int)sizeof(WarpSmem);  // attribute set by ring_prepare()
-    return launch_kernel(ring_kernel<COMP, UPDATE>, ring_ctas(nitems, sc.ctas_per_sm), kBlock, bytes, st, m, s, items,
-                         nitems, pp, err, partial, comp_sq, sc.blocked);
+    const int grid = ring_ctas(nitems, sc.ctas_per_sm);
+    if (pp.model == el::kNeoHookean)
+        return launch_kernel(ring_kernel<COMP, UPDATE, el::kNeoHookean>, grid, kBlock, bytes, st, m, s, items, nitems,
+                             pp, err, partial, comp_sq, sc.blocked);
+    if (pp.model == el::kStableNeoHookean)
+        return launch_kernel(ring_kernel<COMP, UPDATE, el::kStableNeoHookean>, grid, kBlock, bytes, st, m, s, items,
+                             nitems, pp, err, partial, comp_sq, sc.blocked);
+    return launch_kernel(ring_kernel<COMP, UPDATE, el::kCorotated>, grid, kBlock, bytes, st, m, s, items, nitems, pp,
+                         err, partial, comp_sq, sc.blocked);
 }
 
 }  // namespace
@@ -403,8 +476,13 @@ cudaError_t ring_prepare() {
     // Three CTAs of 8 warps with their per-warp stages and queues need almost
     // all of an SM's shared memory: ask for the largest carveout.
     const int bytes = kWarps * (int)sizeof(WarpSmem);
-    const void* fns[4] = {(const void*)ring_kernel<true, true>, (const void*)ring_kernel<false, true>,
-                          (const void*)ring_kernel<true, false>, (const void*)ring_kernel<false, false>};
+    const void* fns[12] = {
+        (const void*)ring_kernel<true, true, 0>,  (const void*)ring_kernel<false, true, 0>,
+        (const void*)ring_kernel<true, false, 0>, (const void*)ring_kernel<false, false, 0>,
+        (const void*)ring_kernel<true, true, 1>,  (const void*)ring_kernel<false, true, 1>,
+        (const void*)ring_kernel<true, false, 1>, (const void*)ring_kernel<false, false, 1>,
+        (const void*)ring_kernel<true, true, 2>,  (const void*)ring_kernel<false, true, 2>,
+        (const void*)ring_kernel<true, false, 2>, (const void*)ring_kernel<false, false, 2>};
     for (const void* f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e == cudaSuccess)
