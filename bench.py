@@ -203,9 +203,14 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
-def kernel_traffic():
+def kernel_traffic(args):
     """Per-launch DRAM bytes of the colour pass from the committed ncu summary,
-    or None when the kernel source changed since it was captured."""
+    or None when the kernel source changed since it was captured or the run
+    is not the captured workload (64^3 sag, corotated, compensated, ring
+    layout)."""
+    if (args.config, args.model, args.precision, args.kernel_path, args.cells) != \
+            ("sag64", "corotated", "compensated", 0, 64):
+        return None
     path = os.path.join(ROOT, "profiles", "colour_pass_traffic.json")
     try:
         with open(path) as f:
@@ -356,7 +361,7 @@ def main():
     alg_bytes_sweep = BYTES_PER_INCIDENCE * prof["incidences"] + BYTES_PER_VERTEX * prof["free_vertices"]
     alg_bytes_launch = alg_bytes_sweep / max(1, prof["ncolours"])
     achieved = alg_bytes_launch / (per_launch_ms * 1e-3) / 1e9
-    tr = kernel_traffic()
+    tr = kernel_traffic(args)
     roofline = {"kernel": "ring_kernel<UPDATE=true> (colour pass)" if args.kernel_path == 0 else "colour_pass_kernel",
                 "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
