@@ -273,3 +273,61 @@ def test_checkpoint_across_handles_is_bit_exact():
     other = Mesh.from_problem(W.twist_block(5))
     with pytest.raises(PbngError):
         other.set_state(blob)
+
+
+def _fan_problem():
+    """A centre vertex joined to the 80 faces of a once-subdivided icosahedron:
+    the centre has 80 incident tets (more than one warp's lanes), the surface
+    vertices 5 or 6.  Five surface vertices are clamped; gravity loads it."""
+    t = (1 + 5 ** 0.5) / 2
+    V = [[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0], [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+         [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]]
+    F = [[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11], [1, 5, 9], [5, 11, 4], [11, 10, 2],
+         [10, 7, 6], [7, 1, 8], [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9], [4, 9, 5], [2, 4, 11],
+         [6, 2, 10], [8, 6, 7], [9, 8, 1]]
+    V = [list(np.asarray(v, float) / np.linalg.norm(v)) for v in V]
+    mid = {}
+
+    def midpoint(a, b):
+        key = (min(a, b), max(a, b))
+        if key not in mid:
+            m = (np.asarray(V[a]) + np.asarray(V[b])) / 2
+            V.append(list(m / np.linalg.norm(m)))
+            mid[key] = len(V) - 1
+        return mid[key]
+
+    F2 = []
+    for a, b, c in F:
+        ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+        F2 += [[a, ab, ca], [b, bc, ab], [c, ca, bc], [ab, bc, ca]]
+    X = np.vstack([np.zeros((1, 3)), np.asarray(V)])
+    tets = np.array([[0, a + 1, b + 1, c + 1] for a, b, c in F2], np.int32)
+    ne = len(tets)
+    dirichlet = np.array([1, 2, 3, 4, 5], np.int32)
+    rng = np.random.default_rng(8)
+    x0 = X + 0.05 * rng.standard_normal(X.shape)
+    x0[dirichlet] = X[dirichlet]
+    return W.Problem(name="fan", X=X, tets=tets, young=np.full(ne, 1e5), poisson=np.full(ne, 0.3),
+                     dirichlet=dirichlet, x0=x0, body_accel=np.array([0.0, 0.0, -9.8]),
+                     density=np.full(ne, 1000.0))
+
+
+def test_high_degree_vertex_uses_direct_loads_and_matches_the_oracle(oracle_mod):
+    """A colour whose vertex has more incident tets than a warp has lanes is
+    laid out for direct loads while the other colours keep the ring layout;
+    the mixed sweep and residual match the oracle."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = _fan_problem()
+    assert np.bincount(p.tets.reshape(-1))[0] == 80
+    m = Mesh.from_problem(p)
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    rel = m.sweep(u, 60, default_params(accel="chebyshev"), want_residual=True)
+    sched = m.schedule()
+    assert 0 in sched["ctas_per_sm"] and any(c > 0 for c in sched["ctas_per_sm"])  # mixed layout
+    om = _oracle(oracle_mod, p)
+    x_ora, st = om.sweeps(p.x0, 60, accel="chebyshev")
+    assert st == 0
+    x_gpu = u.cpu().double().numpy() + p.X
+    assert np.abs(x_gpu - x_ora).max() <= 1e-5 * np.abs(x_ora - p.X).max()
+    rr = om.residual(x_ora) / om.residual(p.x0)
+    assert abs(rel[0] - rr) <= 1e-3 * rr + RES_FLOOR
