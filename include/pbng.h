@@ -72,8 +72,9 @@ typedef struct {
                                "Constitutive Models".  The nodal Hessian is
                                Eq. mod_hess_dens for every model.  The handle
                                keeps the model of its last sweep / solve /
-                               autotune; pbng_residual uses it.  pbng_adjoint
-                               supports PBNG_MODEL_COROTATED only.               */
+                               autotune; pbng_residual uses it.  pbng_adjoint,
+                               pbng_force, pbng_hessian_apply and
+                               pbng_newton_cg use the true Hessian of the model. */
     int32_t accel;          /* PBNG_ACCEL_*                                        */
     double omega;           /* SOR weight (Section "Acceleration Techniques": 1.7) */
     double rho;             /* Chebyshev spectral estimate (0.95).  rho <= 0 with
@@ -253,7 +254,7 @@ pbng_status pbng_step(pbng_mesh* m, float* u_dev, float* u_prev_dev, int32_t nsw
  * call with resume = 0, or pbng_step).  Synchronises. */
 pbng_status pbng_set_dirichlet_targets(pbng_mesh* m, const double* dir_xyz);
 
-/* Force and Hessian of the discrete energy (corotated, kernel_path 0; p may
+/* Force and Hessian of the discrete energy (model p->model, kernel_path 0; p may
  * be NULL for the defaults), for Krylov or optimisation methods around PBNG.
  * pbng_force: f_out_dev (device float [nv][3]) = f(u) + f^ext on free
  *   vertices (the force of Eq. fem_qs with the weak terms; zero rows at
@@ -275,7 +276,7 @@ pbng_status pbng_hessian_apply(pbng_mesh* m, const float* u_dev, const float* p_
  * norm decreases; if none is accepted, the preconditioned residual is tried
  * once.  Stops at |f + f^ext| <= rel_tol r_0 (global 2-norm over all
  * components, r_0 at u_dev) or max_newton iterations (PBNG_ENOTCONVERGED).
- * Corotated model and kernel_path 0 only.  u_dev in / out.  info may be NULL.
+ * Any model (p->model); kernel_path 0 only.  u_dev in / out.  info may be NULL.
  * The acceleration history of the handle is reset.  Synchronises. */
 typedef struct {
     int32_t newton_iterations;

@@ -26,11 +26,13 @@ struct ElemState {
     float H[9];    // F - I
     float C[9];    // cof F
     float Jm1;     // det F - 1
-    float RmI[9];  // R - I
+    float RmI[9];  // R - I (corotated only)
+    float n2;      // |F|^2
 };
 
 // F, its cofactor, J - 1 and the rotation, all from the displacement
 // differences dk = u_jk - u_i and the gradients of the other three vertices.
+template <int MODEL>
 __device__ __forceinline__ void elem_state(float3 d1, float3 d2, float3 d3, float3 g1, float3 g2, float3 g3,
                                            ElemState& E) {
     const float a1[3] = {d1.x, d1.y, d1.z}, a2[3] = {d2.x, d2.y, d2.z}, a3[3] = {d3.x, d3.y, d3.z};
@@ -61,11 +63,69 @@ __device__ __forceinline__ void elem_state(float3 d1, float3 d2, float3 d3, floa
         n2 += Fm[k] * Fm[k];
         c2 += E.C[k] * E.C[k];
     }
-    el::rotation_minus_identity(H, n2, c2, 1.0f + E.Jm1, E.RmI);
+    E.n2 = n2;
+    if (MODEL == el::kCorotated) el::rotation_minus_identity(H, n2, c2, 1.0f + E.Jm1, E.RmI);
+}
+
+// V dC: the bilinear variation of the cofactor, row i of C being the cross
+// product of rows i+1 and i+2 of F.
+__device__ __forceinline__ void cof_variation(const float* F, const float* dF, float* dC) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int p = 3 * ((i + 1) % 3), q = 3 * ((i + 2) % 3);
+        dC[3 * i] = (dF[p + 1] * F[q + 2] - dF[p + 2] * F[q + 1]) + (F[p + 1] * dF[q + 2] - F[p + 2] * dF[q + 1]);
+        dC[3 * i + 1] = (dF[p + 2] * F[q] - dF[p] * F[q + 2]) + (F[p + 2] * dF[q] - F[p] * dF[q + 2]);
+        dC[3 * i + 2] = (dF[p] * F[q + 1] - dF[p + 1] * F[q]) + (F[p] * dF[q + 1] - F[p + 1] * dF[q]);
+    }
+}
+
+// V P (row-major 3x3) of the model (Section "Constitutive Models"), with
+// a = 2 mu V, b = lambda V: corotated a (F - R) + b (J - 1) C; Neo-Hookean
+// (a/2) (F - C) + (a/2 + b) (J - 1) C; stable Neo-Hookean (Lame-consistent
+// mu' = 4mu/3, lambda' = lambda + 5mu/6) (a/2) (F - C) + (a/6) (I_C - 3) /
+// (1 + I_C) F + (b + 5a/12) (J - 1) C.
+template <int MODEL>
+__device__ __forceinline__ void elem_vp(const ElemState& E, float a, float b, float* VP) {
+    if (MODEL == el::kCorotated) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) VP[k] = a * (E.H[k] - E.RmI[k]) + b * E.Jm1 * E.C[k];
+        return;
+    }
+    const float kv = MODEL == el::kNeoHookean ? 0.5f * a + b : b + a * (5.0f / 12.0f);
+    const float qs = MODEL == el::kNeoHookean ? 0.0f : (a * (1.0f / 6.0f)) * (E.n2 - 3.0f) / (1.0f + E.n2);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float F = E.H[k] + ((k % 4 == 0) ? 1.0f : 0.0f);
+        VP[k] = 0.5f * a * (F - E.C[k]) + qs * F + kv * E.Jm1 * E.C[k];
+    }
 }
 
 // out = V dP(dF) (row-major 3x3), a = 2 mu V, b = lambda V.
+//   Neo-Hookean: (a/2) dF + (a/2 + b) (C:dF) C + ((a/2 + b)(J - 1) - a/2) dC
+//   stable NH:   (2a/3) I_C/(1 + I_C) dF + (4a/3) (F:dF)/(1 + I_C)^2 F
+//                + (b + 5a/12) (C:dF) C + ((b + 5a/12)(J - 1) - a/2) dC
+template <int MODEL>
 __device__ __forceinline__ void hess_action(const ElemState& E, float a, float b, const float* dF, float* out) {
+    if (MODEL != el::kCorotated) {
+        float F[9], dC[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) F[k] = E.H[k] + ((k % 4 == 0) ? 1.0f : 0.0f);
+        cof_variation(F, dF, dC);
+        float CdF = 0.f, FdF = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            CdF += E.C[k] * dF[k];
+            FdF += F[k] * dF[k];
+        }
+        const float lv = MODEL == el::kNeoHookean ? 0.5f * a + b : b + a * (5.0f / 12.0f);
+        const float ic = E.n2, q = 1.0f + ic;
+        const float sv = MODEL == el::kNeoHookean ? 0.5f * a : (2.0f * a / 3.0f) * ic / q;
+        const float tv = MODEL == el::kNeoHookean ? 0.0f : (4.0f * a / 3.0f) * FdF / (q * q);
+        const float kv = lv * E.Jm1 - 0.5f * a;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) out[k] = sv * dF[k] + tv * F[k] + lv * CdF * E.C[k] + kv * dC[k];
+        return;
+    }
     float R[9], F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
@@ -132,7 +192,7 @@ __device__ __forceinline__ float3 mat_g(const float* M, float3 g) {
 // lam . H lam per warp.
 enum { kDiag = 0, kSweep = 1, kResid = 2, kForce = 3, kApply = 4 };
 
-template <int W, int MODE>
+template <int W, int MODE, int MODEL>
 __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, float4* lam, const float4* gv,
                                          float4* diag, float4* out4, const Item& it, int lane, int32_t* err,
                                          double& rr) {
@@ -166,20 +226,19 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
     const float3 g1 = f3(ra), g2 = f3(rb), g3 = f3(rc);
     const float3 gi = make_float3(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
     ElemState E;
-    elem_state(d[0], d[1], d[2], g1, g2, g3, E);
+    elem_state<MODEL>(d[0], d[1], d[2], g1, g2, g3, E);
     float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float out[9];
     if (MODE == kForce) {
         // -V P g_i (Eq. cor) and V (2 mu |g_i|^2 I + lambda w w^T), w = cof(F) g_i
         const float3 w = mat_g(E.C, gi);
-        float HR[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) HR[k] = E.H[k] - E.RmI[k];
-        const float3 fr = mat_g(HR, gi);
         const float a = ra.w, b = rb.w;
-        acc[0] = -(a * fr.x + b * E.Jm1 * w.x);
-        acc[1] = -(a * fr.y + b * E.Jm1 * w.y);
-        acc[2] = -(a * fr.z + b * E.Jm1 * w.z);
+        float VP[9];
+        elem_vp<MODEL>(E, a, b, VP);
+        const float3 fr = mat_g(VP, gi);
+        acc[0] = -fr.x;
+        acc[1] = -fr.y;
+        acc[2] = -fr.z;
         const float ag = a * (gi.x * gi.x + gi.y * gi.y + gi.z * gi.z);
         acc[3] = ag + b * w.x * w.x;
         acc[4] = b * w.x * w.y;
@@ -196,7 +255,7 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
             dF[3 * c] = gg[0];
             dF[3 * c + 1] = gg[1];
             dF[3 * c + 2] = gg[2];
-            hess_action(E, ra.w, rb.w, dF, out);
+            hess_action<MODEL>(E, ra.w, rb.w, dF, out);
             const float3 h = mat_g(out, gi);
             col[c][0] = h.x;
             col[c][1] = h.y;
@@ -214,7 +273,7 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
                              e[0].y * g1.y + e[1].y * g2.y + e[2].y * g3.y, e[0].y * g1.z + e[1].y * g2.z + e[2].y * g3.z,
                              e[0].z * g1.x + e[1].z * g2.x + e[2].z * g3.x, e[0].z * g1.y + e[1].z * g2.y + e[2].z * g3.y,
                              e[0].z * g1.z + e[1].z * g2.z + e[2].z * g3.z};
-        hess_action(E, ra.w, rb.w, dF, out);
+        hess_action<MODEL>(E, ra.w, rb.w, dF, out);
         const float3 h = mat_g(out, gi);
         acc[0] = h.x;
         acc[1] = h.y;
@@ -285,7 +344,7 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
                          li.z + inv * (c02 * r0 + c12 * r1 + c22 * r2), 0.f);
 }
 
-template <int MODE>
+template <int MODE, int MODEL>
 __global__ void __launch_bounds__(kBlock) adjoint_vertex_kernel(const DeviceMesh m, State u, float4* lam,
                                                                 const float4* gv, float4* diag, float4* out4,
                                                                 const Item* __restrict__ items, int nitems,
@@ -296,10 +355,10 @@ __global__ void __launch_bounds__(kBlock) adjoint_vertex_kernel(const DeviceMesh
     if (gw < nitems) {
         const Item it = items[gw];
         switch (it.w) {
-            case 4: adj_item<4, MODE>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
-            case 8: adj_item<8, MODE>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
-            case 16: adj_item<16, MODE>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
-            default: adj_item<32, MODE>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
+            case 4: adj_item<4, MODE, MODEL>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
+            case 8: adj_item<8, MODE, MODEL>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
+            case 16: adj_item<16, MODE, MODEL>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
+            default: adj_item<32, MODE, MODEL>(m, u, lam, gv, diag, out4, it, lane, err, rr); break;
         }
     }
     if (MODE == kResid || MODE == kForce || MODE == kApply) {
@@ -312,6 +371,7 @@ __global__ void __launch_bounds__(kBlock) adjoint_vertex_kernel(const DeviceMesh
 // One thread per tet: dL/dlog E_e = -sum_{j free} lambda_j . (V P g_j), and,
 // for tets touching clamped vertices, (H_DF lambda)_d += V dP(dF) g_d with
 // dF = sum_j lambda_j g_j^T (lambda = 0 at clamped vertices).
+template <int MODEL>
 __global__ void adjoint_tet_kernel(int ne, int nfree, const int4* __restrict__ tv, const float4* __restrict__ tb,
                                    State u, const float4* __restrict__ lam, float* dLdlogE, float* hdl) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -330,10 +390,9 @@ __global__ void adjoint_tet_kernel(int ne, int nfree, const int4* __restrict__ t
 #pragma unroll
     for (int k = 0; k < 3; ++k) d[k] = el::pair_diff<true>(u.hi[ids[k + 1]], u.lo[ids[k + 1]], u0h, u0l);
     ElemState E;
-    elem_state(d[0], d[1], d[2], g[1], g[2], g[3], E);
+    elem_state<MODEL>(d[0], d[1], d[2], g[1], g[2], g[3], E);
     float VP[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) VP[k] = a * (E.H[k] - E.RmI[k]) + b * E.Jm1 * E.C[k];
+    elem_vp<MODEL>(E, a, b, VP);
     float3 L[4];
     float grad = 0.f;
     bool touches = false;
@@ -360,7 +419,7 @@ __global__ void adjoint_tet_kernel(int ne, int nfree, const int4* __restrict__ t
         dF[3 * p + 2] = lp[0] * g[0].z + lp[1] * g[1].z + lp[2] * g[2].z + lp[3] * g[3].z;
     }
     float out[9];
-    hess_action(E, a, b, dF, out);
+    hess_action<MODEL>(E, a, b, dF, out);
 #pragma unroll
     for (int jv = 0; jv < 4; ++jv)
         if (ids[jv] >= nfree) {
@@ -515,22 +574,37 @@ __global__ void scatter_vec_kernel(int nv, int nfree, const int32_t* perm, const
 
 int adjoint_warps(int nitems) { return nblocks(nitems, kBlock / 32) * (kBlock / 32); }
 
+template <int MODE, int MODEL>
+cudaError_t vertex_launch(int grid, const DeviceMesh& m, State u, float4* lam, const float4* gv, float4* diag,
+                          float4* out, const Item* items, int nitems, int32_t* err, double* partial, cudaStream_t st) {
+    adjoint_vertex_kernel<MODE, MODEL><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
+    return cudaGetLastError();
+}
+
+template <int MODEL>
+cudaError_t vertex_launch_model(int mode, int grid, const DeviceMesh& m, State u, float4* lam, const float4* gv,
+                                float4* diag, float4* out, const Item* items, int nitems, int32_t* err,
+                                double* partial, cudaStream_t st) {
+    switch (mode) {
+        case kDiag: return vertex_launch<kDiag, MODEL>(grid, m, u, lam, gv, diag, out, items, nitems, err, partial, st);
+        case kSweep: return vertex_launch<kSweep, MODEL>(grid, m, u, lam, gv, diag, out, items, nitems, err, partial, st);
+        case kResid: return vertex_launch<kResid, MODEL>(grid, m, u, lam, gv, diag, out, items, nitems, err, partial, st);
+        case kForce: return vertex_launch<kForce, MODEL>(grid, m, u, lam, gv, diag, out, items, nitems, err, partial, st);
+        default: return vertex_launch<kApply, MODEL>(grid, m, u, lam, gv, diag, out, items, nitems, err, partial, st);
+    }
+}
+
 cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4* lam, const float4* gv,
                                   float4* diag, const Item* items, int nitems, int32_t* err, double* partial,
-                                  cudaStream_t st, float4* out) {
+                                  cudaStream_t st, float4* out, int model) {
     if (nitems <= 0) return cudaSuccess;
     const int grid = nblocks(nitems, kBlock / 32);
-    if (mode == kDiag)
-        adjoint_vertex_kernel<kDiag><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
-    else if (mode == kSweep)
-        adjoint_vertex_kernel<kSweep><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
-    else if (mode == kResid)
-        adjoint_vertex_kernel<kResid><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
-    else if (mode == kForce)
-        adjoint_vertex_kernel<kForce><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
-    else
-        adjoint_vertex_kernel<kApply><<<grid, kBlock, 0, st>>>(m, u, lam, gv, diag, out, items, nitems, err, partial);
-    return cudaGetLastError();
+    if (model == el::kNeoHookean)
+        return vertex_launch_model<el::kNeoHookean>(mode, grid, m, u, lam, gv, diag, out, items, nitems, err, partial, st);
+    if (model == el::kStableNeoHookean)
+        return vertex_launch_model<el::kStableNeoHookean>(mode, grid, m, u, lam, gv, diag, out, items, nitems, err,
+                                                          partial, st);
+    return vertex_launch_model<el::kCorotated>(mode, grid, m, u, lam, gv, diag, out, items, nitems, err, partial, st);
 }
 
 int vec_blocks(int n) { return nblocks(n, kBlock); }
@@ -577,9 +651,15 @@ cudaError_t launch_scatter_vec(int nv, int nfree, const int32_t* perm, const flo
 }
 
 cudaError_t launch_adjoint_tets(int ne, int nfree, const int4* tv, const float4* tb, State u, const float4* lam,
-                                float* dLdlogE, float* hdl, cudaStream_t st) {
+                                float* dLdlogE, float* hdl, cudaStream_t st, int model) {
     if (ne <= 0) return cudaSuccess;
-    adjoint_tet_kernel<<<nblocks(ne, 128), 128, 0, st>>>(ne, nfree, tv, tb, u, lam, dLdlogE, hdl);
+    const int grid = nblocks(ne, 128);
+    if (model == el::kNeoHookean)
+        adjoint_tet_kernel<el::kNeoHookean><<<grid, 128, 0, st>>>(ne, nfree, tv, tb, u, lam, dLdlogE, hdl);
+    else if (model == el::kStableNeoHookean)
+        adjoint_tet_kernel<el::kStableNeoHookean><<<grid, 128, 0, st>>>(ne, nfree, tv, tb, u, lam, dLdlogE, hdl);
+    else
+        adjoint_tet_kernel<el::kCorotated><<<grid, 128, 0, st>>>(ne, nfree, tv, tb, u, lam, dLdlogE, hdl);
     return cudaGetLastError();
 }
 

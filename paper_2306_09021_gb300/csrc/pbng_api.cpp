@@ -1524,7 +1524,7 @@ pbng_status adjoint_resid(pbng_mesh* m, State u, float4* lam, double* out) {
     cudaStream_t st = m->stream;
     PBNG_CUDA(m, launch_adjoint_vertex(kAdjResid, m->dm, u, lam, (const float4*)m->d_gv.p, (float4*)m->d_diag.p,
                                        (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
-                                       (double*)m->d_adj_partial.p, st));
+                                       (double*)m->d_adj_partial.p, st, nullptr, m->model));
     PBNG_CUDA(m, launch_reduce((const double*)m->d_adj_partial.p, adjoint_warps(m->nitems_ring),
                                (double*)m->d_scalar.p, st));
     m->kernel_launches += 2;
@@ -1554,8 +1554,7 @@ pbng_status newton_setup(pbng_mesh* m) {
 // Checks shared by the Newton-CG entry points: corotated, ring layout.
 pbng_status newton_ready(pbng_mesh* m, const pbng_params* p) {
     if (!valid_params(p)) return fail(m, PBNG_EINVAL, "bad parameters");
-    if (p->kernel_path != 0 || p->model != 0)
-        return fail(m, PBNG_EINVAL, "Newton-CG runs the corotated model on the ring layout (model 0, kernel_path 0)");
+    if (p->kernel_path != 0) return fail(m, PBNG_EINVAL, "Newton-CG runs on the ring layout (kernel_path 0)");
     select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
@@ -1570,7 +1569,7 @@ pbng_status newton_force(pbng_mesh* m, State u, double* rr) {
     float4* r = (float4*)m->d_nw[0].p;
     PBNG_CUDA(m, launch_adjoint_vertex(kAdjForce, m->dm, u, nullptr, nullptr, (float4*)m->d_diag.p,
                                        (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
-                                       (double*)m->d_nw_part[0].p, st, r));
+                                       (double*)m->d_nw_part[0].p, st, r, m->model));
     PBNG_CUDA(m, launch_reduce((const double*)m->d_nw_part[0].p, adjoint_warps(m->nitems_ring),
                                (double*)m->d_scalar.p, st));
     m->kernel_launches += 2;
@@ -1591,7 +1590,6 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
     if (!u_eq_dev || !dLdu_dev || !dL_dlogE_dev) return fail(m, PBNG_EINVAL, "NULL argument");
     if (p->kernel_path != 0) return fail(m, PBNG_EINVAL, "the adjoint runs on the ring layout (kernel_path 0)");
-    if (p->model != 0) return fail(m, PBNG_EINVAL, "the adjoint supports the corotated model (model 0) only");
     select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
@@ -1607,7 +1605,8 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     const State u = state_of(m, 3);
     float4* lam = (float4*)m->d_lam[0].p;
     PBNG_CUDA(m, launch_adjoint_vertex(kAdjDiag, m->dm, u, lam, (const float4*)m->d_gv.p, (float4*)m->d_diag.p,
-                                       (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p, nullptr, st));
+                                       (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p, nullptr, st,
+                                       nullptr, m->model));
     m->kernel_launches += 3;
     double g2 = 0.0, r2 = 0.0;
     if ((s = adjoint_resid(m, u, lam, &g2))) return s;  // lambda = 0: |dL/du|^2
@@ -1632,7 +1631,7 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
                 PBNG_CUDA(m, launch_adjoint_vertex(kAdjSweep, m->dm, u, lam, (const float4*)m->d_gv.p,
                                                    (float4*)m->d_diag.p, (const Item*)m->d_items.p + m->item_off[c],
                                                    m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
-                                                   nullptr, st));
+                                                   nullptr, st, nullptr, m->model));
             m->kernel_launches += m->ncol;
             if (p->accel != PBNG_ACCEL_NONE && m->nfree > 0) {
                 const State lc{lam, lam}, l1{(float4*)m->d_lam[p1].p, (float4*)m->d_lam[p1].p},
@@ -1657,7 +1656,7 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     // sensitivities
     PBNG_CUDA(m, cudaMemsetAsync(m->d_hdl.p, 0, sizeof(float4) * (size_t)m->nv, st));
     PBNG_CUDA(m, launch_adjoint_tets(m->ne, m->nfree, (const int4*)m->d_tv.p, (const float4*)m->d_tb.p, u, lam,
-                                     dL_dlogE_dev, (float*)m->d_hdl.p, st));
+                                     dL_dlogE_dev, (float*)m->d_hdl.p, st, m->model));
     m->kernel_launches++;
     if (dL_dxD_dev) {
         PBNG_CUDA(m, launch_clamped_grad((int32_t)m->dir_list.size(), (const int32_t*)m->d_dq_int.p,
@@ -1713,7 +1712,8 @@ pbng_status pbng_hessian_apply(pbng_mesh* m, const float* u_dev, const float* p_
     PBNG_CUDA(m, launch_gather_vec(m->nv, m->nfree, perm, p_dev, (float4*)m->d_nw[3].p, st));
     PBNG_CUDA(m, launch_adjoint_vertex(kAdjApply, m->dm, state_of(m, 3), (float4*)m->d_nw[3].p, nullptr,
                                        (float4*)m->d_diag.p, (const Item*)m->d_items.p, m->nitems_ring,
-                                       (int32_t*)m->d_err.p, (double*)m->d_nw_part[0].p, st, (float4*)m->d_nw[4].p));
+                                       (int32_t*)m->d_err.p, (double*)m->d_nw_part[0].p, st, (float4*)m->d_nw[4].p,
+                                       m->model));
     PBNG_CUDA(m, launch_scatter_vec(m->nv, m->nfree, perm, (const float4*)m->d_nw[4].p, hp_out_dev, st));
     m->kernel_launches += 4;
     PBNG_CUDA(m, cudaStreamSynchronize(st));
@@ -1789,7 +1789,7 @@ pbng_status pbng_newton_cg(pbng_mesh* m, float* u_dev, double rel_tol, int32_t m
         while (k < max_cg) {
             PBNG_CUDA(m, launch_adjoint_vertex(kAdjApply, m->dm, u0, pd, nullptr, (float4*)m->d_diag.p,
                                                (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
-                                               part1, st, hq));
+                                               part1, st, hq, m->model));
             PBNG_CUDA(m, launch_reduce(part1, adjoint_warps(m->nitems_ring), sc + 1, st));
             PBNG_CUDA(m, launch_cg_update(n, sc, x, r, pd, hq, diag, z, part0, part1, flag, st));
             PBNG_CUDA(m, launch_reduce(part0, vec_blocks(n), sc + 2, st));

@@ -162,7 +162,7 @@ enum { kAdjDiag = 0, kAdjSweep = 1, kAdjResid = 2, kAdjForce = 3, kAdjApply = 4 
 int adjoint_warps(int nitems);
 cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4* lam, const float4* gv,
                                   float4* diag, const Item* items, int nitems, int32_t* err, double* partial,
-                                  cudaStream_t st, float4* out = nullptr);
+                                  cudaStream_t st, float4* out = nullptr, int model = 0);
 // Preconditioned conjugate gradients on the free rows (pbng_adjoint.cu): the
 // scalars stay on the device in sc[0..3] = (r.z, p.Hp, new r.z, |r|^2); one
 // FP64 partial per kBlock threads (vec_blocks(n) of them).
@@ -178,7 +178,7 @@ cudaError_t launch_newton_axpy(int nv, int nfree, State src, const float4* x, fl
 cudaError_t launch_gather_vec(int nv, int nfree, const int32_t* perm, const float* in, float4* out, cudaStream_t st);
 cudaError_t launch_scatter_vec(int nv, int nfree, const int32_t* perm, const float4* in, float* out, cudaStream_t st);
 cudaError_t launch_adjoint_tets(int ne, int nfree, const int4* tv, const float4* tb, State u, const float4* lam,
-                                float* dLdlogE, float* hdl, cudaStream_t st);
+                                float* dLdlogE, float* hdl, cudaStream_t st, int model = 0);
 cudaError_t launch_gather_rhs(int nfree, const int32_t* perm, const float* dLdu, float4* gv, cudaStream_t st);
 cudaError_t launch_clamped_grad(int nd, const int32_t* dq_internal, const int32_t* dq_caller, const float* dLdu,
                                 const float* hdl, float* out, cudaStream_t st);

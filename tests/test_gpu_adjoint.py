@@ -65,6 +65,29 @@ def test_adjoint_matches_dense_oracle(oracle_mod, n, accel):
     assert _rel(dD, dD_ref) <= ADJ_TOL
 
 
+@pytest.mark.parametrize("model", ["neohookean", "stable_neohookean"])
+def test_adjoint_of_the_neohookean_models_matches_dense_oracle(oracle_mod, model):
+    """The adjoint with the true Hessian of Eq. nh / Eq. snh (no polar
+    factor) against the oracle's dense adjoint of the same model."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = _loaded(4)
+    om = oracle_mod.OracleMesh.from_problem(p, model=model)
+    xeq, it, _ = om.newton(p.x0, 1e-12, 60)
+    assert it >= 0
+    top = np.isclose(p.X[:, 2], 1.0)
+    rng = np.random.default_rng(17)
+    dLdx = np.where(top[:, None], 2.0 * (xeq - (xeq + 0.01 * rng.standard_normal(xeq.shape))), 0.0)
+    dE_ref, dD_ref = om.adjoint(xeq, dLdx)
+    m = Mesh.from_problem(p)
+    u = torch.tensor(xeq - p.X, dtype=torch.float32, device="cuda")
+    g = torch.tensor(dLdx, dtype=torch.float32, device="cuda")
+    st, dE, dD, sweeps, rel = m.adjoint(u, g, rel_tol=1e-6, max_sweeps=20000,
+                                        params=default_params(model=model, accel="chebyshev"), raise_on_status=False)
+    assert st == 0 or (st == 7 and rel <= 1e-5), (st, sweeps, rel)
+    assert _rel(dE.cpu().double().numpy(), dE_ref) <= ADJ_TOL
+    assert _rel(dD.cpu().double().numpy(), dD_ref) <= ADJ_TOL
+
+
 def test_adjoint_zero_rhs_gives_zero():
     from paper_2306_09021_gb300 import Mesh
     p = _loaded(3)

@@ -104,10 +104,34 @@ def test_direct_and_ring_paths_agree_for_each_model():
         assert np.abs(out[0] - out[1]).max() <= 1e-6 * np.abs(out[0]).max()
 
 
-def test_adjoint_rejects_other_models():
-    from paper_2306_09021_gb300 import Mesh, PbngError, default_params
-    p = W.twist_block(3, 30.0, 0.1)
+@pytest.mark.parametrize("model", MODELS)
+def test_hessian_apply_and_newton_cg_for_the_model(model):
+    """pbng_hessian_apply against the oracle's dense true Hessian of the model,
+    and Newton-CG to the oracle's Newton equilibrium of the model."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.twist_block(3, 60.0, 0.2)
+    om = oracle.OracleMesh.from_problem(p, model=model)
+    x, st = om.sweeps(p.x0, 4)
+    x = x.astype(np.float32).astype(np.float64)
+    free = p.dirichlet_mask() == 0
+    idx = np.flatnonzero(np.repeat(free, 3))
+    H = om.hessian(x)
+    d = np.random.default_rng(5).standard_normal(p.X.shape)
     m = Mesh.from_problem(p)
+    prm = default_params(model=model)
+    hp = m.hessian_apply(_u0_of(x - p.X), _u0_of(d), params=prm).cpu().double().numpy()
+    expect = (H[np.ix_(idx, idx)] @ (d * free[:, None]).reshape(-1)[idx]).reshape(-1, 3)
+    assert np.abs(hp[free] - expect).max() <= 1e-3 * np.abs(expect).max()
+    f = m.force(_u0_of(x - p.X), params=prm).cpu().double().numpy()
+    _, r = om.residual(x, vector=True)
+    assert np.abs(f[free] - r[free]).max() <= 2e-4 * np.abs(r[free]).max()
+    xn, it, _ = om.newton(p.x0, 1e-12, 60)
+    assert it >= 0
     u = _u0(p)
-    with pytest.raises(PbngError):
-        m.adjoint(u, torch.zeros_like(u), 1e-6, 10, default_params(model="neohookean"))
+    st, info = m.newton_cg(u, 1e-5, max_newton=60, max_cg=2000, cg_tol=1e-2, params=prm)
+    assert st == 0
+    assert np.abs(u.cpu().double().numpy() + p.X - xn).max() <= 1e-4 * np.abs(xn - p.X).max()
+
+
+def _u0_of(a):
+    return torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda").contiguous()
