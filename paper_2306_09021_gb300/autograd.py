@@ -15,17 +15,22 @@ class EquilibriumModel:
     """A mesh with fixed topology, Poisson ratios, springs, contact and body
     forces whose per-tet log Young's modulus and clamped positions are the
     differentiable inputs.  ``model(log_young, x_dirichlet)`` returns the
-    equilibrium displacement u [nv, 3] (float32, CUDA)."""
+    equilibrium displacement u [nv, 3] (float32, CUDA).  ``model`` selects the
+    energy density (Section "Constitutive Models"); the adjoint always uses the
+    forward solve's model."""
 
     def __init__(self, problem, mesh_id=None, body_accel=None, rel_tol=1e-6, max_sweeps=200000,
-                 adjoint_tol=1e-6, adjoint_max_sweeps=200000, params=None, adjoint_params=None):
+                 adjoint_tol=1e-6, adjoint_max_sweeps=200000, params=None, adjoint_params=None,
+                 model="corotated"):
         self.p = problem
         self.mesh = Mesh.from_problem(problem, mesh_id=mesh_id)
         self.body_accel = None if body_accel is None else np.asarray(body_accel, dtype=np.float64)
         self.rel_tol, self.max_sweeps = rel_tol, max_sweeps
         self.adjoint_tol, self.adjoint_max_sweeps = adjoint_tol, adjoint_max_sweeps
-        self.params = params if params is not None else default_params(accel="sor", omega=1.5)
-        self.adjoint_params = adjoint_params if adjoint_params is not None else default_params(accel="sor", omega=1.5)
+        self.params = params if params is not None else default_params(model=model, accel="sor", omega=1.5)
+        self.adjoint_params = (adjoint_params if adjoint_params is not None
+                               else default_params(model=model, accel="sor", omega=1.5))
+        self.adjoint_params.model = self.params.model
         self.u_last = None
         self.last_solve = None
         self.last_adjoint = None

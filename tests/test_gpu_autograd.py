@@ -43,10 +43,11 @@ def _loss(model, p, log_e, xd, top, target):
     return L, le, xdt
 
 
-def test_autograd_matches_dense_oracle_adjoint(oracle_mod):
+@pytest.mark.parametrize("energy", ["corotated", "neohookean", "stable_neohookean"])
+def test_autograd_matches_dense_oracle_adjoint(oracle_mod, energy):
     from paper_2306_09021_gb300 import EquilibriumModel
     p, log_e, xd, top, target = _setup()
-    model = EquilibriumModel(p, rel_tol=1e-6)
+    model = EquilibriumModel(p, rel_tol=1e-6, model=energy)
     L, le, xdt = _loss(model, p, log_e, xd, top, target)
     L.backward()
     # oracle: same log E and boundary, Newton equilibrium, dense adjoint
@@ -54,7 +55,7 @@ def test_autograd_matches_dense_oracle_adjoint(oracle_mod):
     q.young = np.exp(log_e)
     q.body_accel = p.body_accel
     q.x0 = p.x0
-    om = oracle_mod.OracleMesh.from_problem(q)
+    om = oracle_mod.OracleMesh.from_problem(q, model=energy)
     xeq, it, _ = om.newton(q.x0, 1e-12, 60)
     assert it >= 0
     dLdx = np.zeros_like(xeq)
