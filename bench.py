@@ -355,20 +355,44 @@ def main():
     m.set_profiling(False)
     prof_ms = pe0.elapsed_time(pe1)
 
+    # Colour passes back to back as the timed steps run them: CUDA graphs of
+    # 50 sweeps with programmatic dependent launch between the passes, from
+    # plain sweeps without acceleration or residual, so that the graphs hold
+    # colour passes only; CUDA events on the library's stream around 4 calls.
+    passes_per_sweep = prof["colour_pass_launches"] / max(1, prof_steps * S)
+    bb_sweeps, bb_reps = 50, 4
+    bb = default_params(model=args.model, precision=args.precision, resume=1, kernel_path=args.kernel_path,
+                        residual_every=bb_sweeps)
+    m.sweep(u, bb_sweeps, bb)   # captures the graph
+    torch.cuda.synchronize()
+    bb0, bb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bb0.record(stream)
+    for _ in range(bb_reps):
+        m.sweep(u, bb_sweeps, bb)
+    bb1.record(stream)
+    torch.cuda.synchronize()
+    bb_launches = bb_reps * bb_sweeps * passes_per_sweep
+    bb_per_launch_ms = bb0.elapsed_time(bb1) / max(1.0, bb_launches)
+
     # roofline of the dominant kernel (the colour pass)
     peak, peak_kind = measured_peaks()
     per_launch_ms = prof["colour_pass_ms"] / max(1, prof["colour_pass_launches"])
     alg_bytes_sweep = BYTES_PER_INCIDENCE * prof["incidences"] + BYTES_PER_VERTEX * prof["free_vertices"]
     alg_bytes_launch = alg_bytes_sweep / max(1, prof["ncolours"])
-    achieved = alg_bytes_launch / (per_launch_ms * 1e-3) / 1e9
+    achieved = alg_bytes_launch / (bb_per_launch_ms * 1e-3) / 1e9
     tr = kernel_traffic(args)
     roofline = {"kernel": "ring_kernel<UPDATE=true> (colour pass)" if args.kernel_path == 0 else "colour_pass_kernel",
                 "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tr is None else tr["dram_bytes_per_launch"],
-                "alg_bytes_per_launch": alg_bytes_launch, "avg_launch_us": per_launch_ms * 1e3,
-                "launches_timed": prof["colour_pass_launches"],
-                "timing": f"CUDA events around each launch over {prof_steps} profiled steps",
+                "alg_bytes_per_launch": alg_bytes_launch, "avg_launch_us": bb_per_launch_ms * 1e3,
+                "launches_timed": int(bb_launches),
+                "timing": (f"CUDA events on the library stream around {bb_reps} x {bb_sweeps} sweeps of colour passes "
+                           "only, launched as in the timed steps (CUDA graph, programmatic dependent launch)"),
+                "avg_launch_us_standalone": per_launch_ms * 1e3,
+                "frac_standalone": alg_bytes_launch / (per_launch_ms * 1e-3) / 1e9 / peak,
+                "standalone_timing": (f"CUDA events around each launch, plain launches without graphs, over "
+                                      f"{prof_steps} profiled steps"),
                 "colour_pass_share_of_step": prof["colour_pass_ms"] / prof_ms,
                 "accel_share_of_step": prof["accel_ms"] / prof_ms,
                 "residual_share_of_step": prof["residual_ms"] / prof_ms}
