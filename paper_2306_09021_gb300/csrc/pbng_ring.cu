@@ -40,7 +40,11 @@ using el::f3;
 using el::kFull;
 
 constexpr int kWarps = kBlock / 32;
-constexpr int kRecStages = 3;
+// Three record stages (items requested two ahead) and 3 CTAs of 8 warps per
+// SM: with two stages and 4 CTAs (64 registers) the passes were 15 % slower,
+// the shorter pipeline exposing more TMA latency than the extra warps hide.
+constexpr int kRecStages = 3;                 // record stages; items are requested kRecStages - 1 ahead
+constexpr int kRecAhead = kRecStages - 1;
 constexpr int kGatStages = 2;
 constexpr int kItemVerts = kRingLanes / 4;
 constexpr int kCtasPerSm = 3;
@@ -58,8 +62,6 @@ struct __align__(16) GatStage {
     float4 nl[kRingLanes];   // 1-ring displacement lo
     float4 oh[kItemVerts];   // own vertex hi
     float4 ol[kItemVerts];   // own vertex lo
-    float4 a0[kItemVerts];   // aux0 (f_ext, K)
-    float4 a1[kItemVerts];   // aux1 (spring target, n.X - d)
 };
 
 // Force r (3) and modified Hessian A (6, upper triangle) of queued vertices,
@@ -173,10 +175,6 @@ __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& 
         const int v = it.v0 + lane;
         cp_async16(G.oh + lane, s.hi + v);
         if (COMP) cp_async16(G.ol + lane, s.lo + v);
-        if (!UPDATE) {  // update passes add the vertex terms when the queue is flushed
-            cp_async16(G.a0 + lane, m.aux0 + v);
-            cp_async16(G.a1 + lane, m.aux1 + v);
-        }
     }
 }
 
@@ -284,8 +282,8 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
 #pragma unroll
     for (int k = 0; k < 3; ++k) rv[k] = el::group_sum<W>(rv[k]);
     if (!active || (lane & (W - 1)) != 0) return;
-    el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
     const int v = it.v0 + j;
+    el::vertex_terms<COMP, UPDATE>(m, m.aux0[v], m.aux1[v], uh, ul, rv, A);
     {
         el::weak_terms<COMP, false>(m, s, v, rv, A);
         const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];
@@ -364,11 +362,10 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         if (lane == 0) {
             for (int i = 0; i < kRecStages; ++i) mbar_init(S.bar + i, 1);
             fence_mbar_init();
-            issue_records(m, items[first], S, 0);
-            if (n > 1) issue_records(m, items[first + stride], S, 1);
-            if (n > 2) next = items[first + 2 * stride];
+            for (int i = 0; i < kRecAhead && i < n; ++i) issue_records(m, items[first + i * stride], S, i);
+            if (n > kRecAhead) next = items[first + kRecAhead * stride];
         }
-        issued = n < 2 ? n : 2;
+        issued = n < kRecAhead ? n : kRecAhead;
         __syncwarp();
         // Records, items and component flags are written by no kernel; the
         // iterate read from here on is written by the previous kernel.
@@ -379,15 +376,16 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         issue_gathers<COMP, UPDATE>(m, s, S, 0, 0, lane);
         cp_async_commit();
         for (int k = 0; k < n; ++k) {
-            // Record stage (k+2)%3 and gather stage (k+1)%2 were last read by
-            // item k-1, finished before the previous __syncwarp.
-            if (k + 2 < n) {
+            // Record stage (k + kRecAhead) % kRecStages and gather stage
+            // (k+1)%2 were last read by item k-1, finished before the previous
+            // __syncwarp.
+            if (k + kRecAhead < n) {
                 if (lane == 0) {
                     fence_proxy_async();
-                    issue_records(m, next, S, (k + 2) % kRecStages);
-                    if (k + 3 < n) next = items[first + (k + 3) * stride];
+                    issue_records(m, next, S, (k + kRecAhead) % kRecStages);
+                    if (k + kRecAhead + 1 < n) next = items[first + (k + kRecAhead + 1) * stride];
                 }
-                issued = k + 3;
+                issued = k + kRecAhead + 1;
             }
             ok = true;
             if (k + 1 < n) {

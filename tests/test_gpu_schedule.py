@@ -97,6 +97,7 @@ def test_autotune_leaves_iterate_and_history_untouched():
 
 def test_schedule_survives_constraint_changes_and_rejects_bad_arguments():
     from paper_2306_09021_gb300 import Mesh, PbngError, default_params
+    from paper_2306_09021_gb300._lib import MAX_CTAS_PER_SM
     p = W.twist_block(6, 45.0, 0.2)
     m = Mesh.from_problem(p)
     ncol = m.colouring()[1]
@@ -105,7 +106,7 @@ def test_schedule_survives_constraint_changes_and_rejects_bad_arguments():
     assert m.colouring()[1] == ncol
     assert m.schedule()["ctas_per_sm"] == [2] * ncol
     m.set_schedule([99] * ncol, [1] * ncol)          # clamped
-    assert m.schedule()["ctas_per_sm"] == [3] * ncol
+    assert m.schedule()["ctas_per_sm"] == [MAX_CTAS_PER_SM] * ncol
     with pytest.raises(PbngError):
         m.autotune(_u0(p), reps=0)
     # direct-load layout: no ring colours, nothing to schedule
