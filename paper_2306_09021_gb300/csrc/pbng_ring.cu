@@ -62,6 +62,8 @@ struct __align__(16) GatStage {
     float4 nl[kRingLanes];   // 1-ring displacement lo
     float4 oh[kItemVerts];   // own vertex hi
     float4 ol[kItemVerts];   // own vertex lo
+    float4 a0[kItemVerts];   // aux0 (f_ext, K), residual passes only
+    float4 a1[kItemVerts];   // aux1 (spring target, n.X - d), residual passes only
 };
 
 // Force r (3) and modified Hessian A (6, upper triangle) of queued vertices,
@@ -175,6 +177,10 @@ __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& 
         const int v = it.v0 + lane;
         cp_async16(G.oh + lane, s.hi + v);
         if (COMP) cp_async16(G.ol + lane, s.lo + v);
+        if (!UPDATE) {  // update passes add the vertex terms when the queue is flushed
+            cp_async16(G.a0 + lane, m.aux0 + v);
+            cp_async16(G.a1 + lane, m.aux1 + v);
+        }
     }
 }
 
@@ -283,7 +289,7 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
     for (int k = 0; k < 3; ++k) rv[k] = el::group_sum<W>(rv[k]);
     if (!active || (lane & (W - 1)) != 0) return;
     const int v = it.v0 + j;
-    el::vertex_terms<COMP, UPDATE>(m, m.aux0[v], m.aux1[v], uh, ul, rv, A);
+    el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
     {
         el::weak_terms<COMP, false>(m, s, v, rv, A);
         const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];
