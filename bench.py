@@ -351,7 +351,7 @@ def main():
     # Per-launch durations: the same steps with each kernel bracketed by CUDA
     # events on the library's stream (plain launches; captured event records
     # cannot be timed).
-    prof_steps = max(3, args.steps // 2)
+    prof_steps = max(3, min(args.steps // 2, 20))
     torch.cuda.synchronize()
     m.set_profiling(True)
     pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
