@@ -362,6 +362,9 @@ pbng_status pbng_get_profile(pbng_mesh* m, pbng_profile* out);
  *   ctas_per_sm  1..PBNG_MAX_CTAS_PER_SM CTAs (8 warps each) per SM
  *   blocked      0: warp w takes items w, w + nwarps, ... (strided);
  *                1: warp w takes one contiguous run of items (blocked)
+ *   balanced     1: the grid is trimmed to the fewest CTAs whose warps still
+ *                finish in the same number of item rounds (no warp idles
+ *                through the last round); 0: the full grid
  * The vertex updates of one colour are independent, so every schedule gives
  * a bit-identical iterate; only the time differs.  Colours laid out for
  * direct loads (vertices with more than 32 incident tets or 1-ring vertices,
@@ -372,6 +375,9 @@ typedef struct {
     int32_t ncolours;                          /* of the current layout       */
     int32_t ctas_per_sm[PBNG_MAX_COLOURS];     /* per colour; 0 = not a ring colour */
     int32_t blocked[PBNG_MAX_COLOURS];
+    int32_t balanced[PBNG_MAX_COLOURS];        /* 1: grid trimmed to the fewest
+                                                  warps taking the same number
+                                                  of item rounds            */
     double default_ms_per_sweep;   /* pbng_autotune: colour passes of one sweep
                                       with the default schedule (3, strided)   */
     double tuned_ms_per_sweep;     /* ... with the schedule it chose           */
@@ -380,8 +386,8 @@ typedef struct {
 } pbng_schedule;
 
 /* Sets the schedule of every ring colour from s->ctas_per_sm[c] (clamped to
- * 1..PBNG_MAX_CTAS_PER_SM) and s->blocked[c] for c < min(s->ncolours,
- * ncolours of the layout).  Builds the layout if needed (p selects
+ * 1..PBNG_MAX_CTAS_PER_SM), s->blocked[c] and s->balanced[c] for
+ * c < min(s->ncolours, ncolours of the layout).  Builds the layout if needed (p selects
  * kernel_path; NULL = defaults).  Captured sweep graphs are dropped and
  * re-captured on next use.  The schedule survives layout rebuilds that keep
  * the colour count. */
@@ -389,7 +395,8 @@ pbng_status pbng_set_schedule(pbng_mesh* m, const pbng_params* p, const pbng_sch
 /* Current schedule (ms fields = 0 unless set by pbng_autotune). */
 pbng_status pbng_get_schedule(pbng_mesh* m, pbng_schedule* out);
 
-/* Autotuner: times every schedule (ctas_per_sm x {strided, blocked}) of every
+/* Autotuner: times every schedule (ctas_per_sm x {strided, blocked} x
+ * {full, balanced grid}) of every
  * ring colour over `reps` sweeps each, on a scratch copy of u_dev (the
  * caller's u_dev, the handle's iterate and its acceleration history are not
  * touched) and keeps the fastest per colour (the default unless another is

@@ -66,6 +66,7 @@ class PbngSchedule(ctypes.Structure):
         ("ncolours", ctypes.c_int32),
         ("ctas_per_sm", ctypes.c_int32 * MAX_COLOURS),
         ("blocked", ctypes.c_int32 * MAX_COLOURS),
+        ("balanced", ctypes.c_int32 * MAX_COLOURS),
         ("default_ms_per_sweep", ctypes.c_double),
         ("tuned_ms_per_sweep", ctypes.c_double),
         ("candidates", ctypes.c_int32),

@@ -442,7 +442,7 @@ pbng_status build_layout(pbng_mesh* m) {
         m->ring_colour[c] = (fits && !m->want_direct) ? 1 : 0;
     }
     if ((int)m->sched.size() != m->ncol) {
-        m->sched.assign(m->ncol, RingSched{ring_max_ctas_per_sm(), 0});
+        m->sched.assign(m->ncol, RingSched{ring_max_ctas_per_sm(), 0, 0});
         m->tune_default_ms = m->tune_ms = 0.0;
         m->tune_cands = 0;
     }
@@ -2022,6 +2022,7 @@ pbng_status pbng_get_schedule(pbng_mesh* m, pbng_schedule* out) {
         const bool ring = c < (int)m->ring_colour.size() && m->ring_colour[c];
         out->ctas_per_sm[c] = ring ? m->sched[c].ctas_per_sm : 0;
         out->blocked[c] = ring ? m->sched[c].blocked : 0;
+        out->balanced[c] = ring ? m->sched[c].balanced : 0;
     }
     out->default_ms_per_sweep = m->tune_default_ms;
     out->tuned_ms_per_sweep = m->tune_ms;
@@ -2044,6 +2045,7 @@ pbng_status pbng_set_schedule(pbng_mesh* m, const pbng_params* p, const pbng_sch
     for (int c = 0; c < std::min<int>(std::min(s->ncolours, m->ncol), PBNG_MAX_COLOURS); ++c) {
         m->sched[c].ctas_per_sm = std::max(1, std::min(cap, (int)s->ctas_per_sm[c]));
         m->sched[c].blocked = s->blocked[c] ? 1 : 0;
+        m->sched[c].balanced = s->balanced[c] ? 1 : 0;
     }
     m->tune_default_ms = m->tune_ms = 0.0;
     m->tune_cands = 0;
@@ -2072,10 +2074,11 @@ pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p
     const PassParams pp{(float)p->step, (float)p->skip_tol, p->model};
     const State scratch = state_of(m, 3);
     const int cap = ring_max_ctas_per_sm();
-    std::vector<RingSched> cands{{cap, 0}};   // the default first
+    std::vector<RingSched> cands{{cap, 0, 0}};   // the default first
     for (int cps = 1; cps <= cap; ++cps)
         for (int b = 0; b < 2; ++b)
-            if (!(cps == cap && b == 0)) cands.push_back({cps, b});
+            for (int bal = 0; bal < 2; ++bal)
+                if (!(cps == cap && b == 0 && bal == 0)) cands.push_back({cps, b, bal});
     const int nc = (int)cands.size(), ncol = m->ncol;
     auto pass = [&](int c, RingSched sc) -> pbng_status {
         if (m->ring_colour[c])

@@ -137,10 +137,13 @@ cudaError_t launch_inertia(int32_t nv, int32_t nfree, const int32_t* perm, float
 // FP64 partial per warp of the grid (ring_warps(nitems) of them) or, with
 // comp_sq, per-component sums.
 // A colour pass's launch schedule: CTAs per SM of the persistent grid
-// (1..ring_max_ctas_per_sm()) and the item order (0 strided, 1 blocked).
+// (1..ring_max_ctas_per_sm()), the item order (0 strided, 1 blocked), and
+// whether the grid is trimmed to the fewest warps that take the same number
+// of item rounds (1 balanced), so that no warp idles through the last round.
 struct RingSched {
     int ctas_per_sm;
     int blocked;
+    int balanced;
 };
 int ring_warps(int nitems);
 int ring_max_ctas_per_sm();

@@ -447,11 +447,18 @@ int sm_count() {
     return cached[dev];
 }
 
-int ring_ctas(int nitems, int ctas_per_sm) {
+int ring_ctas(int nitems, int ctas_per_sm, int balanced = 0) {
     const int want = (nitems + kWarps - 1) / kWarps;
     const int cps = ctas_per_sm < 1 ? 1 : (ctas_per_sm > kCtasPerSm ? kCtasPerSm : ctas_per_sm);
     const int cap = cps * sm_count();
-    return want < cap ? want : cap;
+    int grid = want < cap ? want : cap;
+    if (balanced && grid > 0) {
+        // the same number of item rounds with the fewest warps
+        const int rounds = (nitems + grid * kWarps - 1) / (grid * kWarps);
+        const int warps = (nitems + rounds - 1) / rounds;
+        grid = (warps + kWarps - 1) / kWarps;
+    }
+    return grid;
 }
 
 template <bool COMP, bool UPDATE>
@@ -459,7 +466,7 @@ cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nit
                         int32_t* err, double* partial, double* comp_sq, RingSched sc, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const int bytes = kWarps * (int)sizeof(WarpSmem);  // attribute set by ring_prepare()
-    const int grid = ring_ctas(nitems, sc.ctas_per_sm);
+    const int grid = ring_ctas(nitems, sc.ctas_per_sm, sc.balanced);
     if (pp.model == el::kNeoHookean)
         return launch_kernel(ring_kernel<COMP, UPDATE, el::kNeoHookean>, grid, kBlock, bytes, st, m, s, items, nitems,
                              pp, err, partial, comp_sq, sc.blocked);
@@ -506,7 +513,7 @@ cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items
                                  bool compensated, double* warp_partial, double* comp_sq, int model, int32_t* err,
                                  cudaStream_t st) {
     const PassParams pp{1.f, 0.f, model};
-    const RingSched sc{kCtasPerSm, 0};  // ring_warps() partials
+    const RingSched sc{kCtasPerSm, 0, 0};  // ring_warps() partials
     double* part = comp_sq ? nullptr : warp_partial;
     if (compensated) return launch_impl<true, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
     return launch_impl<false, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);

@@ -268,6 +268,7 @@ class Mesh:
     def _schedule_dict(s):
         n = min(s.ncolours, len(s.ctas_per_sm))
         return {"ncolours": s.ncolours, "ctas_per_sm": list(s.ctas_per_sm[:n]), "blocked": list(s.blocked[:n]),
+                "balanced": list(s.balanced[:n]),
                 "default_ms_per_sweep": s.default_ms_per_sweep, "tuned_ms_per_sweep": s.tuned_ms_per_sweep,
                 "candidates": s.candidates}
 
@@ -277,13 +278,15 @@ class Mesh:
         check(load().pbng_get_schedule(self.h, ctypes.byref(s)), "pbng_get_schedule", self.h)
         return self._schedule_dict(s)
 
-    def set_schedule(self, ctas_per_sm, blocked, params=None):
+    def set_schedule(self, ctas_per_sm, blocked, params=None, balanced=None):
         """pbng_set_schedule from per-colour lists."""
         s = PbngSchedule()
         s.ncolours = len(ctas_per_sm)
-        for c, (a, b) in enumerate(zip(ctas_per_sm, blocked)):
+        bal = balanced if balanced is not None else [0] * len(ctas_per_sm)
+        for c, (a, b, g) in enumerate(zip(ctas_per_sm, blocked, bal)):
             s.ctas_per_sm[c] = int(a)
             s.blocked[c] = int(b)
+            s.balanced[c] = int(g)
         p = params if params is not None else default_params()
         check(load().pbng_set_schedule(self.h, ctypes.byref(p), ctypes.byref(s)), "pbng_set_schedule", self.h)
 

@@ -41,13 +41,15 @@ def test_every_schedule_gives_the_same_iterate():
     m = Mesh.from_problem(p)
     for cps in range(1, MAX_CTAS_PER_SM + 1):
         for blocked in (0, 1):
-            m.set_schedule([cps] * ncol, [blocked] * ncol)
-            s = m.schedule()
-            assert s["ctas_per_sm"] == [cps] * ncol and s["blocked"] == [blocked] * ncol
-            u = _u0(p)
-            m.sweep(u, 25, params)
-            torch.cuda.synchronize()
-            assert torch.equal(u, u_ref), (cps, blocked)
+            for balanced in (0, 1):
+                m.set_schedule([cps] * ncol, [blocked] * ncol, balanced=[balanced] * ncol)
+                s = m.schedule()
+                assert s["ctas_per_sm"] == [cps] * ncol and s["blocked"] == [blocked] * ncol
+                assert s["balanced"] == [balanced] * ncol
+                u = _u0(p)
+                m.sweep(u, 25, params)
+                torch.cuda.synchronize()
+                assert torch.equal(u, u_ref), (cps, blocked, balanced)
 
 
 def test_mixed_schedules_on_a_batch_give_the_same_iterate():
@@ -60,7 +62,8 @@ def test_mixed_schedules_on_a_batch_give_the_same_iterate():
     ref.sweep(u_ref, 30, params)
     m = Mesh.from_problem(batch, mesh_id=mid)
     ncol = m.colouring()[1]
-    m.set_schedule([1 + c % 3 for c in range(ncol)], [c % 2 for c in range(ncol)])
+    m.set_schedule([1 + c % 3 for c in range(ncol)], [c % 2 for c in range(ncol)],
+                   balanced=[(c // 2) % 2 for c in range(ncol)])
     u = _u0(batch)
     m.sweep(u, 30, params)
     torch.cuda.synchronize()
@@ -83,9 +86,9 @@ def test_autotune_leaves_iterate_and_history_untouched():
     torch.cuda.synchronize()
     assert torch.equal(probe, probe_before)
     ncol = sched["ncolours"]
-    assert ncol == 5 and sched["candidates"] == 2 * MAX_CTAS_PER_SM
+    assert ncol == 5 and sched["candidates"] == 4 * MAX_CTAS_PER_SM
     assert all(1 <= c <= MAX_CTAS_PER_SM for c in sched["ctas_per_sm"])
-    assert all(x in (0, 1) for x in sched["blocked"])
+    assert all(x in (0, 1) for x in sched["blocked"]) and all(x in (0, 1) for x in sched["balanced"])
     assert 0.0 < sched["tuned_ms_per_sweep"] <= sched["default_ms_per_sweep"]
     assert a.schedule()["ctas_per_sm"] == sched["ctas_per_sm"]
     ra = a.sweep(ua, 9, cont, want_residual=True)
