@@ -331,3 +331,33 @@ def test_high_degree_vertex_uses_direct_loads_and_matches_the_oracle(oracle_mod)
     assert np.abs(x_gpu - x_ora).max() <= 1e-5 * np.abs(x_ora - p.X).max()
     rr = om.residual(x_ora) / om.residual(p.x0)
     assert abs(rel[0] - rr) <= 1e-3 * rr + RES_FLOOR
+
+
+def test_isolated_vertex(oracle_mod):
+    """A free vertex in no tetrahedron: with a spring its nodal system is the
+    spring alone (A = k I) and it lands on the target in one update, as in the
+    oracle; without one its nodal Hessian is zero and the sweep reports
+    PBNG_EDEGENERATE instead of writing a non-finite value."""
+    from paper_2306_09021_gb300 import Mesh, PbngError, default_params
+    p = W.twist_block(3, 30.0, 0.1)
+    X = np.vstack([p.X, [[2.0, 2.0, 2.0]]])
+    iso = X.shape[0] - 1
+    x0 = np.vstack([p.x0, [[2.0, 2.0, 2.0]]])
+    target = np.array([[2.1, 1.9, 2.05]])
+    m = Mesh(X, p.tets, p.young, p.poisson)
+    m.set_constraints(p.dirichlet, p.x0[p.dirichlet], np.array([iso], np.int32), target, np.array([1e3]))
+    u = torch.tensor(x0 - X, dtype=torch.float32, device="cuda")
+    m.sweep(u, 20, default_params())
+    om = oracle_mod.OracleMesh(X, p.tets, p.young, p.poisson,
+                               np.isin(np.arange(len(X)), p.dirichlet).astype(np.uint8),
+                               spr_idx=np.array([iso]), spr_target=target, spr_k=np.array([1e3]))
+    x_ora, st = om.sweeps(x0, 20)
+    assert st == 0
+    x_gpu = u.cpu().double().numpy() + X
+    assert np.abs(x_gpu[iso] - target[0]).max() <= 1e-6
+    assert np.abs(x_gpu - x_ora).max() <= 1e-5 * np.abs(x_ora - X).max()
+    m.set_constraints(p.dirichlet, p.x0[p.dirichlet])      # spring removed
+    u = torch.tensor(x0 - X, dtype=torch.float32, device="cuda")
+    with pytest.raises(PbngError) as e:
+        m.sweep(u, 2, default_params())
+    assert "DEGENERATE" in str(e.value)
