@@ -30,8 +30,8 @@ __device__ __forceinline__ float3 pair_diff(float4 hj, float4 lj, float3 uh, flo
     return d;
 }
 
-// Slow path of rotation_minus_identity for rotations beyond about 120
-// degrees: the adjugate column with the largest diagonal entry.
+// Slow path of polar_quaternion for rotations beyond about 120 degrees: the
+// adjugate column with the largest diagonal entry.
 static __device__ __noinline__ void adjugate_best_column(const float* M, float q00, float* q) {
     float best = -q00;
     int kbest = 0;
@@ -60,7 +60,8 @@ static __device__ __noinline__ void adjugate_best_column(const float* M, float q
 }
 
 // Rotation part of F = I + H for the corotated energy (Section "Constitutive
-// Models", Eq. cor, with R the rotation of the polar decomposition in SO(3)).
+// Models", Eq. cor, with R the rotation of the polar decomposition in SO(3)),
+// as the unit quaternion q = (w, x, y, z) times `scale`.
 //
 // Method (Horn 1987, "Closed-form solution of absolute orientation using unit
 // quaternions"; the polar use follows Higham & Noferini 2016): R(q) maximises
@@ -77,8 +78,8 @@ static __device__ __noinline__ void adjugate_best_column(const float* M, float q
 // the column with the largest diagonal entry.  N - tI is built from H, so the
 // vector part of q, and with it R - I = 2w[v]x + 2[v]x^2, keep relative
 // accuracy as H -> 0.
-__device__ __forceinline__ void rotation_minus_identity(const float* H, float n2, float c2, float J,
-                                                        float* RmI) {
+__device__ __forceinline__ void polar_quaternion(const float* H, float n2, float c2, float J, float scale,
+                                                 float* qo) {
     const float k0 = n2 * n2 - 4.0f * c2;
     const float n23 = 3.0f * n2;
     float t = n23 * rsqrtf(n23);
@@ -116,12 +117,22 @@ __device__ __forceinline__ void rotation_minus_identity(const float* H, float n2
         adjugate_best_column(M, q[0], q);
     }
     const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
-    float w = 1.0f, x = 0.0f, y = 0.0f, z = 0.0f;
     if (qq > 1e-30f && qq < 3.0e38f) {
-        const float inv = rsqrtf(qq);
-        w = q[0] * inv; x = q[1] * inv; y = q[2] * inv; z = q[3] * inv;
+        const float inv = scale * rsqrtf(qq);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qo[k] = q[k] * inv;
+    } else {
+        qo[0] = scale;
+        qo[1] = qo[2] = qo[3] = 0.0f;
     }
-    // R - I = 2 w [v]x + 2 (v v^T - |v|^2 I), v = (x, y, z).
+}
+
+// R - I (row major) of the rotation of F = I + H: 2 w [v]x + 2 (v v^T - |v|^2 I).
+__device__ __forceinline__ void rotation_minus_identity(const float* H, float n2, float c2, float J,
+                                                        float* RmI) {
+    float q[4];
+    polar_quaternion(H, n2, c2, J, 1.0f, q);
+    const float w = q[0], x = q[1], y = q[2], z = q[3];
     const float xx = x * x, yy = y * y, zz = z * z;
     const float xy = x * y, xz = x * z, yz = y * z, wx = w * x, wy = w * y, wz = w * z;
     RmI[0] = -2.0f * (yy + zz);
@@ -155,9 +166,14 @@ __device__ __forceinline__ void rotation_minus_identity(const float* H, float n2
 //     V P g = (a/2) (F - C) g + (a/6) (I_C - 3) / (1 + I_C) F g + (b + 5a/12) (J - 1) w
 // where F - C = H + H^T - tr(H) I - cof(H) and I_C - 3 = 2 tr H + |H|^2 are
 // formed from H, so the Neo-Hookean stresses keep relative accuracy at rest.
+// Everything is written with s = g_j1 + g_j2 + g_j3 = -g_i: r gains
+// +V P(F) s, and w = -cof(F) s enters A squared.  The corotated rotation
+// acts on s through its quaternion (w, v) scaled by sqrt(2):
+// (R - I) s = w (v x s) + v (v . s) - |v|^2 s.
+// ACC adds to r and A; otherwise it overwrites them.
 enum { kCorotated = 0, kNeoHookean = 1, kStableNeoHookean = 2 };
 
-template <bool NEED_A, int MODEL>
+template <bool NEED_A, int MODEL, bool ACC = true>
 __device__ __forceinline__ void element_math_m(float3 gj1, float3 gj2, float3 gj3, float a, float b,
                                                float3 d1, float3 d2, float3 d3, float* r, float* A) {
     const float g1[3] = {gj1.x, gj1.y, gj1.z}, g2[3] = {gj2.x, gj2.y, gj2.z}, g3[3] = {gj3.x, gj3.y, gj3.z};
@@ -167,7 +183,7 @@ __device__ __forceinline__ void element_math_m(float3 gj1, float3 gj2, float3 gj
     for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int q = 0; q < 3; ++q) H[3 * p + q] = dd1[p] * g1[q] + dd2[p] * g2[q] + dd3[p] * g3[q];
-    const float gi[3] = {-(g1[0] + g2[0] + g3[0]), -(g1[1] + g2[1] + g3[1]), -(g1[2] + g2[2] + g3[2])};
+    const float s[3] = {g1[0] + g2[0] + g3[0], g1[1] + g2[1] + g3[1], g1[2] + g2[2] + g3[2]};
 
     const float F0 = 1.0f + H[0], F4 = 1.0f + H[4], F8 = 1.0f + H[8];
     const float F1 = H[1], F2 = H[2], F3 = H[3], F5 = H[5], F6 = H[6], F7 = H[7];
@@ -185,9 +201,14 @@ __device__ __forceinline__ void element_math_m(float3 gj1, float3 gj2, float3 gj
     const float trH = H[0] + H[4] + H[8];
     const float Jm1 = trH + (H[0] * H[4] - H[1] * H[3] + H[0] * H[8] - H[2] * H[6] + H[4] * H[8] - H[5] * H[7]) +
                       det3(H[0], H[1], H[2], H[3], H[4], H[5], H[6], H[7], H[8]);
-    float w[3];
+    float ws[3], Hs[3];  // cof(F) s = -w, H s
 #pragma unroll
-    for (int p = 0; p < 3; ++p) w[p] = C[3 * p] * gi[0] + C[3 * p + 1] * gi[1] + C[3 * p + 2] * gi[2];
+    for (int p = 0; p < 3; ++p) {
+        ws[p] = C[3 * p] * s[0] + C[3 * p + 1] * s[1] + C[3 * p + 2] * s[2];
+        Hs[p] = H[3 * p] * s[0] + H[3 * p + 1] * s[1] + H[3 * p + 2] * s[2];
+    }
+    float f[3];  // V P(F) s
+    const float bJ = b * Jm1;
     if (MODEL == kCorotated) {
         float n2 = 0.0f, c2 = 0.0f;
         const float Fm[9] = {F0, F1, F2, F3, F4, F5, F6, F7, F8};
@@ -196,16 +217,20 @@ __device__ __forceinline__ void element_math_m(float3 gj1, float3 gj2, float3 gj
             n2 += Fm[k] * Fm[k];
             c2 += C[k] * C[k];
         }
-        float RmI[9];
-        rotation_minus_identity(H, n2, c2, 1.0f + Jm1, RmI);
+        float q[4];
+        polar_quaternion(H, n2, c2, 1.0f + Jm1, 1.41421356237309505f, q);
+        const float x = q[1], y = q[2], z = q[3];
+        const float cr[3] = {y * s[2] - z * s[1], z * s[0] - x * s[2], x * s[1] - y * s[0]};
+        const float vs = x * s[0] + y * s[1] + z * s[2];
+        const float vv = x * x + y * y + z * z;
+        const float vq[3] = {x, y, z};
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const float fr = (H[3 * p] - RmI[3 * p]) * gi[0] + (H[3 * p + 1] - RmI[3 * p + 1]) * gi[1] +
-                             (H[3 * p + 2] - RmI[3 * p + 2]) * gi[2];
-            r[p] -= a * fr + b * Jm1 * w[p];
+            const float rs = q[0] * cr[p] + (vq[p] * vs - vv * s[p]);
+            f[p] = a * (Hs[p] - rs) + bJ * ws[p];
         }
     } else {
-        // cof(H), then F - C = H + H^T - tr(H) I - cof(H)
+        // cof(H), then (F - C) s = H s + H^T s - tr(H) s - cof(H) s
         float K[9];
         K[0] = H[4] * H[8] - H[5] * H[7];
         K[1] = H[5] * H[6] - H[3] * H[8];
@@ -226,28 +251,25 @@ __device__ __forceinline__ void element_math_m(float3 gj1, float3 gj2, float3 gj
             qs = (a * (1.0f / 6.0f)) * __fdividef(ic3, 4.0f + ic3);
             kv = b + a * (5.0f / 12.0f);
         }
+        const float kJ = kv * Jm1;
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            float fc = 0.0f, hg = 0.0f;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const float fmc = H[3 * p + q] + H[3 * q + p] - (p == q ? trH : 0.0f) - K[3 * p + q];
-                fc += fmc * gi[q];
-                hg += H[3 * p + q] * gi[q];
-            }
-            float t = ha * fc + kv * Jm1 * w[p];
-            if (MODEL == kStableNeoHookean) t += qs * (gi[p] + hg);
-            r[p] -= t;
+            const float Hts = H[p] * s[0] + H[3 + p] * s[1] + H[6 + p] * s[2];
+            const float Ks = K[3 * p] * s[0] + K[3 * p + 1] * s[1] + K[3 * p + 2] * s[2];
+            const float fcs = (Hs[p] + Hts) - trH * s[p] - Ks;
+            float t = ha * fcs + kJ * ws[p];
+            if (MODEL == kStableNeoHookean) t += qs * (s[p] + Hs[p]);
+            f[p] = t;
         }
     }
+#pragma unroll
+    for (int p = 0; p < 3; ++p) r[p] = ACC ? r[p] + f[p] : f[p];
     if (NEED_A) {
-        const float ag = a * (gi[0] * gi[0] + gi[1] * gi[1] + gi[2] * gi[2]);
-        A[0] += ag + b * w[0] * w[0];
-        A[1] += b * w[0] * w[1];
-        A[2] += b * w[0] * w[2];
-        A[3] += ag + b * w[1] * w[1];
-        A[4] += b * w[1] * w[2];
-        A[5] += ag + b * w[2] * w[2];
+        const float ag = a * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+        const float bw0 = b * ws[0], bw1 = b * ws[1], bw2 = b * ws[2];
+        const float e[6] = {ag + bw0 * ws[0], bw0 * ws[1], bw0 * ws[2], ag + bw1 * ws[1], bw1 * ws[2], ag + bw2 * ws[2]};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) A[k] = ACC ? A[k] + e[k] : e[k];
     }
 }
 

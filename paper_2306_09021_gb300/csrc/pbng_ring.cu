@@ -265,8 +265,8 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
     const float3 d3 = make_float3(__shfl_sync(kFull, d.x, s3), __shfl_sync(kFull, d.y, s3), __shfl_sync(kFull, d.z, s3));
     float rv[3] = {0.f, 0.f, 0.f};
     float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    el::element_math_m<UPDATE, MODEL>(f3(ra), f3(rb), f3(rc), ra.w, rb.w, d1, d2, d3, rv, A);
-    if (UPDATE) {
+    el::element_math_m<UPDATE, MODEL, false>(f3(ra), f3(rb), f3(rc), ra.w, rb.w, d1, d2, d3, rv, A);
+    if constexpr (UPDATE) {
         // the element sums of the group's vertex go straight into the queue
         // from the lanes that hold them; the vertex terms are added at flush
         float val[9] = {rv[0], rv[1], rv[2], A[0], A[1], A[2], A[3], A[4], A[5]};
@@ -283,14 +283,12 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
         const int v = it.v0 + j;
         // a frozen vertex of a mixed item is not written
         S.q.v[e] = (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) ? -1 : v;
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) rv[k] = el::group_sum<W>(rv[k]);
-    if (!active || (lane & (W - 1)) != 0) return;
-    const int v = it.v0 + j;
-    el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
-    {
+        for (int k = 0; k < 3; ++k) rv[k] = el::group_sum<W>(rv[k]);
+        if (!active || (lane & (W - 1)) != 0) return;
+        const int v = it.v0 + j;
+        el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
         el::weak_terms<COMP, false>(m, s, v, rv, A);
         const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];
         if (comp_sq) atomicAdd(comp_sq + m.comp[v], q);

@@ -29,11 +29,21 @@ def _u0(p):
     return torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
 
 
-def test_every_schedule_gives_the_same_iterate():
+_SCHED_PROBLEMS = {
+    "twist": lambda: W.twist_block(10, 90.0, 0.3),           # 90 degree twist: large rotations
+    "sag": lambda: W.gravity_sag(12),                        # lane widths 8 and 32
+    "bar": lambda: W.contact_bar(4, 4, 20, h=0.05, seed=3),  # springs, contact, lognormal E
+}
+
+
+@pytest.mark.parametrize("model", ["corotated", "neohookean", "stable_neohookean"])
+@pytest.mark.parametrize("prob", list(_SCHED_PROBLEMS))
+@pytest.mark.parametrize("precision", ["compensated", "fp32"])
+def test_every_schedule_gives_the_same_iterate(prob, model, precision):
     from paper_2306_09021_gb300 import Mesh, default_params
     from paper_2306_09021_gb300._lib import MAX_CTAS_PER_SM
-    p = W.twist_block(10, 90.0, 0.3)
-    params = default_params(accel="chebyshev")
+    p = _SCHED_PROBLEMS[prob]()
+    params = default_params(accel="chebyshev", model=model, precision=precision)
     ref = Mesh.from_problem(p)
     u_ref = _u0(p)
     ref.sweep(u_ref, 25, params)
@@ -42,7 +52,7 @@ def test_every_schedule_gives_the_same_iterate():
     for cps in range(1, MAX_CTAS_PER_SM + 1):
         for blocked in (0, 1):
             for balanced in (0, 1):
-                m.set_schedule([cps] * ncol, [blocked] * ncol, balanced=[balanced] * ncol)
+                m.set_schedule([cps] * ncol, [blocked] * ncol, balanced=[balanced] * ncol, params=params)
                 s = m.schedule()
                 assert s["ctas_per_sm"] == [cps] * ncol and s["blocked"] == [blocked] * ncol
                 assert s["balanced"] == [balanced] * ncol
