@@ -206,14 +206,15 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
         uh = f3(u.hi[v]);
         ul = f3(u.lo[v]);
         if (MODE != kForce) li = f3(lam[v]);
-        const int id = m.ring_id[slot];
+        const int id = m.ring[slot >> 5].id[slot & 31];
         du = el::pair_diff<true>(u.hi[id], u.lo[id], uh, ul);
         if (MODE != kDiag && MODE != kForce) {
             const float3 lj = f3(lam[id]);
             dl = make_float3(lj.x - li.x, lj.y - li.y, lj.z - li.z);
         }
     }
-    const float4 ra = m.ring_ra[slot], rb = m.ring_rb[slot], rc = m.ring_rc[slot];
+    const RingBlock& rbk = m.ring[slot >> 5];
+    const float4 ra = rbk.ra[slot & 31], rb = rbk.rb[slot & 31], rc = rbk.rc[slot & 31];
     const int loc = __float_as_int(rc.w);
     const int base = lane & ~(W - 1);
     const int s[3] = {base + (loc & 255), base + ((loc >> 8) & 255), base + ((loc >> 16) & 255)};

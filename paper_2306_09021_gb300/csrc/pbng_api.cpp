@@ -82,7 +82,7 @@ struct pbng_mesh {
 
     // device buffers
     DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
-    DevBuf d_ring_ra, d_ring_rb, d_ring_rc, d_ring_id, d_items;
+    DevBuf d_ring, d_items;
     DevBuf d_active;                   // int32 [ncomp] component flags (1 = active)
     // adjoint (built on first use after each layout)
     DevBuf d_lam[3], d_gv, d_diag, d_hdl, d_tv, d_tb, d_dq_int, d_dq_caller, d_adj_partial;
@@ -622,10 +622,17 @@ pbng_status build_layout(pbng_mesh* m) {
     PBNG_CUDA(m, upload(m->d_rec_b, rb, st));
     PBNG_CUDA(m, upload(m->d_rec_c, rc, st));
     PBNG_CUDA(m, upload(m->d_rec_d, rd, st));
-    PBNG_CUDA(m, upload(m->d_ring_ra, qa, st));
-    PBNG_CUDA(m, upload(m->d_ring_rb, qb, st));
-    PBNG_CUDA(m, upload(m->d_ring_rc, qc, st));
-    PBNG_CUDA(m, upload(m->d_ring_id, qid, st));
+    {
+        std::vector<RingBlock> blocks(qa.size() / kRingLanes);
+        for (size_t q = 0; q < qa.size(); ++q) {
+            RingBlock& b = blocks[q / kRingLanes];
+            b.ra[q % kRingLanes] = qa[q];
+            b.rb[q % kRingLanes] = qb[q];
+            b.rc[q % kRingLanes] = qc[q];
+            b.id[q % kRingLanes] = qid[q];
+        }
+        PBNG_CUDA(m, upload(m->d_ring, blocks, st));
+    }
     PBNG_CUDA(m, upload(m->d_items, m->items, st));
     PBNG_CUDA(m, upload(m->d_aux0, aux0, st));
     PBNG_CUDA(m, upload(m->d_aux1, aux1, st));
@@ -710,10 +717,7 @@ pbng_status build_layout(pbng_mesh* m) {
     d.aux1 = (const float4*)m->d_aux1.p;
     d.comp = m->ncomp > 1 ? (const int32_t*)m->d_comp.p : nullptr;
     d.comp_active = m->ncomp > 1 ? (const int32_t*)m->d_active.p : nullptr;
-    d.ring_ra = (const float4*)m->d_ring_ra.p;
-    d.ring_rb = (const float4*)m->d_ring_rb.p;
-    d.ring_rc = (const float4*)m->d_ring_rc.p;
-    d.ring_id = (const int32_t*)m->d_ring_id.p;
+    d.ring = (const RingBlock*)m->d_ring.p;
     d.pn_x = (float)m->pn[0];
     d.pn_y = (float)m->pn[1];
     d.pn_z = (float)m->pn[2];
@@ -2181,7 +2185,7 @@ void pbng_destroy(pbng_mesh* m) {
     DevBuf* bufs[] = {&m->d_lam[0], &m->d_lam[1], &m->d_lam[2], &m->d_gv, &m->d_diag, &m->d_hdl, &m->d_tv,
                       &m->d_tb, &m->d_dq_int, &m->d_dq_caller, &m->d_adj_partial,
                       &m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
-                      &m->d_ring_ra, &m->d_ring_rb, &m->d_ring_rc, &m->d_ring_id, &m->d_items,
+                      &m->d_ring, &m->d_items,
                       &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k, &m->d_wc_off, &m->d_wc_list, &m->d_wc_v,
                       &m->d_wc_b, &m->d_wc_k, &m->d_wc_c0,

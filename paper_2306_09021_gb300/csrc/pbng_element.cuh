@@ -83,7 +83,7 @@ __device__ __forceinline__ void polar_quaternion(const float* H, float n2, float
     const float k0 = n2 * n2 - 4.0f * c2;
     const float n23 = 3.0f * n2;
     float t = n23 * rsqrtf(n23);
-    float dp = 1.0f;
+    float dp = 1.0f, dprev = 0.0f;
 #pragma unroll 1
     for (int it = 0; it < 16; ++it) {
         const float t2 = t * t;
@@ -91,7 +91,12 @@ __device__ __forceinline__ void polar_quaternion(const float* H, float n2, float
         dp = (4.0f * t2 - 4.0f * n2) * t - 8.0f * J;
         const float d = __fdividef(p, dp);
         t -= d;
-        if (!(fabsf(d) > 2e-7f * t)) break;
+        const float ad = fabsf(d);
+        // Converged; or quadratic convergence has set in (this step is at most
+        // 1/100 of the previous one) and the step is below 1e-4 t, so the
+        // next one would be below float resolution.
+        if (!(ad > 2e-7f * t) || (ad <= 1e-4f * t && ad <= 0.01f * dprev)) break;
+        dprev = ad;
     }
     const float trH = H[0] + H[4] + H[8];
     const float m00 = (3.0f - t) + trH;

@@ -29,6 +29,15 @@ struct SegmentTable {
 // order the colour passes consume them (vertex-major CSR over the internal,
 // colour-ordered free vertices), so consecutive lanes read consecutive
 // records.
+// The records of one 32-slot ring item, contiguous so that one bulk copy
+// fetches them.
+struct __align__(16) RingBlock {
+    float4 ra[32];   // g_j1 (xyz), a = 2 mu V
+    float4 rb[32];   // g_j2 (xyz), b = lambda V
+    float4 rc[32];   // g_j3 (xyz), local ring indices l1 | l2 << 8 | l3 << 16 (int bits)
+    int32_t id[32];  // internal id of the vertex's l-th 1-ring neighbour (own id when padding)
+};
+
 struct DeviceMesh {
     int32_t nv;              // all vertices (free first, then clamped)
     int32_t nfree;
@@ -43,10 +52,8 @@ struct DeviceMesh {
     const int32_t* comp_active;  // [ncomp] 0 = frozen (converged), or nullptr
     // Ring layout (colours whose vertices all fit 32 lanes): one 32-slot
     // item per warp; vertex v of a lane-width-W run owns W consecutive slots.
-    const float4* ring_ra;   // [nslots] g_j1 (xyz), a = 2 mu V
-    const float4* ring_rb;   // [nslots] g_j2 (xyz), b = lambda V
-    const float4* ring_rc;   // [nslots] g_j3 (xyz), local ring indices l1 | l2 << 8 | l3 << 16 (int bits)
-    const int32_t* ring_id;  // [nslots] internal id of the vertex's l-th 1-ring neighbour (own id when padding)
+    // Slot s is entry s % 32 of block s / 32 (RingBlock).
+    const struct RingBlock* ring;  // [nslots / 32]
     float pn_x, pn_y, pn_z;  // contact plane normal (unit)
     float k_contact;         // 0 = no plane
     // General weak constraints (nullptr when there are none): constraint c

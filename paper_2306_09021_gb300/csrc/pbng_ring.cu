@@ -10,8 +10,8 @@
 //
 // Each warp is persistent and runs its own three-stage pipeline, with no
 // block-wide barrier anywhere:
-//   * lane 0 fetches an item's three record arrays and 1-ring ids with TMA
-//     1D bulk copies (cp.async.bulk ... mbarrier::complete_tx) two items ahead;
+//   * lane 0 fetches an item's records and 1-ring ids (one RingBlock) with a
+//     TMA 1D bulk copy (cp.async.bulk ... mbarrier::complete_tx) two items ahead;
 //   * once they land, every lane gathers the displacement pair of its 1-ring
 //     vertex (and the item's own vertices and aux data) with cp.async one item
 //     ahead, so each neighbour is read once per vertex update, not once per
@@ -50,12 +50,8 @@ constexpr int kItemVerts = kRingLanes / 4;
 constexpr int kCtasPerSm = 3;
 constexpr int kQueue = 32;   // deferred vertex updates per warp
 
-struct __align__(16) RecStage {
-    float4 ra[kRingLanes];
-    float4 rb[kRingLanes];
-    float4 rc[kRingLanes];
-    int32_t id[kRingLanes];
-};
+using RecStage = RingBlock;
+static_assert(kRingLanes == 32, "one RingBlock per ring item");
 
 struct __align__(16) GatStage {
     float4 nh[kRingLanes];   // 1-ring displacement hi
@@ -82,7 +78,8 @@ struct __align__(16) WarpSmem {
     unsigned long long bar[kRecStages];
 };
 
-constexpr int kRecBytes = 3 * kRingLanes * 16 + kRingLanes * 4;
+constexpr int kRecBytes = (int)sizeof(RingBlock);
+static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -156,10 +153,7 @@ __device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, Warp
         return;
     }
     mbar_arrive_expect_tx(bar, kRecBytes);
-    bulk_g2s(S.rec[r].ra, m.ring_ra + it.slot0, kRingLanes * 16, bar);
-    bulk_g2s(S.rec[r].rb, m.ring_rb + it.slot0, kRingLanes * 16, bar);
-    bulk_g2s(S.rec[r].rc, m.ring_rc + it.slot0, kRingLanes * 16, bar);
-    bulk_g2s(S.rec[r].id, m.ring_id + it.slot0, kRingLanes * 4, bar);
+    bulk_g2s(&S.rec[r], m.ring + (it.slot0 >> 5), kRecBytes, bar);
 }
 
 // All lanes: gather the 1-ring displacements and own-vertex data of the item
