@@ -63,10 +63,12 @@ struct __align__(16) GatStage {
 };
 
 // Force r (3) and modified Hessian A (6, upper triangle) of queued vertices,
-// structure of arrays so the flush reads without bank conflicts; v = -1 marks
-// a frozen vertex that is not written.
+// structure of arrays so the flush reads without bank conflicts; rows are
+// padded to kQueue + 1 words so that the nine sums of one vertex, written
+// by different lanes of its group, fall in nine different banks.  v = -1
+// marks a frozen vertex that is not written.
 struct __align__(16) UpdQueue {
-    float val[9][kQueue];
+    float val[9][kQueue + 1];
     int32_t v[kQueue];
 };
 
@@ -77,6 +79,9 @@ struct __align__(16) WarpSmem {
     Item desc[kRecStages];
     unsigned long long bar[kRecStages];
 };
+
+static_assert(kCtasPerSm * (kWarps * sizeof(WarpSmem) + 1024) <= 228 * 1024,
+              "the per-warp stages of kCtasPerSm CTAs exceed an SM's shared memory");
 
 constexpr int kRecBytes = (int)sizeof(RingBlock);
 static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
@@ -231,14 +236,26 @@ __device__ __forceinline__ int butterfly_index(int lane, int k) {
 template <int W>
 struct ButterflyShape {
     static constexpr int slots = W >= 16 ? 1 : (W == 8 ? 2 : 3);
+    static constexpr int shift = W == 32 ? 0 : (W == 16 ? 4 : (W == 8 ? 8 : 16));
     static __device__ __forceinline__ bool writer(int lane) { return W == 32 ? (lane & 1) == 0 : true; }
 };
 
+// butterfly_index of every lane width for this lane, computed once per
+// kernel: 4 bits per final slot (15 = padding) at ButterflyShape<W>::shift.
+__device__ __forceinline__ uint32_t butterfly_table(int lane) {
+    uint32_t t = (uint32_t)(butterfly_index<9, 16>(lane, 0) & 15);
+    t |= (uint32_t)(butterfly_index<9, 8>(lane, 0) & 15) << 4;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) t |= (uint32_t)(butterfly_index<9, 4>(lane, k) & 15) << (8 + 4 * k);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t |= (uint32_t)(butterfly_index<9, 2>(lane, k) & 15) << (16 + 4 * k);
+    return t;
+}
+
 template <int W, bool COMP, bool UPDATE, int MODEL>
-__device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, WarpSmem& S, int r, int g,
-                                               int lane, int qn, double& rr, double* comp_sq) {
-    const Item it = S.desc[r];
-    if (it.skip) return;  // uniform over the warp
+__device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
+                                               int g, int lane, uint32_t btab, int qn, double& rr,
+                                               double* comp_sq) {
     const RecStage& R = S.rec[r];
     const GatStage& G = S.gat[g];
     const int j = lane / W;
@@ -269,8 +286,8 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
         if (active && ButterflyShape<W>::writer(lane)) {
 #pragma unroll
             for (int k = 0; k < ButterflyShape<W>::slots; ++k) {
-                const int idx = butterfly_index<9, W / 2>(lane, k);
-                if (idx >= 0) S.q.val[idx][e] = val[k];
+                const int idx = (int)((btab >> (ButterflyShape<W>::shift + 4 * k)) & 15u);
+                if (idx < 9) S.q.val[idx][e] = val[k];
             }
         }
         if (!active || (lane & (W - 1)) != 0) return;
@@ -292,13 +309,14 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
 
 // The lane width is uniform over an item: dispatch once per item.
 template <bool COMP, bool UPDATE, int MODEL>
-__device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, WarpSmem& S, int r, int g,
-                                             int lane, int qn, double& rr, double* comp_sq) {
-    switch (S.desc[r].w) {
-        case 4: compute_item_w<4, COMP, UPDATE, MODEL>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
-        case 8: compute_item_w<8, COMP, UPDATE, MODEL>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
-        case 16: compute_item_w<16, COMP, UPDATE, MODEL>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
-        default: compute_item_w<32, COMP, UPDATE, MODEL>(m, s, S, r, g, lane, qn, rr, comp_sq); break;
+__device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
+                                             int g, int lane, uint32_t btab, int qn, double& rr, double* comp_sq) {
+    if (it.skip) return;  // uniform over the warp
+    switch (it.w) {
+        case 4: compute_item_w<4, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
+        case 8: compute_item_w<8, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
+        case 16: compute_item_w<16, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
+        default: compute_item_w<32, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
     }
 }
 
@@ -352,6 +370,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         n = gw < nitems ? (nitems - gw + nw - 1) / nw : 0;
     }
     double rr = 0.0;
+    const uint32_t btab = UPDATE ? butterfly_table(lane) : 0u;
     int qn = 0;                  // queued vertex updates (warp-uniform)
     int issued = 0, waited = 0;  // items whose records were requested / awaited
     bool ok = true;
@@ -395,9 +414,10 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
             cp_async_wait<1>();  // this lane's gathers of item k have landed
             if (__any_sync(kFull, !ok)) goto abort;
             __syncwarp();        // ... and the other lanes'
-            compute_item<COMP, UPDATE, MODEL>(m, s, S, k % kRecStages, k % kGatStages, lane, qn, rr, comp_sq);
+            const Item it = S.desc[k % kRecStages];
+            compute_item<COMP, UPDATE, MODEL>(m, s, S, it, k % kRecStages, k % kGatStages, lane, btab, qn, rr,
+                                              comp_sq);
             if (UPDATE) {
-                const Item& it = S.desc[k % kRecStages];
                 if (!it.skip) qn += it.nv;
                 if (qn > kQueue - kItemVerts || (k + 1 == n && qn > 0)) {
                     flush_queue<COMP>(m, s, S, qn, lane, pp, err);
