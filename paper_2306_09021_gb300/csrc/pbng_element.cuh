@@ -30,35 +30,6 @@ __device__ __forceinline__ float3 pair_diff(float4 hj, float4 lj, float3 uh, flo
     return d;
 }
 
-// Slow path of polar_quaternion for rotations beyond about 120 degrees: the
-// adjugate column with the largest diagonal entry.
-static __device__ __noinline__ void adjugate_best_column(const float* M, float q00, float* q) {
-    float best = -q00;
-    int kbest = 0;
-    for (int k = 1; k < 4; ++k) {
-        int r[3], n = 0;
-        for (int i = 0; i < 4; ++i)
-            if (i != k) r[n++] = i;
-        const float dkk = det3(M[4 * r[0] + r[0]], M[4 * r[0] + r[1]], M[4 * r[0] + r[2]],
-                               M[4 * r[1] + r[0]], M[4 * r[1] + r[1]], M[4 * r[1] + r[2]],
-                               M[4 * r[2] + r[0]], M[4 * r[2] + r[1]], M[4 * r[2] + r[2]]);
-        if (-dkk > best) { best = -dkk; kbest = k; }
-    }
-    if (kbest == 0) return;
-    for (int j = 0; j < 4; ++j) {
-        // adj_jk = (-1)^{j+k} det(M without row k and column j)
-        int rr[3], cc[3], nr = 0, nc = 0;
-        for (int i = 0; i < 4; ++i) {
-            if (i != kbest) rr[nr++] = i;
-            if (i != j) cc[nc++] = i;
-        }
-        const float dm = det3(M[4 * rr[0] + cc[0]], M[4 * rr[0] + cc[1]], M[4 * rr[0] + cc[2]],
-                              M[4 * rr[1] + cc[0]], M[4 * rr[1] + cc[1]], M[4 * rr[1] + cc[2]],
-                              M[4 * rr[2] + cc[0]], M[4 * rr[2] + cc[1]], M[4 * rr[2] + cc[2]]);
-        q[j] = ((j + kbest) & 1) ? -dm : dm;
-    }
-}
-
 // Rotation part of F = I + H for the corotated energy (Section "Constitutive
 // Models", Eq. cor, with R the rotation of the polar decomposition in SO(3)),
 // as the unit quaternion q = (w, x, y, z) times `scale`.
@@ -115,11 +86,29 @@ __device__ __forceinline__ void polar_quaternion(const float* H, float n2, float
     q[1] = -(m01 * k23 - m12 * k03 + m13 * k02);
     q[2] = m01 * k13 - m11 * k03 + m13 * k01;
     q[3] = -(m01 * k12 - m11 * k02 + m12 * k01);
-    // adj(M) = -p'(t) q q^T, so q_0^2 = -adj_00 / p'(t).
+    // adj(M) = -p'(t) q q^T, so q_0^2 = -adj_00 / p'(t).  Beyond about 120
+    // degrees column 0 is poorly scaled: take the column of adj(M) with the
+    // largest diagonal entry instead.  M is symmetric, so is adj(M); its other
+    // diagonal and off-diagonal cofactors, in registers:
     if (!(-q[0] > 0.25f * dp)) {
-        const float M[16] = {m00, m01, m02, m03, m01, m11, m12, m13,
-                             m02, m12, m22, m23, m03, m13, m23, m33};
-        adjugate_best_column(M, q[0], q);
+        const float a11 = det3(m00, m02, m03, m02, m22, m23, m03, m23, m33);
+        const float a22 = det3(m00, m01, m03, m01, m11, m13, m03, m13, m33);
+        const float a33 = det3(m00, m01, m02, m01, m11, m12, m02, m12, m22);
+        const float a12 = -det3(m00, m02, m03, m01, m12, m13, m03, m23, m33);
+        const float a13 = det3(m00, m02, m03, m01, m12, m13, m02, m22, m23);
+        const float a23 = -det3(m00, m01, m03, m01, m11, m13, m02, m12, m23);
+        float best = -q[0];
+        int kb = 0;
+        if (-a11 > best) { best = -a11; kb = 1; }
+        if (-a22 > best) { best = -a22; kb = 2; }
+        if (-a33 > best) { kb = 3; }
+        if (kb == 1) {
+            q[0] = q[1]; q[1] = a11; q[2] = a12; q[3] = a13;
+        } else if (kb == 2) {
+            q[0] = q[2]; q[1] = a12; q[2] = a22; q[3] = a23;
+        } else if (kb == 3) {
+            q[0] = q[3]; q[1] = a13; q[2] = a23; q[3] = a33;
+        }
     }
     const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     if (qq > 1e-30f && qq < 3.0e38f) {

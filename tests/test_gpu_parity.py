@@ -361,3 +361,23 @@ def test_isolated_vertex(oracle_mod):
     with pytest.raises(PbngError) as e:
         m.sweep(u, 2, default_params())
     assert "DEGENERATE" in str(e.value)
+
+
+@pytest.mark.parametrize("angle", [150.0, 179.0])
+def test_large_rotation_matches_oracle(oracle_mod, angle):
+    """The deformed state and the clamp targets of a twisted block turned
+    rigidly by more than 120 degrees about an oblique axis: every element's
+    polar factor takes the adjugate column with the largest diagonal instead
+    of column 0 (Horn's eigenvector for rotations near 180 degrees), and the
+    iterate still follows the FP64 oracle."""
+    p = W.twist_block(4, 45.0, 0.1)
+    axis = np.array([1.0, 2.0, 3.0]) / np.sqrt(14.0)
+    t = np.radians(angle)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    Q = np.eye(3) + np.sin(t) * K + (1 - np.cos(t)) * K @ K
+    c = p.X.mean(axis=0)
+    p.x0 = (p.x0 - c) @ Q.T + c
+    _, x_gpu, _ = _gpu_run(p, 30)
+    x_ora, st = _oracle(oracle_mod, p).sweeps(p.x0, 30)
+    assert st == 0
+    assert np.abs(x_gpu - x_ora).max() <= POS_TOL * np.abs(x_ora - p.X).max()
