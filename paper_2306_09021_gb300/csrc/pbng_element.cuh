@@ -54,7 +54,10 @@ __device__ __forceinline__ void polar_quaternion(const float* H, float n2, float
     const float k0 = n2 * n2 - 4.0f * c2;
     const float n23 = 3.0f * n2;
     float t = n23 * rsqrtf(n23);
-    float dp = 1.0f, dprev = 0.0f;
+    // dprev starts as an assumed previous step of 3e-3 t, so that a first
+    // step below 3e-5 t (already in the quadratic range near a simple root)
+    // ends the iteration.
+    float dp = 1.0f, dprev = 3e-3f * t;
 #pragma unroll 1
     for (int it = 0; it < 16; ++it) {
         const float t2 = t * t;
@@ -65,7 +68,8 @@ __device__ __forceinline__ void polar_quaternion(const float* H, float n2, float
         const float ad = fabsf(d);
         // Converged; or quadratic convergence has set in (this step is at most
         // 1/100 of the previous one) and the step is below 1e-4 t, so the
-        // next one would be below float resolution.
+        // next one would be below float resolution.  Near a double root the
+        // steps only halve, so the iteration goes on to the 2e-7 t test.
         if (!(ad > 2e-7f * t) || (ad <= 1e-4f * t && ad <= 0.01f * dprev)) break;
         dprev = ad;
     }
