@@ -16,9 +16,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   sweeps (plain)                               pinned (fixed point = Newton
                                                equilibrium, patch test, rotation
                                                invariance, single-vertex Newton)
-  sweeps (Chebyshev / SOR)                     parity unpinned beyond the printed
-                                               update: reduces to plain for unit
-                                               weights; converges to the same point
+  sweeps (Chebyshev / SOR)                     pinned (linear-iteration theory on
+                                               the linearised sweep: the scaled
+                                               Chebyshev polynomial, the closed
+                                               form of the two-step recurrence)
   newton, hessian_dense                        pinned (FD of the residual)
   adjoint_dense                                pinned (FD of the loss)
 """
