@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", choices=["sag64", "twist10", "bar", "batched", "adjoint"], default="sag64",
+    ap.add_argument("--config", choices=["sag64", "twist10", "bar", "batched", "adjoint", "blocks"], default="sag64",
                     help="sag64: 64^3 gravity-sag cube (default); twist10: 10^3 twisted block; "
                          "bar: 40x40x200 bar with springs and contact; batched: 256 uneven blocks; "
                          "adjoint: 32 load cases of a 48^3 cube, forward + adjoint")
@@ -91,6 +91,11 @@ def workload(args):
                         "bottom clamped to seeded rigid motions (initial guess: that motion of the whole "
                         "block), seeded gravity directions, nu=0.3; "
                         "forward solve and adjoint of |x_top - target|^2"), dict(accel="sor", omega=1.5)
+    if args.config == "blocks":
+        p = W.two_blocks_hanging(64, 48, k=1e5)
+        return p, None, (f"two cubes bound by {len(p.meta['weak'][0])} two-vertex weak constraints "
+                         "(k_n = k_t = 1e5): 64^3 cells hanging from its top face, 48^3 cells below "
+                         f"({p.nv} verts, {p.ne} tets), E=1e3 nu=0.3 rho=10, gravity"), dict(accel="chebyshev")
     if args.config == "batched":
         probs = W.batched_blocks()
         p, mid, _ = W.concat_problems(probs)
@@ -231,6 +236,8 @@ def cpu_baseline(p, acc, model="corotated", sweeps_budget_s=12.0, max_sweeps=400
     ncpu = os.cpu_count() or 1
     threads = oracle.threads_available(ncpu)
     om = oracle.OracleMesh.from_problem(p, model=model)
+    if "weak" in p.meta:
+        om.set_weak_constraints(*p.meta["weak"])
 
     def run(nthreads, budget, cap):
         x = p.x0.copy()
@@ -261,6 +268,8 @@ def run_reference(args):
     p, _, desc, acc = workload(args)
     threads = oracle.threads_available(os.cpu_count() or 1)
     om = oracle.OracleMesh.from_problem(p, model=args.model)
+    if "weak" in p.meta:
+        om.set_weak_constraints(*p.meta["weak"])
     x = p.x0.copy()
     for _ in range(args.warmup):
         x, _ = om.sweeps(x, 1, threads=threads, **acc)
@@ -308,6 +317,8 @@ def main():
     m = Mesh.from_problem(p, stream=stream, mesh_id=mesh_id)
     if "case_accel" in p.meta:
         m.set_body_accel(p.meta["case_accel"], p.density)
+    if "weak" in p.meta:
+        m.set_weak_constraints(*p.meta["weak"])
     u0 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
     u = u0.clone()
     S = args.sweeps_per_step
@@ -440,7 +451,8 @@ def main():
                           ("sor", dict(accel="sor", omega=1.5), 1e-5)],
                 "bar": [("plain", {}, 1e-5), auto, ("sor", dict(accel="sor", omega=1.5), 1e-5)],
                 "batched": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto, ("plain", {}, 1e-5)],
-                "adjoint": [("sor", dict(accel="sor", omega=1.5), 1e-5), auto]}[args.config]
+                "adjoint": [("sor", dict(accel="sor", omega=1.5), 1e-5), auto],
+                "blocks": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto]}[args.config]
         max_sw = 4000 if args.config == "adjoint" else 20000
         u_eq, best_rel = None, 0.0
         for name, kw, tol in runs:
@@ -494,6 +506,26 @@ def main():
                                             "ms_per_frame": ms / frames, "mean_sweeps": float(np.mean(sw)),
                                             "max_sweeps": int(np.max(sw)), "max_rel_residual": worst}
             del md
+        if args.config == "blocks":
+            # colouring with the constraints as elements, from scratch, against
+            # the incremental recolouring of the constraint vertices of a
+            # handle coloured without them (Section "Collision Coloring")
+            from paper_2306_09021_gb300 import Mesh as _Mesh
+            weak = p.meta["weak"]
+            full = _Mesh.from_problem(p)
+            full.set_weak_constraints(*weak)
+            ncol_full = full.colouring()[1]
+            pf = full.profile()
+            inc = _Mesh.from_problem(p)
+            inc.colouring()
+            inc.set_weak_constraints(*weak, recolour=True)
+            ncol_inc = inc.colouring()[1]
+            pi = inc.profile()
+            ttr["recolouring"] = {"constraints": int(len(weak[0])), "full_colour_ms": pf["colour_ms"],
+                                  "full_layout_ms": pf["layout_ms"], "ncolours_full": int(ncol_full),
+                                  "incremental_colour_ms": pi["colour_ms"], "incremental_layout_ms": pi["layout_ms"],
+                                  "ncolours_incremental": int(ncol_inc)}
+            del full, inc
         if args.config in ("batched", "adjoint"):
             # the same meshes solved one handle at a time (handles built
             # before the clock starts), Chebyshev with the paper's rho

@@ -251,11 +251,25 @@ def two_blocks_hanging(n_top: int = 4, n_bottom: int = 3, young: float = 1000.0,
     X = np.vstack([Xa, Xb])
     tets = np.vstack([ta, tb + na]).astype(np.int32)
     dirichlet = np.flatnonzero(np.isclose(X[:, 2], 2.0)).astype(np.int32)
-    bottom_faces = [t for t in ta if np.isclose(Xa[t, 2], 1.0).sum() == 3]
+    bottom_faces = ta[np.isclose(Xa[ta][:, :, 2], 1.0).sum(axis=1) == 3]   # tets with a face on z = 1
+    TF = Xa[bottom_faces]                                             # [nf, 4, 3]
+    MF = np.stack([TF[:, 1] - TF[:, 0], TF[:, 2] - TF[:, 0], TF[:, 3] - TF[:, 0]], axis=2)
+    MF_inv = np.linalg.inv(MF)
     idx, w = [], []
-    for v in np.flatnonzero(np.isclose(Xb[:, 2], 1.0)):
+    verts = np.flatnonzero(np.isclose(Xb[:, 2], 1.0))
+    # candidate tets by barycentric coordinates, vectorised over chunks of
+    # binding points; the first containing one, in tet order, is then solved
+    # exactly as one system
+    cands = []
+    for c0 in range(0, len(verts), 64):
+        Pc = Xb[verts[c0:c0 + 64]]
+        l_all = np.einsum("fij,vfj->vfi", MF_inv, Pc[:, None, :] - TF[None, :, 0])
+        lmin = np.minimum(1.0 - l_all.sum(axis=2), l_all.min(axis=2))
+        cands.extend(np.flatnonzero(row >= -1e-9) for row in lmin)
+    for v, cand in zip(verts, cands):
         P = Xb[v]
-        for t in bottom_faces:
+        for f in cand:
+            t = bottom_faces[f]
             T = Xa[t]
             M = np.column_stack([T[1] - T[0], T[2] - T[0], T[3] - T[0]])
             l123 = np.linalg.solve(M, P - T[0])
