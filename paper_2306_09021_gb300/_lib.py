@@ -124,6 +124,7 @@ SIGNATURES = {
     "pbng_set_state": (_I32, [_P, _P, ctypes.c_size_t]),
     "pbng_residual_noalloc": (_I32, [_P, _P, _PD]),
     "pbng_set_profiling": (_I32, [_P, _I32]),
+    "pbng_test_set_copy_shortfall": (_I32, [_P, _I32]),
     "pbng_get_profile": (_I32, [_P, ctypes.POINTER(PbngProfile)]),
     "pbng_set_schedule": (_I32, [_P, ctypes.POINTER(PbngParams), ctypes.POINTER(PbngSchedule)]),
     "pbng_get_schedule": (_I32, [_P, ctypes.POINTER(PbngSchedule)]),

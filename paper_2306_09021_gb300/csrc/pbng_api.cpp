@@ -30,6 +30,7 @@ struct DevBuf {
 
 struct pbng_mesh {
     int device = 0;
+    int32_t copy_shortfall = 0;  // pbng_test_set_copy_shortfall
     cudaStream_t stream = nullptr;
     int32_t nv = 0, ne = 0, ncomp = 1;
     std::vector<double> X;          // 3 nv
@@ -95,7 +96,7 @@ struct pbng_mesh {
     DevBuf d_dir_hi, d_dir_lo;
     DevBuf d_state[4][2];           // cur, p1, p2, tmp; hi/lo
     DevBuf d_partial, d_comp_sq, d_scalar, d_err;
-    double* h_pinned = nullptr;     // ncomp + 2 doubles for readbacks
+    double* h_pinned = nullptr;     // ncomp + 2 doubles for readbacks; [ncomp] also carries the error flag
     DeviceMesh dm{};
 
     // iteration state
@@ -718,6 +719,7 @@ pbng_status build_layout(pbng_mesh* m) {
     d.comp = m->ncomp > 1 ? (const int32_t*)m->d_comp.p : nullptr;
     d.comp_active = m->ncomp > 1 ? (const int32_t*)m->d_active.p : nullptr;
     d.ring = (const RingBlock*)m->d_ring.p;
+    d.copy_shortfall = m->copy_shortfall;
     d.pn_x = (float)m->pn[0];
     d.pn_y = (float)m->pn[1];
     d.pn_z = (float)m->pn[2];
@@ -777,6 +779,8 @@ pbng_status enqueue_residual(pbng_mesh* m, State s, bool compensated, double* pa
     return PBNG_OK;
 }
 
+pbng_status sync_with_err(pbng_mesh* m, cudaStream_t st);
+
 // FP64 squared residual norms (per component) of state `slot` -> host `out`.
 pbng_status residual_sq(pbng_mesh* m, int slot, bool compensated, double* out) {
     cudaStream_t st = m->stream;
@@ -788,7 +792,7 @@ pbng_status residual_sq(pbng_mesh* m, int slot, bool compensated, double* out) {
     prof_end(m, pslot);
     PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? m->d_comp_sq.p : m->d_scalar.p,
                                  sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
-    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    if ((r = sync_with_err(m, st))) return r;  // a timed-out warp left its partial at zero
     for (int k = 0; k < m->ncomp; ++k) out[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
     return PBNG_OK;
 }
@@ -804,6 +808,17 @@ pbng_status check_err(pbng_mesh* m) {
         return fail(m, PBNG_EDIVERGED, "non-finite vertex update");
     }
     return PBNG_OK;
+}
+
+// Synchronises the stream after also reading the device error flag into the
+// spare pinned slot after the per-component readbacks, and reports a set
+// flag (which check_err then clears): one synchronisation for both.
+pbng_status sync_with_err(pbng_mesh* m, cudaStream_t st) {
+    int32_t* herr = reinterpret_cast<int32_t*>(m->h_pinned + m->ncomp);
+    *herr = 0;
+    PBNG_CUDA(m, cudaMemcpyAsync(herr, m->d_err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    return *herr ? check_err(m) : PBNG_OK;
 }
 
 // kernel_path 1 (direct loads everywhere) needs CSR records for every
@@ -1976,8 +1991,16 @@ pbng_status pbng_residual_noalloc(pbng_mesh* m, const float* u_dev, double* resi
     if (r) return r;
     PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? scratch : scratch + nparts,
                                  sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
-    PBNG_CUDA(m, cudaStreamSynchronize(st));
+    if ((r = sync_with_err(m, st))) return r;
     for (int k = 0; k < m->ncomp; ++k) residual_out[k] = (m->ncol == 0) ? 0.0 : std::sqrt(m->h_pinned[k]);
+    return PBNG_OK;
+}
+
+pbng_status pbng_test_set_copy_shortfall(pbng_mesh* m, int32_t bytes) {
+    if (!m || bytes < 0 || bytes > 1024 || bytes % 16 != 0) return PBNG_EINVAL;
+    m->copy_shortfall = bytes;
+    m->dm.copy_shortfall = bytes;
+    destroy_graphs(m);  // captured launches carry the old value
     return PBNG_OK;
 }
 

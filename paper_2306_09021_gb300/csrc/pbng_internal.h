@@ -54,6 +54,10 @@ struct DeviceMesh {
     // item per warp; vertex v of a lane-width-W run owns W consecutive slots.
     // Slot s is entry s % 32 of block s / 32 (RingBlock).
     const struct RingBlock* ring;  // [nslots / 32]
+    // Test hook (pbng_test_set_copy_shortfall): bytes that each warp's first
+    // record copy of a ring pass is expected to carry beyond its size, so
+    // that its bounded wait runs out; 0 in normal use.
+    int32_t copy_shortfall;
     float pn_x, pn_y, pn_z;  // contact plane normal (unit)
     float k_contact;         // 0 = no plane
     // General weak constraints (nullptr when there are none): constraint c

@@ -149,7 +149,9 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Lane 0: request the records and 1-ring ids of item `it` into stage r.  An
 // item whose whole component is frozen is marked skipped and fetches nothing.
-__device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, WarpSmem& S, int r) {
+// `extra` bytes are expected beyond the copy (the timeout test hook).
+__device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, WarpSmem& S, int r,
+                                              uint32_t extra = 0u) {
     it.skip = (it.comp >= 0 && m.comp_active && !m.comp_active[it.comp]) ? 1 : 0;
     S.desc[r] = it;
     unsigned long long* bar = S.bar + r;
@@ -157,7 +159,7 @@ __device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, Warp
         mbar_arrive_expect_tx(bar, 0);
         return;
     }
-    mbar_arrive_expect_tx(bar, kRecBytes);
+    mbar_arrive_expect_tx(bar, kRecBytes + extra);
     bulk_g2s(&S.rec[r], m.ring + (it.slot0 >> 5), kRecBytes, bar);
 }
 
@@ -379,7 +381,8 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         if (lane == 0) {
             for (int i = 0; i < kRecStages; ++i) mbar_init(S.bar + i, 1);
             fence_mbar_init();
-            for (int i = 0; i < kRecAhead && i < n; ++i) issue_records(m, items[first + i * stride], S, i);
+            for (int i = 0; i < kRecAhead && i < n; ++i)
+                issue_records(m, items[first + i * stride], S, i, i == 0 ? (uint32_t)m.copy_shortfall : 0u);
             if (n > kRecAhead) next = items[first + kRecAhead * stride];
         }
         issued = n < kRecAhead ? n : kRecAhead;

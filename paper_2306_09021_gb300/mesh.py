@@ -299,6 +299,11 @@ class Mesh:
                                    ctypes.byref(s)), "pbng_autotune", self.h)
         return self._schedule_dict(s)
 
+    def test_set_copy_shortfall(self, nbytes):
+        """pbng_test_set_copy_shortfall: make each warp's first record-copy wait
+        of the ring passes run out (test hook; 0 restores normal operation)."""
+        check(load().pbng_test_set_copy_shortfall(self.h, int(nbytes)), "pbng_test_set_copy_shortfall", self.h)
+
     def set_profiling(self, enable=True):
         """pbng_set_profiling: per-launch event timing of the library's kernels."""
         check(load().pbng_set_profiling(self.h, 1 if enable else 0), "pbng_set_profiling", self.h)
