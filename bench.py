@@ -501,9 +501,9 @@ def main():
                 worst = max(worst, float(np.max(relr)))
                 st_max = max(st_max, int(st))
             torch.cuda.synchronize()
-            ms = 1e3 * (time.perf_counter() - t0)
+            be_ms = 1e3 * (time.perf_counter() - t0)
             ttr["backward_euler_frames"] = {"tol": 1e-4, "dt": 1.0 / 60.0, "frames": frames, "worst_status": st_max,
-                                            "ms_per_frame": ms / frames, "mean_sweeps": float(np.mean(sw)),
+                                            "ms_per_frame": be_ms / frames, "mean_sweeps": float(np.mean(sw)),
                                             "max_sweeps": int(np.max(sw)), "max_rel_residual": worst}
             del md
         if args.config == "blocks":
