@@ -164,6 +164,19 @@ pbng_status pbng_get_colouring(pbng_mesh* m, int32_t* colour_out, int32_t* ncolo
 pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_params* p,
                        double* rel_residual_out);
 
+/* pbng_sweep from and to host memory, in one round trip: copies u_host
+ * (host float [nv][3], in/out; pinned memory makes the copies asynchronous)
+ * to a device buffer of the handle, loads it (p->resume is ignored: every
+ * call starts a fresh acceleration history), runs nsweeps iterations as
+ * pbng_sweep does, and copies the iterate back with the clamped entries set
+ * to x_D - X.  If residual_out (host double [ncomp], or NULL) is given, the
+ * FP64 absolute residual |f + f^ext|_free of each component after the last
+ * sweep is written: the step's metric, which needs no residual at the
+ * start.  Everything is enqueued on the handle's stream and the call
+ * synchronises once, at the end. */
+pbng_status pbng_sweep_host(pbng_mesh* m, float* u_host, int32_t nsweeps, const pbng_params* p,
+                            double* residual_out);
+
 /* Sweeps until every component's relative residual is <= rel_tol (checked
  * every p->residual_every sweeps) or max_sweeps is reached.  sweeps_out (host,
  * may be NULL) receives the sweeps done; rel_residual_out (host double

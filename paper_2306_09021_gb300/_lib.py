@@ -118,6 +118,7 @@ SIGNATURES = {
     "pbng_get_colouring": (_I32, [_P, _PI, _PI]),
     "pbng_adjoint": (_I32, [_P, _P, _P, _P, _P, _D, _I32, ctypes.POINTER(PbngParams), _PI, _PD]),
     "pbng_sweep": (_I32, [_P, _P, _I32, ctypes.POINTER(PbngParams), _PD]),
+    "pbng_sweep_host": (_I32, [_P, _P, _I32, ctypes.POINTER(PbngParams), _PD]),
     "pbng_solve": (_I32, [_P, _P, _D, _I32, ctypes.POINTER(PbngParams), _PI, _PD]),
     "pbng_residual": (_I32, [_P, _P, _PD]),
     "pbng_get_state": (_I32, [_P, _P, ctypes.POINTER(ctypes.c_size_t)]),

@@ -84,6 +84,7 @@ struct pbng_mesh {
     // device buffers
     DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
     DevBuf d_ring, d_items;
+    DevBuf d_host_u;  // device copy of the caller's host iterate (pbng_sweep_host)
     DevBuf d_active;                   // int32 [ncomp] component flags (1 = active)
     // adjoint (built on first use after each layout)
     DevBuf d_lam[3], d_gv, d_diag, d_hdl, d_tv, d_tb, d_dq_int, d_dq_caller, d_adj_partial;
@@ -1346,6 +1347,53 @@ pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_p
     return PBNG_OK;
 }
 
+pbng_status pbng_sweep_host(pbng_mesh* m, float* u_host, int32_t nsweeps, const pbng_params* p,
+                            double* residual_out) {
+    if (!m) return PBNG_EINVAL;
+    if (!valid_params(p) || nsweeps < 0) return fail(m, PBNG_EINVAL, "bad parameters");
+    if (p->accel == PBNG_ACCEL_CHEBYSHEV && !(p->rho > 0.0))
+        return fail(m, PBNG_EINVAL, "automatic rho (rho <= 0) needs the residual checks of pbng_solve");
+    select_path(m, p);
+    pbng_status s = ensure_ready(m);
+    if (s) return s;
+    if (!u_host) return fail(m, PBNG_EINVAL, "u_host is NULL");
+    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const size_t bytes = sizeof(float) * 3 * (size_t)m->nv;
+    cudaStream_t st = m->stream;
+    PBNG_CUDA(m, ensure_buf(m->d_host_u, bytes));
+    float* d_u = (float*)m->d_host_u.p;
+    PBNG_CUDA(m, cudaMemcpyAsync(d_u, u_host, bytes, cudaMemcpyHostToDevice, st));
+    pbng_params q = *p;
+    q.resume = 0;
+    m->has_state = false;  // load d_u, fresh acceleration history
+    if ((s = begin(m, d_u, &q, false))) return s;
+    if ((s = ensure_wg(m, (size_t)std::max<int32_t>(1, nsweeps)))) return s;
+    const int32_t K = std::min<int32_t>(q.residual_every, kMaxChunk);
+    bool res_done = false;
+    for (int32_t done = 0; done < nsweeps;) {
+        const int32_t chunk = std::min<int32_t>(K, nsweeps - done);
+        const bool with_res = done + chunk == nsweeps && residual_out != nullptr;
+        if ((s = run_chunk(m, &q, chunk, with_res, m->h_wg + done))) return s;
+        res_done = res_done || with_res;
+        done += chunk;
+    }
+    if (residual_out && !res_done) {  // no sweep: the residual of the loaded iterate
+        const bool multi = m->ncomp > 1;
+        if ((s = enqueue_residual(m, state_of(m, 0), comp, (double*)m->d_partial.p, (double*)m->d_comp_sq.p,
+                                  (double*)m->d_scalar.p, st)))
+            return s;
+        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? m->d_comp_sq.p : m->d_scalar.p,
+                                     sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
+    }
+    PBNG_CUDA(m, launch_store(m->nv, (const int32_t*)m->d_perm.p, state_of(m, 0), d_u, st));
+    m->kernel_launches++;
+    PBNG_CUDA(m, cudaMemcpyAsync(u_host, d_u, bytes, cudaMemcpyDeviceToHost, st));
+    if ((s = sync_with_err(m, st))) return s;
+    if (residual_out)
+        for (int k = 0; k < m->ncomp; ++k) residual_out[k] = (m->ncol == 0) ? 0.0 : std::sqrt(m->h_pinned[k]);
+    return PBNG_OK;
+}
+
 pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps,
                        const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out) {
     if (!m) return PBNG_EINVAL;
@@ -2208,7 +2256,7 @@ void pbng_destroy(pbng_mesh* m) {
     DevBuf* bufs[] = {&m->d_lam[0], &m->d_lam[1], &m->d_lam[2], &m->d_gv, &m->d_diag, &m->d_hdl, &m->d_tv,
                       &m->d_tb, &m->d_dq_int, &m->d_dq_caller, &m->d_adj_partial,
                       &m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
-                      &m->d_ring, &m->d_items,
+                      &m->d_ring, &m->d_items, &m->d_host_u,
                       &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k, &m->d_wc_off, &m->d_wc_list, &m->d_wc_v,
                       &m->d_wc_b, &m->d_wc_k, &m->d_wc_c0,

@@ -154,6 +154,28 @@ class Mesh:
         check(st, "pbng_sweep", self.h)
         return out
 
+    def sweep_host(self, u_host, nsweeps, params=None, want_residual=False):
+        """pbng_sweep_host in place on a host float32 [nv, 3] array or CPU
+        tensor (pinned memory for asynchronous copies); returns the absolute
+        residual norms per component (or None)."""
+        import torch
+        if isinstance(u_host, torch.Tensor):
+            if u_host.is_cuda or u_host.dtype != torch.float32 or not u_host.is_contiguous() \
+                    or tuple(u_host.shape) != (self.nv, 3):
+                raise ValueError(f"u_host must be a contiguous float32 host tensor of shape ({self.nv}, 3)")
+            ptr = u_host.data_ptr()
+        else:
+            if not (isinstance(u_host, np.ndarray) and u_host.dtype == np.float32 and u_host.flags["C_CONTIGUOUS"]
+                    and u_host.shape == (self.nv, 3)):
+                raise ValueError(f"u_host must be a C-contiguous float32 array of shape ({self.nv}, 3)")
+            ptr = u_host.ctypes.data
+        p = params if params is not None else default_params()
+        out = np.zeros(self.ncomp) if want_residual else None
+        st = load().pbng_sweep_host(self.h, ctypes.c_void_p(ptr), int(nsweeps), ctypes.byref(p),
+                                    None if out is None else _dptr(out))
+        check(st, "pbng_sweep_host", self.h)
+        return out
+
     def solve(self, u, rel_tol, max_sweeps, params=None, raise_on_status=True):
         """pbng_solve in place on u; returns (status, sweeps, rel_residuals)."""
         _check_u(u, self.nv)

@@ -381,3 +381,33 @@ def test_large_rotation_matches_oracle(oracle_mod, angle):
     x_ora, st = _oracle(oracle_mod, p).sweeps(p.x0, 30)
     assert st == 0
     assert np.abs(x_gpu - x_ora).max() <= POS_TOL * np.abs(x_ora - p.X).max()
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_sweep_equals_device_sweep(pinned):
+    """pbng_sweep_host (host iterate in and out, one synchronisation) gives the
+    bits of pbng_sweep with resume = 0 on a device copy, and the absolute
+    residual that pbng_residual reports for the result."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = W.twist_block(8, 60.0, 0.2)
+    params = default_params(accel="chebyshev")
+    m = Mesh.from_problem(p)
+    u_dev = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    r_start = m.residual(u_dev)[0]
+    rel = m.sweep(u_dev, 23, params, want_residual=True)
+    h = torch.tensor(p.x0 - p.X, dtype=torch.float32)
+    if pinned:
+        h = h.pin_memory()
+    r_host = m.sweep_host(h, 23, params, want_residual=True)
+    torch.cuda.synchronize()
+    assert torch.equal(h, u_dev.cpu())
+    # the same FP64 residual of the same (compensated) state
+    assert r_host[0] == pytest.approx(rel[0] * r_start, rel=1e-12)
+    # twice in a row from the returned host iterate: a fresh history each call
+    m.sweep_host(h, 5, params)
+    u2 = u_dev.clone()
+    m.sweep(u2, 5, params)
+    assert torch.equal(h, u2.cpu())
+    # no sweep: the residual of the loaded iterate
+    r0 = m.sweep_host(h.clone(), 0, params, want_residual=True)
+    assert r0[0] == pytest.approx(m.residual(u2)[0], rel=1e-12)
