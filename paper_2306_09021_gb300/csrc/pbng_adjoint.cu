@@ -346,7 +346,7 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
 }
 
 template <int MODE, int MODEL>
-__global__ void __launch_bounds__(kBlock) adjoint_vertex_kernel(const DeviceMesh m, State u, float4* lam,
+__global__ void __launch_bounds__(kBlock, 3) adjoint_vertex_kernel(const DeviceMesh m, State u, float4* lam,
                                                                 const float4* gv, float4* diag, float4* out4,
                                                                 const Item* __restrict__ items, int nitems,
                                                                 int32_t* err, double* partial) {
