@@ -411,3 +411,59 @@ def test_host_buffer_sweep_equals_device_sweep(pinned):
     # no sweep: the residual of the loaded iterate
     r0 = m.sweep_host(h.clone(), 0, params, want_residual=True)
     assert r0[0] == pytest.approx(m.residual(u2)[0], rel=1e-12)
+
+
+def _full_size_case(name):
+    if name == "bar":
+        return W.contact_bar(), None, {}
+    if name == "blocks":
+        return W.two_blocks_hanging(64, 48, k=1e5), None, {}
+    if name == "batched":
+        p, mid, _ = W.concat_problems(W.batched_blocks())
+        return p, mid, {}
+    model = {"sag64_nh": "neohookean", "sag64_snh": "stable_neohookean"}[name]
+    return W.gravity_sag(64), None, {"model": model}
+
+
+@pytest.mark.parametrize("name", ["bar", "blocks", "batched", "sag64_nh", "sag64_snh"])
+def test_full_size_workloads_sampled(oracle_mod, name):
+    """The other benchmark workloads at full size, in the benchmark's launch
+    configuration: the contact bar (1.6 M tets, springs, plane, lognormal E),
+    the weak-constraint blocks (1.86 M tets, 2,401 bindings), the 256-mesh
+    batch (14.2 M tets) and the Neo-Hookean models on the 64^3 cube.  After
+    three sweeps, one more GPU sweep moves sampled vertices of every colour
+    (constraint vertices among them) by the oracle's Newton step on its local
+    system, taken from the state that vertex's update saw."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    from paper_2306_09021_gb300._lib import MODEL
+    p, mid, kw = _full_size_case(name)
+    m = Mesh.from_problem(p, mesh_id=mid)
+    om = oracle_mod.OracleMesh.from_problem(p, model=MODEL[kw.get("model", "corotated")])
+    bound = np.zeros(p.nv, bool)
+    if "weak" in p.meta:
+        m.set_weak_constraints(*p.meta["weak"])
+        om.set_weak_constraints(*p.meta["weak"])
+        idx = p.meta["weak"][0]
+        bound[idx[idx >= 0]] = True
+    params = default_params(**kw)
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    m.sweep(u, 3, params)
+    s0 = u.cpu().double().numpy() + p.X
+    m.sweep(u, 1, params)
+    s1 = u.cpu().double().numpy() + p.X
+    col, ncol = m.colouring()
+    rng = np.random.default_rng(17)
+    for c in range(ncol):
+        members = np.flatnonzero(col == c)
+        ids = list(rng.choice(members, min(8, len(members)), replace=False))
+        on = np.flatnonzero(bound[members])
+        ids += list(members[rng.choice(on, min(4, len(on)), replace=False)]) if len(on) else []
+        mixed = np.ascontiguousarray(np.where((col < c)[:, None] & (col >= 0)[:, None], s1, s0))
+        for i in ids:
+            r, A = om.local_system(mixed, i)
+            d_ora = np.linalg.solve(A, r)
+            d_gpu = s1[i] - s0[i]
+            # the states are read back as float32 displacements: a few ulps of
+            # u on top of the relative tolerance
+            ulps = 4.0 * 2.0 ** -23 * np.abs(s0[i] - p.X[i]).max()
+            assert np.abs(d_gpu - d_ora).max() <= 2e-4 * np.abs(d_ora).max() + ulps + 1e-12, (name, c, i)
