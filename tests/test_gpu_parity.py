@@ -421,16 +421,25 @@ def _full_size_case(name):
     if name == "batched":
         p, mid, _ = W.concat_problems(W.batched_blocks())
         return p, mid, {}
+    if name == "adjoint_case":
+        # one load case of the adjoint workload's 48^3 block: the clamp's
+        # rigid motion extended to the block, its own gravity direction
+        p = W.adjoint_block(48)
+        xall, accs = W.adjoint_load_cases(p, count=32, full_body=True)
+        p.x0 = xall[5]
+        p.body_accel = np.asarray(accs[5], dtype=np.float64)
+        return p, None, {}
     model = {"sag64_nh": "neohookean", "sag64_snh": "stable_neohookean"}[name]
     return W.gravity_sag(64), None, {"model": model}
 
 
-@pytest.mark.parametrize("name", ["bar", "blocks", "batched", "sag64_nh", "sag64_snh"])
+@pytest.mark.parametrize("name", ["bar", "blocks", "batched", "adjoint_case", "sag64_nh", "sag64_snh"])
 def test_full_size_workloads_sampled(oracle_mod, name):
     """The other benchmark workloads at full size, in the benchmark's launch
     configuration: the contact bar (1.6 M tets, springs, plane, lognormal E),
     the weak-constraint blocks (1.86 M tets, 2,401 bindings), the 256-mesh
-    batch (14.2 M tets) and the Neo-Hookean models on the 64^3 cube.  After
+    batch (14.2 M tets), one load case of the adjoint workload's 48^3 block
+    and the Neo-Hookean models on the 64^3 cube.  After
     three sweeps, one more GPU sweep moves sampled vertices of every colour
     (constraint vertices among them) by the oracle's Newton step on its local
     system, taken from the state that vertex's update saw."""
