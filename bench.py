@@ -202,7 +202,8 @@ def kernel_sources_sha256():
     """Hash of the CUDA sources that define the sweep kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_09021_gb300", "csrc")
-    for name in ("pbng_element.cuh", "pbng_internal.h", "pbng_kernels.cu", "pbng_launch.cuh", "pbng_ring.cu"):
+    for name in ("pbng_async.cuh", "pbng_element.cuh", "pbng_internal.h", "pbng_kernels.cu", "pbng_launch.cuh",
+                 "pbng_ring.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()

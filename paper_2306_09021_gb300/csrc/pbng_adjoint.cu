@@ -12,7 +12,10 @@
 //
 // Vertex kernels use the ring layout of pbng_ring.cu (one warp per 32-slot
 // item, W lanes per vertex, 1-ring values exchanged by shuffles) with direct
-// loads; the gradient kernel runs one thread per tetrahedron.
+// loads; the block Gauss-Seidel pass also runs pipelined like the colour
+// pass (adjoint_ring_sweep_kernel).  The gradient kernel runs one thread per
+// tetrahedron.
+#include "pbng_async.cuh"
 #include "pbng_element.cuh"
 #include "pbng_internal.h"
 
@@ -452,6 +455,233 @@ __global__ void clamped_grad_kernel(int nd, const int32_t* dq_internal, const in
 
 inline int nblocks(int n, int b) { return (n + b - 1) / b; }
 
+// ---- block Gauss-Seidel pass, pipelined -----------------------------------
+// The kSweep pass of adj_item with the colour pass's pipeline: persistent
+// warps, each item's record block by a TMA bulk copy two items ahead; the
+// 1-ring displacement pairs and multipliers, and the own vertices'
+// displacement pair, multiplier, right-hand side, diagonal block and aux
+// records, by cp.async one item ahead.  The multipliers a pass gathers belong
+// to other colours, and an item's own vertices are written only by its warp
+// after they were read, so the result is the direct-load pass's.
+using namespace async;
+
+constexpr int kAdjWarps = 6;  // per CTA
+constexpr int kAdjCtasPerSm = 3;
+constexpr int kAdjRecStages = 3;
+constexpr int kAdjGatStages = 2;
+constexpr int kAdjItemVerts = kRingLanes / 4;
+
+struct __align__(16) AdjGat {
+    float4 nh[kRingLanes];     // 1-ring displacement hi
+    float4 nl[kRingLanes];     // 1-ring displacement lo
+    float4 nlam[kRingLanes];   // 1-ring multiplier
+    float4 oh[kAdjItemVerts];  // own displacement hi, lo, multiplier, dL/du
+    float4 ol[kAdjItemVerts];
+    float4 olam[kAdjItemVerts];
+    float4 ogv[kAdjItemVerts];
+    float4 od0[kAdjItemVerts];  // own diagonal block (two float4)
+    float4 od1[kAdjItemVerts];
+    float4 oa0[kAdjItemVerts];  // own aux records
+    float4 oa1[kAdjItemVerts];
+};
+
+struct __align__(16) AdjWarpSmem {
+    RingBlock rec[kAdjRecStages];
+    AdjGat gat[kAdjGatStages];
+    Item desc[kAdjRecStages];
+    unsigned long long bar[kAdjRecStages];
+};
+
+static_assert(kAdjCtasPerSm * (kAdjWarps * sizeof(AdjWarpSmem) + 1024) <= 228 * 1024,
+              "the adjoint pass's per-warp stages exceed an SM's shared memory");
+static_assert(sizeof(RingBlock) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+__device__ __forceinline__ void adj_issue_records(const DeviceMesh& m, Item it, AdjWarpSmem& S, int r) {
+    S.desc[r] = it;
+    mbar_arrive_expect_tx(S.bar + r, (uint32_t)sizeof(RingBlock));
+    bulk_g2s(&S.rec[r], m.ring + (it.slot0 >> 5), (uint32_t)sizeof(RingBlock), S.bar + r);
+}
+
+__device__ __forceinline__ void adj_issue_gathers(const DeviceMesh& m, const State& u, const float4* lam,
+                                                  const float4* gv, const float4* diag, AdjWarpSmem& S, int r,
+                                                  int g, int lane) {
+    const Item it = S.desc[r];
+    AdjGat& G = S.gat[g];
+    const int id = S.rec[r].id[lane];
+    cp_async16(G.nh + lane, u.hi + id);
+    cp_async16(G.nl + lane, u.lo + id);
+    cp_async16(G.nlam + lane, lam + id);
+    if (lane < it.nv) {
+        const int v = it.v0 + lane;
+        cp_async16(G.oh + lane, u.hi + v);
+        cp_async16(G.ol + lane, u.lo + v);
+        cp_async16(G.olam + lane, lam + v);
+        cp_async16(G.ogv + lane, gv + v);
+        cp_async16(G.od0 + lane, diag + 2 * v);
+        cp_async16(G.od1 + lane, diag + 2 * v + 1);
+        cp_async16(G.oa0 + lane, m.aux0 + v);
+        cp_async16(G.oa1 + lane, m.aux1 + v);
+    }
+}
+
+template <int W, int MODEL>
+__device__ __forceinline__ void adj_ring_item(const DeviceMesh& m, float4* lam, const AdjWarpSmem& S, int r, int g,
+                                              int lane, int32_t* err) {
+    const Item it = S.desc[r];
+    const RingBlock& R = S.rec[r];
+    const AdjGat& G = S.gat[g];
+    const int j = lane / W;
+    const bool active = j < it.nv;
+    const int v = it.v0 + j;
+    const float3 z3 = make_float3(0.f, 0.f, 0.f);
+    float3 uh = z3, ul = z3, li = z3, du = z3, dl = z3;
+    if (active) {
+        uh = f3(G.oh[j]);
+        ul = f3(G.ol[j]);
+        li = f3(G.olam[j]);
+        du = el::pair_diff<true>(G.nh[lane], G.nl[lane], uh, ul);
+        const float3 lj = f3(G.nlam[lane]);
+        dl = make_float3(lj.x - li.x, lj.y - li.y, lj.z - li.z);
+    }
+    const float4 ra = R.ra[lane], rb = R.rb[lane], rc = R.rc[lane];
+    const int loc = __float_as_int(rc.w);
+    const int base = lane & ~(W - 1);
+    const int sl[3] = {base + (loc & 255), base + ((loc >> 8) & 255), base + ((loc >> 16) & 255)};
+    float3 d[3], e[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        d[k] = make_float3(__shfl_sync(kFull, du.x, sl[k]), __shfl_sync(kFull, du.y, sl[k]),
+                           __shfl_sync(kFull, du.z, sl[k]));
+        e[k] = make_float3(__shfl_sync(kFull, dl.x, sl[k]), __shfl_sync(kFull, dl.y, sl[k]),
+                           __shfl_sync(kFull, dl.z, sl[k]));
+    }
+    const float3 g1 = f3(ra), g2 = f3(rb), g3 = f3(rc);
+    const float3 gi = make_float3(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+    ElemState E;
+    elem_state<MODEL>(d[0], d[1], d[2], g1, g2, g3, E);
+    const float dF[9] = {e[0].x * g1.x + e[1].x * g2.x + e[2].x * g3.x, e[0].x * g1.y + e[1].x * g2.y + e[2].x * g3.y,
+                         e[0].x * g1.z + e[1].x * g2.z + e[2].x * g3.z, e[0].y * g1.x + e[1].y * g2.x + e[2].y * g3.x,
+                         e[0].y * g1.y + e[1].y * g2.y + e[2].y * g3.y, e[0].y * g1.z + e[1].y * g2.z + e[2].y * g3.z,
+                         e[0].z * g1.x + e[1].z * g2.x + e[2].z * g3.x, e[0].z * g1.y + e[1].z * g2.y + e[2].z * g3.y,
+                         e[0].z * g1.z + e[1].z * g2.z + e[2].z * g3.z};
+    float out[9];
+    hess_action<MODEL>(E, ra.w, rb.w, dF, out);
+    const float3 h = mat_g(out, gi);
+    float acc[3] = {h.x, h.y, h.z};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] = el::group_sum<W>(acc[k]);
+    if (!active || (lane & (W - 1)) != 0) return;
+    // weak terms: springs K I, active plane contact k n n^T
+    const float4 x0 = G.oa0[j], x1 = G.oa1[j];
+    const float K = x0.w;
+    bool contact = false;
+    if (m.k_contact > 0.0f) {
+        const float sd = x1.w + (m.pn_x * (uh.x + ul.x) + m.pn_y * (uh.y + ul.y) + m.pn_z * (uh.z + ul.z));
+        contact = sd < 0.0f;
+    }
+    const float kc = contact ? m.k_contact : 0.0f;
+    const float n[3] = {m.pn_x, m.pn_y, m.pn_z};
+    const float nl = kc * (n[0] * li.x + n[1] * li.y + n[2] * li.z);
+    const float4 gvv = G.ogv[j];
+    const float r0 = gvv.x - (acc[0] + K * li.x + nl * n[0]);
+    const float r1 = gvv.y - (acc[1] + K * li.y + nl * n[1]);
+    const float r2 = gvv.z - (acc[2] + K * li.z + nl * n[2]);
+    const float4 D0 = G.od0[j], D1 = G.od1[j];
+    const float A[6] = {D0.x, D0.y, D0.z, D0.w, D1.x, D1.y};
+    const float c00 = A[3] * A[5] - A[4] * A[4], c01 = A[2] * A[4] - A[1] * A[5], c02 = A[1] * A[4] - A[2] * A[3];
+    const float c11 = A[0] * A[5] - A[2] * A[2], c12 = A[1] * A[2] - A[0] * A[4], c22 = A[0] * A[3] - A[1] * A[1];
+    const float det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    if (!(det > 0.0f) || !(det < 3.0e38f)) {
+        atomicOr(err, kErrNonSPD);
+        return;
+    }
+    const float inv = 1.0f / det;
+    lam[v] = make_float4(li.x + inv * (c00 * r0 + c01 * r1 + c02 * r2), li.y + inv * (c01 * r0 + c11 * r1 + c12 * r2),
+                         li.z + inv * (c02 * r0 + c12 * r1 + c22 * r2), 0.f);
+}
+
+// Warp gw takes items gw, gw + nw, ... of one colour.  Every wait is bounded:
+// on a timeout the warp records it, lets its copies land (bounded) and
+// returns.
+template <int MODEL>
+__global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
+    adjoint_ring_sweep_kernel(const DeviceMesh m, State u, float4* lam, const float4* __restrict__ gv,
+                              const float4* __restrict__ diag, const Item* __restrict__ items, int nitems,
+                              int32_t* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    AdjWarpSmem& S = reinterpret_cast<AdjWarpSmem*>(smem)[warp];
+    const int gw = (int)blockIdx.x * kAdjWarps + warp, nw = (int)gridDim.x * kAdjWarps;
+    const int n = gw < nitems ? (nitems - gw + nw - 1) / nw : 0;
+    const int first = gw, stride = nw;
+    int issued = 0, waited = 0;  // items whose records were requested / awaited
+    bool ok = true;
+    Item next{};                 // lane 0: next item to request, loaded one item early
+    if (n > 0) {
+        if (lane == 0) {
+            for (int i = 0; i < kAdjRecStages; ++i) mbar_init(S.bar + i, 1);
+            fence_mbar_init();
+            for (int i = 0; i < kAdjRecStages - 1 && i < n; ++i) adj_issue_records(m, items[first + i * stride], S, i);
+            if (n > kAdjRecStages - 1) next = items[first + (kAdjRecStages - 1) * stride];
+        }
+        issued = n < kAdjRecStages - 1 ? n : kAdjRecStages - 1;
+        __syncwarp();
+        ok = mbar_wait(S.bar + 0, 0);
+        waited = 1;
+        if (__any_sync(kFull, !ok)) goto abort;
+        adj_issue_gathers(m, u, lam, gv, diag, S, 0, 0, lane);
+        cp_async_commit();
+        for (int k = 0; k < n; ++k) {
+            // Record stage (k + 2) % 3 and gather stage (k + 1) % 2 were last
+            // read by item k - 1, finished before the previous __syncwarp.
+            if (k + kAdjRecStages - 1 < n) {
+                if (lane == 0) {
+                    fence_proxy_async();
+                    adj_issue_records(m, next, S, (k + kAdjRecStages - 1) % kAdjRecStages);
+                    if (k + kAdjRecStages < n) next = items[first + (k + kAdjRecStages) * stride];
+                }
+                issued = k + kAdjRecStages;
+            }
+            ok = true;
+            if (k + 1 < n) {
+                ok = mbar_wait(S.bar + (k + 1) % kAdjRecStages, ((k + 1) / kAdjRecStages) & 1);
+                waited = k + 2;
+                if (ok) adj_issue_gathers(m, u, lam, gv, diag, S, (k + 1) % kAdjRecStages, (k + 1) % kAdjGatStages, lane);
+            }
+            cp_async_commit();
+            cp_async_wait<1>();  // this lane's gathers of item k have landed
+            if (__any_sync(kFull, !ok)) goto abort;
+            __syncwarp();        // ... and the other lanes'
+            const int r = k % kAdjRecStages, g = k % kAdjGatStages;
+            switch (S.desc[r].w) {
+                case 4: adj_ring_item<4, MODEL>(m, lam, S, r, g, lane, err); break;
+                case 8: adj_ring_item<8, MODEL>(m, lam, S, r, g, lane, err); break;
+                case 16: adj_ring_item<16, MODEL>(m, lam, S, r, g, lane, err); break;
+                default: adj_ring_item<32, MODEL>(m, lam, S, r, g, lane, err); break;
+            }
+            __syncwarp();
+        }
+    }
+    return;
+
+abort:
+    if (lane == 0) {
+        atomicOr(err, kErrTimeout);
+        for (int k = waited; k < issued; ++k) (void)mbar_wait(S.bar + k % kAdjRecStages, (k / kAdjRecStages) & 1);
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+int adj_sm_count() {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return 148;
+    return nsm;
+}
+
+
 // ---- preconditioned conjugate gradients on H x = r (free vertices) --------
 // Scalars live on the device: sc[0] = r.z, sc[1] = p.Hp, sc[2] = new r.z,
 // sc[3] = |r|^2.  A direction with p.Hp <= 0 (H not positive definite along
@@ -606,6 +836,38 @@ cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4
         return vertex_launch_model<el::kStableNeoHookean>(mode, grid, m, u, lam, gv, diag, out, items, nitems, err,
                                                           partial, st);
     return vertex_launch_model<el::kCorotated>(mode, grid, m, u, lam, gv, diag, out, items, nitems, err, partial, st);
+}
+
+cudaError_t adjoint_prepare() {
+    const int bytes = kAdjWarps * (int)sizeof(AdjWarpSmem);
+    const void* fns[3] = {(const void*)adjoint_ring_sweep_kernel<el::kCorotated>,
+                          (const void*)adjoint_ring_sweep_kernel<el::kNeoHookean>,
+                          (const void*)adjoint_ring_sweep_kernel<el::kStableNeoHookean>};
+    for (const void* f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_adjoint_ring_sweep(const DeviceMesh& m, State u, float4* lam, const float4* gv, const float4* diag,
+                                      const Item* items, int nitems, int32_t* err, int model, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const int bytes = kAdjWarps * (int)sizeof(AdjWarpSmem);  // attribute set by adjoint_prepare()
+    const int want = nblocks(nitems, kAdjWarps), cap = kAdjCtasPerSm * adj_sm_count();
+    const int grid = want < cap ? want : cap;
+    if (model == el::kNeoHookean)
+        adjoint_ring_sweep_kernel<el::kNeoHookean><<<grid, kAdjWarps * 32, bytes, st>>>(m, u, lam, gv, diag, items,
+                                                                                        nitems, err);
+    else if (model == el::kStableNeoHookean)
+        adjoint_ring_sweep_kernel<el::kStableNeoHookean><<<grid, kAdjWarps * 32, bytes, st>>>(m, u, lam, gv, diag,
+                                                                                              items, nitems, err);
+    else
+        adjoint_ring_sweep_kernel<el::kCorotated><<<grid, kAdjWarps * 32, bytes, st>>>(m, u, lam, gv, diag, items,
+                                                                                      nitems, err);
+    return cudaGetLastError();
 }
 
 int vec_blocks(int n) { return nblocks(n, kBlock); }

@@ -694,6 +694,7 @@ pbng_status build_layout(pbng_mesh* m) {
         for (auto& b : sb) PBNG_CUDA(m, ensure_buf(b, sizeof(float4) * (size_t)nv));
     destroy_graphs(m);
     PBNG_CUDA(m, ring_prepare());
+    PBNG_CUDA(m, adjoint_prepare());
     PBNG_CUDA(m, ensure_buf(m->d_wg, sizeof(float2) * kMaxChunk));
     m->ring_partials = ring_warps(m->nitems_ring);
     PBNG_CUDA(m, ensure_buf(m->d_partial, sizeof(double) * (size_t)std::max(1, m->ring_partials + m->total_partials)));
@@ -1695,10 +1696,11 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
         PBNG_CUDA(m, cudaMemcpyAsync(m->d_wg.p, m->h_wg, sizeof(float2) * chunk, cudaMemcpyHostToDevice, st));
         for (int32_t k = 0; k < chunk; ++k) {
             for (int c = 0; c < m->ncol; ++c)
-                PBNG_CUDA(m, launch_adjoint_vertex(kAdjSweep, m->dm, u, lam, (const float4*)m->d_gv.p,
-                                                   (float4*)m->d_diag.p, (const Item*)m->d_items.p + m->item_off[c],
-                                                   m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
-                                                   nullptr, st, nullptr, m->model));
+                PBNG_CUDA(m, launch_adjoint_ring_sweep(m->dm, u, lam, (const float4*)m->d_gv.p,
+                                                       (const float4*)m->d_diag.p,
+                                                       (const Item*)m->d_items.p + m->item_off[c],
+                                                       m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
+                                                       m->model, st));
             m->kernel_launches += m->ncol;
             if (p->accel != PBNG_ACCEL_NONE && m->nfree > 0) {
                 const State lc{lam, lam}, l1{(float4*)m->d_lam[p1].p, (float4*)m->d_lam[p1].p},

@@ -177,6 +177,12 @@ int adjoint_warps(int nitems);
 cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4* lam, const float4* gv,
                                   float4* diag, const Item* items, int nitems, int32_t* err, double* partial,
                                   cudaStream_t st, float4* out = nullptr, int model = 0);
+// The block Gauss-Seidel pass (mode 1) of one ring colour, pipelined like the
+// colour pass; adjoint_prepare sets its kernel attributes (call outside
+// stream capture).
+cudaError_t launch_adjoint_ring_sweep(const DeviceMesh& m, State u, float4* lam, const float4* gv, const float4* diag,
+                                      const Item* items, int nitems, int32_t* err, int model, cudaStream_t st);
+cudaError_t adjoint_prepare();
 // Preconditioned conjugate gradients on the free rows (pbng_adjoint.cu): the
 // scalars stay on the device in sc[0..3] = (r.z, p.Hp, new r.z, |r|^2); one
 // FP64 partial per kBlock threads (vec_blocks(n) of them).
