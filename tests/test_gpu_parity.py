@@ -476,3 +476,23 @@ def test_full_size_workloads_sampled(oracle_mod, name):
             # u on top of the relative tolerance
             ulps = 4.0 * 2.0 ** -23 * np.abs(s0[i] - p.X[i]).max()
             assert np.abs(d_gpu - d_ora).max() <= 2e-4 * np.abs(d_ora).max() + ulps + 1e-12, (name, c, i)
+
+
+def test_host_buffer_sweep_on_a_batch_reports_every_component():
+    """Three meshes in one handle: pbng_sweep_host gives the device sweep's
+    iterate and, per component, its residual (relative residual times the
+    starting residual)."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    probs = W.batched_blocks(count=3, side_lo=3, side_hi=6, seed=9)
+    p, mid, _ = W.concat_problems(probs)
+    params = default_params(accel="chebyshev")
+    m = Mesh.from_problem(p, mesh_id=mid)
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    r_start = m.residual(u)
+    rel = m.sweep(u, 17, params, want_residual=True)
+    h = torch.tensor(p.x0 - p.X, dtype=torch.float32).pin_memory()
+    r_host = m.sweep_host(h, 17, params, want_residual=True)
+    torch.cuda.synchronize()
+    assert len(r_host) == 3
+    assert torch.equal(h, u.cpu())
+    assert np.allclose(r_host, rel * r_start, rtol=1e-12, atol=0.0)
