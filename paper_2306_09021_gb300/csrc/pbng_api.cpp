@@ -1759,8 +1759,7 @@ pbng_status pbng_force(pbng_mesh* m, const float* u_dev, const pbng_params* p, f
     PBNG_CUDA(m, launch_scatter_vec(m->nv, m->nfree, (const int32_t*)m->d_perm.p, (const float4*)m->d_nw[0].p,
                                     f_out_dev, st));
     m->kernel_launches += 2;
-    PBNG_CUDA(m, cudaStreamSynchronize(st));
-    return PBNG_OK;
+    return check_err(m);  // synchronises
 }
 
 pbng_status pbng_hessian_apply(pbng_mesh* m, const float* u_dev, const float* p_dev, const pbng_params* p,
