@@ -238,7 +238,7 @@ def cpu_baseline(p, acc, model="corotated", sweeps_budget_s=12.0, max_sweeps=400
     threads = oracle.threads_available(ncpu)
     om = oracle.OracleMesh.from_problem(p, model=model)
     if "weak" in p.meta:
-        om.set_weak_constraints(*p.meta["weak"])
+        om.set_weak_constraints(*p.meta["weak"], recolour=True)
 
     def run(nthreads, budget, cap):
         x = p.x0.copy()
@@ -270,7 +270,7 @@ def run_reference(args):
     threads = oracle.threads_available(os.cpu_count() or 1)
     om = oracle.OracleMesh.from_problem(p, model=args.model)
     if "weak" in p.meta:
-        om.set_weak_constraints(*p.meta["weak"])
+        om.set_weak_constraints(*p.meta["weak"], recolour=True)
     x = p.x0.copy()
     for _ in range(args.warmup):
         x, _ = om.sweeps(x, 1, threads=threads, **acc)
@@ -319,7 +319,10 @@ def main():
     if "case_accel" in p.meta:
         m.set_body_accel(p.meta["case_accel"], p.density)
     if "weak" in p.meta:
-        m.set_weak_constraints(*p.meta["weak"])
+        # the constraints join a coloured mesh by incremental recolouring
+        # (Section "Collision Coloring")
+        m.colouring()
+        m.set_weak_constraints(*p.meta["weak"], recolour=True)
     u0 = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
     u = u0.clone()
     S = args.sweeps_per_step
