@@ -20,6 +20,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                                                the linearised sweep: the scaled
                                                Chebyshev polynomial, the closed
                                                form of the two-step recurrence)
+  sweeps (symmetric colour order)              pinned (the linearised sweep is
+                                               self-adjoint in the Hessian's inner
+                                               product with spectrum in [0, 1);
+                                               Chebyshev polynomial error)
   newton, hessian_dense                        pinned (FD of the residual)
   adjoint_dense                                pinned (FD of the loss)
 """
@@ -51,6 +55,7 @@ def lib():
             "ora_pk1": (None, [_D, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]),
             "ora_dpk1": (None, [_D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]),
             "ora_set_model": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+            "ora_set_colour_order": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
             "ora_set_inertia": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, _D, _D]),
             "ora_lumped_mass": (None, [ctypes.c_void_p, _D]),
             "ora_set_weak_constraints": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _I, _D, _D, _D, _D,
@@ -117,6 +122,7 @@ def polar(F):
 
 
 MODELS = {"corotated": 0, "neohookean": 1, "stable_neohookean": 2}
+COLOUR_ORDERS = {"forward": 0, "symmetric": 1}
 
 
 def _model(model):
@@ -271,8 +277,11 @@ class OracleMesh:
         return lib().ora_energy(self.h, _d(x))
 
     def sweeps(self, x, n, accel="none", omega=1.7, rho=0.95, gamma=1.7, skip_tol=0.0,
-               threads=1, history=False):
-        """Returns (x_new, status[, residual history])."""
+               threads=1, history=False, order="forward"):
+        """Returns (x_new, status[, residual history]).  order: "forward"
+        (colours 0..C-1 per sweep) or "symmetric" (0..C-1, then C-2..0)."""
+        if lib().ora_set_colour_order(self.h, COLOUR_ORDERS[order]) != 0:
+            raise ValueError(f"unknown colour order {order!r}")
         xx = _f64(x, (-1, 3)).copy()
         code = {"none": 0, "chebyshev": 1, "sor": 2}[accel]
         hist = np.zeros(n + 1) if history else None

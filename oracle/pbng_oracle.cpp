@@ -378,6 +378,9 @@ struct Mesh {
     std::vector<std::vector<int>> vert_wc;
     std::vector<int> colour;               // nv, -1 clamped
     std::vector<std::vector<int>> by_colour;
+    // Order of the colour passes in one sweep: 0 = ascending (one
+    // Gauss-Seidel pass, 0..C-1); 1 = symmetric (0..C-1, then C-2..0).
+    int colour_order = 0;
 };
 
 // g_j = dN_j/dX in tet e: rows of B for j = 1..3, g_0 = -(g_1 + g_2 + g_3).
@@ -855,6 +858,12 @@ int ora_set_model(void* h, int model) {
     return 0;
 }
 
+int ora_set_colour_order(void* h, int order) {
+    if (order != 0 && order != 1) return 1;
+    static_cast<Mesh*>(h)->colour_order = order;
+    return 0;
+}
+
 int ora_num_colours(const void* h) { return (int)static_cast<const Mesh*>(h)->by_colour.size(); }
 
 void ora_get_colours(const void* h, int* colour) {
@@ -897,7 +906,13 @@ int ora_sweeps(const void* h, double* x, int nsweeps, int accel, double omega, d
         // One PBNG iteration: colours in ascending order (Section "Coloring
         // and Parallelism"); nodes of one colour share no element, so their
         // order inside the colour does not change the result.
-        for (const auto& list : m.by_colour) {
+        // With the symmetric order the sweep goes back down after the last
+        // colour (0..C-1, C-2..0), the palindromic colour sequence of a
+        // symmetric Gauss-Seidel iteration.
+        const int C = (int)m.by_colour.size();
+        const int npass = (m.colour_order == 1 && C > 0) ? 2 * C - 1 : C;
+        for (int t = 0; t < npass; ++t) {
+            const auto& list = m.by_colour[t < C ? t : 2 * C - 2 - t];
             const int cnt = (int)list.size();
 #pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : bad)
             for (int q = 0; q < cnt; ++q)

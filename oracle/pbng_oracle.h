@@ -63,6 +63,12 @@ void ora_destroy(void* h);
  * modified Hessian of Eq. mod_hess_dens is the same for every model.
  * Returns nonzero for an unknown model. */
 int ora_set_model(void* h, int model);
+/* Order of the colour passes inside one sweep (ora_sweeps).  0: ascending,
+ * colours 0..C-1 (Section "Coloring and Parallelism"; the default).
+ * 1: symmetric, colours 0..C-1 and then C-2..0 (2C - 1 passes), the
+ * palindromic order of symmetric Gauss-Seidel; the paper does not fix the
+ * order of the colour loop.  Returns nonzero for another value. */
+int ora_set_colour_order(void* h, int order);
 /* Backward Euler (Eq. fem_be): with dt > 0 every free vertex gets the
  * inertial term -m_ii (x_i - xhat_i) / dt^2 in its force, m_ii / dt^2 on the
  * diagonal of its Hessian and (m_ii / 2 dt^2)|x_i - xhat_i|^2 in the energy,
@@ -99,7 +105,8 @@ double ora_residual(const void* h, const double* x, double* r_out);
 /* Total potential sum V Psi + weak/contact energy - sum f^ext . x. */
 double ora_energy(const void* h, const double* x);
 
-/* nsweeps PBNG sweeps in place on x.  accel: 0 plain, 1 Chebyshev (rho,
+/* nsweeps PBNG sweeps in place on x, colours in the order of
+ * ora_set_colour_order.  accel: 0 plain, 1 Chebyshev (rho,
  * gamma), 2 SOR (omega), both applied after each whole sweep with
  * x^{-1} = x^0.  skip_tol > 0 skips vertices with |r| <= skip_tol.
  * res_hist (NULL or nsweeps+1 doubles) receives |r| before and after every

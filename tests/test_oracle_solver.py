@@ -121,15 +121,16 @@ def test_single_free_vertex_is_modified_newton(oracle_mod):
 @pytest.mark.parametrize("maker", [lambda: W.twist_block(2, 45.0, 0.2),
                                    lambda: W.twist_block(3, 90.0, 0.3),
                                    lambda: W.gravity_sag(3)])
-@pytest.mark.parametrize("accel", ["none", "chebyshev", "sor"])
-def test_pbng_reaches_newton_equilibrium(oracle_mod, maker, accel):
+@pytest.mark.parametrize("accel,order", [("none", "forward"), ("chebyshev", "forward"), ("sor", "forward"),
+                                         ("none", "symmetric"), ("chebyshev", "symmetric")])
+def test_pbng_reaches_newton_equilibrium(oracle_mod, maker, accel, order):
     p = maker()
     m = oracle_mod.OracleMesh.from_problem(p)
     xn, it, res = m.newton(p.x0, 1e-13, 60)
     assert it >= 0
     omega = 1.5 if accel == "sor" else 1.7
     gamma = 1.0 if (accel == "chebyshev" and p.body_accel is None and p.nv > 30) else 1.7
-    xs, st, hist = m.sweeps(p.x0, 3000, accel=accel, omega=omega, gamma=gamma, history=True)
+    xs, st, hist = m.sweeps(p.x0, 3000, accel=accel, omega=omega, gamma=gamma, history=True, order=order)
     assert st == 0
     assert hist[-1] <= 1e-9 * hist[0]
     assert np.abs(xs - xn).max() <= 1e-9 * max(1.0, np.abs(xn - p.X).max())
@@ -142,6 +143,22 @@ def test_acceleration_reduces_to_plain(oracle_mod):
     xc, _ = m.sweeps(p.x0, 20, accel="chebyshev", rho=0.0, gamma=1.0)
     xs, _ = m.sweeps(p.x0, 20, accel="sor", omega=1.0)
     assert np.abs(xc - xp).max() <= 1e-12 and np.abs(xs - xp).max() <= 1e-12
+
+
+def test_symmetric_order_chebyshev_beats_forward_on_a_sag_cube(oracle_mod):
+    # The symmetric colour order's real spectrum is what the Chebyshev weights
+    # assume: on a bending-dominated, nearly incompressible cube it reaches a
+    # residual that the ascending order does not, for the same number of
+    # colour passes, with rho near the measured plain rate.
+    p = W.gravity_sag(6)
+    m = oracle_mod.OracleMesh.from_problem(p)
+    C = m.ncolours
+    nf = 300
+    ns = nf * C // (2 * C - 1)
+    _, _, hf = m.sweeps(p.x0, nf, accel="chebyshev", rho=0.98, history=True, threads=4)
+    _, _, hs = m.sweeps(p.x0, ns, accel="chebyshev", rho=0.995, history=True, threads=4, order="symmetric")
+    assert hs[-1] < 1e-6 * hs[0]
+    assert hs[-1] < 1e-2 * hf[-1]
 
 
 def test_chebyshev_beats_plain_at_equal_sweeps(oracle_mod):
