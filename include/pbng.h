@@ -45,7 +45,8 @@ typedef enum {
     PBNG_ECUDA = 3,           /* a CUDA runtime call failed                   */
     PBNG_EDEGENERATE = 4,     /* rest tet of (near) zero volume, or a nodal
                                  Hessian that is not positive definite         */
-    PBNG_EDIVERGED = 5,       /* non-finite value or residual > 1e3 r_0        */
+    PBNG_EDIVERGED = 5,       /* non-finite value, residual > 1e3 r_0, or
+                                 sustained growth (pbng_solve)                 */
     PBNG_ETIMEOUT = 6,        /* a bounded device wait gave up                 */
     PBNG_ENOTCONVERGED = 7    /* max_sweeps reached before rel_tol             */
 } pbng_status;
@@ -99,12 +100,27 @@ typedef struct {
                                1-ring vertices, CSR direct loads for the others;
                                1: CSR direct-load kernels everywhere.  Changing it
                                rebuilds the layout.                               */
-    int32_t reserved[3];
+    int32_t colour_order;   /* PBNG_ORDER_FORWARD: one sweep runs the colour
+                               passes 0..C-1 (Section "Coloring and
+                               Parallelism").  PBNG_ORDER_SYMMETRIC: 0..C-1 and
+                               then C-2..0 (2C - 1 passes), the palindromic
+                               order of symmetric Gauss-Seidel.  The paper does
+                               not fix the order of the colour loop.  Linearised
+                               at an equilibrium, the symmetric sweep is
+                               self-adjoint in the Hessian's inner product, with
+                               real eigenvalues in [0, 1) where the modified
+                               nodal Hessian dominates the true diagonal block:
+                               the spectrum the Chebyshev weights assume.  The
+                               ascending order's eigenvalues are complex.  Also
+                               the order of the adjoint's block Gauss-Seidel.   */
+    int32_t reserved[2];
 } pbng_params;
+
+enum { PBNG_ORDER_FORWARD = 0, PBNG_ORDER_SYMMETRIC = 1 };
 
 /* Fills p with the paper's defaults: corotated, no acceleration, omega 1.7,
  * rho 0.95, gamma 1.7, step 1, skip_tol 0, residual_every 10, resume 0,
- * compensated precision, kernel_path 0. */
+ * compensated precision, kernel_path 0, forward colour order. */
 void pbng_default_params(pbng_params* p);
 
 /* Creates a mesh handle (Section "Discretization": P1 tetrahedra, per-tet
@@ -181,8 +197,11 @@ pbng_status pbng_sweep_host(pbng_mesh* m, float* u_host, int32_t nsweeps, const 
  * every p->residual_every sweeps) or max_sweeps is reached.  sweeps_out (host,
  * may be NULL) receives the sweeps done; rel_residual_out (host double
  * [ncomp], may be NULL) the final relative residuals.  Returns
- * PBNG_ENOTCONVERGED when max_sweeps ran out, PBNG_EDIVERGED on a non-finite
- * or growing (> 1e3 r_0) residual. */
+ * PBNG_ENOTCONVERGED when max_sweeps ran out, PBNG_EDIVERGED when a check
+ * finds a component's residual non-finite, above 1e3 r_0, or above r_0 and
+ * 100 times the smallest residual of that component in this solve (sustained
+ * growth).  On every exit, errors included, each component of a batch is
+ * left active for later calls. */
 pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps,
                        const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out);
 
@@ -324,7 +343,10 @@ pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out
  * cudaMalloc or cudaFree (either can synchronise the whole device) is not
  * allowed.  It computes the same per-component FP64 residual norms as
  * pbng_residual with the same kernels, but calls no cudaMalloc, cudaFree or
- * other allocating routine, on the device or the host.
+ * other allocating routine, on the device or the host (its error texts go
+ * into a buffer the handle reserves when it is created; only the text of a
+ * PBNG_ECUDA failure, after which the handle is unusable, may take host
+ * memory).
  *   - Its FP64 partial sums live in one fixed array of 65,536 doubles
  *     (512 KiB) that the library reserves on every GPU that loads it, until
  *     the process exits.  A mesh whose residual launch needs more partial

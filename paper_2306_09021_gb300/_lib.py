@@ -20,6 +20,7 @@ STATUS_NAMES = {
 ACCEL = {"none": 0, "chebyshev": 1, "sor": 2}
 PRECISION = {"fp32": 0, "compensated": 1}
 MODEL = {"corotated": 0, "neohookean": 1, "stable_neohookean": 2}
+ORDER = {"forward": 0, "symmetric": 1}
 
 
 class PbngParams(ctypes.Structure):
@@ -35,7 +36,8 @@ class PbngParams(ctypes.Structure):
         ("resume", ctypes.c_int32),
         ("precision", ctypes.c_int32),
         ("kernel_path", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("colour_order", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

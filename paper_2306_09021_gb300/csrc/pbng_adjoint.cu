@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
         issued = n < kAdjRecStages - 1 ? n : kAdjRecStages - 1;
         __syncwarp();
         ok = mbar_wait(S.bar + 0, 0);
-        waited = 1;
+        waited = ok ? 1 : 0;  // a stage whose wait gave up is drained again on abort
         if (__any_sync(kFull, !ok)) goto abort;
         adj_issue_gathers(m, u, lam, gv, diag, S, 0, 0, lane);
         cp_async_commit();
@@ -645,7 +645,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
             ok = true;
             if (k + 1 < n) {
                 ok = mbar_wait(S.bar + (k + 1) % kAdjRecStages, ((k + 1) / kAdjRecStages) & 1);
-                waited = k + 2;
+                waited = ok ? k + 2 : k + 1;
                 if (ok) adj_issue_gathers(m, u, lam, gv, diag, S, (k + 1) % kAdjRecStages, (k + 1) % kAdjGatStages, lane);
             }
             cp_async_commit();

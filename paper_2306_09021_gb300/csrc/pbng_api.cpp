@@ -109,7 +109,7 @@ struct pbng_mesh {
 
     // captured chunks of sweeps (CUDA graphs), keyed by their configuration
     struct GraphEntry {
-        int32_t K, accel, prec, with_res, p1, prof, model;
+        int32_t K, accel, prec, with_res, p1, prof, model, order;
         float step, skip;
         cudaGraphExec_t exec = nullptr;
         int64_t nkernels = 0;
@@ -186,6 +186,15 @@ void prof_end(pbng_mesh* m, int slot) {
 
 pbng_status fail(pbng_mesh* m, pbng_status s, const std::string& msg) {
     if (m) m->err = msg;
+    return s;
+}
+
+constexpr size_t kErrTextReserve = 512;
+
+// For literal messages: assigning into the handle's reserved text buffer
+// takes no host allocation (pbng_residual_noalloc relies on it).
+pbng_status fail(pbng_mesh* m, pbng_status s, const char* msg) {
+    if (m) m->err.assign(msg);
     return s;
 }
 
@@ -835,7 +844,18 @@ bool valid_params(const pbng_params* p) {
     return p && p->model >= 0 && p->model <= 2 && p->accel >= 0 && p->accel <= 2 && p->residual_every >= 1 &&
            (p->precision == PBNG_PREC_FP32 || p->precision == PBNG_PREC_COMPENSATED) &&
            std::isfinite(p->omega) && std::isfinite(p->rho) && std::isfinite(p->gamma) &&
-           std::isfinite(p->step) && p->skip_tol >= 0.0 && (p->kernel_path == 0 || p->kernel_path == 1);
+           std::isfinite(p->step) && p->skip_tol >= 0.0 && (p->kernel_path == 0 || p->kernel_path == 1) &&
+           (p->colour_order == PBNG_ORDER_FORWARD || p->colour_order == PBNG_ORDER_SYMMETRIC);
+}
+
+// Colour passes of one sweep: 0..C-1, and for the symmetric order back down
+// C-2..0 (the palindrome of symmetric Gauss-Seidel).
+std::vector<int> colour_sequence(int ncol, int order) {
+    std::vector<int> seq;
+    for (int c = 0; c < ncol; ++c) seq.push_back(c);
+    if (order == PBNG_ORDER_SYMMETRIC)
+        for (int c = ncol - 2; c >= 0; --c) seq.push_back(c);
+    return seq;
 }
 
 // Loads u_dev (or keeps the stored iterate) and resets the history.
@@ -907,8 +927,9 @@ pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool wi
         return PBNG_OK;
     };
     pbng_status r;
+    const std::vector<int> seq = colour_sequence(m->ncol, p->colour_order);
     for (int32_t k = 0; k < K; ++k) {
-        for (int c = 0; c < m->ncol; ++c) {
+        for (const int c : seq) {
             if (m->tables[c].total_blocks <= 0) continue;
             if ((r = mark(kProfColour))) return r;
             if (m->ring_colour[c])
@@ -966,7 +987,8 @@ pbng_status run_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_r
     pbng_mesh::GraphEntry* g = nullptr;
     for (auto& e : m->graphs)
         if (e.K == K && e.accel == accel && e.prec == p->precision && e.with_res == (int)with_res &&
-            e.p1 == m->p1_slot && e.step == (float)p->step && e.skip == (float)p->skip_tol && e.model == p->model)
+            e.p1 == m->p1_slot && e.step == (float)p->step && e.skip == (float)p->skip_tol && e.model == p->model &&
+            e.order == p->colour_order)
             g = &e;
     if (!g) {
         pbng_mesh::GraphEntry e;
@@ -979,6 +1001,7 @@ pbng_status run_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_r
         e.step = (float)p->step;
         e.skip = (float)p->skip_tol;
         e.model = p->model;
+        e.order = p->colour_order;
         if (!m->cap_stream) PBNG_CUDA(m, cudaStreamCreateWithFlags(&m->cap_stream, cudaStreamNonBlocking));
         cudaGraph_t graph = nullptr;
         PBNG_CUDA(m, cudaStreamBeginCapture(m->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1046,6 +1069,7 @@ pbng_status pbng_create_mesh(const double* rest_xyz, int32_t nv, const int32_t* 
     try {
         if (cudaGetDevice(&m->device) != cudaSuccess) { delete m; return PBNG_ECUDA; }
         m->stream = (cudaStream_t)stream;
+        m->err.reserve(kErrTextReserve);
         m->nv = nv;
         m->ne = ne;
         m->X.assign(rest_xyz, rest_xyz + 3 * (size_t)nv);
@@ -1395,9 +1419,10 @@ pbng_status pbng_sweep_host(pbng_mesh* m, float* u_host, int32_t nsweeps, const 
     return PBNG_OK;
 }
 
-pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps,
-                       const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out) {
-    if (!m) return PBNG_EINVAL;
+namespace {
+
+pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps, const pbng_params* p,
+                       int32_t* sweeps_out, double* rel_residual_out) {
     if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
     select_path(m, p);
     pbng_status s = ensure_ready(m);
@@ -1413,6 +1438,11 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     // rel_tol, exactly as if it were solved on its own.
     const bool freeze = m->ncomp > 1;
     std::vector<uint8_t> frozen(m->ncomp, 0);
+    // Divergence: a non-finite residual, one above kDivergedRel r_0, or one
+    // that stays above r_0 after growing kGrowth-fold from the smallest this
+    // solve has seen for that component (sustained growth).
+    constexpr double kDivergedRel = 1e3, kGrowth = 100.0;
+    std::vector<double> least(m->ncomp, 1.0);
     bool changed = false;
     auto converged = [&]() {
         bool all = true;
@@ -1420,7 +1450,9 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
         for (int k = 0; k < m->ncomp; ++k) {
             if (frozen[k]) continue;
             rel[k] = std::sqrt(sq[k]) / (m->r0[k] > 0 ? m->r0[k] : 1.0);
-            if (!std::isfinite(rel[k]) || rel[k] > 1e3) return -1;
+            if (!std::isfinite(rel[k]) || rel[k] > kDivergedRel) return -1;
+            least[k] = std::min(least[k], rel[k]);
+            if (rel[k] > 1.0 && rel[k] > kGrowth * least[k]) return -1;
             if (rel[k] > rel_tol) all = false;
             else if (freeze) {
                 frozen[k] = 1;
@@ -1433,6 +1465,9 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     for (int k = 0; k < m->ncomp; ++k) sq[k] = m->r0[k] * m->r0[k];
     int cv = converged();
     if (cv == 1) result = PBNG_OK;
+    if (changed && cv == 0)  // components already at rel_tol take no part from the first sweep on
+        PBNG_CUDA(m, cudaMemcpyAsync(m->d_active.p, m->h_active, sizeof(int32_t) * m->ncomp,
+                                     cudaMemcpyHostToDevice, m->stream));
     const int32_t K = std::min<int32_t>(p->residual_every, kMaxChunk);
     if ((s = ensure_wg(m, (size_t)K))) return s;
     // Chebyshev with rho <= 0: rho from the FP64 residuals.  Plain sweeps
@@ -1515,12 +1550,6 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     }
     PBNG_CUDA(m, launch_store(m->nv, (const int32_t*)m->d_perm.p, state_of(m, 0), u_dev, m->stream));
     m->kernel_launches++;
-    if (freeze) {  // leave every component active for later calls
-        PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
-        for (int32_t k = 0; k < m->ncomp; ++k) m->h_active[k] = 1;
-        PBNG_CUDA(m, cudaMemcpyAsync(m->d_active.p, m->h_active, sizeof(int32_t) * m->ncomp,
-                                     cudaMemcpyHostToDevice, m->stream));
-    }
     PBNG_CUDA(m, cudaStreamSynchronize(m->stream));
     if (sweeps_out) *sweeps_out = done;
     if (rel_residual_out)
@@ -1528,6 +1557,32 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     if (result == PBNG_ENOTCONVERGED) m->err = "max_sweeps reached";
     if (result == PBNG_EDIVERGED) m->err = "residual diverged";
     return result;
+}
+
+}  // namespace
+
+pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps,
+                       const pbng_params* p, int32_t* sweeps_out, double* rel_residual_out) {
+    if (!m) return PBNG_EINVAL;
+    pbng_status r = solve_impl(m, u_dev, rel_tol, max_sweeps, p, sweeps_out, rel_residual_out);
+    // A batch's components are frozen one by one as they converge: leave
+    // every component active for later calls on every exit path, errors
+    // included (after PBNG_ECUDA this is best effort and reports nothing).
+    if (m->ncomp > 1 && m->h_active && m->d_active.p) {
+        const std::string err = m->err;
+        const cudaError_t e1 = cudaStreamSynchronize(m->stream);
+        for (int32_t k = 0; k < m->ncomp; ++k) m->h_active[k] = 1;
+        const cudaError_t e2 = cudaMemcpyAsync(m->d_active.p, m->h_active, sizeof(int32_t) * m->ncomp,
+                                               cudaMemcpyHostToDevice, m->stream);
+        const cudaError_t e3 = cudaStreamSynchronize(m->stream);
+        if (r == PBNG_OK || r == PBNG_ENOTCONVERGED || r == PBNG_EDIVERGED) {
+            if (e1 != cudaSuccess) return cuda_fail(m, e1, "cudaStreamSynchronize");
+            if (e2 != cudaSuccess) return cuda_fail(m, e2, "cudaMemcpyAsync");
+            if (e3 != cudaSuccess) return cuda_fail(m, e3, "cudaStreamSynchronize");
+        }
+        m->err = err;
+    }
+    return r;
 }
 
 pbng_status pbng_step(pbng_mesh* m, float* u_dev, float* u_prev_dev, int32_t nsweeps, double rel_tol,
@@ -1690,18 +1745,19 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     pbng_status result = PBNG_ENOTCONVERGED;
     const int32_t K = std::min<int32_t>(p->residual_every, kMaxChunk);
     if ((s = ensure_wg(m, (size_t)K))) return s;
+    const std::vector<int> seq = colour_sequence(m->ncol, p->colour_order);
     while (g2 > 0.0 && done < max_sweeps) {
         const int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
         chunk_weights(m, p, chunk, m->h_wg);
         PBNG_CUDA(m, cudaMemcpyAsync(m->d_wg.p, m->h_wg, sizeof(float2) * chunk, cudaMemcpyHostToDevice, st));
         for (int32_t k = 0; k < chunk; ++k) {
-            for (int c = 0; c < m->ncol; ++c)
+            for (const int c : seq)
                 PBNG_CUDA(m, launch_adjoint_ring_sweep(m->dm, u, lam, (const float4*)m->d_gv.p,
                                                        (const float4*)m->d_diag.p,
                                                        (const Item*)m->d_items.p + m->item_off[c],
                                                        m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
                                                        m->model, st));
-            m->kernel_launches += m->ncol;
+            m->kernel_launches += (int64_t)seq.size();
             if (p->accel != PBNG_ACCEL_NONE && m->nfree > 0) {
                 const State lc{lam, lam}, l1{(float4*)m->d_lam[p1].p, (float4*)m->d_lam[p1].p},
                     l2{(float4*)m->d_lam[p2].p, (float4*)m->d_lam[p2].p};

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         // iterate read from here on is written by the previous kernel.
         pdl_wait();
         ok = mbar_wait(S.bar + 0, 0);
-        waited = 1;
+        waited = ok ? 1 : 0;  // a stage whose wait gave up is drained again on abort
         if (__any_sync(kFull, !ok)) goto abort;
         issue_gathers<COMP, UPDATE>(m, s, S, 0, 0, lane);
         cp_async_commit();
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
             ok = true;
             if (k + 1 < n) {
                 ok = mbar_wait(S.bar + (k + 1) % kRecStages, ((k + 1) / kRecStages) & 1);
-                waited = k + 2;
+                waited = ok ? k + 2 : k + 1;
                 if (ok) issue_gathers<COMP, UPDATE>(m, s, S, (k + 1) % kRecStages, (k + 1) % kGatStages, lane);
             }
             cp_async_commit();

@@ -9,7 +9,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (ACCEL, MODEL, PRECISION, PbngNewtonInfo, PbngParams, PbngProfile, PbngSchedule, PbngSolveInfo,
+from ._lib import (ACCEL, MODEL, ORDER, PRECISION, PbngNewtonInfo, PbngParams, PbngProfile, PbngSchedule, PbngSolveInfo,
                    check, load)
 
 
@@ -25,7 +25,7 @@ def default_params(**kw):
     """pbng_default_params, then overrides: model ('corotated'|'neohookean'|
     'stable_neohookean'), accel ('none'|'chebyshev'|'sor'), precision
     ('fp32'|'compensated'), omega, rho, gamma, step, skip_tol, residual_every,
-    resume, kernel_path."""
+    resume, kernel_path, colour_order ('forward'|'symmetric')."""
     p = PbngParams()
     load().pbng_default_params(ctypes.byref(p))
     for k, v in kw.items():
@@ -35,6 +35,8 @@ def default_params(**kw):
             v = PRECISION[v] if isinstance(v, str) else int(v)
         elif k == "model":
             v = MODEL[v] if isinstance(v, str) else int(v)
+        elif k == "colour_order":
+            v = ORDER[v] if isinstance(v, str) else int(v)
         setattr(p, k, v)
     return p
 

@@ -88,3 +88,24 @@ def test_autograd_matches_finite_differences():
         fd = (vals[0] - vals[1]) / 2.0
         an = epsE * (gE @ dE) + epsD * np.sum(gD * dD)
         assert fd == pytest.approx(an, rel=2e-2, abs=1e-3 * abs(an) + 1e-12)
+
+
+def test_unconverged_solves_raise_unless_allowed():
+    """A forward or adjoint solve that stops at its sweep limit gives no
+    equilibrium gradient: the autograd function raises, or warns with the
+    residual reached when the model allows it."""
+    from paper_2306_09021_gb300 import EquilibriumModel
+    from paper_2306_09021_gb300.autograd import NotConvergedError
+    p, log_e, xd, top, target = _setup(n=4, seed=7)
+    model = EquilibriumModel(p, rel_tol=1e-9, max_sweeps=20)
+    with pytest.raises(NotConvergedError, match="relative residual"):
+        _loss(model, p, log_e, xd, top, target)
+    model = EquilibriumModel(p, rel_tol=1e-6, max_sweeps=30000, adjoint_tol=1e-9, adjoint_max_sweeps=5)
+    L, le, xdt = _loss(model, p, log_e, xd, top, target)
+    assert model.last_solve[0] == 0
+    with pytest.raises(NotConvergedError, match="adjoint"):
+        L.backward()
+    model = EquilibriumModel(p, rel_tol=1e-9, max_sweeps=20, allow_unconverged=True)
+    with pytest.warns(RuntimeWarning, match="relative residual"):
+        L, le, xdt = _loss(model, p, log_e, xd, top, target)
+    assert model.last_solve[0] == 7

@@ -84,3 +84,29 @@ def test_noalloc_residual_batch_of_two(lib):
     got2 = _noalloc(lib, m, u2)
     np.testing.assert_allclose(got1, ref1, rtol=RES_REL_TOL)
     np.testing.assert_allclose(got2, ref2, rtol=RES_REL_TOL)
+
+
+def test_noalloc_residual_rejects_an_unbuilt_layout_and_allocates_nothing(lib):
+    """Before the layout exists the call must fail with PBNG_EINVAL (building
+    the layout allocates); once it exists, repeated calls leave the device's
+    free memory and torch's allocator untouched."""
+    from paper_2306_09021_gb300 import Mesh
+    p = W.gravity_sag(6)
+    m = Mesh.from_problem(p)
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    out = np.zeros(1)
+    st = lib.pbng_residual_noalloc(m.h, ctypes.c_void_p(u.data_ptr()),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert st == 1  # PBNG_EINVAL
+    assert b"layout" in lib.pbng_last_error(m.h)
+    ref = m.residual(u)           # builds the layout
+    _noalloc(lib, m, u)           # first call: looks the scratch address up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    got = _noalloc(lib, m, u)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    np.testing.assert_allclose(got, ref, rtol=RES_REL_TOL)
