@@ -39,6 +39,11 @@ UNIT = "vertex-updates/s"
 # f_ext 12 B, CSR offset 4 B.
 BYTES_PER_INCIDENCE = 96
 BYTES_PER_VERTEX = 40
+# Compulsory bytes of a sweep (each datum once): per tet dN/dX 36 B, V 4 B,
+# (mu, lambda) 8 B, four ids 16 B; per free vertex u read + write 24 B, f_ext
+# 12 B, offset 4 B.
+COMPULSORY_BYTES_PER_TET = 64
+COMPULSORY_BYTES_PER_VERTEX = 40
 
 
 def parse():
@@ -53,7 +58,7 @@ def parse():
                          "adjoint: 32 load cases of a 48^3 cube, forward + adjoint")
     ap.add_argument("--cells", type=int, default=64, help="cube cells per side for sag64")
     ap.add_argument("--sweeps-per-step", type=int, default=10)
-    ap.add_argument("--precision", choices=["compensated", "fp32"], default="compensated")
+    ap.add_argument("--precision", choices=["compensated", "fp32", "extended", "auto"], default="compensated")
     ap.add_argument("--kernel-path", type=int, choices=[0, 1], default=0,
                     help="0: 1-ring layout kernels (TMA-staged), 1: CSR direct-load kernels")
     ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-1e-5 solves")
@@ -202,8 +207,8 @@ def kernel_sources_sha256():
     """Hash of the CUDA sources that define the sweep kernels."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_09021_gb300", "csrc")
-    for name in ("pbng_async.cuh", "pbng_element.cuh", "pbng_internal.h", "pbng_kernels.cu", "pbng_launch.cuh",
-                 "pbng_ring.cu"):
+    for name in ("pbng_async.cuh", "pbng_element.cuh", "pbng_ff.cuh", "pbng_internal.h", "pbng_kernels.cu",
+                 "pbng_launch.cuh", "pbng_ring.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -405,10 +410,25 @@ def main():
     alg_bytes_launch = alg_bytes_sweep / max(1, prof["ncolours"])
     achieved = alg_bytes_launch / (bb_per_launch_ms * 1e-3) / 1e9
     tr = kernel_traffic(args)
+    # ncu figures of the committed capture (only while the kernel sources
+    # still hash to it): DRAM bytes, FP32 flops and what limits the pass
+    dram_frac = None if tr is None else tr["dram_bytes_per_launch"] / (bb_per_launch_ms * 1e-3) / 1e9 / peak
+    from paper_2306_09021_gb300 import measure_fp32_peak
+    fp32_peak = measure_fp32_peak(stream)
+    fp32_flops = None if tr is None else tr.get("fp32_flops_per_launch")
     roofline = {"kernel": "ring_kernel<UPDATE=true> (colour pass)" if args.kernel_path == 0 else "colour_pass_kernel",
                 "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                "model": "per-pass gather bytes (96 B per incidence + 40 B per free vertex) per launch",
                 "traffic": None if tr is None else tr["dram_bytes_per_launch"],
+                "dram_achieved_gbs": None if tr is None else tr["dram_bytes_per_launch"] / (bb_per_launch_ms * 1e-3) / 1e9,
+                "dram_frac": dram_frac,
+                "frac_compulsory": (COMPULSORY_BYTES_PER_TET * p.ne + COMPULSORY_BYTES_PER_VERTEX * p.n_free)
+                / max(1, prof["ncolours"]) / (bb_per_launch_ms * 1e-3) / 1e9 / peak,
+                "limiter": None if tr is None else tr.get("limiter"),
+                "fp32": {"peak_tflops": fp32_peak, "peak_source": "measured (pbng_measure_fp32_peak, FMA chains)",
+                         "flops_per_launch": fp32_flops,
+                         "frac": None if not fp32_flops else fp32_flops / (bb_per_launch_ms * 1e-3) / 1e12 / fp32_peak},
                 "alg_bytes_per_launch": alg_bytes_launch, "avg_launch_us": bb_per_launch_ms * 1e3,
                 "launches_timed": int(bb_launches),
                 "timing": (f"CUDA events on the library stream around {bb_reps} x {bb_sweeps} sweeps of colour passes "
@@ -445,10 +465,16 @@ def main():
     ttr = {}
     if not args.no_ttr:
         auto = ("chebyshev_auto_rho", dict(accel="chebyshev", rho=-1.0), 1e-5)
+        # symmetric colour order with automatic rho, the float32 passes
+        # moving to extended precision at their floor (PBNG_PREC_AUTO)
+        sym = dict(accel="chebyshev", rho=-1.0, colour_order="symmetric", precision="auto")
+        sym_runs = [(f"symmetric_auto_rho_to_{t:.0e}", sym, t) for t in (1e-3, 1e-4, 1e-5)]
         runs = {"twist10": [("plain", {}, 1e-5), ("chebyshev", dict(accel="chebyshev"), 1e-5), auto,
-                            ("sor", dict(accel="sor", omega=1.5), 1e-5)],
+                            ("sor", dict(accel="sor", omega=1.5), 1e-5)] + sym_runs[2:],
                 "sag64": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto,
-                          ("sor", dict(accel="sor", omega=1.5), 1e-5)],
+                          ("sor", dict(accel="sor", omega=1.5), 1e-5)] + sym_runs +
+                         [("symmetric_auto_rho_compensated_to_1e-04",
+                           dict(accel="chebyshev", rho=-1.0, colour_order="symmetric"), 1e-4)],
                 "bar": [("plain", {}, 1e-5), auto, ("sor", dict(accel="sor", omega=1.5), 1e-5)],
                 "batched": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto, ("plain", {}, 1e-5)],
                 "adjoint": [("sor", dict(accel="sor", omega=1.5), 1e-5), auto],
@@ -459,15 +485,22 @@ def main():
             uu = u0.clone()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
+            kw = dict(kw)
+            prec = kw.pop("precision", args.precision)
             st, sweeps, relr = m.solve(uu, tol, max_sw,
-                                       default_params(model=args.model, precision=args.precision, residual_every=10,
+                                       default_params(model=args.model, precision=prec, residual_every=10,
                                                       kernel_path=args.kernel_path, **kw),
                                        raise_on_status=False)
             torch.cuda.synchronize()
             ttr[name] = {"tol": tol, "status": int(st), "sweeps": int(sweeps),
                          "max_rel_residual": float(np.max(relr)), "ms": 1e3 * (time.perf_counter() - t0)}
+            if kw.get("colour_order") == "symmetric":
+                ttr[name]["colour_order"] = "symmetric"
+                ttr[name]["precision"] = prec
             if kw.get("rho", 1.0) <= 0.0:
-                ttr[name]["solve_info"] = m.solve_info()
+                info = m.solve_info()
+                ttr[name]["solve_info"] = {k: info[k] for k in ("rho", "plain_rate", "estimate_sweeps", "restarts",
+                                                                "raises", "extended_from")}
             if u_eq is None or float(np.max(relr)) < best_rel:
                 u_eq, best_rel = uu, float(np.max(relr))
         if args.config in ("twist10", "sag64") and args.model == "corotated" and args.kernel_path == 0:

@@ -54,7 +54,34 @@ typedef enum {
 typedef struct pbng_mesh pbng_mesh;   /* opaque, library-owned */
 
 enum { PBNG_ACCEL_NONE = 0, PBNG_ACCEL_CHEBYSHEV = 1, PBNG_ACCEL_SOR = 2 };
-enum { PBNG_PREC_FP32 = 0, PBNG_PREC_COMPENSATED = 1 };
+/* Precision of the sweep (pbng_params.precision).
+ *   PBNG_PREC_FP32         iterate and element arithmetic float32
+ *   PBNG_PREC_COMPENSATED  iterate as a float32 pair (hi + lo), element
+ *                          arithmetic float32
+ *   PBNG_PREC_EXTENDED     iterate as a float32 pair; every element force of
+ *                          the colour passes and residuals in float-float
+ *                          arithmetic (pairs of float32, about 48 bits) from
+ *                          float-pair element constants, each vertex's sum in
+ *                          FP64; the nodal Hessian stays float32.  Needed where
+ *                          the per-element forces are far larger than their
+ *                          sum: on a 64^3 cube under gravity float32 forces
+ *                          and constants leave a relative-residual floor of
+ *                          about 3e-4.  Ring layout only (kernel_path 0).
+ *   PBNG_PREC_AUTO         colour passes and pbng_solve's residual checks as
+ *                          COMPENSATED until the checks stall below 1e-2
+ *                          (the best of the last 20 not below half the best
+ *                          before them: the float32 passes' floor), then
+ *                          EXTENDED;
+ *                          a float32 check that puts a component at the
+ *                          tolerance is confirmed with the extended residual
+ *                          first.  r_0 and the residuals that pbng_sweep and
+ *                          pbng_sweep_host report are extended.  Ring layout
+ *                          only.
+ * Every residual sums each vertex's element terms and its vertex terms in
+ * float-float arithmetic and the squares in FP64 (a float32-pair sum keeps
+ * FP64's accuracy here at float32 throughput: FP64 arithmetic on this GPU
+ * runs at a small fraction of the float32 rate). */
+enum { PBNG_PREC_FP32 = 0, PBNG_PREC_COMPENSATED = 1, PBNG_PREC_EXTENDED = 2, PBNG_PREC_AUTO = 3 };
 /* Constitutive models (Section "Constitutive Models"), mu and lambda from
  * Eq. lame:
  *   PBNG_MODEL_COROTATED   Eq. cor, mu |F - R|^2 + (lambda/2)(J - 1)^2
@@ -89,11 +116,11 @@ typedef struct {
     int32_t resume;         /* 1: continue from the handle's iterate, its
                                acceleration history and sweep index; u_dev is
                                then output only.  0: start from u_dev.             */
-    int32_t precision;      /* PBNG_PREC_FP32: the iterate is float32.
-                               PBNG_PREC_COMPENSATED: the iterate is kept as a
-                               float32 pair (hi + lo), neighbour differences and
-                               updates are formed in that pair; all element
-                               arithmetic stays float32.                          */
+    int32_t precision;      /* PBNG_PREC_*: FP32, COMPENSATED (the iterate is a
+                               float32 pair, hi + lo; neighbour differences and
+                               updates are formed in that pair; element
+                               arithmetic float32), EXTENDED or AUTO (see the
+                               enum)                                              */
     int32_t kernel_path;    /* 0: 1-ring layout kernels (TMA-staged records,
                                cp.async 1-ring gathers) for every colour whose
                                vertices have at most 32 incident tets and 32
@@ -215,8 +242,12 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
  *   dL/dx_D = dL/du_D - H_DF lambda.
  * lambda is found with the same colour-by-colour block Gauss-Seidel as the
  * forward sweep (true Hessian applied matrix-free, 3x3 diagonal blocks
- * solved exactly), with p->accel acceleration, until
- * |dL/du - H lambda| <= rel_tol |dL/du| or max_sweeps.
+ * solved exactly), in p->colour_order, with p->accel acceleration
+ * (Chebyshev with rho <= 0: the automatic rho of pbng_solve, measured on
+ * this iteration), until |dL/du - H lambda| <= rel_tol |dL/du| or
+ * max_sweeps.  With the symmetric order the iteration is symmetric block
+ * Gauss-Seidel on H, whose spectrum is real in [0, 1) at a stable
+ * equilibrium (H positive definite).
  *   u_eq_dev      device float [nv][3]  equilibrium displacement (input)
  *   dLdu_dev      device float [nv][3]  dL/du (caller order; clamped rows are dL/dx_D)
  *   dL_dlogE_dev  device float [ne]     output, caller tet order
@@ -249,8 +280,10 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
  * adding constraints to a coloured mesh recolours only their vertices.
  * The layout is rebuilt on the next call (pbng_get_profile reports the
  * colouring and layout times).  nc = 0 removes all constraints.  A
- * constraint may not join two batch components.  pbng_adjoint and
- * pbng_newton_cg reject meshes with such constraints. */
+ * constraint may not join two batch components.  pbng_adjoint, pbng_force,
+ * pbng_hessian_apply and pbng_newton_cg include the constraints (their true
+ * Hessian blocks beta_i beta_j K_c; a constraint's clamped vertices enter
+ * dL/dx_D). */
 pbng_status pbng_set_weak_constraints(pbng_mesh* m, int32_t nc, const int32_t* idx, const double* w,
                                       const double* kn, const double* kt, const double* normal, int32_t recolour);
 
@@ -333,7 +366,9 @@ pbng_status pbng_set_state(pbng_mesh* m, const void* buf, size_t bytes);
 
 /* FP64 2-norm of (f + f^ext) over free vertices at u_dev (Section "PBNG vs.
  * PBD and Limited Newton": the 2-norm of the Newton residual), per component
- * (host double [ncomp]).  Does not modify u_dev. */
+ * (host double [ncomp]).  The element forces are evaluated in float-float
+ * arithmetic (as PBNG_PREC_EXTENDED) when every colour is in the ring layout,
+ * else in float32; each vertex's sum in FP64.  Does not modify u_dev. */
 pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out);
 
 /* pbng_residual without any allocation.  The paper has no counterpart: this
@@ -457,22 +492,53 @@ pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p
  * rho <= 0) pbng_solve first runs max(30, 3 residual_every) plain sweeps,
  * takes the per-sweep contraction q = (r_b / r_a)^(1 / (b - a)) of the
  * slowest active component between the residual check a at or after a third
- * of them and the last one b, sets rho = clamp(1 - 2 (1 - q), 0.5, 0.98) and
- * restarts the Chebyshev schedule (omega_1 = omega_2 = 1, x^{-1} = x^0) at
- * the current iterate.  The Chebyshev weights assume the iteration's error
- * modes decay with real factors up to rho; colour-ordered Gauss-Seidel on
- * more than two colours does not guarantee that, and a rho at the measured
- * rate itself can diverge, hence the factor 2 and the cap.  A residual check
- * whose worst component exceeds 4x the best seen since the last (re)start
- * doubles 1 - rho and restarts the schedule; after 4 such back-offs the
- * remaining sweeps are plain.  The estimate is not kept across calls. */
+ * of them and the last one b, and restarts the Chebyshev schedule
+ * (omega_1 = omega_2 = 1, x^{-1} = x^0) at the current iterate with
+ *   forward order:   rho = clamp(1 - 2 (1 - q), 0.5, 0.98).  The Chebyshev
+ *                    weights assume error modes that decay with real factors
+ *                    up to rho; colour-ordered Gauss-Seidel on more than two
+ *                    colours does not guarantee that, and a rho at the
+ *                    measured rate itself can diverge, hence the factor 2 and
+ *                    the cap;
+ *   symmetric order: rho = clamp(1 - gamma (1 - q), 0.5, 1 - 1e-6), the
+ *                    spectral radius of gamma B + (1 - gamma) I for a real
+ *                    spectrum of B in [0, q].  A few plain sweeps underrate
+ *                    the slowest mode, so once a window of
+ *                    max(4 residual_every, 3 / sqrt(2 (1 - rho))) sweeps has
+ *                    passed since the last (re)start, an observed per-sweep
+ *                    factor f (over its second half) that lowered the
+ *                    residual at least 2x but at under 70 % of the log-rate
+ *                    of k = rho / (1 + sqrt(1 - rho^2)) raises rho to
+ *                    rho (z + 1/z) / 2, z = f / k (where a mode above rho
+ *                    sits), and restarts (at most 12 raises).
+ * A residual check whose worst component exceeds 4x the best seen since the
+ * last (re)start doubles 1 - rho and restarts the schedule; after 4 such
+ * back-offs the remaining sweeps are plain.  The estimate is not kept across
+ * calls. */
+#define PBNG_MAX_SOLVE_EVENTS 16
 typedef struct {
     double rho;              /* Chebyshev rho in use at the end (0: none)     */
     double plain_rate;       /* automatic rho: measured q; else 0              */
     int32_t estimate_sweeps; /* automatic rho: plain sweeps before Chebyshev   */
     int32_t restarts;        /* automatic rho: divergence back-offs            */
+    int32_t raises;          /* automatic rho, symmetric order: rho raises     */
+    int32_t extended_from;   /* sweeps done before the colour passes ran in
+                                PBNG_PREC_EXTENDED (0 for EXTENDED, the stall
+                                point for AUTO); -1: never                    */
+    int32_t nevents;         /* automatic rho: schedule (re)starts recorded    */
+    int32_t event_sweep[PBNG_MAX_SOLVE_EVENTS];  /* sweeps done at each (re)start */
+    double event_rho[PBNG_MAX_SOLVE_EVENTS];     /* its rho (0: plain from there) */
 } pbng_solve_info;
 pbng_status pbng_get_solve_info(const pbng_mesh* m, pbng_solve_info* out);
+
+/* Measurement aid (no counterpart in the paper): the FP32 FMA throughput of
+ * the current device in TFLOP/s (one FMA = 2 flops), the denominator of the
+ * float32 element arithmetic's roofline.  Runs 6 launches of 8 CTAs of 256
+ * threads per SM, each thread carrying 8 independent FMA chains for 32,768
+ * rounds, timed with CUDA events on `stream` (cudaStream_t as void*, NULL =
+ * legacy default stream); reports the best of the last 5.  Allocates and
+ * frees a small output buffer; changes no device setting.  Synchronises. */
+pbng_status pbng_measure_fp32_peak(void* stream, double* tflops_out);
 
 /* Number of independent components (1 unless mesh_id was given). */
 int32_t pbng_num_components(const pbng_mesh* m);

@@ -6,8 +6,8 @@ only marshals arguments to it.
 """
 
 from ._lib import ACCEL, PRECISION, PbngError, PbngParams, load
-from .mesh import Mesh, default_params
+from .mesh import Mesh, default_params, measure_fp32_peak
 from .autograd import EquilibriumModel
 
 __all__ = ["ACCEL", "PRECISION", "PbngError", "PbngParams", "load", "Mesh", "default_params",
-           "EquilibriumModel"]
+           "EquilibriumModel", "measure_fp32_peak"]

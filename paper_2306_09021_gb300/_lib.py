@@ -18,7 +18,7 @@ STATUS_NAMES = {
 }
 
 ACCEL = {"none": 0, "chebyshev": 1, "sor": 2}
-PRECISION = {"fp32": 0, "compensated": 1}
+PRECISION = {"fp32": 0, "compensated": 1, "extended": 2, "auto": 3}
 MODEL = {"corotated": 0, "neohookean": 1, "stable_neohookean": 2}
 ORDER = {"forward": 0, "symmetric": 1}
 
@@ -76,12 +76,20 @@ class PbngSchedule(ctypes.Structure):
     ]
 
 
+MAX_SOLVE_EVENTS = 16  # PBNG_MAX_SOLVE_EVENTS
+
+
 class PbngSolveInfo(ctypes.Structure):
     _fields_ = [
         ("rho", ctypes.c_double),
         ("plain_rate", ctypes.c_double),
         ("estimate_sweeps", ctypes.c_int32),
         ("restarts", ctypes.c_int32),
+        ("raises", ctypes.c_int32),
+        ("extended_from", ctypes.c_int32),
+        ("nevents", ctypes.c_int32),
+        ("event_sweep", ctypes.c_int32 * MAX_SOLVE_EVENTS),
+        ("event_rho", ctypes.c_double * MAX_SOLVE_EVENTS),
     ]
 
 
@@ -133,6 +141,7 @@ SIGNATURES = {
     "pbng_get_schedule": (_I32, [_P, ctypes.POINTER(PbngSchedule)]),
     "pbng_autotune": (_I32, [_P, _P, ctypes.POINTER(PbngParams), _I32, ctypes.POINTER(PbngSchedule)]),
     "pbng_get_solve_info": (_I32, [_P, ctypes.POINTER(PbngSolveInfo)]),
+    "pbng_measure_fp32_peak": (_I32, [_P, _PD]),
     "pbng_set_inertia": (_I32, [_P, _D, _PD]),
     "pbng_set_weak_constraints": (_I32, [_P, _I32, _PI, _PD, _PD, _PD, _PD, _I32]),
     "pbng_step": (_I32, [_P, _P, _P, _I32, _D, ctypes.POINTER(PbngParams), _PI, _PD]),

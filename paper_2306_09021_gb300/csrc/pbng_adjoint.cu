@@ -195,6 +195,44 @@ __device__ __forceinline__ float3 mat_g(const float* M, float3 g) {
 // lam . H lam per warp.
 enum { kDiag = 0, kSweep = 1, kResid = 2, kForce = 3, kApply = 4 };
 
+// Two-sided weak constraints (Section "Weak Constraints") in the true
+// Hessian: constraint c adds beta_v beta_j K_c to block (v, j), so
+// (H lam)_v gains sum_c beta_v K_c (sum_q b_q lam_q) (lam zero at clamped
+// vertices) and the diagonal block sum_c beta_v^2 K_c (the same term as in
+// Eq. mod_hess).  h (3) and D (upper triangle, 6, or nullptr) are added to.
+__device__ __forceinline__ void weak_hessian(const DeviceMesh& m, const float4* lam, int v, float* h, float* D) {
+    if (!m.wc_off) return;
+    const int k1 = m.wc_off[v + 1];
+    for (int k = m.wc_off[v]; k < k1; ++k) {
+        const int2 e = m.wc_list[k];
+        const int c = e.x;
+        const float beta = __int_as_float(e.y);
+        float Cl[3] = {0.f, 0.f, 0.f};
+        if (h) {
+            for (int q = 0; q < 8; ++q) {
+                const int jq = m.wc_v[8 * c + q];
+                if (jq < 0) break;
+                const float bq = m.wc_b[8 * c + q];
+                const float4 l = lam[jq];
+                Cl[0] += bq * l.x;
+                Cl[1] += bq * l.y;
+                Cl[2] += bq * l.z;
+            }
+        }
+        const float* K = m.wc_k + 6 * c;
+        if (h) {
+            h[0] += beta * (K[0] * Cl[0] + K[1] * Cl[1] + K[2] * Cl[2]);
+            h[1] += beta * (K[1] * Cl[0] + K[3] * Cl[1] + K[4] * Cl[2]);
+            h[2] += beta * (K[2] * Cl[0] + K[4] * Cl[1] + K[5] * Cl[2]);
+        }
+        if (D) {
+            const float b2 = beta * beta;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) D[t] += b2 * K[t];
+        }
+    }
+}
+
 template <int W, int MODE, int MODEL>
 __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, float4* lam, const float4* gv,
                                          float4* diag, float4* out4, const Item& it, int lane, int32_t* err,
@@ -291,6 +329,7 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
         float r[3] = {acc[0], acc[1], acc[2]};
         float A[6] = {acc[3], acc[4], acc[5], acc[6], acc[7], acc[8]};
         el::vertex_terms<true, true>(m, m.aux0[v], m.aux1[v], uh, ul, r, A);
+        el::weak_terms<true, true>(m, u, v, r, A);
         out4[v] = make_float4(r[0], r[1], r[2], 0.f);
         diag[2 * v] = make_float4(A[0], A[1], A[2], A[3]);
         diag[2 * v + 1] = make_float4(A[4], A[5], 0.f, 0.f);
@@ -314,11 +353,13 @@ __device__ __forceinline__ void adj_item(const DeviceMesh& m, const State& u, fl
         acc[3] += K + kc * n[1] * n[1];
         acc[4] += kc * n[1] * n[2];
         acc[5] += K + kc * n[2] * n[2];
+        weak_hessian(m, lam, v, nullptr, acc);
         diag[2 * v] = make_float4(acc[0], acc[1], acc[2], acc[3]);
         diag[2 * v + 1] = make_float4(acc[4], acc[5], 0.f, 0.f);
         return;
     }
     const float nl = kc * (n[0] * li.x + n[1] * li.y + n[2] * li.z);
+    weak_hessian(m, lam, v, acc, nullptr);
     if (MODE == kApply) {
         const float h0 = acc[0] + K * li.x + nl * n[0], h1 = acc[1] + K * li.y + nl * n[1],
                     h2 = acc[2] + K * li.z + nl * n[2];
@@ -432,6 +473,40 @@ __global__ void adjoint_tet_kernel(int ne, int nfree, const int4* __restrict__ t
             atomicAdd(hdl + 4 * ids[jv] + 1, h.y);
             atomicAdd(hdl + 4 * ids[jv] + 2, h.z);
         }
+}
+
+// H_DF lam of the two-sided weak constraints: each constraint c with a
+// clamped vertex D adds b_D K_c (sum_q b_q lam_q) to hdl[D] (lam zero at
+// clamped vertices); one thread per constraint.
+__global__ void adjoint_weak_clamped_kernel(int nwc, int nfree, const DeviceMesh m, const float4* __restrict__ lam,
+                                            float* hdl) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nwc) return;
+    bool any = false;
+    float Cl[3] = {0.f, 0.f, 0.f};
+    for (int q = 0; q < 8; ++q) {
+        const int jq = m.wc_v[8 * c + q];
+        if (jq < 0) break;
+        any = any || jq >= nfree;
+        const float bq = m.wc_b[8 * c + q];
+        const float4 l = lam[jq];
+        Cl[0] += bq * l.x;
+        Cl[1] += bq * l.y;
+        Cl[2] += bq * l.z;
+    }
+    if (!any) return;
+    const float* K = m.wc_k + 6 * c;
+    const float KC[3] = {K[0] * Cl[0] + K[1] * Cl[1] + K[2] * Cl[2], K[1] * Cl[0] + K[3] * Cl[1] + K[4] * Cl[2],
+                         K[2] * Cl[0] + K[4] * Cl[1] + K[5] * Cl[2]};
+    for (int q = 0; q < 8; ++q) {
+        const int jq = m.wc_v[8 * c + q];
+        if (jq < 0) break;
+        if (jq < nfree) continue;
+        const float bq = m.wc_b[8 * c + q];
+        atomicAdd(hdl + 4 * jq, bq * KC[0]);
+        atomicAdd(hdl + 4 * jq + 1, bq * KC[1]);
+        atomicAdd(hdl + 4 * jq + 2, bq * KC[2]);
+    }
 }
 
 // gvec[w] = dL/du of internal free vertex w (caller layout in).
@@ -582,6 +657,9 @@ __device__ __forceinline__ void adj_ring_item(const DeviceMesh& m, float4* lam, 
     const float kc = contact ? m.k_contact : 0.0f;
     const float n[3] = {m.pn_x, m.pn_y, m.pn_z};
     const float nl = kc * (n[0] * li.x + n[1] * li.y + n[2] * li.z);
+    // the multipliers of a constraint's other vertices belong to other
+    // colours (a constraint is an element of the colouring)
+    weak_hessian(m, lam, v, acc, nullptr);
     const float4 gvv = G.ogv[j];
     const float r0 = gvv.x - (acc[0] + K * li.x + nl * n[0]);
     const float r1 = gvv.y - (acc[1] + K * li.y + nl * n[1]);
@@ -923,6 +1001,13 @@ cudaError_t launch_adjoint_tets(int ne, int nfree, const int4* tv, const float4*
         adjoint_tet_kernel<el::kStableNeoHookean><<<grid, 128, 0, st>>>(ne, nfree, tv, tb, u, lam, dLdlogE, hdl);
     else
         adjoint_tet_kernel<el::kCorotated><<<grid, 128, 0, st>>>(ne, nfree, tv, tb, u, lam, dLdlogE, hdl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_weak_clamped(int nwc, int nfree, const DeviceMesh& m, const float4* lam, float* hdl,
+                                        cudaStream_t st) {
+    if (nwc <= 0 || !m.wc_v) return cudaSuccess;
+    adjoint_weak_clamped_kernel<<<nblocks(nwc, 256), 256, 0, st>>>(nwc, nfree, m, lam, hdl);
     return cudaGetLastError();
 }
 

@@ -83,9 +83,10 @@ struct pbng_mesh {
 
     // device buffers
     DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
-    DevBuf d_ring, d_items;
+    DevBuf d_ring, d_ring_lo, d_items;
     DevBuf d_host_u;  // device copy of the caller's host iterate (pbng_sweep_host)
     DevBuf d_active;                   // int32 [ncomp] component flags (1 = active)
+    DevBuf d_vsq, d_comp_off, d_comp_list;  // several components: per-vertex |r|^2, component -> vertices
     // adjoint (built on first use after each layout)
     DevBuf d_lam[3], d_gv, d_diag, d_hdl, d_tv, d_tb, d_dq_int, d_dq_caller, d_adj_partial;
     // Newton-CG (pbng_newton_cg, pbng_force, pbng_hessian_apply): r, x, z, p, q
@@ -215,6 +216,8 @@ void free_buf(DevBuf& b) {
 }
 
 constexpr int32_t kMaxChunk = 1024;
+// Largest automatic Chebyshev rho (symmetric colour order).
+constexpr double kRhoCap = 1.0 - 1e-6;
 
 void destroy_graphs(pbng_mesh* m) {
     for (auto& g : m->graphs) {
@@ -519,8 +522,9 @@ pbng_status build_layout(pbng_mesh* m) {
     // ring layout: per lane-width run, 32-slot aligned; W slots per vertex
     m->items.clear();
     m->item_off.assign(m->ncol + 1, 0);
-    std::vector<float4> qa, qb, qc;
+    std::vector<float4> qa, qb, qc, la, lb, lc;  // records and their low words
     std::vector<int32_t> qid;
+    auto lo = [](double x) { return (float)(x - (double)(float)x); };
     for (int c = 0; c < m->ncol; ++c) {
         if (m->ring_colour[c]) {
             const SegmentTable& t = m->tables[c];
@@ -532,6 +536,9 @@ pbng_status build_layout(pbng_mesh* m) {
                 qa.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
                 qb.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
                 qc.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
+                la.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
+                lb.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
+                lc.resize(slot_base + nslots, make_float4(0.f, 0.f, 0.f, 0.f));
                 qid.resize(slot_base + nslots, 0);
                 for (int32_t vv = sg.v_begin; vv < sg.v_end; ++vv) {
                     const int32_t i = order[vv];
@@ -561,6 +568,11 @@ pbng_status build_layout(pbng_mesh* m) {
                         qb[slot] = make_float4((float)g[oth[1]][0], (float)g[oth[1]][1], (float)g[oth[1]][2],
                                                (float)(m->lam[e] * m->vol[e]));
                         qc[slot] = make_float4((float)g[oth[2]][0], (float)g[oth[2]][1], (float)g[oth[2]][2], pk);
+                        la[slot] = make_float4(lo(g[oth[0]][0]), lo(g[oth[0]][1]), lo(g[oth[0]][2]),
+                                               lo(2.0 * m->mu[e] * m->vol[e]));
+                        lb[slot] = make_float4(lo(g[oth[1]][0]), lo(g[oth[1]][1]), lo(g[oth[1]][2]),
+                                               lo(m->lam[e] * m->vol[e]));
+                        lc[slot] = make_float4(lo(g[oth[2]][0]), lo(g[oth[2]][1]), lo(g[oth[2]][2]), 0.f);
                     }
                 }
                 const int per_item = kRingLanes / W;
@@ -643,6 +655,14 @@ pbng_status build_layout(pbng_mesh* m) {
             b.id[q % kRingLanes] = qid[q];
         }
         PBNG_CUDA(m, upload(m->d_ring, blocks, st));
+        std::vector<RingLoBlock> lblocks(la.size() / kRingLanes);
+        for (size_t q = 0; q < la.size(); ++q) {
+            RingLoBlock& b = lblocks[q / kRingLanes];
+            b.la[q % kRingLanes] = la[q];
+            b.lb[q % kRingLanes] = lb[q];
+            b.lc[q % kRingLanes] = lc[q];
+        }
+        PBNG_CUDA(m, upload(m->d_ring_lo, lblocks, st));
     }
     PBNG_CUDA(m, upload(m->d_items, m->items, st));
     PBNG_CUDA(m, upload(m->d_aux0, aux0, st));
@@ -696,6 +716,16 @@ pbng_status build_layout(pbng_mesh* m) {
         PBNG_CUDA(m, upload(m->d_wc_c0, c0, st));
     }
     PBNG_CUDA(m, upload(m->d_comp, comp, st));
+    if (m->ncomp > 1) {  // component -> its free vertices (internal ids, ascending)
+        std::vector<int32_t> coff(m->ncomp + 1, 0), clist(m->nfree);
+        for (int32_t w = 0; w < m->nfree; ++w) coff[comp[w] + 1]++;
+        for (int32_t k = 0; k < m->ncomp; ++k) coff[k + 1] += coff[k];
+        std::vector<int32_t> fill(coff.begin(), coff.end() - 1);
+        for (int32_t w = 0; w < m->nfree; ++w) clist[fill[comp[w]]++] = w;
+        PBNG_CUDA(m, upload(m->d_comp_off, coff, st));
+        PBNG_CUDA(m, upload(m->d_comp_list, clist, st));
+        PBNG_CUDA(m, ensure_buf(m->d_vsq, sizeof(double) * (size_t)std::max(1, m->nfree)));
+    }
     PBNG_CUDA(m, upload(m->d_perm, m->perm, st));
     PBNG_CUDA(m, upload(m->d_dir_hi, dhi, st));
     PBNG_CUDA(m, upload(m->d_dir_lo, dlo, st));
@@ -729,7 +759,9 @@ pbng_status build_layout(pbng_mesh* m) {
     d.aux1 = (const float4*)m->d_aux1.p;
     d.comp = m->ncomp > 1 ? (const int32_t*)m->d_comp.p : nullptr;
     d.comp_active = m->ncomp > 1 ? (const int32_t*)m->d_active.p : nullptr;
+    d.vsq = m->ncomp > 1 ? (double*)m->d_vsq.p : nullptr;
     d.ring = (const RingBlock*)m->d_ring.p;
+    d.ring_lo = (const RingLoBlock*)m->d_ring_lo.p;
     d.copy_shortfall = m->copy_shortfall;
     d.pn_x = (float)m->pn[0];
     d.pn_y = (float)m->pn[1];
@@ -767,24 +799,40 @@ pbng_status ensure_ready(pbng_mesh* m) {
 // writes ring_partials per-warp partials at partial[0..), each direct-load
 // colour its per-block partials after them; then the sum lands in *scalar.
 // With several components the sums go to comp_sq (zeroed here) instead.
+// extended: float-float element forces (every colour is in the ring layout).
+// With several components each vertex's |r|^2 lands in its slot of d_vsq
+// and the per-component sums follow in a fixed order (the same bits every
+// run); atomic_comp (the allocation-free residual, which has no slots) sums
+// them atomically into comp_sq instead.
 pbng_status enqueue_residual(pbng_mesh* m, State s, bool compensated, double* partial, double* comp_sq,
-                             double* scalar, cudaStream_t st) {
+                             double* scalar, cudaStream_t st, bool extended = false, bool atomic_comp = false) {
     const bool multi = m->ncomp > 1;
-    if (multi) PBNG_CUDA(m, cudaMemsetAsync(comp_sq, 0, sizeof(double) * m->ncomp, st));
+    DeviceMesh dm = m->dm;
+    if (multi && atomic_comp) {
+        dm.vsq = nullptr;
+        PBNG_CUDA(m, cudaMemsetAsync(comp_sq, 0, sizeof(double) * m->ncomp, st));
+    } else if (multi) {  // vertices of frozen items are not written: they count as zero
+        PBNG_CUDA(m, cudaMemsetAsync(m->d_vsq.p, 0, sizeof(double) * (size_t)m->nfree, st));
+    }
     if (m->nitems_ring > 0) {
-        PBNG_CUDA(m, launch_ring_residual(m->dm, s, (const Item*)m->d_items.p, m->nitems_ring, compensated,
-                                          partial, multi ? comp_sq : nullptr, m->model, (int32_t*)m->d_err.p, st));
+        PBNG_CUDA(m, launch_ring_residual(dm, s, (const Item*)m->d_items.p, m->nitems_ring, compensated,
+                                          partial, multi ? comp_sq : nullptr, m->model, (int32_t*)m->d_err.p, st,
+                                          extended && compensated));
         m->kernel_launches++;
     }
     for (int c = 0; c < m->ncol; ++c) {
         if (m->ring_colour[c]) continue;
-        PBNG_CUDA(m, launch_residual(m->dm, s, m->tables[c], compensated,
+        PBNG_CUDA(m, launch_residual(dm, s, m->tables[c], compensated,
                                      partial + m->ring_partials + m->table_partial_off[c],
                                      multi ? comp_sq : nullptr, m->ncomp, nullptr, m->model, st));
         if (m->tables[c].total_blocks > 0) m->kernel_launches++;
     }
     if (!multi) {
         PBNG_CUDA(m, launch_reduce(partial, m->ring_partials + m->total_partials, scalar, st));
+        m->kernel_launches++;
+    } else if (!atomic_comp) {
+        PBNG_CUDA(m, launch_comp_reduce(m->ncomp, (const int32_t*)m->d_comp_off.p, (const int32_t*)m->d_comp_list.p,
+                                        (const double*)m->d_vsq.p, comp_sq, st));
         m->kernel_launches++;
     }
     return PBNG_OK;
@@ -793,12 +841,12 @@ pbng_status enqueue_residual(pbng_mesh* m, State s, bool compensated, double* pa
 pbng_status sync_with_err(pbng_mesh* m, cudaStream_t st);
 
 // FP64 squared residual norms (per component) of state `slot` -> host `out`.
-pbng_status residual_sq(pbng_mesh* m, int slot, bool compensated, double* out) {
+pbng_status residual_sq(pbng_mesh* m, int slot, bool compensated, double* out, bool extended = false) {
     cudaStream_t st = m->stream;
     const bool multi = m->ncomp > 1;
     const int pslot = prof_begin(m, kProfResidual);
     pbng_status r = enqueue_residual(m, state_of(m, slot), compensated, (double*)m->d_partial.p,
-                                     (double*)m->d_comp_sq.p, (double*)m->d_scalar.p, st);
+                                     (double*)m->d_comp_sq.p, (double*)m->d_scalar.p, st, extended);
     if (r) return r;
     prof_end(m, pslot);
     PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? m->d_comp_sq.p : m->d_scalar.p,
@@ -842,10 +890,27 @@ void select_path(pbng_mesh* m, const pbng_params* p) {
 
 bool valid_params(const pbng_params* p) {
     return p && p->model >= 0 && p->model <= 2 && p->accel >= 0 && p->accel <= 2 && p->residual_every >= 1 &&
-           (p->precision == PBNG_PREC_FP32 || p->precision == PBNG_PREC_COMPENSATED) &&
+           p->precision >= PBNG_PREC_FP32 && p->precision <= PBNG_PREC_AUTO &&
            std::isfinite(p->omega) && std::isfinite(p->rho) && std::isfinite(p->gamma) &&
            std::isfinite(p->step) && p->skip_tol >= 0.0 && (p->kernel_path == 0 || p->kernel_path == 1) &&
            (p->colour_order == PBNG_ORDER_FORWARD || p->colour_order == PBNG_ORDER_SYMMETRIC);
+}
+
+// Precision modes: the iterate is a float pair unless FP32; colour passes,
+// and the residual checks inside a chunk of sweeps, use the float-float
+// element force only in EXTENDED; the reported residuals (r_0, the final
+// residual of pbng_sweep / pbng_sweep_host, the confirmation of a converged
+// AUTO solve) use it in EXTENDED and AUTO.  pbng_solve moves AUTO's passes
+// to EXTENDED when its checks stall.
+bool pair_iterate(int prec) { return prec != PBNG_PREC_FP32; }
+bool ext_passes(int prec) { return prec == PBNG_PREC_EXTENDED; }
+bool ext_residual(int prec) { return prec == PBNG_PREC_EXTENDED || prec == PBNG_PREC_AUTO; }
+
+// Extended-precision passes and residuals run on the ring layout only.
+pbng_status check_ext(pbng_mesh* m, const pbng_params* p) {
+    if ((ext_passes(p->precision) || ext_residual(p->precision)) && !m->all_ring)
+        return fail(m, PBNG_EINVAL, "extended precision needs every colour in the ring layout (kernel_path 0)");
+    return PBNG_OK;
 }
 
 // Colour passes of one sweep: 0..C-1, and for the symmetric order back down
@@ -860,7 +925,7 @@ std::vector<int> colour_sequence(int ncol, int order) {
 
 // Loads u_dev (or keeps the stored iterate) and resets the history.
 pbng_status begin(pbng_mesh* m, const float* u_dev, const pbng_params* p, bool need_r0) {
-    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const bool comp = pair_iterate(p->precision);
     if (!p->resume || !m->has_state) {
         if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
         PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, (const int32_t*)m->d_perm.p,
@@ -878,7 +943,7 @@ pbng_status begin(pbng_mesh* m, const float* u_dev, const pbng_params* p, bool n
     }
     if (need_r0 && (m->r0.empty() || m->r0[0] < 0.0)) {
         m->r0.assign(m->ncomp, 0.0);
-        pbng_status s = residual_sq(m, 0, comp, m->r0.data());
+        pbng_status s = residual_sq(m, 0, comp, m->r0.data(), ext_residual(p->precision));
         if (s) return s;
         for (auto& r : m->r0) r = std::sqrt(r);
     }
@@ -913,7 +978,8 @@ void chunk_weights(pbng_mesh* m, const pbng_params* p, int32_t K, float2* out) {
 // stream when profiling.  p1 is the slot holding x^l at the start.
 pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool with_res, int p1,
                           bool prof, int64_t* nkernels, cudaStream_t st) {
-    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const bool comp = pair_iterate(p->precision);
+    const bool ext = ext_passes(p->precision);
     const PassParams pp{(float)p->step, (float)p->skip_tol, p->model};
     const State cur = state_of(m, 0);
     int p2 = 3 - p1;
@@ -935,7 +1001,7 @@ pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool wi
             if (m->ring_colour[c])
                 PBNG_CUDA(m, launch_ring_pass(m->dm, cur, (const Item*)m->d_items.p + m->item_off[c],
                                               m->item_off[c + 1] - m->item_off[c], pp, comp, m->sched[c],
-                                              (int32_t*)m->d_err.p, st));
+                                              (int32_t*)m->d_err.p, st, ext));
             else
                 PBNG_CUDA(m, launch_colour_pass(m->dm, cur, m->tables[c], pp, comp, (int32_t*)m->d_err.p, st));
             if ((r = mark(kProfColour))) return r;
@@ -955,7 +1021,7 @@ pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool wi
         if ((r = mark(kProfResidual))) return r;
         const int64_t before = m->kernel_launches;
         if ((r = enqueue_residual(m, cur, comp, (double*)m->d_partial.p, (double*)m->d_comp_sq.p,
-                                  (double*)m->d_scalar.p, st)))
+                                  (double*)m->d_scalar.p, st, ext)))
             return r;
         *nkernels += m->kernel_launches - before;
         m->kernel_launches = before;
@@ -1340,8 +1406,9 @@ pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_p
     select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
+    if ((s = check_ext(m, p))) return s;
     if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
-    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const bool comp = pair_iterate(p->precision);
     if ((s = begin(m, u_dev, p, rel_residual_out != nullptr))) return s;
     // Chunks of up to residual_every sweeps, each one graph launch; the last
     // chunk also computes the residual when it is requested.
@@ -1351,7 +1418,8 @@ pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_p
     for (int32_t done = 0; done < nsweeps;) {
         const int32_t chunk = std::min<int32_t>(K, nsweeps - done);
         const bool last = done + chunk == nsweeps;
-        const bool with_res = last && rel_residual_out != nullptr;
+        // (AUTO reports the extended residual, taken after the chunks)
+        const bool with_res = last && rel_residual_out != nullptr && p->precision != PBNG_PREC_AUTO;
         if ((s = run_chunk(m, p, chunk, with_res, m->h_wg + done))) return s;
         res_done = res_done || with_res;
         done += chunk;
@@ -1363,7 +1431,7 @@ pbng_status pbng_sweep(pbng_mesh* m, float* u_dev, int32_t nsweeps, const pbng_p
         std::vector<double> sq(m->ncomp);
         if (res_done) {
             for (int k = 0; k < m->ncomp; ++k) sq[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
-        } else if ((s = residual_sq(m, 0, comp, sq.data()))) {
+        } else if ((s = residual_sq(m, 0, comp, sq.data(), ext_residual(p->precision)))) {
             return s;
         }
         for (int k = 0; k < m->ncomp; ++k)
@@ -1381,8 +1449,9 @@ pbng_status pbng_sweep_host(pbng_mesh* m, float* u_host, int32_t nsweeps, const 
     select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
+    if ((s = check_ext(m, p))) return s;
     if (!u_host) return fail(m, PBNG_EINVAL, "u_host is NULL");
-    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const bool comp = pair_iterate(p->precision);
     const size_t bytes = sizeof(float) * 3 * (size_t)m->nv;
     cudaStream_t st = m->stream;
     PBNG_CUDA(m, ensure_buf(m->d_host_u, bytes));
@@ -1397,7 +1466,7 @@ pbng_status pbng_sweep_host(pbng_mesh* m, float* u_host, int32_t nsweeps, const 
     bool res_done = false;
     for (int32_t done = 0; done < nsweeps;) {
         const int32_t chunk = std::min<int32_t>(K, nsweeps - done);
-        const bool with_res = done + chunk == nsweeps && residual_out != nullptr;
+        const bool with_res = done + chunk == nsweeps && residual_out != nullptr && q.precision != PBNG_PREC_AUTO;
         if ((s = run_chunk(m, &q, chunk, with_res, m->h_wg + done))) return s;
         res_done = res_done || with_res;
         done += chunk;
@@ -1405,7 +1474,7 @@ pbng_status pbng_sweep_host(pbng_mesh* m, float* u_host, int32_t nsweeps, const 
     if (residual_out && !res_done) {  // no sweep: the residual of the loaded iterate
         const bool multi = m->ncomp > 1;
         if ((s = enqueue_residual(m, state_of(m, 0), comp, (double*)m->d_partial.p, (double*)m->d_comp_sq.p,
-                                  (double*)m->d_scalar.p, st)))
+                                  (double*)m->d_scalar.p, st, ext_residual(q.precision))))
             return s;
         PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? m->d_comp_sq.p : m->d_scalar.p,
                                      sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
@@ -1421,14 +1490,46 @@ pbng_status pbng_sweep_host(pbng_mesh* m, float* u_host, int32_t nsweeps, const 
 
 namespace {
 
+// Automatic Chebyshev rho (pbng_solve, pbng_adjoint): the rho after the
+// plain sweeps measured the per-sweep contraction q.
+double initial_rho(bool symmetric, double gamma, double q) {
+    if (!(q < 1.0)) q = 0.9999;
+    if (symmetric) return std::min(kRhoCap, std::max(0.5, 1.0 - gamma * (1.0 - q)));
+    return std::min(0.98, std::max(0.5, 1.0 - 2.0 * (1.0 - q)));
+}
+
+// The raise rule of the symmetric order: `since` holds (sweeps done, worst
+// residual) of the checks since the last (re)start, the last one being the
+// current check.  Returns the raised rho, or rho itself.
+double raised_rho(const std::vector<std::pair<int32_t, double>>& since, int32_t K, double rho) {
+    if (since.size() < 2) return rho;
+    const int32_t done = since.back().first;
+    const double w = since.back().second;
+    const int32_t span = done - since.front().first;
+    const int32_t win = std::max<int32_t>(4 * K, (int32_t)std::ceil(3.0 / std::sqrt(2.0 * (1.0 - rho))));
+    if (span < win) return rho;
+    size_t a = 0;
+    while (a + 1 < since.size() && since[a].first - since.front().first < span / 2) ++a;
+    const double wa = since[a].second;
+    const int32_t ds = done - since[a].first;
+    if (!(ds > 0 && wa > 0.0 && w > 0.0 && w < 0.5 * wa)) return rho;
+    const double lam_pred = -std::log(rho / (1.0 + std::sqrt(1.0 - rho * rho)));
+    const double lam_obs = -std::log(w / wa) / ds;
+    if (!(lam_obs < 0.7 * lam_pred)) return rho;
+    const double z = std::exp(lam_pred - lam_obs);
+    const double mu = std::min(kRhoCap, rho * 0.5 * (z + 1.0 / z));
+    return mu > rho + 0.05 * (1.0 - rho) ? mu : rho;
+}
+
 pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_sweeps, const pbng_params* p,
                        int32_t* sweeps_out, double* rel_residual_out) {
     if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
     select_path(m, p);
     pbng_status s = ensure_ready(m);
     if (s) return s;
+    if ((s = check_ext(m, p))) return s;
     if (!u_dev) return fail(m, PBNG_EINVAL, "u_dev is NULL");
-    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const bool comp = pair_iterate(p->precision);
     if ((s = begin(m, u_dev, p, true))) return s;
     std::vector<double> sq(m->ncomp), rel(m->ncomp, 0.0);
     int32_t done = 0;
@@ -1472,21 +1573,53 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     if ((s = ensure_wg(m, (size_t)K))) return s;
     // Chebyshev with rho <= 0: rho from the FP64 residuals.  Plain sweeps
     // first; from the residual ratio over the last two thirds of them, the
-    // per-sweep contraction q of the slowest active component; then
-    // rho = clamp(1 - 2 (1 - q), 0.5, 0.98) and the Chebyshev schedule
-    // restarts at the current iterate.  A check whose worst residual exceeds
-    // 4x the best one seen since the last (re)start backs rho off
-    // (1 - rho doubles) and restarts; after kMaxBackoffs the sweeps go plain.
+    // per-sweep contraction q of the slowest active component.  Ascending
+    // colour order: rho = clamp(1 - 2 (1 - q), 0.5, 0.98).  Symmetric order
+    // (real spectrum in [0, q]): rho = 1 - gamma (1 - q), the spectral radius
+    // of gamma B + (1 - gamma) I, capped at 1 - 1e-6; since the plain rate of
+    // a few sweeps underestimates the slowest mode, rho is then raised while
+    // the observed Chebyshev rate stays below the one rho predicts (a mode
+    // above rho, Manteuffel's adaptive Chebyshev idea): with the predicted
+    // per-sweep factor k = rho / (1 + sqrt(1 - rho^2)) and the observed one
+    // f > k, that mode sits at rho (z + 1/z) / 2, z = f / k.  Every change
+    // restarts the schedule at the current iterate.  A check whose worst
+    // residual exceeds 4x the best one seen since the last (re)start backs
+    // rho off (1 - rho doubles) and restarts; after kMaxBackoffs the sweeps
+    // go plain.
     pbng_params cp = *p;
     const bool auto_rho = p->accel == PBNG_ACCEL_CHEBYSHEV && !(p->rho > 0.0);
+    const bool symmetric = p->colour_order == PBNG_ORDER_SYMMETRIC;
     const int32_t est_sweeps = std::max<int32_t>(30, 3 * K);
-    constexpr int kMaxBackoffs = 4;
+    constexpr int kMaxBackoffs = 4, kMaxRaises = 12, kMaxEvents = PBNG_MAX_SOLVE_EVENTS;
     int phase = auto_rho ? 0 : 1;
     int32_t mark_done = -1;
     std::vector<double> mark_rel(m->ncomp, 0.0);
     double best = 0.0;
+    // checks since the last (re)start: (sweeps done, worst active residual)
+    std::vector<std::pair<int32_t, double>> since;
+    // PBNG_PREC_AUTO: worst residual of each check while the passes are
+    // float32; a window of kStallChecks checks whose best is not below
+    // kStallFactor times the best before it, once the residual is below
+    // kStallBelow (a slow start is not a floor), is a stall at the float32
+    // passes' rounding floor.
+    constexpr int kStallChecks = 20;
+    constexpr double kStallFactor = 0.5, kStallBelow = 1e-2;
+    std::vector<double> stall_hist;
+    auto to_extended = [&]() {
+        cp.precision = PBNG_PREC_EXTENDED;
+        m->info.extended_from = done;
+        stall_hist.clear();
+    };
     m->info = pbng_solve_info{};
     m->info.rho = (p->accel == PBNG_ACCEL_CHEBYSHEV && !auto_rho) ? p->rho : 0.0;
+    m->info.extended_from = p->precision == PBNG_PREC_EXTENDED ? 0 : -1;
+    auto log_event = [&](double rho) {
+        if (m->info.nevents < kMaxEvents) {
+            m->info.event_sweep[m->info.nevents] = done;
+            m->info.event_rho[m->info.nevents] = rho;
+            m->info.nevents++;
+        }
+    };
     if (auto_rho) cp.accel = PBNG_ACCEL_NONE;
     auto restart_history = [&]() -> pbng_status {
         PBNG_CUDA(m, launch_copy_state(m->nv, state_of(m, 0), state_of(m, m->p1_slot), m->stream));
@@ -1495,6 +1628,8 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
         m->sweep_l = 0;
         m->omega_l = 1.0;
         best = 0.0;
+        since.clear();
+        log_event(cp.accel == PBNG_ACCEL_CHEBYSHEV ? cp.rho : 0.0);
         return PBNG_OK;
     };
     auto worst_active = [&]() {
@@ -1512,13 +1647,40 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
         done += chunk;
         if ((s = check_err(m))) return s;
         for (int k = 0; k < m->ncomp; ++k) sq[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
+        if (cp.precision == PBNG_PREC_AUTO) {
+            // a float32 check that puts an active component at the tolerance
+            // is replaced by the extended residual; if that is above it, the
+            // passes go extended
+            auto below = [&](int k) { return std::sqrt(sq[k]) <= rel_tol * (m->r0[k] > 0 ? m->r0[k] : 1.0); };
+            std::vector<uint8_t> was(m->ncomp, 0);
+            bool any = false;
+            for (int k = 0; k < m->ncomp; ++k)
+                if (!frozen[k] && below(k)) was[k] = 1, any = true;
+            if (any) {
+                if ((s = residual_sq(m, 0, true, sq.data(), true))) return s;
+                bool ok = true;
+                for (int k = 0; k < m->ncomp; ++k) ok = ok && (!was[k] || below(k));
+                if (!ok) to_extended();
+            }
+        }
         cv = converged();
         if (changed && cv == 0)  // ordered before the next chunk; h_active is not touched until the next sync
             PBNG_CUDA(m, cudaMemcpyAsync(m->d_active.p, m->h_active, sizeof(int32_t) * m->ncomp,
                                          cudaMemcpyHostToDevice, m->stream));
         if (cv == 1) result = PBNG_OK;
         if (cv < 0) result = PBNG_EDIVERGED;
-        if (cv != 0 || !auto_rho) continue;
+        if (cv != 0) continue;
+        const double w = worst_active();
+        if (cp.precision == PBNG_PREC_AUTO && phase == 1) {
+            stall_hist.push_back(w);
+            const size_t n = stall_hist.size();
+            if (n >= 2 * kStallChecks) {
+                const double recent = *std::min_element(stall_hist.end() - kStallChecks, stall_hist.end());
+                const double before = *std::min_element(stall_hist.begin(), stall_hist.end() - kStallChecks);
+                if (recent > kStallFactor * before && recent < kStallBelow) to_extended();
+            }
+        }
+        if (!auto_rho) continue;
         if (phase == 0) {
             if (mark_done < 0 && 3 * done >= est_sweeps) {
                 mark_done = done;
@@ -1530,7 +1692,7 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
                         q = std::max(q, std::pow(rel[k] / mark_rel[k], 1.0 / (done - mark_done)));
                 if (!(q < 1.0)) q = 0.9999;
                 cp.accel = PBNG_ACCEL_CHEBYSHEV;
-                cp.rho = std::min(0.98, std::max(0.5, 1.0 - 2.0 * (1.0 - q)));
+                cp.rho = initial_rho(symmetric, p->gamma, q);
                 m->info.plain_rate = q;
                 m->info.estimate_sweeps = done;
                 m->info.rho = cp.rho;
@@ -1538,13 +1700,21 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
                 if ((s = restart_history())) return s;
             }
         } else if (cp.accel == PBNG_ACCEL_CHEBYSHEV) {
-            const double w = worst_active();
+            since.emplace_back(done, w);
             if (best == 0.0 || w < best) best = w;
-            else if (w > 4.0 * best) {
+            if (w > 4.0 * best) {
                 if (++m->info.restarts > kMaxBackoffs) cp.accel = PBNG_ACCEL_NONE;
                 else cp.rho = std::max(0.5, 1.0 - 2.0 * (1.0 - cp.rho));
                 m->info.rho = cp.accel == PBNG_ACCEL_CHEBYSHEV ? cp.rho : 0.0;
                 if ((s = restart_history())) return s;
+            } else if (symmetric && m->info.raises < kMaxRaises) {
+                const double mu = raised_rho(since, K, cp.rho);
+                if (mu > cp.rho) {
+                    cp.rho = mu;
+                    m->info.rho = mu;
+                    m->info.raises++;
+                    if ((s = restart_history())) return s;
+                }
             }
         }
     }
@@ -1682,7 +1852,6 @@ pbng_status newton_ready(pbng_mesh* m, const pbng_params* p) {
     pbng_status s = ensure_ready(m);
     if (s) return s;
     if (!m->all_ring) return fail(m, PBNG_EINVAL, "Newton-CG needs every colour in the ring layout");
-    if (!m->wc_v.empty()) return fail(m, PBNG_EINVAL, "Newton-CG does not support two-sided weak constraints");
     return newton_setup(m);
 }
 
@@ -1717,7 +1886,6 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     pbng_status s = ensure_ready(m);
     if (s) return s;
     if (!m->all_ring) return fail(m, PBNG_EINVAL, "the adjoint needs every colour in the ring layout");
-    if (!m->wc_v.empty()) return fail(m, PBNG_EINVAL, "the adjoint does not support two-sided weak constraints");
     if ((s = adjoint_setup(m))) return s;
     cudaStream_t st = m->stream;
     // u_eq -> state slot 3 (clamped vertices at their targets)
@@ -1746,9 +1914,32 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     const int32_t K = std::min<int32_t>(p->residual_every, kMaxChunk);
     if ((s = ensure_wg(m, (size_t)K))) return s;
     const std::vector<int> seq = colour_sequence(m->ncol, p->colour_order);
+    // Automatic rho (Chebyshev with rho <= 0) as in pbng_solve: plain sweeps
+    // measure q, then Chebyshev from rho(q), raised (symmetric order) or
+    // backed off (growth) with a restart of the multiplier history.
+    pbng_params cp = *p;
+    const bool auto_rho = p->accel == PBNG_ACCEL_CHEBYSHEV && !(p->rho > 0.0);
+    const bool symmetric = p->colour_order == PBNG_ORDER_SYMMETRIC;
+    const int32_t est_sweeps = std::max<int32_t>(30, 3 * K);
+    int phase = auto_rho ? 0 : 1, backoffs = 0, raises = 0;
+    int32_t mark_done = -1;
+    double mark_rel = 0.0, best = 0.0;
+    std::vector<std::pair<int32_t, double>> since;
+    if (auto_rho) cp.accel = PBNG_ACCEL_NONE;
+    auto restart = [&]() -> pbng_status {
+        for (int q = 1; q <= 2; ++q)
+            PBNG_CUDA(m, cudaMemcpyAsync(m->d_lam[q].p, lam, sizeof(float4) * (size_t)m->nv, cudaMemcpyDeviceToDevice,
+                                         st));
+        m->sweep_l = 0;
+        m->omega_l = 1.0;
+        best = 0.0;
+        since.clear();
+        return PBNG_OK;
+    };
     while (g2 > 0.0 && done < max_sweeps) {
-        const int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
-        chunk_weights(m, p, chunk, m->h_wg);
+        int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
+        if (phase == 0) chunk = std::min<int32_t>(chunk, est_sweeps - done);
+        chunk_weights(m, &cp, chunk, m->h_wg);
         PBNG_CUDA(m, cudaMemcpyAsync(m->d_wg.p, m->h_wg, sizeof(float2) * chunk, cudaMemcpyHostToDevice, st));
         for (int32_t k = 0; k < chunk; ++k) {
             for (const int c : seq)
@@ -1758,7 +1949,7 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
                                                        m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
                                                        m->model, st));
             m->kernel_launches += (int64_t)seq.size();
-            if (p->accel != PBNG_ACCEL_NONE && m->nfree > 0) {
+            if (cp.accel != PBNG_ACCEL_NONE && m->nfree > 0) {
                 const State lc{lam, lam}, l1{(float4*)m->d_lam[p1].p, (float4*)m->d_lam[p1].p},
                     l2{(float4*)m->d_lam[p2].p, (float4*)m->d_lam[p2].p};
                 PBNG_CUDA(m, launch_accel(m->nfree, lc, l1, l2, (const float2*)m->d_wg.p + k, nullptr, nullptr,
@@ -1773,6 +1964,34 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
         rel = std::sqrt(r2 / g2);
         if (!std::isfinite(rel) || rel > 1e3) { result = PBNG_EDIVERGED; break; }
         if (rel <= rel_tol) { result = PBNG_OK; break; }
+        if (!auto_rho) continue;
+        if (phase == 0) {
+            if (mark_done < 0 && 3 * done >= est_sweeps) {
+                mark_done = done;
+                mark_rel = rel;
+            } else if (done >= est_sweeps && mark_done >= 0 && done > mark_done) {
+                const double q = mark_rel > 0.0 && rel > 0.0 ? std::pow(rel / mark_rel, 1.0 / (done - mark_done)) : 0.0;
+                cp.accel = PBNG_ACCEL_CHEBYSHEV;
+                cp.rho = initial_rho(symmetric, p->gamma, q);
+                phase = 1;
+                if ((s = restart())) break;
+            }
+        } else if (cp.accel == PBNG_ACCEL_CHEBYSHEV) {
+            since.emplace_back(done, rel);
+            if (best == 0.0 || rel < best) best = rel;
+            if (rel > 4.0 * best) {
+                if (++backoffs > 4) cp.accel = PBNG_ACCEL_NONE;
+                else cp.rho = std::max(0.5, 1.0 - 2.0 * (1.0 - cp.rho));
+                if ((s = restart())) break;
+            } else if (symmetric && raises < 12) {
+                const double mu = raised_rho(since, K, cp.rho);
+                if (mu > cp.rho) {
+                    cp.rho = mu;
+                    raises++;
+                    if ((s = restart())) break;
+                }
+            }
+        }
     }
     m->sweep_l = saved_l;
     m->omega_l = saved_om;
@@ -1782,7 +2001,8 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     PBNG_CUDA(m, cudaMemsetAsync(m->d_hdl.p, 0, sizeof(float4) * (size_t)m->nv, st));
     PBNG_CUDA(m, launch_adjoint_tets(m->ne, m->nfree, (const int4*)m->d_tv.p, (const float4*)m->d_tb.p, u, lam,
                                      dL_dlogE_dev, (float*)m->d_hdl.p, st, m->model));
-    m->kernel_launches++;
+    PBNG_CUDA(m, launch_adjoint_weak_clamped((int)m->wc_v.size(), m->nfree, m->dm, lam, (float*)m->d_hdl.p, st));
+    m->kernel_launches += m->wc_v.empty() ? 1 : 2;
     if (dL_dxD_dev) {
         PBNG_CUDA(m, launch_clamped_grad((int32_t)m->dir_list.size(), (const int32_t*)m->d_dq_int.p,
                                          (const int32_t*)m->d_dq_caller.p, dLdu_dev, (const float*)m->d_hdl.p,
@@ -2060,7 +2280,7 @@ pbng_status pbng_residual(pbng_mesh* m, const float* u_dev, double* residual_out
                              state_of(m, 3), m->stream));
     m->kernel_launches++;
     std::vector<double> sq(m->ncomp);
-    if ((s = residual_sq(m, 3, true, sq.data()))) return s;
+    if ((s = residual_sq(m, 3, true, sq.data(), m->all_ring))) return s;
     for (int k = 0; k < m->ncomp; ++k) residual_out[k] = std::sqrt(sq[k]);
     return PBNG_OK;
 }
@@ -2092,7 +2312,8 @@ pbng_status pbng_residual_noalloc(pbng_mesh* m, const float* u_dev, double* resi
                              state_of(m, 3), st));
     // per-component sums accumulate atomically and start at zero (the memset
     // in enqueue_residual); every partial is written before it is summed
-    pbng_status r = enqueue_residual(m, state_of(m, 3), true, scratch, scratch, scratch + nparts, st);
+    pbng_status r = enqueue_residual(m, state_of(m, 3), true, scratch, scratch, scratch + nparts, st, m->all_ring,
+                                     true);
     if (r) return r;
     PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, multi ? scratch : scratch + nparts,
                                  sizeof(double) * (multi ? m->ncomp : 1), cudaMemcpyDeviceToHost, st));
@@ -2202,7 +2423,7 @@ pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p
     pbng_status r = ensure_ready(m);
     if (r) return r;
     cudaStream_t st = m->stream;
-    const bool comp = p->precision == PBNG_PREC_COMPENSATED;
+    const bool comp = pair_iterate(p->precision);
     const PassParams pp{(float)p->step, (float)p->skip_tol, p->model};
     const State scratch = state_of(m, 3);
     const int cap = ring_max_ctas_per_sm();
@@ -2290,6 +2511,37 @@ pbng_status pbng_get_solve_info(const pbng_mesh* m, pbng_solve_info* out) {
 
 int32_t pbng_num_components(const pbng_mesh* m) { return m ? m->ncomp : 0; }
 
+pbng_status pbng_measure_fp32_peak(void* stream, double* tflops_out) {
+    if (!tflops_out) return PBNG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return PBNG_ECUDA;
+    const int blocks = nsm * 8;  // 2048 threads per SM
+    float* out = nullptr;
+    if (cudaMalloc((void**)&out, sizeof(float) * 256 * (size_t)blocks) != cudaSuccess) return PBNG_ENOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    pbng_status r = PBNG_OK;
+    double best = 0.0;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = PBNG_ECUDA;
+    for (int rep = 0; rep < 6 && r == PBNG_OK; ++rep) {  // the first launch warms up
+        double flops = 0.0;
+        float ms = 0.0f;
+        if (pbng::fma_peak(st, out, blocks, 1 << 15, e0, e1, &flops) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            r = PBNG_ECUDA;
+            break;
+        }
+        if (rep > 0 && ms > 0.0f) best = std::max(best, flops / (ms * 1e-3) / 1e12);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(out);
+    if (r == PBNG_OK) *tflops_out = best;
+    return r;
+}
+
 const char* pbng_status_string(pbng_status s) {
     switch (s) {
         case PBNG_OK: return "ok";
@@ -2313,7 +2565,8 @@ void pbng_destroy(pbng_mesh* m) {
     DevBuf* bufs[] = {&m->d_lam[0], &m->d_lam[1], &m->d_lam[2], &m->d_gv, &m->d_diag, &m->d_hdl, &m->d_tv,
                       &m->d_tb, &m->d_dq_int, &m->d_dq_caller, &m->d_adj_partial,
                       &m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
-                      &m->d_ring, &m->d_items, &m->d_host_u,
+                      &m->d_ring, &m->d_ring_lo, &m->d_items, &m->d_host_u, &m->d_vsq, &m->d_comp_off,
+                      &m->d_comp_list,
                       &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k, &m->d_wc_off, &m->d_wc_list, &m->d_wc_v,
                       &m->d_wc_b, &m->d_wc_k, &m->d_wc_c0,

@@ -4,6 +4,7 @@
 // formed relative to the rest state so that nothing cancels as F -> I.
 #pragma once
 
+#include "pbng_ff.cuh"
 #include "pbng_internal.h"
 
 namespace pbng {
@@ -271,6 +272,62 @@ __device__ __forceinline__ void element_math_m(float3 gj1, float3 gj2, float3 gj
     }
 }
 
+// The float32 companions of the extended-precision force (pbng_ff.cuh): the
+// modified Hessian of Eq. mod_hess_dens, A = V (2 mu |g_i|^2 I + lambda w w^T)
+// with w = cof(F) g_i (upper triangle, overwritten), and the quaternion
+// estimate of the corotated polar rotation (scale 1) that the float-float
+// force refines.  Same operands as element_math_m.
+template <bool NEED_A, bool NEED_Q>
+__device__ __forceinline__ void element_fp32_parts(float3 gj1, float3 gj2, float3 gj3, float a, float b, float3 d1,
+                                                   float3 d2, float3 d3, float* A, float* q) {
+    const float g1[3] = {gj1.x, gj1.y, gj1.z}, g2[3] = {gj2.x, gj2.y, gj2.z}, g3[3] = {gj3.x, gj3.y, gj3.z};
+    const float dd1[3] = {d1.x, d1.y, d1.z}, dd2[3] = {d2.x, d2.y, d2.z}, dd3[3] = {d3.x, d3.y, d3.z};
+    float H[9];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) H[3 * p + c] = dd1[p] * g1[c] + dd2[p] * g2[c] + dd3[p] * g3[c];
+    const float F0 = 1.0f + H[0], F4 = 1.0f + H[4], F8 = 1.0f + H[8];
+    const float F1 = H[1], F2 = H[2], F3 = H[3], F5 = H[5], F6 = H[6], F7 = H[7];
+    float C[9];
+    C[0] = F4 * F8 - F5 * F7;
+    C[1] = F5 * F6 - F3 * F8;
+    C[2] = F3 * F7 - F4 * F6;
+    C[3] = F7 * F2 - F8 * F1;
+    C[4] = F8 * F0 - F6 * F2;
+    C[5] = F6 * F1 - F7 * F0;
+    C[6] = F1 * F5 - F2 * F4;
+    C[7] = F2 * F3 - F0 * F5;
+    C[8] = F0 * F4 - F1 * F3;
+    if (NEED_A) {
+        const float s[3] = {g1[0] + g2[0] + g3[0], g1[1] + g2[1] + g3[1], g1[2] + g2[2] + g3[2]};
+        float ws[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) ws[p] = C[3 * p] * s[0] + C[3 * p + 1] * s[1] + C[3 * p + 2] * s[2];
+        const float ag = a * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+        const float bw0 = b * ws[0], bw1 = b * ws[1], bw2 = b * ws[2];
+        A[0] = ag + bw0 * ws[0];
+        A[1] = bw0 * ws[1];
+        A[2] = bw0 * ws[2];
+        A[3] = ag + bw1 * ws[1];
+        A[4] = bw1 * ws[2];
+        A[5] = ag + bw2 * ws[2];
+    }
+    if (NEED_Q) {
+        const float trH = H[0] + H[4] + H[8];
+        const float Jm1 = trH + (H[0] * H[4] - H[1] * H[3] + H[0] * H[8] - H[2] * H[6] + H[4] * H[8] - H[5] * H[7]) +
+                          det3(H[0], H[1], H[2], H[3], H[4], H[5], H[6], H[7], H[8]);
+        const float Fm[9] = {F0, F1, F2, F3, F4, F5, F6, F7, F8};
+        float n2 = 0.0f, c2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            n2 += Fm[k] * Fm[k];
+            c2 += C[k] * C[k];
+        }
+        polar_quaternion(H, n2, c2, 1.0f + Jm1, 1.0f, q);
+    }
+}
+
 // The model is uniform over a launch (PassParams::model): one branch per call.
 template <bool NEED_A>
 __device__ __forceinline__ void element_math(int model, float3 gj1, float3 gj2, float3 gj3, float a, float b,
@@ -310,6 +367,50 @@ __device__ __forceinline__ void vertex_terms(const DeviceMesh& m, float4 x0, flo
             r[0] -= ks * m.pn_x;
             r[1] -= ks * m.pn_y;
             r[2] -= ks * m.pn_z;
+            if (NEED_A) {
+                A[0] += m.k_contact * m.pn_x * m.pn_x;
+                A[1] += m.k_contact * m.pn_x * m.pn_y;
+                A[2] += m.k_contact * m.pn_x * m.pn_z;
+                A[3] += m.k_contact * m.pn_y * m.pn_y;
+                A[4] += m.k_contact * m.pn_y * m.pn_z;
+                A[5] += m.k_contact * m.pn_z * m.pn_z;
+            }
+        }
+    }
+}
+
+// The same vertex terms added to a float-float force r (residuals and the
+// extended-precision passes): f^ext, and the spring and contact forces
+// formed from the float-pair displacement (u - t by TwoSum).  The contact
+// test is taken in float.
+template <bool NEED_A>
+__device__ __forceinline__ void vertex_terms_ff(const DeviceMesh& m, float4 x0, float4 x1, float3 uh, float3 ul,
+                                                ff::F2* r, float* A) {
+    r[0] = ff::add(r[0], x0.x);
+    r[1] = ff::add(r[1], x0.y);
+    r[2] = ff::add(r[2], x0.z);
+    if (x0.w != 0.0f) {
+        const ff::F2 e0 = ff::add(ff::two_sum(uh.x, -x1.x), ul.x);
+        const ff::F2 e1 = ff::add(ff::two_sum(uh.y, -x1.y), ul.y);
+        const ff::F2 e2 = ff::add(ff::two_sum(uh.z, -x1.z), ul.z);
+        r[0] = ff::sub(r[0], ff::mul(e0, x0.w));
+        r[1] = ff::sub(r[1], ff::mul(e1, x0.w));
+        r[2] = ff::sub(r[2], ff::mul(e2, x0.w));
+        if (NEED_A) { A[0] += x0.w; A[3] += x0.w; A[5] += x0.w; }
+    }
+    if (m.k_contact > 0.0f) {
+        const float sdf = x1.w + (m.pn_x * (uh.x + ul.x) + m.pn_y * (uh.y + ul.y) + m.pn_z * (uh.z + ul.z));
+        if (sdf < 0.0f) {
+            // gap n.X - d + n.u with the products exact
+            ff::F2 sd = ff::mk(x1.w);
+            sd = ff::add(sd, ff::two_prod(m.pn_x, uh.x));
+            sd = ff::add(sd, ff::two_prod(m.pn_y, uh.y));
+            sd = ff::add(sd, ff::two_prod(m.pn_z, uh.z));
+            sd = ff::add(sd, m.pn_x * ul.x + m.pn_y * ul.y + m.pn_z * ul.z);
+            const ff::F2 ks = ff::mul(sd, m.k_contact);
+            r[0] = ff::sub(r[0], ff::mul(ks, m.pn_x));
+            r[1] = ff::sub(r[1], ff::mul(ks, m.pn_y));
+            r[2] = ff::sub(r[2], ff::mul(ks, m.pn_z));
             if (NEED_A) {
                 A[0] += m.k_contact * m.pn_x * m.pn_x;
                 A[1] += m.k_contact * m.pn_x * m.pn_y;
@@ -381,6 +482,51 @@ __device__ __forceinline__ void weak_terms(const DeviceMesh& m, const State& s, 
     }
 }
 
+// The weak-constraint terms added to a float-float force r: C as the float
+// pair S + E of the error-free accumulation above, K C and beta K C in
+// float-float.
+template <bool COMP, bool NEED_A>
+__device__ __forceinline__ void weak_terms_ff(const DeviceMesh& m, const State& s, int v, ff::F2* r, float* A) {
+    if (!m.wc_off) return;
+    const int k1 = m.wc_off[v + 1];
+    for (int k = m.wc_off[v]; k < k1; ++k) {
+        const int2 e = m.wc_list[k];
+        const int c = e.x;
+        const float beta = __int_as_float(e.y);
+        const float4 c0 = m.wc_c0[2 * c], c0l = m.wc_c0[2 * c + 1];
+        float S[3] = {c0.x, c0.y, c0.z}, E[3] = {c0l.x, c0l.y, c0l.z};
+        for (int q = 0; q < 8; ++q) {
+            const int j = m.wc_v[8 * c + q];
+            if (j < 0) break;
+            const float bq = m.wc_b[8 * c + q];
+            const float4 h = s.hi[j];
+            acc_exact(S[0], E[0], bq, h.x);
+            acc_exact(S[1], E[1], bq, h.y);
+            acc_exact(S[2], E[2], bq, h.z);
+            if (COMP) {
+                const float4 l = s.lo[j];
+                E[0] += bq * l.x;
+                E[1] += bq * l.y;
+                E[2] += bq * l.z;
+            }
+        }
+        const ff::F2 C[3] = {ff::two_sum(S[0], E[0]), ff::two_sum(S[1], E[1]), ff::two_sum(S[2], E[2])};
+        const float* K = m.wc_k + 6 * c;
+        const int kk[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+            const ff::F2 KC = ff::add(ff::add(ff::mul(C[0], K[kk[p][0]]), ff::mul(C[1], K[kk[p][1]])),
+                                      ff::mul(C[2], K[kk[p][2]]));
+            r[p] = ff::sub(r[p], ff::mul(KC, beta));
+        }
+        if (NEED_A) {
+            const float b2 = beta * beta;
+#pragma unroll
+            for (int t = 0; t < 6; ++t) A[t] += b2 * K[t];
+        }
+    }
+}
+
 // hi + lo += d, keeping the pair normalised (TwoSum, then Fast2Sum).
 __device__ __forceinline__ void pair_add(float& hi, float& lo, float d) {
     const float s = __fadd_rn(hi, d);
@@ -397,6 +543,34 @@ __device__ __forceinline__ float group_sum(float v) {
 #pragma unroll
     for (int off = W / 2; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off, W);
     return v;
+}
+
+// The same W-lane sum in float-float arithmetic (the residual's vertex sums:
+// their terms are far larger than the sum near an equilibrium): the high
+// words are summed by TwoSum, their rounding errors and the low words in a
+// float (Ogita, Rump and Oishi's Sum2), normalised once at the end.
+template <int W>
+__device__ __forceinline__ ff::F2 group_sum_ff(ff::F2 v) {
+    float h = v.h, e = v.l;
+#pragma unroll
+    for (int off = W / 2; off > 0; off >>= 1) {
+        const float ho = __shfl_xor_sync(kFull, h, off, W), eo = __shfl_xor_sync(kFull, e, off, W);
+        const ff::F2 t = ff::two_sum(h, ho);
+        h = t.h;
+        e = ff::fadd(e, ff::fadd(eo, t.l));
+    }
+    return ff::quick_two_sum(h, e);
+}
+
+// |r|^2 of a float-float force in FP64.
+__device__ __forceinline__ double norm2_ff(const ff::F2* r) {
+    double q = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double v = ff::to_d(r[k]);
+        q += v * v;
+    }
+    return q;
 }
 
 // Eq. pbgn_dx / pbgn_update: Delta = step A^{-1} r (adjugate; A is SPD by

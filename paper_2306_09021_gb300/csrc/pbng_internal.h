@@ -38,6 +38,15 @@ struct __align__(16) RingBlock {
     int32_t id[32];  // internal id of the vertex's l-th 1-ring neighbour (own id when padding)
 };
 
+// Low words of the same slots (extended precision, PBNG_PREC_EXTENDED):
+// each record value x is held as the float pair hi + lo with hi the RingBlock
+// entry and lo = x - hi, so that the element constants keep about 48 bits.
+struct __align__(16) RingLoBlock {
+    float4 la[32];   // g_j1 low words (xyz), a low word
+    float4 lb[32];   // g_j2 low words (xyz), b low word
+    float4 lc[32];   // g_j3 low words (xyz), 0
+};
+
 struct DeviceMesh {
     int32_t nv;              // all vertices (free first, then clamped)
     int32_t nfree;
@@ -50,10 +59,15 @@ struct DeviceMesh {
     const float4* aux1;      // [nfree] spring target displacement (xyz), n.X - d
     const int32_t* comp;     // [nfree] component id, or nullptr for one component
     const int32_t* comp_active;  // [ncomp] 0 = frozen (converged), or nullptr
+    // Residuals of several components: each free vertex's |r|^2 goes to
+    // vsq[v] and the per-component sums follow in a fixed order
+    // (launch_comp_reduce); nullptr: atomic per-component sums instead.
+    double* vsq;
     // Ring layout (colours whose vertices all fit 32 lanes): one 32-slot
     // item per warp; vertex v of a lane-width-W run owns W consecutive slots.
     // Slot s is entry s % 32 of block s / 32 (RingBlock).
     const struct RingBlock* ring;  // [nslots / 32]
+    const struct RingLoBlock* ring_lo;  // [nslots / 32] low words of the same records
     // Test hook (pbng_test_set_copy_shortfall): bytes that each warp's first
     // record copy of a ring pass is expected to carry beyond its size, so
     // that its bounded wait runs out; 0 in normal use.
@@ -128,6 +142,9 @@ cudaError_t launch_residual(const DeviceMesh& m, State s, const SegmentTable& t,
                             double* block_partial, double* comp_sq, int32_t ncomp,
                             float* r_out, int model, cudaStream_t st);
 cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStream_t st);
+// out[c] = sum of vsq[list[k]] for k in off[c] .. off[c + 1], in a fixed order.
+cudaError_t launch_comp_reduce(int32_t ncomp, const int32_t* off, const int32_t* list, const double* vsq,
+                               double* out, cudaStream_t st);
 cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, const float2* wg,
                          const int32_t* comp, const int32_t* comp_active, bool compensated, cudaStream_t st);
 cudaError_t launch_load(int32_t nv, int32_t nfree, const float* u_user, const int32_t* perm,
@@ -159,11 +176,13 @@ struct RingSched {
 int ring_warps(int nitems);
 int ring_max_ctas_per_sm();
 cudaError_t ring_prepare();  // sets kernel attributes (call outside stream capture)
+// extended: float-float element forces from the float-pair records (needs
+// compensated and ring_lo), summed in FP64 (pbng_ff.cuh).
 cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
-                             bool compensated, RingSched sc, int32_t* err, cudaStream_t st);
+                             bool compensated, RingSched sc, int32_t* err, cudaStream_t st, bool extended = false);
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
                                  bool compensated, double* warp_partial, double* comp_sq, int model,
-                                 int32_t* err, cudaStream_t st);
+                                 int32_t* err, cudaStream_t st, bool extended = false);
 
 // Equilibrium adjoint (pbng_adjoint.cu).  Vertex kernels: one warp per
 // ring item; mode 0 computes the 3x3 diagonal blocks of H, mode 1 is one
@@ -200,8 +219,18 @@ cudaError_t launch_scatter_vec(int nv, int nfree, const int32_t* perm, const flo
 cudaError_t launch_adjoint_tets(int ne, int nfree, const int4* tv, const float4* tb, State u, const float4* lam,
                                 float* dLdlogE, float* hdl, cudaStream_t st, int model = 0);
 cudaError_t launch_gather_rhs(int nfree, const int32_t* perm, const float* dLdu, float4* gv, cudaStream_t st);
+// The two-sided weak constraints' part of H_DF lam (into hdl, float4 rows).
+cudaError_t launch_adjoint_weak_clamped(int nwc, int nfree, const DeviceMesh& m, const float4* lam, float* hdl,
+                                        cudaStream_t st);
 cudaError_t launch_clamped_grad(int nd, const int32_t* dq_internal, const int32_t* dq_caller, const float* dLdu,
                                 const float* hdl, float* out, cudaStream_t st);
+
+// FP32 FMA throughput probe (pbng_kernels.cu): one launch of `blocks` CTAs
+// of 256 threads, each running `iters` rounds of independent FMA chains into
+// out[blocks * 256], bracketed by events e0 / e1 on st; *flops = the flops
+// it executes.
+cudaError_t fma_peak(cudaStream_t st, float* out, int blocks, int iters, cudaEvent_t e0, cudaEvent_t e1,
+                     double* flops);
 
 // Fixed device scratch of the allocation-free residual (pbng_kernels.cu).
 int noalloc_scratch_capacity();

@@ -13,7 +13,8 @@
 // strains, everything is formed relative to the rest state: H = F - I from
 // displacement differences, J - 1 from the invariants of H, and R - I of the
 // polar rotation from a quaternion whose vector part carries the rotation.
-// Residual norms are accumulated in float64.
+// Residuals sum each vertex's element terms, its vertex terms and the norms
+// in float64.
 #include "pbng_element.cuh"
 #include "pbng_internal.h"
 #include "pbng_launch.cuh"
@@ -57,24 +58,30 @@ __device__ __forceinline__ void vertex_group(const DeviceMesh& m, State s, int v
         el::element_math<UPDATE>(pp.model, make_float3(rb.x, rb.y, rb.z), make_float3(rc.x, rc.y, rc.z),
                                  make_float3(rc.w, rd.x, rd.y), ra.w, rb.w, d1, d2, d3, r, A);
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) r[k] = el::group_sum<W>(r[k]);
-    if (UPDATE) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
-    }
-    if (!active || lane != 0) return;
-    el::vertex_terms<COMP, UPDATE>(m, __ldg(m.aux0 + v), __ldg(m.aux1 + v), uh, ul, r, A);
-    el::weak_terms<COMP, UPDATE>(m, s, v, r, A);
     if (!UPDATE) {
-        *rr = (double)r[0] * r[0] + (double)r[1] * r[1] + (double)r[2] * r[2];
+        // residual: the W-lane sum of the float32 element terms and the
+        // vertex terms in float-float
+        ff::F2 rf[3] = {ff::mk(r[0]), ff::mk(r[1]), ff::mk(r[2])};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) rf[k] = el::group_sum_ff<W>(rf[k]);
+        if (!active || lane != 0) return;
+        el::vertex_terms_ff<false>(m, __ldg(m.aux0 + v), __ldg(m.aux1 + v), uh, ul, rf, A);
+        el::weak_terms_ff<COMP, false>(m, s, v, rf, A);
+        *rr = el::norm2_ff(rf);
         if (r_out) {
-            r_out[3 * v] = r[0];
-            r_out[3 * v + 1] = r[1];
-            r_out[3 * v + 2] = r[2];
+            r_out[3 * v] = rf[0].h + rf[0].l;
+            r_out[3 * v + 1] = rf[1].h + rf[1].l;
+            r_out[3 * v + 2] = rf[2].h + rf[2].l;
         }
         return;
     }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] = el::group_sum<W>(r[k]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
+    if (!active || lane != 0) return;
+    el::vertex_terms<COMP, UPDATE>(m, __ldg(m.aux0 + v), __ldg(m.aux1 + v), uh, ul, r, A);
+    el::weak_terms<COMP, UPDATE>(m, s, v, r, A);
     if (m.comp_active && !m.comp_active[m.comp[v]]) return;  // frozen (converged) component
     el::solve_and_write<COMP>(s, v, uh, ul, r, A, pp, err);
 }
@@ -125,7 +132,10 @@ __global__ void __launch_bounds__(kBlock) residual_kernel(const DeviceMesh m, St
     if (comp_sq) {
         const int tid = (blockIdx.x - sg->block_begin) * kBlock + threadIdx.x;
         const int v = sg->v_begin + tid / sg->width;
-        if (rr != 0.0 && v < sg->v_end) atomicAdd(comp_sq + m.comp[v], rr);
+        if (v < sg->v_end && (tid & (sg->width - 1)) == 0) {
+            if (m.vsq) m.vsq[v] = rr;  // summed per component in a fixed order afterwards
+            else if (rr != 0.0) atomicAdd(comp_sq + m.comp[v], rr);
+        }
         return;
     }
     // Block sum in a fixed order (warp shuffles, then shared memory).
@@ -154,6 +164,28 @@ __global__ void reduce_kernel(const double* partial, int n, double* out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = sh[0];
+}
+
+// Per-component sums of the vertices' |r|^2 in a fixed order, so that a
+// batch's residuals (and its per-mesh stopping decisions) are the same bits
+// on every run: one block per component sums vsq over its vertex list
+// (internal ids) with a fixed thread-to-entry assignment and tree.
+__global__ void __launch_bounds__(256) comp_reduce_kernel(const int32_t* __restrict__ off,
+                                                          const int32_t* __restrict__ list,
+                                                          const double* __restrict__ vsq, double* out) {
+    pdl_release();
+    pdl_wait();
+    const int c = blockIdx.x;
+    double acc = 0.0;
+    for (int k = off[c] + threadIdx.x; k < off[c + 1]; k += blockDim.x) acc += vsq[list[k]];
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = sh[0];
 }
 
 // Section "Acceleration Techniques", applied after a whole sweep:
@@ -264,6 +296,12 @@ cudaError_t launch_reduce(const double* partial, int32_t n, double* out, cudaStr
     return launch_kernel(reduce_kernel, 1, 1024, 0, st, partial, (int)n, out);
 }
 
+cudaError_t launch_comp_reduce(int32_t ncomp, const int32_t* off, const int32_t* list, const double* vsq,
+                               double* out, cudaStream_t st) {
+    if (ncomp <= 0) return cudaSuccess;
+    return launch_kernel(comp_reduce_kernel, ncomp, 256, 0, st, off, list, vsq, out);
+}
+
 cudaError_t launch_accel(int32_t nfree, State cur, State p1, State p2, const float2* wg,
                          const int32_t* comp, const int32_t* comp_active, bool compensated, cudaStream_t st) {
     if (nfree <= 0) return cudaSuccess;
@@ -324,6 +362,37 @@ cudaError_t launch_copy_state(int32_t n, State src, State dst, cudaStream_t st) 
     if (n <= 0) return cudaSuccess;
     copy_state_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, src, dst);
     return cudaGetLastError();
+}
+
+// FP32 FMA throughput probe (the roofline denominator of float32 element
+// arithmetic): every thread runs kFmaChains independent FMA chains, enough
+// to cover the FMA pipe's latency at full occupancy; one FMA = 2 flops.
+constexpr int kFmaChains = 8;
+
+__global__ void __launch_bounds__(256) fma_peak_kernel(float* out, int iters, float a, float b) {
+    float x[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) x[k] = (float)(threadIdx.x + k) * 1e-3f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < kFmaChains; ++k) x[k] = __fmaf_rn(x[k], a, b);
+    }
+    float sum = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) sum += x[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = sum;  // keeps the chains live
+}
+
+cudaError_t fma_peak(cudaStream_t st, float* out, int blocks, int iters, cudaEvent_t e0, cudaEvent_t e1,
+                     double* flops) {
+    cudaError_t e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+        fma_peak_kernel<<<blocks, 256, 0, st>>>(out, iters, 0.999999f, 1e-7f);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    *flops = 2.0 * kFmaChains * (double)iters * (double)blocks * 256.0;
+    return e;
 }
 
 }  // namespace pbng

@@ -29,6 +29,7 @@
 // nothing that another update of the same pass reads.
 #include "pbng_async.cuh"
 #include "pbng_element.cuh"
+#include "pbng_ff.cuh"
 #include "pbng_internal.h"
 #include "pbng_launch.cuh"
 
@@ -50,6 +51,9 @@ constexpr int kRecAhead = kRecStages - 1;
 constexpr int kGatStages = 2;
 constexpr int kItemVerts = kRingLanes / 4;
 constexpr int kCtasPerSm = 3;
+// Extended-precision passes (float-float element forces) need more registers
+// than 3 CTAs of 8 warps leave.
+constexpr int kCtasPerSmExt = 2;
 constexpr int kQueue = 32;   // deferred vertex updates per warp
 
 using RecStage = RingBlock;
@@ -105,8 +109,9 @@ __device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, Warp
 }
 
 // All lanes: gather the 1-ring displacements and own-vertex data of the item
-// in record stage r into gather stage g.
-template <bool COMP, bool UPDATE>
+// in record stage r into gather stage g.  AUX: also the vertices' aux data
+// (passes that add the vertex terms when the element sums are done).
+template <bool COMP, bool AUX>
 __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& s, WarpSmem& S, int r, int g,
                                               int lane) {
     const Item it = S.desc[r];
@@ -119,7 +124,7 @@ __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& 
         const int v = it.v0 + lane;
         cp_async16(G.oh + lane, s.hi + v);
         if (COMP) cp_async16(G.ol + lane, s.lo + v);
-        if (!UPDATE) {  // update passes add the vertex terms when the queue is flushed
+        if (AUX) {  // the float32 update passes add the vertex terms when the queue is flushed
             cp_async16(G.a0 + lane, m.aux0 + v);
             cp_async16(G.a1 + lane, m.aux1 + v);
         }
@@ -195,6 +200,81 @@ __device__ __forceinline__ uint32_t butterfly_table(int lane) {
     return t;
 }
 
+// A vertex's |r|^2: into the warp's partial (one component), the vertex's
+// slot of m.vsq (several components, summed per component in a fixed order
+// afterwards), or atomically into its component's sum (several components,
+// no slots: the allocation-free residual).
+__device__ __forceinline__ void store_sq(const DeviceMesh& m, int v, double q, double& rr, double* comp_sq) {
+    if (!comp_sq) rr += q;
+    else if (m.vsq) m.vsq[v] = q;
+    else atomicAdd(comp_sq + m.comp[v], q);
+}
+
+// Extended precision: the element force of the lane's slot in float-float
+// arithmetic from float-pair records and displacements (pbng_ff.cuh), its
+// W-lane sum and the vertex terms in float-float too; the modified Hessian
+// stays float32.  UPDATE: the group's first lane solves and writes its vertex at
+// once (Eq. pbgn_dx, Eq. pbgn_update).  Otherwise: |r|^2 of the vertex.
+template <int W, bool UPDATE, int MODEL>
+__device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
+                                                 int g, int lane, PassParams pp, int32_t* err, double& rr,
+                                                 double* comp_sq) {
+    const RecStage& R = S.rec[r];
+    const GatStage& G = S.gat[g];
+    const int j = lane / W;
+    const bool active = j < it.nv;
+    float3 uh = make_float3(0.f, 0.f, 0.f), ul = uh;
+    // u_j - u_i as an exact float pair: (hi_j - hi_i) by TwoSum, plus the low words
+    ff::F2 dv[3] = {ff::mk(0.f), ff::mk(0.f), ff::mk(0.f)};
+    if (active) {
+        uh = f3(G.oh[j]);
+        ul = f3(G.ol[j]);
+        const float4 hj = G.nh[lane], lj = G.nl[lane];
+        dv[0] = ff::add(ff::two_sum(hj.x, -uh.x), ff::fadd(lj.x, -ul.x));
+        dv[1] = ff::add(ff::two_sum(hj.y, -uh.y), ff::fadd(lj.y, -ul.y));
+        dv[2] = ff::add(ff::two_sum(hj.z, -uh.z), ff::fadd(lj.z, -ul.z));
+    }
+    const float4 ra = R.ra[lane], rb = R.rb[lane], rc = R.rc[lane];
+    const RingLoBlock& L = m.ring_lo[it.slot0 >> 5];
+    const float4 la = L.la[lane], lb = L.lb[lane], lc = L.lc[lane];
+    const int loc = __float_as_int(rc.w);
+    const int base = lane & ~(W - 1);
+    const int src[3] = {base + (loc & 255), base + ((loc >> 8) & 255), base + ((loc >> 16) & 255)};
+    ff::F2 d[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            d[k][c] = ff::mk(__shfl_sync(kFull, dv[c].h, src[k]), __shfl_sync(kFull, dv[c].l, src[k]));
+    const ff::F2 gg[3][3] = {{ff::mk(ra.x, la.x), ff::mk(ra.y, la.y), ff::mk(ra.z, la.z)},
+                             {ff::mk(rb.x, lb.x), ff::mk(rb.y, lb.y), ff::mk(rb.z, lb.z)},
+                             {ff::mk(rc.x, lc.x), ff::mk(rc.y, lc.y), ff::mk(rc.z, lc.z)}};
+    float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float q[4] = {1.f, 0.f, 0.f, 0.f};
+    el::element_fp32_parts<UPDATE, MODEL == el::kCorotated>(
+        f3(ra), f3(rb), f3(rc), ra.w, rb.w, make_float3(d[0][0].h, d[0][1].h, d[0][2].h),
+        make_float3(d[1][0].h, d[1][1].h, d[1][2].h), make_float3(d[2][0].h, d[2][1].h, d[2][2].h), A, q);
+    ff::F2 f[3];
+    ff::element_force<MODEL>(gg, ff::mk(ra.w, la.w), ff::mk(rb.w, lb.w), d, q, f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = el::group_sum_ff<W>(f[k]);
+    if (UPDATE) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
+    }
+    if (!active || (lane & (W - 1)) != 0) return;
+    const int v = it.v0 + j;
+    el::vertex_terms_ff<UPDATE>(m, G.a0[j], G.a1[j], uh, ul, f, A);
+    el::weak_terms_ff<true, UPDATE>(m, s, v, f, A);
+    if constexpr (UPDATE) {
+        if (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) return;  // frozen vertex of a mixed item
+        const float rf[3] = {f[0].h + f[0].l, f[1].h + f[1].l, f[2].h + f[2].l};
+        el::solve_and_write<true>(s, v, uh, ul, rf, A, pp, err);
+    } else {
+        store_sq(m, v, el::norm2_ff(f), rr, comp_sq);
+    }
+}
+
 template <int W, bool COMP, bool UPDATE, int MODEL>
 __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
                                                int g, int lane, uint32_t btab, int qn, double& rr,
@@ -238,23 +318,34 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
         // a frozen vertex of a mixed item is not written
         S.q.v[e] = (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) ? -1 : v;
     } else {
+        // the element terms of the lane in float32, their W-lane sum and the
+        // vertex terms in float-float
+        ff::F2 rf[3] = {ff::mk(rv[0]), ff::mk(rv[1]), ff::mk(rv[2])};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) rv[k] = el::group_sum<W>(rv[k]);
+        for (int k = 0; k < 3; ++k) rf[k] = el::group_sum_ff<W>(rf[k]);
         if (!active || (lane & (W - 1)) != 0) return;
         const int v = it.v0 + j;
-        el::vertex_terms<COMP, UPDATE>(m, G.a0[j], G.a1[j], uh, ul, rv, A);
-        el::weak_terms<COMP, false>(m, s, v, rv, A);
-        const double q = (double)rv[0] * rv[0] + (double)rv[1] * rv[1] + (double)rv[2] * rv[2];
-        if (comp_sq) atomicAdd(comp_sq + m.comp[v], q);
-        else rr += q;
+        el::vertex_terms_ff<false>(m, G.a0[j], G.a1[j], uh, COMP ? ul : zero3, rf, A);
+        el::weak_terms_ff<COMP, false>(m, s, v, rf, A);
+        store_sq(m, v, el::norm2_ff(rf), rr, comp_sq);
     }
 }
 
 // The lane width is uniform over an item: dispatch once per item.
-template <bool COMP, bool UPDATE, int MODEL>
+template <bool COMP, bool UPDATE, int MODEL, bool EXT>
 __device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
-                                             int g, int lane, uint32_t btab, int qn, double& rr, double* comp_sq) {
+                                             int g, int lane, uint32_t btab, int qn, double& rr, double* comp_sq,
+                                             PassParams pp, int32_t* err) {
     if (it.skip) return;  // uniform over the warp
+    if constexpr (EXT) {
+        switch (it.w) {
+            case 4: compute_item_ext<4, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
+            case 8: compute_item_ext<8, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
+            case 16: compute_item_ext<16, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
+            default: compute_item_ext<32, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
+        }
+        return;
+    }
     switch (it.w) {
         case 4: compute_item_w<4, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
         case 8: compute_item_w<8, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
@@ -291,10 +382,14 @@ __device__ __forceinline__ void flush_queue(const DeviceMesh& m, State s, const 
 // blocked (warp gw takes a contiguous run of ceil(nitems / nw) items).  The
 // order only decides which warp updates which vertices of one colour; the
 // updates of a colour are independent, so the iterate is the same.
-template <bool COMP, bool UPDATE, int MODEL>
-__global__ void __launch_bounds__(kBlock, kCtasPerSm)
+// EXT: extended precision (compute_item_ext; COMP must be true).
+template <bool COMP, bool UPDATE, int MODEL, bool EXT>
+__global__ void __launch_bounds__(kBlock, EXT ? kCtasPerSmExt : kCtasPerSm)
     ring_kernel(const DeviceMesh m, State s, const Item* __restrict__ items, int nitems, PassParams pp,
                 int32_t* err, double* partial, double* comp_sq, int blocked) {
+    static_assert(!EXT || COMP, "extended precision keeps the iterate as a float pair");
+    constexpr bool AUX = !UPDATE || EXT;
+    constexpr bool QUEUE = UPDATE && !EXT;
     extern __shared__ __align__(128) unsigned char smem[];
     pdl_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -313,7 +408,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         n = gw < nitems ? (nitems - gw + nw - 1) / nw : 0;
     }
     double rr = 0.0;
-    const uint32_t btab = UPDATE ? butterfly_table(lane) : 0u;
+    const uint32_t btab = QUEUE ? butterfly_table(lane) : 0u;
     int qn = 0;                  // queued vertex updates (warp-uniform)
     int issued = 0, waited = 0;  // items whose records were requested / awaited
     bool ok = true;
@@ -334,7 +429,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         ok = mbar_wait(S.bar + 0, 0);
         waited = ok ? 1 : 0;  // a stage whose wait gave up is drained again on abort
         if (__any_sync(kFull, !ok)) goto abort;
-        issue_gathers<COMP, UPDATE>(m, s, S, 0, 0, lane);
+        issue_gathers<COMP, AUX>(m, s, S, 0, 0, lane);
         cp_async_commit();
         for (int k = 0; k < n; ++k) {
             // Record stage (k + kRecAhead) % kRecStages and gather stage
@@ -352,16 +447,16 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
             if (k + 1 < n) {
                 ok = mbar_wait(S.bar + (k + 1) % kRecStages, ((k + 1) / kRecStages) & 1);
                 waited = ok ? k + 2 : k + 1;
-                if (ok) issue_gathers<COMP, UPDATE>(m, s, S, (k + 1) % kRecStages, (k + 1) % kGatStages, lane);
+                if (ok) issue_gathers<COMP, AUX>(m, s, S, (k + 1) % kRecStages, (k + 1) % kGatStages, lane);
             }
             cp_async_commit();
             cp_async_wait<1>();  // this lane's gathers of item k have landed
             if (__any_sync(kFull, !ok)) goto abort;
             __syncwarp();        // ... and the other lanes'
             const Item it = S.desc[k % kRecStages];
-            compute_item<COMP, UPDATE, MODEL>(m, s, S, it, k % kRecStages, k % kGatStages, lane, btab, qn, rr,
-                                              comp_sq);
-            if (UPDATE) {
+            compute_item<COMP, UPDATE, MODEL, EXT>(m, s, S, it, k % kRecStages, k % kGatStages, lane, btab, qn, rr,
+                                                   comp_sq, pp, err);
+            if (QUEUE) {
                 if (!it.skip) qn += it.nv;
                 if (qn > kQueue - kItemVerts || (k + 1 == n && qn > 0)) {
                     flush_queue<COMP>(m, s, S, qn, lane, pp, err);
@@ -403,9 +498,9 @@ int sm_count() {
     return cached[dev];
 }
 
-int ring_ctas(int nitems, int ctas_per_sm, int balanced = 0) {
+int ring_ctas(int nitems, int ctas_per_sm, int balanced = 0, int max_cps = kCtasPerSm) {
     const int want = (nitems + kWarps - 1) / kWarps;
-    const int cps = ctas_per_sm < 1 ? 1 : (ctas_per_sm > kCtasPerSm ? kCtasPerSm : ctas_per_sm);
+    const int cps = ctas_per_sm < 1 ? 1 : (ctas_per_sm > max_cps ? max_cps : ctas_per_sm);
     const int cap = cps * sm_count();
     int grid = want < cap ? want : cap;
     if (balanced && grid > 0) {
@@ -417,20 +512,23 @@ int ring_ctas(int nitems, int ctas_per_sm, int balanced = 0) {
     return grid;
 }
 
-template <bool COMP, bool UPDATE>
+template <bool COMP, bool UPDATE, bool EXT = false>
 cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams pp,
                         int32_t* err, double* partial, double* comp_sq, RingSched sc, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const int bytes = kWarps * (int)sizeof(WarpSmem);  // attribute set by ring_prepare()
-    const int grid = ring_ctas(nitems, sc.ctas_per_sm, sc.balanced);
+    // An extended residual writes the partials of the float32 residual's grid
+    // (2 CTAs per SM are resident, the rest follow); an extended update pass
+    // keeps its grid to what is resident.
+    const int grid = ring_ctas(nitems, sc.ctas_per_sm, sc.balanced, (EXT && UPDATE) ? kCtasPerSmExt : kCtasPerSm);
     if (pp.model == el::kNeoHookean)
-        return launch_kernel(ring_kernel<COMP, UPDATE, el::kNeoHookean>, grid, kBlock, bytes, st, m, s, items, nitems,
-                             pp, err, partial, comp_sq, sc.blocked);
-    if (pp.model == el::kStableNeoHookean)
-        return launch_kernel(ring_kernel<COMP, UPDATE, el::kStableNeoHookean>, grid, kBlock, bytes, st, m, s, items,
+        return launch_kernel(ring_kernel<COMP, UPDATE, el::kNeoHookean, EXT>, grid, kBlock, bytes, st, m, s, items,
                              nitems, pp, err, partial, comp_sq, sc.blocked);
-    return launch_kernel(ring_kernel<COMP, UPDATE, el::kCorotated>, grid, kBlock, bytes, st, m, s, items, nitems, pp,
-                         err, partial, comp_sq, sc.blocked);
+    if (pp.model == el::kStableNeoHookean)
+        return launch_kernel(ring_kernel<COMP, UPDATE, el::kStableNeoHookean, EXT>, grid, kBlock, bytes, st, m, s,
+                             items, nitems, pp, err, partial, comp_sq, sc.blocked);
+    return launch_kernel(ring_kernel<COMP, UPDATE, el::kCorotated, EXT>, grid, kBlock, bytes, st, m, s, items, nitems,
+                         pp, err, partial, comp_sq, sc.blocked);
 }
 
 }  // namespace
@@ -443,13 +541,16 @@ cudaError_t ring_prepare() {
     // Three CTAs of 8 warps with their per-warp stages and queues need almost
     // all of an SM's shared memory: ask for the largest carveout.
     const int bytes = kWarps * (int)sizeof(WarpSmem);
-    const void* fns[12] = {
-        (const void*)ring_kernel<true, true, 0>,  (const void*)ring_kernel<false, true, 0>,
-        (const void*)ring_kernel<true, false, 0>, (const void*)ring_kernel<false, false, 0>,
-        (const void*)ring_kernel<true, true, 1>,  (const void*)ring_kernel<false, true, 1>,
-        (const void*)ring_kernel<true, false, 1>, (const void*)ring_kernel<false, false, 1>,
-        (const void*)ring_kernel<true, true, 2>,  (const void*)ring_kernel<false, true, 2>,
-        (const void*)ring_kernel<true, false, 2>, (const void*)ring_kernel<false, false, 2>};
+    const void* fns[18] = {
+        (const void*)ring_kernel<true, true, 0, false>,  (const void*)ring_kernel<false, true, 0, false>,
+        (const void*)ring_kernel<true, false, 0, false>, (const void*)ring_kernel<false, false, 0, false>,
+        (const void*)ring_kernel<true, true, 1, false>,  (const void*)ring_kernel<false, true, 1, false>,
+        (const void*)ring_kernel<true, false, 1, false>, (const void*)ring_kernel<false, false, 1, false>,
+        (const void*)ring_kernel<true, true, 2, false>,  (const void*)ring_kernel<false, true, 2, false>,
+        (const void*)ring_kernel<true, false, 2, false>, (const void*)ring_kernel<false, false, 2, false>,
+        (const void*)ring_kernel<true, true, 0, true>,   (const void*)ring_kernel<true, false, 0, true>,
+        (const void*)ring_kernel<true, true, 1, true>,   (const void*)ring_kernel<true, false, 1, true>,
+        (const void*)ring_kernel<true, true, 2, true>,   (const void*)ring_kernel<true, false, 2, true>};
     for (const void* f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e == cudaSuccess)
@@ -460,17 +561,25 @@ cudaError_t ring_prepare() {
 }
 
 cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
-                             bool compensated, RingSched sc, int32_t* err, cudaStream_t st) {
+                             bool compensated, RingSched sc, int32_t* err, cudaStream_t st, bool extended) {
+    if (extended) {
+        if (!compensated || !m.ring_lo) return cudaErrorInvalidValue;
+        return launch_impl<true, true, true>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
+    }
     if (compensated) return launch_impl<true, true>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
     return launch_impl<false, true>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
 }
 
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
                                  bool compensated, double* warp_partial, double* comp_sq, int model, int32_t* err,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, bool extended) {
     const PassParams pp{1.f, 0.f, model};
     const RingSched sc{kCtasPerSm, 0, 0};  // ring_warps() partials
     double* part = comp_sq ? nullptr : warp_partial;
+    if (extended) {
+        if (!compensated || !m.ring_lo) return cudaErrorInvalidValue;
+        return launch_impl<true, false, true>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
+    }
     if (compensated) return launch_impl<true, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
     return launch_impl<false, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
 }

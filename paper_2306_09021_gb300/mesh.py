@@ -24,7 +24,7 @@ def _iptr(a):
 def default_params(**kw):
     """pbng_default_params, then overrides: model ('corotated'|'neohookean'|
     'stable_neohookean'), accel ('none'|'chebyshev'|'sor'), precision
-    ('fp32'|'compensated'), omega, rho, gamma, step, skip_tol, residual_every,
+    ('fp32'|'compensated'|'extended'|'auto'), omega, rho, gamma, step, skip_tol, residual_every,
     resume, kernel_path, colour_order ('forward'|'symmetric')."""
     p = PbngParams()
     load().pbng_default_params(ctypes.byref(p))
@@ -53,6 +53,13 @@ def _check_u(u, nv):
     if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dtype == torch.float32
             and u.is_contiguous() and tuple(u.shape) == (nv, 3)):
         raise ValueError(f"u must be a contiguous float32 CUDA tensor of shape ({nv}, 3)")
+
+
+def measure_fp32_peak(stream=None):
+    """pbng_measure_fp32_peak: FP32 FMA throughput of the current device, TFLOP/s."""
+    out = ctypes.c_double()
+    check(load().pbng_measure_fp32_peak(_stream_ptr(stream), ctypes.byref(out)), "pbng_measure_fp32_peak")
+    return out.value
 
 
 class Mesh:
@@ -266,7 +273,11 @@ class Mesh:
         """pbng_get_solve_info of the last solve as a dict."""
         i = PbngSolveInfo()
         check(load().pbng_get_solve_info(self.h, ctypes.byref(i)), "pbng_get_solve_info", self.h)
-        return {k: getattr(i, k) for k, _ in PbngSolveInfo._fields_}
+        out = {k: getattr(i, k) for k, _ in PbngSolveInfo._fields_}
+        n = i.nevents
+        out["event_sweep"] = list(i.event_sweep)[:n]
+        out["event_rho"] = list(i.event_rho)[:n]
+        return out
 
     def residual(self, u):
         """pbng_residual: absolute FP64 residual norms per component."""

@@ -11,6 +11,11 @@ import workloads as W
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+# The float32 adjoint sweep (true Hessian applied in float32) reaches a
+# relative residual near 1e-5 and no lower on these blocks; 3e-5 is well
+# inside the gradient tolerance (2e-3) below.
+ADJ_TOL = 3e-5
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _cuda():
@@ -47,7 +52,7 @@ def _loss(model, p, log_e, xd, top, target):
 def test_autograd_matches_dense_oracle_adjoint(oracle_mod, energy):
     from paper_2306_09021_gb300 import EquilibriumModel
     p, log_e, xd, top, target = _setup()
-    model = EquilibriumModel(p, rel_tol=1e-6, model=energy)
+    model = EquilibriumModel(p, rel_tol=1e-6, model=energy, adjoint_tol=ADJ_TOL)
     L, le, xdt = _loss(model, p, log_e, xd, top, target)
     L.backward()
     # oracle: same log E and boundary, Newton equilibrium, dense adjoint
@@ -70,7 +75,7 @@ def test_autograd_matches_dense_oracle_adjoint(oracle_mod, energy):
 def test_autograd_matches_finite_differences():
     from paper_2306_09021_gb300 import EquilibriumModel
     p, log_e, xd, top, target = _setup(n=4, seed=5)
-    model = EquilibriumModel(p, rel_tol=1e-6, max_sweeps=30000)
+    model = EquilibriumModel(p, rel_tol=1e-6, max_sweeps=30000, adjoint_tol=ADJ_TOL)
     L, le, xdt = _loss(model, p, log_e, xd, top, target)
     L.backward()
     gE, gD = le.grad.cpu().numpy(), xdt.grad.cpu().numpy()

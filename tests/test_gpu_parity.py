@@ -390,7 +390,9 @@ def test_host_buffer_sweep_equals_device_sweep(pinned):
     residual that pbng_residual reports for the result."""
     from paper_2306_09021_gb300 import Mesh, default_params
     p = W.twist_block(8, 60.0, 0.2)
-    params = default_params(accel="chebyshev")
+    # pbng_residual evaluates the element forces in extended precision, so
+    # the sweeps' residuals are taken in that precision too
+    params = default_params(accel="chebyshev", precision="extended")
     m = Mesh.from_problem(p)
     u_dev = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
     r_start = m.residual(u_dev)[0]
@@ -431,6 +433,50 @@ def _full_size_case(name):
         return p, None, {}
     model = {"sag64_nh": "neohookean", "sag64_snh": "stable_neohookean"}[name]
     return W.gravity_sag(64), None, {"model": model}
+
+
+@pytest.mark.parametrize("name,kw", [
+    ("sag64", dict(accel="chebyshev")),
+    ("sag64_symmetric", dict(accel="chebyshev", rho=0.999, colour_order="symmetric")),
+    ("bar", dict(accel="none", precision="extended")),
+], ids=["sag64_chebyshev", "sag64_symmetric_chebyshev", "bar_plain_without_plane_extended"])
+def test_full_size_trajectory_matches_the_oracle(oracle_mod, name, kw):
+    """Every position after 30 sweeps from x^0 at full size, in the benchmark's
+    launch configuration (Eq. pbgn_update colour by colour, Section "Coloring
+    and Parallelism"; acceleration after each sweep, Section "Acceleration
+    Techniques"): the 64^3 gravity-sag cube (274,625 vertices, 1,310,720
+    tets) with Chebyshev rho = 0.95 in ascending and rho = 0.999 in symmetric
+    colour order, and the 40x40x200 bar (1.6 M tets, lognormal E, 2 % of the
+    vertices on springs) with plain sweeps.  The bar runs without its contact
+    plane here: with k_n = 1e8 a vertex in contact settles within about 1e-11
+    of the plane, below float32 resolution of its position, so whether the
+    penalty is active (n.x < d) is decided differently in float32 and FP64
+    and the two trajectories part (1.5e-2 after 30 sweeps); the plane is
+    covered by the ragged-bar trajectory and the sampled full-size step.  Its
+    springs pull single vertices 5 cm on 5 mm elements, which inverts
+    elements around them; there the float32 element forces leave the
+    trajectory 2.3e-4 from the oracle's after 30 sweeps, so the bar runs in
+    extended precision (float-float element forces).
+    The oracle runs on every host core (its colour loop parallelises without
+    changing a bit)."""
+    import os
+    if name == "bar":
+        p = W.contact_bar()
+        p.plane, p.k_contact = None, 0.0
+    else:
+        p = W.gravity_sag(64)
+    sweeps = 30
+    _, x, rel = _gpu_run(p, sweeps, **kw)
+    om = _oracle(oracle_mod, p)
+    threads = oracle_mod.threads_available(os.cpu_count() or 1)
+    okw = {k: v for k, v in kw.items() if k not in ("colour_order", "precision")}
+    xr, st = om.sweeps(p.x0, sweeps, threads=threads, order=kw.get("colour_order", "forward"), **okw)
+    assert st == 0
+    err = _pos_err(x, xr, p.X)
+    rr = om.residual(xr) / om.residual(p.x0)
+    print(f"{name} {sweeps} sweeps: pos err {err:.2e}, rel residual gpu {rel[0]:.4e} oracle {rr:.4e}")
+    assert err <= POS_TOL
+    assert abs(rel[0] - rr) <= 1e-3 * rr
 
 
 @pytest.mark.parametrize("name", ["bar", "blocks", "batched", "adjoint_case", "sag64_nh", "sag64_snh"])
@@ -485,7 +531,7 @@ def test_host_buffer_sweep_on_a_batch_reports_every_component():
     from paper_2306_09021_gb300 import Mesh, default_params
     probs = W.batched_blocks(count=3, side_lo=3, side_hi=6, seed=9)
     p, mid, _ = W.concat_problems(probs)
-    params = default_params(accel="chebyshev")
+    params = default_params(accel="chebyshev", precision="extended")  # as pbng_residual
     m = Mesh.from_problem(p, mesh_id=mid)
     u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
     r_start = m.residual(u)

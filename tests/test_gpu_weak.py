@@ -115,3 +115,46 @@ def test_weak_constraint_errors():
     mb = Mesh.from_problem(p, mesh_id=mid)
     with pytest.raises(PbngError):
         mb.set_weak_constraints(idx, w, kn, kt, nrm)
+
+
+def _blocks_equilibrium(k=1e4, young=1e4):
+    p = W.two_blocks_hanging(3, 2, young=young, k=k)
+    m, om = _pair(p)
+    xeq, it, _ = om.newton(p.x0, 1e-11, 60)
+    assert it >= 0
+    return p, m, om, xeq
+
+
+def test_adjoint_with_two_sided_constraints_matches_the_dense_oracle():
+    """The coloured block Gauss-Seidel adjoint on the two-blocks scene: the
+    constraints' true Hessian blocks beta_i beta_j K (Section "Weak
+    Constraints") in the diagonal blocks, in the off-diagonal products and in
+    dL/dx_D, against the oracle's dense adjoint."""
+    from paper_2306_09021_gb300 import default_params
+    p, m, om, xeq = _blocks_equilibrium()
+    rng = np.random.default_rng(4)
+    low = np.isclose(p.X[:, 2], 0.0)          # the hanging block's bottom face
+    dLdx = np.where(low[:, None], 2.0 * 0.01 * rng.standard_normal(xeq.shape), 0.0)
+    dLdx[p.dirichlet] = 0.05 * rng.standard_normal((len(p.dirichlet), 3))
+    dE_ref, dD_ref = om.adjoint(xeq, dLdx)
+    u = torch.tensor(xeq - p.X, dtype=torch.float32, device="cuda")
+    g = torch.tensor(dLdx, dtype=torch.float32, device="cuda")
+    st, dE, dD, sweeps, rel = m.adjoint(u, g, rel_tol=1e-5, max_sweeps=200000,
+                                        params=default_params(accel="chebyshev", rho=-1.0,
+                                                              colour_order="symmetric"))
+    assert st == 0
+    dE, dD = dE.cpu().double().numpy(), dD.cpu().double().numpy()
+    assert np.abs(dE - dE_ref).max() <= 1e-3 * np.abs(dE_ref).max()
+    assert np.abs(dD - dD_ref).max() <= 1e-3 * np.abs(dD_ref).max()
+
+
+def test_newton_cg_with_two_sided_constraints_reaches_the_oracle_equilibrium():
+    """Newton-CG with the constraints in the force, the preconditioner blocks
+    and the Hessian apply reaches the oracle's Newton equilibrium."""
+    from paper_2306_09021_gb300 import default_params
+    p, m, om, xeq = _blocks_equilibrium()
+    u = _u0(p)
+    st, info = m.newton_cg(u, 1e-6, max_newton=60, max_cg=2000, cg_tol=0.05, params=default_params())
+    assert st == 0, info
+    x = u.cpu().double().numpy() + p.X
+    assert np.abs(x - xeq).max() <= 1e-4 * np.abs(xeq - p.X).max()
