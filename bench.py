@@ -476,10 +476,10 @@ def main():
                          [("symmetric_auto_rho_compensated_to_1e-04",
                            dict(accel="chebyshev", rho=-1.0, colour_order="symmetric"), 1e-4)],
                 "bar": [("plain", {}, 1e-5), auto, ("sor", dict(accel="sor", omega=1.5), 1e-5)],
-                "batched": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto, ("plain", {}, 1e-5)],
-                "adjoint": [("sor", dict(accel="sor", omega=1.5), 1e-5), auto],
-                "blocks": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto]}[args.config]
-        max_sw = 4000 if args.config == "adjoint" else 20000
+                "batched": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto, ("plain", {}, 1e-5)] + sym_runs[2:],
+                "adjoint": [("sor", dict(accel="sor", omega=1.5), 1e-5), auto] + sym_runs[2:],
+                "blocks": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto] + sym_runs[2:]}[args.config]
+        max_sw = 8000 if args.config == "adjoint" else 20000
         u_eq, best_rel = None, 0.0
         for name, kw, tol in runs:
             uu = u0.clone()
@@ -592,13 +592,18 @@ def main():
             x_eq = u_eq.double().cpu().numpy() + p.X
             g = np.where(top[:, None], 2.0 * (x_eq - tgt), 0.0)
             gd = torch.tensor(g, dtype=torch.float32, device="cuda")
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st, dE, dD, asw, arel = m.adjoint(u_eq, gd, 1e-5, 4000, default_params(accel="sor", omega=1.5),
-                                             raise_on_status=False)
-            torch.cuda.synchronize()
-            ttr["adjoint_sor"] = {"tol": 1e-5, "status": int(st), "sweeps": int(asw), "rel_residual": float(arel),
-                                  "ms": 1e3 * (time.perf_counter() - t0)}
+            for name, prm in (("adjoint_sor", default_params(accel="sor", omega=1.5)),
+                              ("adjoint_symmetric_auto_rho",
+                               default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric")),
+                              ("adjoint_symmetric_auto_rho_refined",
+                               default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric",
+                                              precision="auto"))):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                st, dE, dD, asw, arel = m.adjoint(u_eq, gd, 1e-5, max_sw, prm, raise_on_status=False)
+                torch.cuda.synchronize()
+                ttr[name] = {"tol": 1e-5, "status": int(st), "sweeps": int(asw), "rel_residual": float(arel),
+                             "ms": 1e3 * (time.perf_counter() - t0)}
 
     if rank != 0:
         if dist is not None:

@@ -509,6 +509,78 @@ __global__ void adjoint_weak_clamped_kernel(int nwc, int nfree, const DeviceMesh
     }
 }
 
+// Refined adjoint: the shifted states u +- eps lam for the central difference
+// of the float-float force.
+__global__ void adjoint_shift_kernel(int nv, State u, const float4* __restrict__ lh, const float4* __restrict__ ll,
+                                     float eps, State up, State um) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const float4 uh = u.hi[v], ul = u.lo[v], a = lh[v], b = ll[v];
+    const float uhv[3] = {uh.x, uh.y, uh.z}, ulv[3] = {ul.x, ul.y, ul.z};
+    const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z};
+    float ph[3], pl[3], mh[3], ml[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const ff::F2 x = ff::mk(uhv[k], ulv[k]);
+        const ff::F2 d = ff::mul(ff::add(ff::mk(av[k]), bv[k]), eps);
+        const ff::F2 p = ff::add(x, d), q = ff::sub(x, d);
+        ph[k] = p.h;
+        pl[k] = p.l;
+        mh[k] = q.h;
+        ml[k] = q.l;
+    }
+    up.hi[v] = make_float4(ph[0], ph[1], ph[2], 0.f);
+    up.lo[v] = make_float4(pl[0], pl[1], pl[2], 0.f);
+    um.hi[v] = make_float4(mh[0], mh[1], mh[2], 0.f);
+    um.lo[v] = make_float4(ml[0], ml[1], ml[2], 0.f);
+}
+
+constexpr int kVecBlock = 256;
+
+__global__ void __launch_bounds__(kVecBlock) adjoint_refine_rhs_kernel(int n, const float4* __restrict__ gv,
+                                                                      const float4* __restrict__ ph,
+                                                                      const float4* __restrict__ pl,
+                                                                      const float4* __restrict__ mh,
+                                                                      const float4* __restrict__ ml, double inv2eps,
+                                                                      float4* rhs, double* partial) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    double q = 0.0;
+    if (w < n) {
+        const float4 g = gv[w], a = ph[w], b = pl[w], c = mh[w], d = ml[w];
+        const double r0 = (double)g.x + (((double)a.x + b.x) - ((double)c.x + d.x)) * inv2eps;
+        const double r1 = (double)g.y + (((double)a.y + b.y) - ((double)c.y + d.y)) * inv2eps;
+        const double r2 = (double)g.z + (((double)a.z + b.z) - ((double)c.z + d.z)) * inv2eps;
+        rhs[w] = make_float4((float)r0, (float)r1, (float)r2, 0.f);
+        q = r0 * r0 + r1 * r1 + r2 * r2;
+    }
+    __shared__ double sh[kVecBlock];
+    sh[threadIdx.x] = q;
+    __syncthreads();
+    for (int k = kVecBlock / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+__global__ void adjoint_accumulate_kernel(int n, const float4* __restrict__ d, float4* lh, float4* ll, float* maxabs) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n) return;
+    const float4 a = lh[w], b = ll[w], e = d[w];
+    const float av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z}, ev[3] = {e.x, e.y, e.z};
+    float h[3], l[3], mx = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const ff::F2 s = ff::add(ff::mk(av[k], bv[k]), ev[k]);
+        h[k] = s.h;
+        l[k] = s.l;
+        mx = fmaxf(mx, fabsf(s.h));
+    }
+    lh[w] = make_float4(h[0], h[1], h[2], 0.f);
+    ll[w] = make_float4(l[0], l[1], l[2], 0.f);
+    atomicMax(reinterpret_cast<int*>(maxabs), __float_as_int(mx));  // non-negative floats order as ints
+}
+
 // gvec[w] = dL/du of internal free vertex w (caller layout in).
 __global__ void gather_rhs_kernel(int nfree, const int32_t* perm, const float* dLdu, float4* gv) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1008,6 +1080,31 @@ cudaError_t launch_adjoint_weak_clamped(int nwc, int nfree, const DeviceMesh& m,
                                         cudaStream_t st) {
     if (nwc <= 0 || !m.wc_v) return cudaSuccess;
     adjoint_weak_clamped_kernel<<<nblocks(nwc, 256), 256, 0, st>>>(nwc, nfree, m, lam, hdl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_shift(int nv, State u, const float4* lam_hi, const float4* lam_lo, float eps, State up,
+                                 State um, cudaStream_t st) {
+    if (nv <= 0) return cudaSuccess;
+    adjoint_shift_kernel<<<nblocks(nv, 256), 256, 0, st>>>(nv, u, lam_hi, lam_lo, eps, up, um);
+    return cudaGetLastError();
+}
+
+int adj_vec_blocks(int n) { return n > 0 ? nblocks(n, kVecBlock) : 0; }
+
+cudaError_t launch_adjoint_refine_rhs(int nfree, const float4* gv, const float4* fp_hi, const float4* fp_lo,
+                                      const float4* fm_hi, const float4* fm_lo, double inv2eps, float4* rhs,
+                                      double* partial, cudaStream_t st) {
+    if (nfree <= 0) return cudaSuccess;
+    adjoint_refine_rhs_kernel<<<nblocks(nfree, kVecBlock), kVecBlock, 0, st>>>(nfree, gv, fp_hi, fp_lo, fm_hi, fm_lo,
+                                                                                inv2eps, rhs, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_accumulate(int nfree, const float4* d, float4* lam_hi, float4* lam_lo, float* maxabs,
+                                      cudaStream_t st) {
+    if (nfree <= 0) return cudaSuccess;
+    adjoint_accumulate_kernel<<<nblocks(nfree, 256), 256, 0, st>>>(nfree, d, lam_hi, lam_lo, maxabs);
     return cudaGetLastError();
 }
 

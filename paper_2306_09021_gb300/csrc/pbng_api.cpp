@@ -82,13 +82,17 @@ struct pbng_mesh {
     int32_t tune_cands = 0;
 
     // device buffers
-    DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_comp, d_perm;
+    DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_aux_lo, d_comp, d_perm;
     DevBuf d_ring, d_ring_lo, d_items;
     DevBuf d_host_u;  // device copy of the caller's host iterate (pbng_sweep_host)
     DevBuf d_active;                   // int32 [ncomp] component flags (1 = active)
     DevBuf d_vsq, d_comp_off, d_comp_list;  // several components: per-vertex |r|^2, component -> vertices
     // adjoint (built on first use after each layout)
     DevBuf d_lam[3], d_gv, d_diag, d_hdl, d_tv, d_tb, d_dq_int, d_dq_caller, d_adj_partial;
+    // refined adjoint (extended precision): multipliers as float pairs, the
+    // correction's right-hand side, the forces at u +- eps lam, the shifted states
+    DevBuf d_lam_hi, d_lam_lo, d_rhs, d_fp[4], d_shift[2][2], d_maxabs, d_refine_partial;
+    double h_min = 0.0;                // smallest rest element size (cube root of 6 V)
     // Newton-CG (pbng_newton_cg, pbng_force, pbng_hessian_apply): r, x, z, p, q
     DevBuf d_nw[5], d_nw_part[2], d_nw_sc, d_nw_flag;
     double* h_nw = nullptr;            // pinned: sc[3], flag
@@ -593,12 +597,14 @@ pbng_status build_layout(pbng_mesh* m) {
     }
     m->nitems_ring = (int32_t)m->items.size();
 
-    std::vector<float4> aux0(m->nfree), aux1(m->nfree);
+    std::vector<float4> aux0(m->nfree), aux1(m->nfree), auxlo(m->nfree);
     std::vector<int32_t> comp(m->ncomp > 1 ? m->nfree : 0);
     for (int32_t w = 0; w < m->nfree; ++w) {
         const int32_t i = order[w];
         const double K = m->spr_K[i];
         float4 a0 = make_float4((float)m->fext[3 * i], (float)m->fext[3 * i + 1], (float)m->fext[3 * i + 2], (float)K);
+        auxlo[w] = make_float4((float)(m->fext[3 * i] - (double)a0.x), (float)(m->fext[3 * i + 1] - (double)a0.y),
+                               (float)(m->fext[3 * i + 2] - (double)a0.z), 0.f);
         float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
         if (K > 0.0)
             for (int a = 0; a < 3; ++a)
@@ -667,6 +673,7 @@ pbng_status build_layout(pbng_mesh* m) {
     PBNG_CUDA(m, upload(m->d_items, m->items, st));
     PBNG_CUDA(m, upload(m->d_aux0, aux0, st));
     PBNG_CUDA(m, upload(m->d_aux1, aux1, st));
+    PBNG_CUDA(m, upload(m->d_aux_lo, auxlo, st));
     if (m->be_dt > 0.0) {
         PBNG_CUDA(m, upload(m->d_aux_base0, base0, st));
         PBNG_CUDA(m, upload(m->d_aux_base1, base1, st));
@@ -757,6 +764,7 @@ pbng_status build_layout(pbng_mesh* m) {
     d.rec_d = (const float2*)m->d_rec_d.p;
     d.aux0 = (const float4*)m->d_aux0.p;
     d.aux1 = (const float4*)m->d_aux1.p;
+    d.aux_lo = (const float4*)m->d_aux_lo.p;
     d.comp = m->ncomp > 1 ? (const int32_t*)m->d_comp.p : nullptr;
     d.comp_active = m->ncomp > 1 ? (const int32_t*)m->d_active.p : nullptr;
     d.vsq = m->ncomp > 1 ? (double*)m->d_vsq.p : nullptr;
@@ -1808,14 +1816,17 @@ pbng_status adjoint_setup(pbng_mesh* m) {
     PBNG_CUDA(m, ensure_buf(m->d_diag, 2 * sizeof(float4) * (size_t)std::max(1, m->nfree)));
     PBNG_CUDA(m, ensure_buf(m->d_hdl, sizeof(float4) * (size_t)m->nv));
     PBNG_CUDA(m, ensure_buf(m->d_adj_partial, sizeof(double) * (size_t)std::max(1, adjoint_warps(m->nitems_ring))));
+    double vmin = 0.0;
+    for (int32_t e = 0; e < m->ne; ++e) vmin = (e == 0) ? m->vol[e] : std::min(vmin, m->vol[e]);
+    m->h_min = std::cbrt(6.0 * vmin);
     m->adj_ready = true;
     return PBNG_OK;
 }
 
-// FP64 |dL/du - H lambda|^2 -> host.
-pbng_status adjoint_resid(pbng_mesh* m, State u, float4* lam, double* out) {
+// FP64 |rhs - H lambda|^2 -> host.
+pbng_status adjoint_resid(pbng_mesh* m, State u, float4* lam, const float4* rhs, double* out) {
     cudaStream_t st = m->stream;
-    PBNG_CUDA(m, launch_adjoint_vertex(kAdjResid, m->dm, u, lam, (const float4*)m->d_gv.p, (float4*)m->d_diag.p,
+    PBNG_CUDA(m, launch_adjoint_vertex(kAdjResid, m->dm, u, lam, rhs, (float4*)m->d_diag.p,
                                        (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
                                        (double*)m->d_adj_partial.p, st, nullptr, m->model));
     PBNG_CUDA(m, launch_reduce((const double*)m->d_adj_partial.p, adjoint_warps(m->nitems_ring),
@@ -1888,6 +1899,7 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     if (!m->all_ring) return fail(m, PBNG_EINVAL, "the adjoint needs every colour in the ring layout");
     if ((s = adjoint_setup(m))) return s;
     cudaStream_t st = m->stream;
+    const bool refine = p->precision == PBNG_PREC_EXTENDED || p->precision == PBNG_PREC_AUTO;
     // u_eq -> state slot 3 (clamped vertices at their targets)
     PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_eq_dev, (const int32_t*)m->d_perm.p, (const float4*)m->d_dir_hi.p,
                              (const float4*)m->d_dir_lo.p, state_of(m, 3), st));
@@ -1899,15 +1911,12 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
                                        (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p, nullptr, st,
                                        nullptr, m->model));
     m->kernel_launches += 3;
-    double g2 = 0.0, r2 = 0.0;
-    if ((s = adjoint_resid(m, u, lam, &g2))) return s;  // lambda = 0: |dL/du|^2
+    double g2 = 0.0;
+    if ((s = adjoint_resid(m, u, lam, (const float4*)m->d_gv.p, &g2))) return s;  // lambda = 0: |dL/du|^2
     // Gauss-Seidel sweeps with the forward's acceleration, on a local sweep
     // index so the forward iterate's history is left alone
     const int32_t saved_l = m->sweep_l;
     const double saved_om = m->omega_l;
-    m->sweep_l = 0;
-    m->omega_l = 1.0;
-    int p1 = 1, p2 = 2;
     int32_t done = 0;
     double rel = g2 > 0.0 ? 1.0 : 0.0;
     pbng_status result = PBNG_ENOTCONVERGED;
@@ -1916,82 +1925,179 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     const std::vector<int> seq = colour_sequence(m->ncol, p->colour_order);
     // Automatic rho (Chebyshev with rho <= 0) as in pbng_solve: plain sweeps
     // measure q, then Chebyshev from rho(q), raised (symmetric order) or
-    // backed off (growth) with a restart of the multiplier history.
+    // backed off (growth) with a restart of the multiplier history.  The
+    // estimate carries over from one inner solve to the next (same H).
     pbng_params cp = *p;
     const bool auto_rho = p->accel == PBNG_ACCEL_CHEBYSHEV && !(p->rho > 0.0);
     const bool symmetric = p->colour_order == PBNG_ORDER_SYMMETRIC;
     const int32_t est_sweeps = std::max<int32_t>(30, 3 * K);
     int phase = auto_rho ? 0 : 1, backoffs = 0, raises = 0;
-    int32_t mark_done = -1;
-    double mark_rel = 0.0, best = 0.0;
-    std::vector<std::pair<int32_t, double>> since;
     if (auto_rho) cp.accel = PBNG_ACCEL_NONE;
-    auto restart = [&]() -> pbng_status {
-        for (int q = 1; q <= 2; ++q)
-            PBNG_CUDA(m, cudaMemcpyAsync(m->d_lam[q].p, lam, sizeof(float4) * (size_t)m->nv, cudaMemcpyDeviceToDevice,
-                                         st));
+    // One block Gauss-Seidel solve of H lam = rhs from lam = 0, until its
+    // float32 relative residual is <= tol, or (stall) its best over the last
+    // kStall checks is not below half the best before them, or the budget.
+    constexpr int kStall = 10;
+    auto inner_solve = [&](const float4* rhs, double rhs2, double tol, bool stall_stop, double* rel_end) -> pbng_status {
+        for (auto& b : m->d_lam) PBNG_CUDA(m, cudaMemsetAsync(b.p, 0, sizeof(float4) * (size_t)m->nv, st));
         m->sweep_l = 0;
         m->omega_l = 1.0;
-        best = 0.0;
-        since.clear();
-        return PBNG_OK;
-    };
-    while (g2 > 0.0 && done < max_sweeps) {
-        int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
-        if (phase == 0) chunk = std::min<int32_t>(chunk, est_sweeps - done);
-        chunk_weights(m, &cp, chunk, m->h_wg);
-        PBNG_CUDA(m, cudaMemcpyAsync(m->d_wg.p, m->h_wg, sizeof(float2) * chunk, cudaMemcpyHostToDevice, st));
-        for (int32_t k = 0; k < chunk; ++k) {
-            for (const int c : seq)
-                PBNG_CUDA(m, launch_adjoint_ring_sweep(m->dm, u, lam, (const float4*)m->d_gv.p,
-                                                       (const float4*)m->d_diag.p,
-                                                       (const Item*)m->d_items.p + m->item_off[c],
-                                                       m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
-                                                       m->model, st));
-            m->kernel_launches += (int64_t)seq.size();
-            if (cp.accel != PBNG_ACCEL_NONE && m->nfree > 0) {
-                const State lc{lam, lam}, l1{(float4*)m->d_lam[p1].p, (float4*)m->d_lam[p1].p},
-                    l2{(float4*)m->d_lam[p2].p, (float4*)m->d_lam[p2].p};
-                PBNG_CUDA(m, launch_accel(m->nfree, lc, l1, l2, (const float2*)m->d_wg.p + k, nullptr, nullptr,
-                                          false, st));
-                m->kernel_launches++;
-                std::swap(p1, p2);
+        int p1 = 1, p2 = 2;
+        int32_t mark_done = -1, start = done;
+        double mark_rel = 0.0, best = 0.0, r2 = 0.0, irel = 1.0;
+        std::vector<std::pair<int32_t, double>> since;
+        std::vector<double> hist;
+        auto restart = [&]() -> pbng_status {
+            for (int q = 1; q <= 2; ++q)
+                PBNG_CUDA(m, cudaMemcpyAsync(m->d_lam[q].p, lam, sizeof(float4) * (size_t)m->nv,
+                                             cudaMemcpyDeviceToDevice, st));
+            m->sweep_l = 0;
+            m->omega_l = 1.0;
+            best = 0.0;
+            since.clear();
+            return PBNG_OK;
+        };
+        while (rhs2 > 0.0 && done < max_sweeps) {
+            int32_t chunk = std::min<int32_t>(K, max_sweeps - done);
+            if (phase == 0) chunk = std::min<int32_t>(chunk, start + est_sweeps - done);
+            chunk_weights(m, &cp, chunk, m->h_wg);
+            PBNG_CUDA(m, cudaMemcpyAsync(m->d_wg.p, m->h_wg, sizeof(float2) * chunk, cudaMemcpyHostToDevice, st));
+            for (int32_t k = 0; k < chunk; ++k) {
+                for (const int c : seq)
+                    PBNG_CUDA(m, launch_adjoint_ring_sweep(m->dm, u, lam, rhs, (const float4*)m->d_diag.p,
+                                                           (const Item*)m->d_items.p + m->item_off[c],
+                                                           m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
+                                                           m->model, st));
+                m->kernel_launches += (int64_t)seq.size();
+                if (cp.accel != PBNG_ACCEL_NONE && m->nfree > 0) {
+                    const State lc{lam, lam}, l1{(float4*)m->d_lam[p1].p, (float4*)m->d_lam[p1].p},
+                        l2{(float4*)m->d_lam[p2].p, (float4*)m->d_lam[p2].p};
+                    PBNG_CUDA(m, launch_accel(m->nfree, lc, l1, l2, (const float2*)m->d_wg.p + k, nullptr, nullptr,
+                                              false, st));
+                    m->kernel_launches++;
+                    std::swap(p1, p2);
+                }
             }
-        }
-        done += chunk;
-        if ((s = check_err(m))) break;
-        if ((s = adjoint_resid(m, u, lam, &r2))) break;
-        rel = std::sqrt(r2 / g2);
-        if (!std::isfinite(rel) || rel > 1e3) { result = PBNG_EDIVERGED; break; }
-        if (rel <= rel_tol) { result = PBNG_OK; break; }
-        if (!auto_rho) continue;
-        if (phase == 0) {
-            if (mark_done < 0 && 3 * done >= est_sweeps) {
-                mark_done = done;
-                mark_rel = rel;
-            } else if (done >= est_sweeps && mark_done >= 0 && done > mark_done) {
-                const double q = mark_rel > 0.0 && rel > 0.0 ? std::pow(rel / mark_rel, 1.0 / (done - mark_done)) : 0.0;
-                cp.accel = PBNG_ACCEL_CHEBYSHEV;
-                cp.rho = initial_rho(symmetric, p->gamma, q);
-                phase = 1;
-                if ((s = restart())) break;
+            done += chunk;
+            pbng_status e = check_err(m);
+            if (e) return e;
+            if ((e = adjoint_resid(m, u, lam, rhs, &r2))) return e;
+            irel = std::sqrt(r2 / rhs2);
+            *rel_end = irel;
+            if (!std::isfinite(irel) || irel > 1e3) return PBNG_EDIVERGED;
+            if (irel <= tol) return PBNG_OK;
+            hist.push_back(irel);
+            if (stall_stop && hist.size() >= 2 * kStall) {
+                const double recent = *std::min_element(hist.end() - kStall, hist.end());
+                const double before = *std::min_element(hist.begin(), hist.end() - kStall);
+                if (recent > 0.5 * before) return PBNG_OK;  // at this solve's float32 floor
             }
-        } else if (cp.accel == PBNG_ACCEL_CHEBYSHEV) {
-            since.emplace_back(done, rel);
-            if (best == 0.0 || rel < best) best = rel;
-            if (rel > 4.0 * best) {
-                if (++backoffs > 4) cp.accel = PBNG_ACCEL_NONE;
-                else cp.rho = std::max(0.5, 1.0 - 2.0 * (1.0 - cp.rho));
-                if ((s = restart())) break;
-            } else if (symmetric && raises < 12) {
-                const double mu = raised_rho(since, K, cp.rho);
-                if (mu > cp.rho) {
-                    cp.rho = mu;
-                    raises++;
-                    if ((s = restart())) break;
+            if (!auto_rho) continue;
+            if (phase == 0) {
+                if (mark_done < 0 && 3 * (done - start) >= est_sweeps) {
+                    mark_done = done;
+                    mark_rel = irel;
+                } else if (done - start >= est_sweeps && mark_done >= 0 && done > mark_done) {
+                    const double q = mark_rel > 0.0 && irel > 0.0 ? std::pow(irel / mark_rel, 1.0 / (done - mark_done))
+                                                                  : 0.0;
+                    cp.accel = PBNG_ACCEL_CHEBYSHEV;
+                    cp.rho = initial_rho(symmetric, p->gamma, q);
+                    phase = 1;
+                    if ((e = restart())) return e;
+                }
+            } else if (cp.accel == PBNG_ACCEL_CHEBYSHEV) {
+                since.emplace_back(done, irel);
+                if (best == 0.0 || irel < best) best = irel;
+                if (irel > 4.0 * best) {
+                    if (++backoffs > 4) cp.accel = PBNG_ACCEL_NONE;
+                    else cp.rho = std::max(0.5, 1.0 - 2.0 * (1.0 - cp.rho));
+                    if ((e = restart())) return e;
+                } else if (symmetric && raises < 12) {
+                    const double mu = raised_rho(since, K, cp.rho);
+                    if (mu > cp.rho) {
+                        cp.rho = mu;
+                        raises++;
+                        if ((e = restart())) return e;
+                    }
                 }
             }
         }
+        return rhs2 > 0.0 ? PBNG_ENOTCONVERGED : PBNG_OK;
+    };
+    if (!refine) {
+        double irel = rel;
+        s = inner_solve((const float4*)m->d_gv.p, g2, rel_tol, false, &irel);
+        if (g2 > 0.0) rel = irel;
+        if (s == PBNG_OK || s == PBNG_ENOTCONVERGED || s == PBNG_EDIVERGED) {
+            result = s;
+            s = PBNG_OK;
+        }
+    } else {
+        // Mixed-precision iterative refinement (the adjoint is linear): the
+        // multipliers accumulate as float pairs, the residual dL/du - H lam
+        // is formed by central differences of the float-float force,
+        // H lam = -(F(u + eps lam) - F(u - eps lam)) / (2 eps), and each
+        // correction solves H d = residual with the float32 sweeps to 1e-2
+        // or to their floor.  eps makes the largest step eps |lam| 1e-4 of
+        // the smallest element size, where the central difference's error
+        // (~(eps |lam| / h)^2) is below the forces' rounding.
+        const size_t vbytes = sizeof(float4) * (size_t)m->nv;
+        PBNG_CUDA(m, ensure_buf(m->d_lam_hi, vbytes));
+        PBNG_CUDA(m, ensure_buf(m->d_lam_lo, vbytes));
+        PBNG_CUDA(m, ensure_buf(m->d_rhs, sizeof(float4) * (size_t)std::max(1, m->nfree)));
+        for (auto* b : {&m->d_fp[0], &m->d_fp[1], &m->d_fp[2], &m->d_fp[3]})
+            PBNG_CUDA(m, ensure_buf(*b, sizeof(float4) * (size_t)std::max(1, m->nfree)));
+        for (auto& sb : m->d_shift)
+            for (auto& b : sb) PBNG_CUDA(m, ensure_buf(b, vbytes));
+        PBNG_CUDA(m, ensure_buf(m->d_maxabs, sizeof(float) * 4));
+        PBNG_CUDA(m, ensure_buf(m->d_refine_partial, sizeof(double) * (size_t)std::max(1, adj_vec_blocks(m->nfree))));
+        PBNG_CUDA(m, cudaMemsetAsync(m->d_lam_hi.p, 0, vbytes, st));
+        PBNG_CUDA(m, cudaMemsetAsync(m->d_lam_lo.p, 0, vbytes, st));
+        PBNG_CUDA(m, cudaMemcpyAsync(m->d_rhs.p, m->d_gv.p, sizeof(float4) * (size_t)m->nfree, cudaMemcpyDeviceToDevice,
+                                     st));
+        const State up{(float4*)m->d_shift[0][0].p, (float4*)m->d_shift[0][1].p};
+        const State um{(float4*)m->d_shift[1][0].p, (float4*)m->d_shift[1][1].p};
+        double r2 = g2;
+        result = g2 > 0.0 ? PBNG_ENOTCONVERGED : PBNG_OK;
+        while (g2 > 0.0 && done < max_sweeps && s == PBNG_OK) {
+            double irel = 1.0;
+            pbng_status is = inner_solve((const float4*)m->d_rhs.p, r2, 1e-2, true, &irel);
+            if (is == PBNG_EDIVERGED) { result = is; break; }
+            if (is != PBNG_OK && is != PBNG_ENOTCONVERGED) { s = is; break; }
+            // lam += d, then the residual at the new lam
+            PBNG_CUDA(m, cudaMemsetAsync(m->d_maxabs.p, 0, sizeof(float), st));
+            PBNG_CUDA(m, launch_adjoint_accumulate(m->nfree, lam, (float4*)m->d_lam_hi.p, (float4*)m->d_lam_lo.p,
+                                                   (float*)m->d_maxabs.p, st));
+            float maxabs = 0.0f;
+            PBNG_CUDA(m, cudaMemcpyAsync(&maxabs, m->d_maxabs.p, sizeof(float), cudaMemcpyDeviceToHost, st));
+            PBNG_CUDA(m, cudaStreamSynchronize(st));
+            if (!(maxabs > 0.0f) || !std::isfinite(maxabs)) { result = PBNG_EDIVERGED; break; }
+            const float eps = (float)(1e-4 * m->h_min / (double)maxabs);
+            PBNG_CUDA(m, launch_adjoint_shift(m->nv, u, (const float4*)m->d_lam_hi.p, (const float4*)m->d_lam_lo.p, eps,
+                                              up, um, st));
+            for (int k = 0; k < 2; ++k) {
+                DeviceMesh d = m->dm;
+                d.fout_hi = (float4*)m->d_fp[2 * k].p;
+                d.fout_lo = (float4*)m->d_fp[2 * k + 1].p;
+                d.vsq = nullptr;
+                PBNG_CUDA(m, launch_ring_residual(d, k == 0 ? up : um, (const Item*)m->d_items.p, m->nitems_ring, true,
+                                                  (double*)m->d_partial.p, nullptr, m->model, (int32_t*)m->d_err.p, st,
+                                                  true));
+            }
+            PBNG_CUDA(m, launch_adjoint_refine_rhs(m->nfree, (const float4*)m->d_gv.p, (const float4*)m->d_fp[0].p,
+                                                   (const float4*)m->d_fp[1].p, (const float4*)m->d_fp[2].p,
+                                                   (const float4*)m->d_fp[3].p, 0.5 / (double)eps, (float4*)m->d_rhs.p,
+                                                   (double*)m->d_refine_partial.p, st));
+            PBNG_CUDA(m, launch_reduce((const double*)m->d_refine_partial.p, adj_vec_blocks(m->nfree),
+                                       (double*)m->d_scalar.p, st));
+            m->kernel_launches += 6;
+            PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_scalar.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+            if ((s = sync_with_err(m, st))) break;
+            r2 = m->h_pinned[0];
+            rel = std::sqrt(r2 / g2);
+            if (!std::isfinite(rel) || rel > 1e3) { result = PBNG_EDIVERGED; break; }
+            if (rel <= rel_tol) { result = PBNG_OK; break; }
+        }
+        lam = (float4*)m->d_lam_hi.p;  // the gradients use the accumulated multipliers
     }
     m->sweep_l = saved_l;
     m->omega_l = saved_om;
@@ -2566,8 +2672,10 @@ void pbng_destroy(pbng_mesh* m) {
                       &m->d_tb, &m->d_dq_int, &m->d_dq_caller, &m->d_adj_partial,
                       &m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
                       &m->d_ring, &m->d_ring_lo, &m->d_items, &m->d_host_u, &m->d_vsq, &m->d_comp_off,
-                      &m->d_comp_list,
-                      &m->d_aux0, &m->d_aux1, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
+                      &m->d_comp_list, &m->d_lam_hi, &m->d_lam_lo, &m->d_rhs, &m->d_fp[0], &m->d_fp[1], &m->d_fp[2],
+                      &m->d_fp[3], &m->d_shift[0][0], &m->d_shift[0][1], &m->d_shift[1][0], &m->d_shift[1][1],
+                      &m->d_maxabs, &m->d_refine_partial,
+                      &m->d_aux0, &m->d_aux1, &m->d_aux_lo, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k, &m->d_wc_off, &m->d_wc_list, &m->d_wc_v,
                       &m->d_wc_b, &m->d_wc_k, &m->d_wc_c0,
                       &m->d_nw[0], &m->d_nw[1], &m->d_nw[2], &m->d_nw[3], &m->d_nw[4], &m->d_nw_part[0],

@@ -57,12 +57,17 @@ struct DeviceMesh {
     const float2* rec_d;     // [ninc] g_j3.y, g_j3.z
     const float4* aux0;      // [nfree] f_ext (xyz), total spring stiffness K
     const float4* aux1;      // [nfree] spring target displacement (xyz), n.X - d
+    const float4* aux_lo;    // [nfree] low words of f_ext (xyz): f_ext = aux0 + aux_lo
     const int32_t* comp;     // [nfree] component id, or nullptr for one component
     const int32_t* comp_active;  // [ncomp] 0 = frozen (converged), or nullptr
     // Residuals of several components: each free vertex's |r|^2 goes to
     // vsq[v] and the per-component sums follow in a fixed order
     // (launch_comp_reduce); nullptr: atomic per-component sums instead.
     double* vsq;
+    // Extended residual only (nullptr otherwise): each free vertex's
+    // float-float force f + f^ext as fout_hi[v] + fout_lo[v] (xyz).
+    float4* fout_hi;
+    float4* fout_lo;
     // Ring layout (colours whose vertices all fit 32 lanes): one 32-slot
     // item per warp; vertex v of a lane-width-W run owns W consecutive slots.
     // Slot s is entry s % 32 of block s / 32 (RingBlock).
@@ -219,6 +224,22 @@ cudaError_t launch_scatter_vec(int nv, int nfree, const int32_t* perm, const flo
 cudaError_t launch_adjoint_tets(int ne, int nfree, const int4* tv, const float4* tb, State u, const float4* lam,
                                 float* dLdlogE, float* hdl, cudaStream_t st, int model = 0);
 cudaError_t launch_gather_rhs(int nfree, const int32_t* perm, const float* dLdu, float4* gv, cudaStream_t st);
+// Refined adjoint (pbng_adjoint in extended precision), pbng_adjoint.cu:
+// u_plus / u_minus = u +- eps (lam_hi + lam_lo) over all nv vertices (lam is
+// zero at clamped ones), in float-float;
+cudaError_t launch_adjoint_shift(int nv, State u, const float4* lam_hi, const float4* lam_lo, float eps, State up,
+                                 State um, cudaStream_t st);
+// rhs[w] = gv[w] + (F+ - F-)[w] / (2 eps) (that is dL/du - H lam, H = -dF/du
+// by central differences of the float-float force), FP64 |rhs|^2 per block
+// into partial (adj_vec_blocks(nfree) of them);
+int adj_vec_blocks(int n);
+cudaError_t launch_adjoint_refine_rhs(int nfree, const float4* gv, const float4* fp_hi, const float4* fp_lo,
+                                      const float4* fm_hi, const float4* fm_lo, double inv2eps, float4* rhs,
+                                      double* partial, cudaStream_t st);
+// lam_hi + lam_lo += d (float-float), and the largest |component| of the sum
+// into *maxabs (float bits; zero it first).
+cudaError_t launch_adjoint_accumulate(int nfree, const float4* d, float4* lam_hi, float4* lam_lo, float* maxabs,
+                                      cudaStream_t st);
 // The two-sided weak constraints' part of H_DF lam (into hdl, float4 rows).
 cudaError_t launch_adjoint_weak_clamped(int nwc, int nfree, const DeviceMesh& m, const float4* lam, float* hdl,
                                         cudaStream_t st);

@@ -65,8 +65,8 @@ __device__ __forceinline__ void vertex_group(const DeviceMesh& m, State s, int v
 #pragma unroll
         for (int k = 0; k < 3; ++k) rf[k] = el::group_sum_ff<W>(rf[k]);
         if (!active || lane != 0) return;
-        el::vertex_terms_ff<false>(m, __ldg(m.aux0 + v), __ldg(m.aux1 + v), uh, ul, rf, A);
-        el::weak_terms_ff<COMP, false>(m, s, v, rf, A);
+        el::vertex_terms_ff<false>(m, v, __ldg(m.aux0 + v), __ldg(m.aux1 + v), uh, ul, rf, nullptr);
+        el::weak_terms_ff<COMP, false>(m, s, v, rf, nullptr);
         *rr = el::norm2_ff(rf);
         if (r_out) {
             r_out[3 * v] = rf[0].h + rf[0].l;

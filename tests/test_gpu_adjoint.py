@@ -96,3 +96,33 @@ def test_adjoint_zero_rhs_gives_zero():
     st, dE, dD, sweeps, rel = m.adjoint(u, torch.zeros_like(u))
     assert st == 0 and sweeps == 0
     assert torch.count_nonzero(dE) == 0 and torch.count_nonzero(dD) == 0
+
+
+@pytest.mark.parametrize("n", [4, 6])
+def test_refined_adjoint_matches_dense_oracle_tightly(oracle_mod, n):
+    """Extended precision: iterative refinement with the float-float force's
+    central differences takes the adjoint residual far below the float32
+    sweeps' floor, and the sensitivities to the dense oracle adjoint's within
+    float32 rounding of the gradients themselves."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = _loaded(n)
+    om = oracle_mod.OracleMesh.from_problem(p)
+    xeq, it, _ = om.newton(p.x0, 1e-11, 60)
+    assert it >= 0
+    top = np.isclose(p.X[:, 2], 1.0)
+    rng = np.random.default_rng(n + 1)
+    dLdx = np.where(top[:, None], 2.0 * 0.01 * rng.standard_normal(xeq.shape), 0.0)
+    dLdx[p.dirichlet] = 0.05 * rng.standard_normal((len(p.dirichlet), 3))
+    dE_ref, dD_ref = om.adjoint(xeq, dLdx)
+    m = Mesh.from_problem(p)
+    # the equilibrium as the float pair nearest the oracle's (float32 input)
+    u = torch.tensor(xeq - p.X, dtype=torch.float32, device="cuda")
+    g = torch.tensor(dLdx, dtype=torch.float32, device="cuda")
+    st, dE, dD, sweeps, rel = m.adjoint(u, g, rel_tol=1e-8, max_sweeps=200000,
+                                        params=default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric",
+                                                              precision="extended"))
+    print(f"refined adjoint {n}^3: {sweeps} sweeps, rel residual {rel:.2e}")
+    assert st == 0 and rel <= 1e-8
+    # the float32 rounding of u_eq moves the gradients by about its own size
+    assert _rel(dE.cpu().double().numpy(), dE_ref) <= 2e-5
+    assert _rel(dD.cpu().double().numpy(), dD_ref) <= 2e-5

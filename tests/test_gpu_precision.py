@@ -133,17 +133,18 @@ def test_extended_precision_needs_the_ring_layout():
         m.sweep(u, 2, default_params(precision="extended", kernel_path=1))
 
 
-@pytest.mark.parametrize("prec,above", [("compensated", 1e-3), ("extended", 1e-8)])
-def test_residual_history_matches_the_oracle_down_to_the_floor(oracle_mod, prec, above):
+@pytest.mark.parametrize("prec,floor", [("compensated", 1e-4), ("extended", 1e-10)])
+def test_residual_history_matches_the_oracle_down_to_the_floor(oracle_mod, prec, floor):
     """A 10^3 gravity-sag cube, symmetric colour order, Chebyshev rho 0.998:
-    the GPU's relative residual every 50 sweeps against the oracle's history
-    of the same run, to 1e-3 relative wherever the oracle's residual is above
-    the GPU path's floor (1e-3 for the float32 passes, 1e-8 extended)."""
+    the GPU's relative residual every 10 sweeps against the oracle's history
+    of the same run agrees to 1e-3 relative plus the GPU path's floor (1e-4
+    for the float32 passes, 1e-10 extended), at every check where the
+    oracle's residual is above ten times that floor."""
     import os
     from paper_2306_09021_gb300 import Mesh, default_params
     p = W.gravity_sag(10)
     om = oracle_mod.OracleMesh.from_problem(p)
-    total, every = 700, 50
+    total, every = 700, 10
     _, st, hist = om.sweeps(p.x0, total, accel="chebyshev", rho=0.998, gamma=1.7, order="symmetric",
                             threads=oracle_mod.threads_available(os.cpu_count() or 1), history=True)
     assert st == 0
@@ -156,9 +157,9 @@ def test_residual_history_matches_the_oracle_down_to_the_floor(oracle_mod, prec,
         rel = m.sweep(u, every, prm, want_residual=True)[0]
         prm.resume = 1
         r_ora = hist[(k + 1) * every]
-        if r_ora > above:
-            assert abs(rel - r_ora) <= 1e-3 * r_ora, (prec, (k + 1) * every, rel, r_ora)
+        if r_ora > 10.0 * floor:
+            assert abs(rel - r_ora) <= 1e-3 * r_ora + floor, (prec, (k + 1) * every, rel, r_ora)
             compared += 1
-    assert compared >= 3
+    assert compared >= 10
     if prec == "extended":
         assert hist[-1] < 1e-8 and rel < 1e-8

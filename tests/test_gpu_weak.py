@@ -104,11 +104,6 @@ def test_weak_constraint_errors():
     with pytest.raises(PbngError):
         m.set_weak_constraints(idx, bad, kn, kt, nrm)
     m.set_weak_constraints(idx, w, kn, kt, nrm)
-    u = _u0(p)
-    with pytest.raises(PbngError):
-        m.newton_cg(u, 1e-5)
-    with pytest.raises(PbngError):
-        m.adjoint(u, torch.zeros_like(u), 1e-6, 10, default_params())
     # a constraint across two batch components is rejected
     mid = np.zeros(p.nv, np.int32)
     mid[W.box_grid(2, 2, 2, 1.0)[0].shape[0]:] = 1
