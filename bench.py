@@ -479,7 +479,7 @@ def main():
                 "batched": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto, ("plain", {}, 1e-5)] + sym_runs[2:],
                 "adjoint": [("sor", dict(accel="sor", omega=1.5), 1e-5), auto] + sym_runs[2:],
                 "blocks": [("chebyshev", dict(accel="chebyshev"), 1e-5), auto] + sym_runs[2:]}[args.config]
-        max_sw = 8000 if args.config == "adjoint" else 20000
+        max_sw = 20000
         u_eq, best_rel = None, 0.0
         for name, kw, tol in runs:
             uu = u0.clone()
@@ -487,7 +487,10 @@ def main():
             t0 = time.perf_counter()
             kw = dict(kw)
             prec = kw.pop("precision", args.precision)
-            st, sweeps, relr = m.solve(uu, tol, max_sw,
+            # on the 32-case adjoint workload the forward-order runs are known not
+            # to converge: a shorter cap keeps the bench within minutes
+            cap = 4000 if (args.config == "adjoint" and not name.startswith("symmetric")) else max_sw
+            st, sweeps, relr = m.solve(uu, tol, cap,
                                        default_params(model=args.model, precision=prec, residual_every=10,
                                                       kernel_path=args.kernel_path, **kw),
                                        raise_on_status=False)
@@ -592,15 +595,17 @@ def main():
             x_eq = u_eq.double().cpu().numpy() + p.X
             g = np.where(top[:, None], 2.0 * (x_eq - tgt), 0.0)
             gd = torch.tensor(g, dtype=torch.float32, device="cuda")
-            for name, prm in (("adjoint_sor", default_params(accel="sor", omega=1.5)),
-                              ("adjoint_symmetric_auto_rho",
-                               default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric")),
-                              ("adjoint_symmetric_auto_rho_refined",
-                               default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric",
-                                              precision="auto"))):
+            # the float32 adjoints stall at their floor (about 2e-3 here):
+            # 4000 sweeps show it; the refined one gets 20000
+            for name, prm, cap in (("adjoint_sor", default_params(accel="sor", omega=1.5), 4000),
+                                   ("adjoint_symmetric_auto_rho",
+                                    default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric"), 4000),
+                                   ("adjoint_symmetric_auto_rho_refined",
+                                    default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric",
+                                                   precision="auto"), max_sw)):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                st, dE, dD, asw, arel = m.adjoint(u_eq, gd, 1e-5, max_sw, prm, raise_on_status=False)
+                st, dE, dD, asw, arel = m.adjoint(u_eq, gd, 1e-5, cap, prm, raise_on_status=False)
                 torch.cuda.synchronize()
                 ttr[name] = {"tol": 1e-5, "status": int(st), "sweeps": int(asw), "rel_residual": float(arel),
                              "ms": 1e3 * (time.perf_counter() - t0)}

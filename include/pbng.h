@@ -518,10 +518,11 @@ pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p
  *                    max(4 residual_every, 3 / sqrt(2 (1 - rho))) sweeps has
  *                    passed since the last (re)start, an observed per-sweep
  *                    factor f (over its second half) that lowered the
- *                    residual at least 2x but at under 70 % of the log-rate
- *                    of k = rho / (1 + sqrt(1 - rho^2)) raises rho to
- *                    rho (z + 1/z) / 2, z = f / k (where a mode above rho
- *                    sits), and restarts (at most 12 raises).
+ *                    residual below 0.8 of its value (after a first half
+ *                    that lowered it below 0.9) but at under 70 % of the
+ *                    log-rate of k = rho / (1 + sqrt(1 - rho^2)) raises rho
+ *                    to rho (z + 1/z) / 2, z = f / k (where a mode above
+ *                    rho sits), and restarts (at most 12 raises).
  * A residual check whose worst component exceeds 4x the best seen since the
  * last (re)start doubles 1 - rho and restarts the schedule; after 4 such
  * back-offs the remaining sweeps are plain.  The estimate is not kept across

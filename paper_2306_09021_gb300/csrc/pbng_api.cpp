@@ -1518,9 +1518,11 @@ double raised_rho(const std::vector<std::pair<int32_t, double>>& since, int32_t 
     if (span < win) return rho;
     size_t a = 0;
     while (a + 1 < since.size() && since[a].first - since.front().first < span / 2) ++a;
-    const double wa = since[a].second;
+    const double wa = since[a].second, w0 = since.front().second;
     const int32_t ds = done - since[a].first;
-    if (!(ds > 0 && wa > 0.0 && w > 0.0 && w < 0.5 * wa)) return rho;
+    // still falling over both halves of the window (a floor's fluctuations
+    // rarely do), and measurably over the second one
+    if (!(ds > 0 && wa > 0.0 && w > 0.0 && w < 0.8 * wa && wa < 0.9 * w0)) return rho;
     const double lam_pred = -std::log(rho / (1.0 + std::sqrt(1.0 - rho * rho)));
     const double lam_obs = -std::log(w / wa) / ds;
     if (!(lam_obs < 0.7 * lam_pred)) return rho;
@@ -1679,6 +1681,7 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
         if (cv < 0) result = PBNG_EDIVERGED;
         if (cv != 0) continue;
         const double w = worst_active();
+        if (changed) stall_hist.clear();  // the worst active component changed: a new history
         if (cp.precision == PBNG_PREC_AUTO && phase == 1) {
             stall_hist.push_back(w);
             const size_t n = stall_hist.size();

@@ -385,7 +385,7 @@ __device__ __forceinline__ void vertex_terms(const DeviceMesh& m, float4 x0, flo
 // test is taken in float.
 template <bool NEED_A>
 __device__ __forceinline__ void vertex_terms_ff(const DeviceMesh& m, int v, float4 x0, float4 x1, float3 uh,
-                                                float3 ul, ff::F2* r, ff::F2* A) {
+                                                float3 ul, ff::F2* r, float* A) {
     r[0] = ff::add(r[0], x0.x);
     r[1] = ff::add(r[1], x0.y);
     r[2] = ff::add(r[2], x0.z);
@@ -402,11 +402,7 @@ __device__ __forceinline__ void vertex_terms_ff(const DeviceMesh& m, int v, floa
         r[0] = ff::sub(r[0], ff::mul(e0, x0.w));
         r[1] = ff::sub(r[1], ff::mul(e1, x0.w));
         r[2] = ff::sub(r[2], ff::mul(e2, x0.w));
-        if (NEED_A) {
-            A[0] = ff::add(A[0], x0.w);
-            A[3] = ff::add(A[3], x0.w);
-            A[5] = ff::add(A[5], x0.w);
-        }
+        if (NEED_A) { A[0] += x0.w; A[3] += x0.w; A[5] += x0.w; }
     }
     if (m.k_contact > 0.0f) {
         const float sdf = x1.w + (m.pn_x * (uh.x + ul.x) + m.pn_y * (uh.y + ul.y) + m.pn_z * (uh.z + ul.z));
@@ -422,11 +418,12 @@ __device__ __forceinline__ void vertex_terms_ff(const DeviceMesh& m, int v, floa
             r[1] = ff::sub(r[1], ff::mul(ks, m.pn_y));
             r[2] = ff::sub(r[2], ff::mul(ks, m.pn_z));
             if (NEED_A) {
-                const float n[3] = {m.pn_x, m.pn_y, m.pn_z};
-                const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
-#pragma unroll
-                for (int t = 0; t < 6; ++t)
-                    A[t] = ff::add(A[t], ff::mul(ff::two_prod(m.k_contact, n[ij[t][0]]), n[ij[t][1]]));
+                A[0] += m.k_contact * m.pn_x * m.pn_x;
+                A[1] += m.k_contact * m.pn_x * m.pn_y;
+                A[2] += m.k_contact * m.pn_x * m.pn_z;
+                A[3] += m.k_contact * m.pn_y * m.pn_y;
+                A[4] += m.k_contact * m.pn_y * m.pn_z;
+                A[5] += m.k_contact * m.pn_z * m.pn_z;
             }
         }
     }
@@ -495,7 +492,7 @@ __device__ __forceinline__ void weak_terms(const DeviceMesh& m, const State& s, 
 // pair S + E of the error-free accumulation above, K C and beta K C in
 // float-float.
 template <bool COMP, bool NEED_A>
-__device__ __forceinline__ void weak_terms_ff(const DeviceMesh& m, const State& s, int v, ff::F2* r, ff::F2* A) {
+__device__ __forceinline__ void weak_terms_ff(const DeviceMesh& m, const State& s, int v, ff::F2* r, float* A) {
     if (!m.wc_off) return;
     const int k1 = m.wc_off[v + 1];
     for (int k = m.wc_off[v]; k < k1; ++k) {
@@ -529,50 +526,11 @@ __device__ __forceinline__ void weak_terms_ff(const DeviceMesh& m, const State& 
             r[p] = ff::sub(r[p], ff::mul(KC, beta));
         }
         if (NEED_A) {
-            const ff::F2 b2 = ff::two_prod(beta, beta);
+            const float b2 = beta * beta;
 #pragma unroll
-            for (int t = 0; t < 6; ++t) A[t] = ff::add(A[t], ff::mul(b2, K[t]));
+            for (int t = 0; t < 6; ++t) A[t] += b2 * K[t];
         }
     }
-}
-
-// Eq. pbgn_dx / pbgn_update in extended precision: Delta = step A^{-1} r with
-// the float-float force and nodal Hessian, solved in FP64 (adjugate; one
-// lane per vertex), and u_v += Delta formed in float-float.
-__device__ __forceinline__ void solve_and_write_ff(State s, int v, float3 uh, float3 ul, const ff::F2* r,
-                                                   const ff::F2* A, PassParams pp, int32_t* err) {
-    const double rd[3] = {ff::to_d(r[0]), ff::to_d(r[1]), ff::to_d(r[2])};
-    if (pp.skip_tol > 0.0f &&
-        rd[0] * rd[0] + rd[1] * rd[1] + rd[2] * rd[2] <= (double)pp.skip_tol * (double)pp.skip_tol)
-        return;
-    double a[6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) a[k] = ff::to_d(A[k]);
-    const double c00 = a[3] * a[5] - a[4] * a[4], c01 = a[2] * a[4] - a[1] * a[5], c02 = a[1] * a[4] - a[2] * a[3];
-    const double c11 = a[0] * a[5] - a[2] * a[2], c12 = a[1] * a[2] - a[0] * a[4], c22 = a[0] * a[3] - a[1] * a[1];
-    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-    if (!(det > 0.0) || !(det < 1e300)) {
-        atomicOr(err, kErrNonSPD);
-        return;
-    }
-    const double sc = (double)pp.step / det;
-    const double d[3] = {sc * (c00 * rd[0] + c01 * rd[1] + c02 * rd[2]), sc * (c01 * rd[0] + c11 * rd[1] + c12 * rd[2]),
-                         sc * (c02 * rd[0] + c12 * rd[1] + c22 * rd[2])};
-    if (!(fabs(d[0]) + fabs(d[1]) + fabs(d[2]) < 3.0e38)) {
-        atomicOr(err, kErrNonFinite);
-        return;
-    }
-    const float uhv[3] = {uh.x, uh.y, uh.z}, ulv[3] = {ul.x, ul.y, ul.z};
-    float h[3], l[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float dh = (float)d[k];
-        const ff::F2 u = ff::add(ff::mk(uhv[k], ulv[k]), ff::mk(dh, (float)(d[k] - (double)dh)));
-        h[k] = u.h;
-        l[k] = u.l;
-    }
-    s.lo[v] = make_float4(l[0], l[1], l[2], 0.f);
-    s.hi[v] = make_float4(h[0], h[1], h[2], 0.f);
 }
 
 // hi + lo += d, keeping the pair normalised (TwoSum, then Fast2Sum).

@@ -148,13 +148,9 @@ enum { kCorotated = 0, kNeoHookean = 1, kStableNeoHookean = 2 };
 // P is Eq. cor (corotated), Eq. nh (Neo-Hookean, lambda_hat = mu + lambda),
 // or Eq. snh with lambda' on its volume term and the Lame reparametrisation
 // mu' = 4mu/3, lambda' = lambda + 5mu/6 (stable Neo-Hookean), as in the
-// float32 element term.  Writes f as float pairs; with Aout (not null) also
-// the element's modified Hessian of Eq. mod_hess_dens contracted with g_i,
-// V (2 mu |g_i|^2 I + lambda w w^T), w = cof(F) g_i, upper triangle
-// (a00 a01 a02 a11 a12 a22).
+// float32 element term.  Writes f as float pairs.
 template <int MODEL>
-PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], const float* q, F2* fout,
-                              F2* Aout = nullptr) {
+PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], const float* q, F2* fout) {
     F2 H[9];
 #pragma unroll
     for (int p = 0; p < 3; ++p)
@@ -289,16 +285,6 @@ PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], co
     }
 #pragma unroll
     for (int p = 0; p < 3; ++p) fout[p] = f[p];
-    if (Aout) {
-        const F2 ag = mul(a, add(add(mul(s[0], s[0]), mul(s[1], s[1])), mul(s[2], s[2])));
-        const F2 bw[3] = {mul(b, ws[0]), mul(b, ws[1]), mul(b, ws[2])};
-        Aout[0] = add(ag, mul(bw[0], ws[0]));
-        Aout[1] = mul(bw[0], ws[1]);
-        Aout[2] = mul(bw[0], ws[2]);
-        Aout[3] = add(ag, mul(bw[1], ws[1]));
-        Aout[4] = mul(bw[1], ws[2]);
-        Aout[5] = add(ag, mul(bw[2], ws[2]));
-    }
 }
 
 }  // namespace ff

@@ -210,11 +210,12 @@ __device__ __forceinline__ void store_sq(const DeviceMesh& m, int v, double q, d
     else atomicAdd(comp_sq + m.comp[v], q);
 }
 
-// Extended precision: the element force and nodal Hessian of the lane's
-// slot in float-float arithmetic from float-pair records and displacements
-// (pbng_ff.cuh), their W-lane sums and the vertex terms in float-float too.
-// UPDATE: the group's first lane solves in FP64 and writes its vertex at once
-// (Eq. pbgn_dx, Eq. pbgn_update).  Otherwise: |r|^2 of the vertex.
+// Extended precision: the element force of the lane's slot in float-float
+// arithmetic from float-pair records and displacements (pbng_ff.cuh), its
+// W-lane sum and the vertex terms in float-float too; the nodal Hessian,
+// which only scales the step, stays float32.  UPDATE: the group's first lane
+// solves and writes its vertex at once (Eq. pbgn_dx, Eq. pbgn_update).
+// Otherwise: |r|^2 of the vertex.
 template <int W, bool UPDATE, int MODEL>
 __device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
                                                  int g, int lane, PassParams pp, int32_t* err, double& rr,
@@ -249,18 +250,18 @@ __device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, W
     const ff::F2 gg[3][3] = {{ff::mk(ra.x, la.x), ff::mk(ra.y, la.y), ff::mk(ra.z, la.z)},
                              {ff::mk(rb.x, lb.x), ff::mk(rb.y, lb.y), ff::mk(rb.z, lb.z)},
                              {ff::mk(rc.x, lc.x), ff::mk(rc.y, lc.y), ff::mk(rc.z, lc.z)}};
+    float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float q[4] = {1.f, 0.f, 0.f, 0.f};
-    if (MODEL == el::kCorotated)
-        el::element_fp32_parts<false, true>(
-            f3(ra), f3(rb), f3(rc), ra.w, rb.w, make_float3(d[0][0].h, d[0][1].h, d[0][2].h),
-            make_float3(d[1][0].h, d[1][1].h, d[1][2].h), make_float3(d[2][0].h, d[2][1].h, d[2][2].h), nullptr, q);
-    ff::F2 f[3], A[6];
-    ff::element_force<MODEL>(gg, ff::mk(ra.w, la.w), ff::mk(rb.w, lb.w), d, q, f, UPDATE ? A : nullptr);
+    el::element_fp32_parts<UPDATE, MODEL == el::kCorotated>(
+        f3(ra), f3(rb), f3(rc), ra.w, rb.w, make_float3(d[0][0].h, d[0][1].h, d[0][2].h),
+        make_float3(d[1][0].h, d[1][1].h, d[1][2].h), make_float3(d[2][0].h, d[2][1].h, d[2][2].h), A, q);
+    ff::F2 f[3];
+    ff::element_force<MODEL>(gg, ff::mk(ra.w, la.w), ff::mk(rb.w, lb.w), d, q, f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) f[k] = el::group_sum_ff<W>(f[k]);
     if (UPDATE) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) A[k] = el::group_sum_ff<W>(A[k]);
+        for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
     }
     if (!active || (lane & (W - 1)) != 0) return;
     const int v = it.v0 + j;
@@ -268,7 +269,8 @@ __device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, W
     el::weak_terms_ff<true, UPDATE>(m, s, v, f, A);
     if constexpr (UPDATE) {
         if (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) return;  // frozen vertex of a mixed item
-        el::solve_and_write_ff(s, v, uh, ul, f, A, pp, err);
+        const float rf[3] = {f[0].h + f[0].l, f[1].h + f[1].l, f[2].h + f[2].l};
+        el::solve_and_write<true>(s, v, uh, ul, rf, A, pp, err);
     } else {
         if (m.fout_hi) {
             m.fout_hi[v] = make_float4(f[0].h, f[1].h, f[2].h, 0.f);
