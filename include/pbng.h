@@ -71,10 +71,12 @@ enum { PBNG_ACCEL_NONE = 0, PBNG_ACCEL_CHEBYSHEV = 1, PBNG_ACCEL_SOR = 2 };
  *                          COMPENSATED until the checks stall below 1e-2
  *                          (the best of the last 20 not below half the best
  *                          before them: the float32 passes' floor), then
- *                          EXTENDED;
- *                          a float32 check that puts a component at the
- *                          tolerance is confirmed with the extended residual
- *                          first.  r_0 and the residuals that pbng_sweep and
+ *                          EXTENDED; a float32 check that puts a component
+ *                          at the tolerance is confirmed with the extended
+ *                          residual first, and once half of the active
+ *                          components have failed such a confirmation the
+ *                          passes go EXTENDED too.  r_0 and the residuals
+ *                          that pbng_sweep and
  *                          pbng_sweep_host report are extended.  Ring layout
  *                          only.
  * Every residual sums each vertex's element terms and its vertex terms in

@@ -1615,6 +1615,7 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
     constexpr int kStallChecks = 20;
     constexpr double kStallFactor = 0.5, kStallBelow = 1e-2;
     std::vector<double> stall_hist;
+    std::vector<uint8_t> failed_conf(m->ncomp, 0);  // AUTO: a float32 check at tol not confirmed
     auto to_extended = [&]() {
         cp.precision = PBNG_PREC_EXTENDED;
         m->info.extended_from = done;
@@ -1659,8 +1660,9 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
         for (int k = 0; k < m->ncomp; ++k) sq[k] = (m->ncol == 0) ? 0.0 : m->h_pinned[k];
         if (cp.precision == PBNG_PREC_AUTO) {
             // a float32 check that puts an active component at the tolerance
-            // is replaced by the extended residual; if that is above it, the
-            // passes go extended
+            // is replaced by the extended residual; the passes go extended
+            // once at least half of the active components have failed such a
+            // confirmation (they sit at their float32 floor)
             auto below = [&](int k) { return std::sqrt(sq[k]) <= rel_tol * (m->r0[k] > 0 ? m->r0[k] : 1.0); };
             std::vector<uint8_t> was(m->ncomp, 0);
             bool any = false;
@@ -1668,9 +1670,15 @@ pbng_status solve_impl(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
                 if (!frozen[k] && below(k)) was[k] = 1, any = true;
             if (any) {
                 if ((s = residual_sq(m, 0, true, sq.data(), true))) return s;
-                bool ok = true;
-                for (int k = 0; k < m->ncomp; ++k) ok = ok && (!was[k] || below(k));
-                if (!ok) to_extended();
+                int failed_active = 0, active = 0;
+                for (int k = 0; k < m->ncomp; ++k) {
+                    if (was[k] && !below(k)) failed_conf[k] = 1;
+                    if (!frozen[k]) {
+                        active++;
+                        failed_active += failed_conf[k];
+                    }
+                }
+                if (2 * failed_active >= active) to_extended();
             }
         }
         cv = converged();

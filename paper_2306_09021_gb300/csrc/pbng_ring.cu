@@ -35,6 +35,8 @@
 
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pbng {
 namespace {
 
@@ -89,6 +91,22 @@ struct __align__(16) WarpSmem {
 static_assert(kCtasPerSm * (kWarps * sizeof(WarpSmem) + 1024) <= 228 * 1024,
               "the per-warp stages of kCtasPerSm CTAs exceed an SM's shared memory");
 
+// Extended-precision passes also stage the low words of the item's records
+// (RingLoBlock), gathered with the 1-ring one item ahead.
+struct __align__(16) LoStage {
+    float4 la[kRingLanes];
+    float4 lb[kRingLanes];
+    float4 lc[kRingLanes];
+};
+struct __align__(16) WarpSmemExt : WarpSmem {
+    LoStage lo[kGatStages];
+};
+static_assert(kCtasPerSmExt * (kWarps * sizeof(WarpSmemExt) + 1024) <= 228 * 1024,
+              "the per-warp stages of kCtasPerSmExt extended CTAs exceed an SM's shared memory");
+
+template <bool EXT>
+using SmemOf = typename std::conditional<EXT, WarpSmemExt, WarpSmem>::type;
+
 constexpr int kRecBytes = (int)sizeof(RingBlock);
 static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 
@@ -111,8 +129,8 @@ __device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, Warp
 // All lanes: gather the 1-ring displacements and own-vertex data of the item
 // in record stage r into gather stage g.  AUX: also the vertices' aux data
 // (passes that add the vertex terms when the element sums are done).
-template <bool COMP, bool AUX>
-__device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& s, WarpSmem& S, int r, int g,
+template <bool COMP, bool AUX, typename SM>
+__device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& s, SM& S, int r, int g,
                                               int lane) {
     const Item it = S.desc[r];
     if (it.skip) return;
@@ -128,6 +146,12 @@ __device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& 
             cp_async16(G.a0 + lane, m.aux0 + v);
             cp_async16(G.a1 + lane, m.aux1 + v);
         }
+    }
+    if constexpr (std::is_same<SM, WarpSmemExt>::value) {
+        const RingLoBlock& L = m.ring_lo[it.slot0 >> 5];
+        cp_async16(S.lo[g].la + lane, L.la + lane);
+        cp_async16(S.lo[g].lb + lane, L.lb + lane);
+        cp_async16(S.lo[g].lc + lane, L.lc + lane);
     }
 }
 
@@ -217,7 +241,7 @@ __device__ __forceinline__ void store_sq(const DeviceMesh& m, int v, double q, d
 // solves and writes its vertex at once (Eq. pbgn_dx, Eq. pbgn_update).
 // Otherwise: |r|^2 of the vertex.
 template <int W, bool UPDATE, int MODEL>
-__device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
+__device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, WarpSmemExt& S, const Item& it, int r,
                                                  int g, int lane, PassParams pp, int32_t* err, double& rr,
                                                  double* comp_sq) {
     const RecStage& R = S.rec[r];
@@ -236,7 +260,7 @@ __device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, W
         dv[2] = ff::add(ff::two_sum(hj.z, -uh.z), ff::fadd(lj.z, -ul.z));
     }
     const float4 ra = R.ra[lane], rb = R.rb[lane], rc = R.rc[lane];
-    const RingLoBlock& L = m.ring_lo[it.slot0 >> 5];
+    const LoStage& L = S.lo[g];
     const float4 la = L.la[lane], lb = L.lb[lane], lc = L.lc[lane];
     const int loc = __float_as_int(rc.w);
     const int base = lane & ~(W - 1);
@@ -338,7 +362,7 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
 
 // The lane width is uniform over an item: dispatch once per item.
 template <bool COMP, bool UPDATE, int MODEL, bool EXT>
-__device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
+__device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, SmemOf<EXT>& S, const Item& it, int r,
                                              int g, int lane, uint32_t btab, int qn, double& rr, double* comp_sq,
                                              PassParams pp, int32_t* err) {
     if (it.skip) return;  // uniform over the warp
@@ -398,7 +422,7 @@ __global__ void __launch_bounds__(kBlock, EXT ? kCtasPerSmExt : kCtasPerSm)
     extern __shared__ __align__(128) unsigned char smem[];
     pdl_release();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WarpSmem& S = reinterpret_cast<WarpSmem*>(smem)[warp];
+    SmemOf<EXT>& S = reinterpret_cast<SmemOf<EXT>*>(smem)[warp];
     const int gw = (int)blockIdx.x * kWarps + warp, nw = (int)gridDim.x * kWarps;
     int n, first, stride;
     if (blocked) {
@@ -521,7 +545,7 @@ template <bool COMP, bool UPDATE, bool EXT = false>
 cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams pp,
                         int32_t* err, double* partial, double* comp_sq, RingSched sc, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    const int bytes = kWarps * (int)sizeof(WarpSmem);  // attribute set by ring_prepare()
+    const int bytes = kWarps * (int)sizeof(SmemOf<EXT>);  // attribute set by ring_prepare()
     // An extended residual writes the partials of the float32 residual's grid
     // (2 CTAs per SM are resident, the rest follow); an extended update pass
     // keeps its grid to what is resident.
@@ -545,7 +569,7 @@ int ring_max_ctas_per_sm() { return kCtasPerSm; }
 cudaError_t ring_prepare() {
     // Three CTAs of 8 warps with their per-warp stages and queues need almost
     // all of an SM's shared memory: ask for the largest carveout.
-    const int bytes = kWarps * (int)sizeof(WarpSmem);
+    const int bytes = kWarps * (int)sizeof(WarpSmem), bytes_ext = kWarps * (int)sizeof(WarpSmemExt);
     const void* fns[18] = {
         (const void*)ring_kernel<true, true, 0, false>,  (const void*)ring_kernel<false, true, 0, false>,
         (const void*)ring_kernel<true, false, 0, false>, (const void*)ring_kernel<false, false, 0, false>,
@@ -556,8 +580,9 @@ cudaError_t ring_prepare() {
         (const void*)ring_kernel<true, true, 0, true>,   (const void*)ring_kernel<true, false, 0, true>,
         (const void*)ring_kernel<true, true, 1, true>,   (const void*)ring_kernel<true, false, 1, true>,
         (const void*)ring_kernel<true, true, 2, true>,   (const void*)ring_kernel<true, false, 2, true>};
-    for (const void* f : fns) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    for (int k = 0; k < 18; ++k) {
+        const void* f = fns[k];
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, k < 12 ? bytes : bytes_ext);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
