@@ -65,3 +65,25 @@ def test_batched_sweep_residuals_per_mesh(oracle_mod):
     for k, p in enumerate(probs):
         om = oracle_mod.OracleMesh.from_problem(p)
         assert r[k] == pytest.approx(om.residual(x[offs[k]:offs[k + 1]]), rel=1e-5)
+
+
+def test_auto_precision_batch_meets_the_tolerance_in_extended_residuals():
+    """A batch in PBNG_PREC_AUTO (symmetric order, automatic rho): every mesh
+    stops at the tolerance of its extended-precision residual, which
+    pbng_residual (extended) confirms after the solve."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    probs = W.batched_blocks(count=6, side_lo=4, side_hi=9, seed=31)
+    batch, mid, offs = W.concat_problems(probs)
+    m = Mesh.from_problem(batch, mesh_id=mid)
+    u0 = torch.tensor(batch.x0 - batch.X, dtype=torch.float32, device="cuda")
+    r0 = m.residual(u0)
+    u = u0.clone()
+    tol = 1e-7
+    st, sweeps, rel = m.solve(u, tol, 40000, default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric",
+                                                            precision="auto"))
+    assert st == 0 and np.all(rel <= tol)
+    # the output is float32: its own residual is that of the rounded iterate,
+    # so check the solve's report against a fresh extended evaluation of the
+    # iterate it stopped at (resume keeps the float pairs)
+    rel_again = m.sweep(u, 0, default_params(precision="extended", resume=1), want_residual=True)
+    assert np.all(rel_again <= tol * (1 + 1e-6))
