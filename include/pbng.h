@@ -451,7 +451,7 @@ pbng_status pbng_get_profile(pbng_mesh* m, pbng_profile* out);
 /* Launch schedules of the 1-ring colour passes (kernel_path 0).  The paper
  * runs each colour as one parallel loop (Section "Coloring and
  * Parallelism"); here each colour is one launch of a persistent grid whose
- * warps stream 32-slot work items, and two knobs decide how:
+ * warps stream 32-lane work items, and three knobs decide how:
  *   ctas_per_sm  1..PBNG_MAX_CTAS_PER_SM CTAs (8 warps each) per SM
  *   blocked      0: warp w takes items w, w + nwarps, ... (strided);
  *                1: warp w takes one contiguous run of items (blocked)
@@ -463,7 +463,7 @@ pbng_status pbng_get_profile(pbng_mesh* m, pbng_profile* out);
  * direct loads (vertices with more than 32 incident tets or 1-ring vertices,
  * or kernel_path 1) have no schedule and report ctas_per_sm = 0. */
 #define PBNG_MAX_COLOURS 64
-#define PBNG_MAX_CTAS_PER_SM 3
+#define PBNG_MAX_CTAS_PER_SM 2
 typedef struct {
     int32_t ncolours;                          /* of the current layout       */
     int32_t ctas_per_sm[PBNG_MAX_COLOURS];     /* per colour; 0 = not a ring colour */

@@ -60,7 +60,7 @@ class PbngProfile(ctypes.Structure):
 
 
 MAX_COLOURS = 64      # PBNG_MAX_COLOURS
-MAX_CTAS_PER_SM = 3   # PBNG_MAX_CTAS_PER_SM
+MAX_CTAS_PER_SM = 2   # PBNG_MAX_CTAS_PER_SM
 
 
 class PbngSchedule(ctypes.Structure):

@@ -65,7 +65,10 @@ struct pbng_mesh {
     std::vector<Item> items;           // ring items, colour by colour
     std::vector<int32_t> item_off;     // ncol + 1 offsets into items
     int32_t nitems_ring = 0;
-    int32_t ring_partials = 0;         // residual partials of the ring launch
+    std::vector<Item> pitems;          // pair items (float32 passes and residuals), colour by colour
+    std::vector<int32_t> pitem_off;    // ncol + 1 offsets into pitems
+    int32_t nitems_pair = 0;
+    int32_t ring_partials = 0;         // residual partials of the ring launch (either item list)
     bool want_direct = false;          // params.kernel_path == 1 requested
     int model = 0;                     // constitutive model of the last sweep / solve (residuals use it)
     // backward Euler (pbng_set_inertia): dt > 0 and lumped masses, caller order
@@ -83,7 +86,7 @@ struct pbng_mesh {
 
     // device buffers
     DevBuf d_inc_off, d_rec_a, d_rec_b, d_rec_c, d_rec_d, d_aux0, d_aux1, d_aux_lo, d_comp, d_perm;
-    DevBuf d_ring, d_ring_lo, d_items;
+    DevBuf d_ring, d_ring_lo, d_items, d_prec, d_pids, d_pitems;
     DevBuf d_host_u;  // device copy of the caller's host iterate (pbng_sweep_host)
     DevBuf d_active;                   // int32 [ncomp] component flags (1 = active)
     DevBuf d_vsq, d_comp_off, d_comp_list;  // several components: per-vertex |r|^2, component -> vertices
@@ -410,6 +413,8 @@ pbng_status build_layout(pbng_mesh* m) {
     }
     auto ring_n = [&](int32_t i) { return ring_off[i + 1] - ring_off[i]; };
     auto lanes = [&](int32_t i) { return width_for(std::max(deg(i), ring_n(i))); };
+    // pair items: two tets and two 1-ring vertices per lane
+    auto lanes2 = [&](int32_t i) { return width_for(std::max((deg(i) + 1) / 2, (ring_n(i) + 1) / 2)); };
 
     std::vector<int32_t> order;
     order.reserve(nv);
@@ -421,6 +426,7 @@ pbng_status build_layout(pbng_mesh* m) {
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         if (m->colour[a] != m->colour[b]) return m->colour[a] < m->colour[b];
         if (lanes(a) != lanes(b)) return lanes(a) > lanes(b);
+        if (lanes2(a) != lanes2(b)) return lanes2(a) > lanes2(b);
         if (m->ncomp > 1 && m->comp_of[a] != m->comp_of[b]) return m->comp_of[a] < m->comp_of[b];
         return false;
     });
@@ -597,6 +603,86 @@ pbng_status build_layout(pbng_mesh* m) {
     }
     m->nitems_ring = (int32_t)m->items.size();
 
+    // pair layout of the same colours: per run of equal pair width W2 inside
+    // a lane-width run, items of 32 / W2 vertices, one PairRec and one
+    // PairIds each; lane l of a vertex's group holds its 1-ring vertices l and
+    // W2 + l and its tets l and W2 + l
+    m->pitems.clear();
+    m->pitem_off.assign(m->ncol + 1, 0);
+    std::vector<PairRec> precs;
+    std::vector<PairIds> pids;
+    for (int c = 0; c < m->ncol; ++c) {
+        if (m->ring_colour[c]) {
+            const SegmentTable& t = m->tables[c];
+            for (int k = 0; k < t.count; ++k) {
+                const Segment& sg = t.seg[k];
+                for (int32_t rb = sg.v_begin; rb < sg.v_end;) {
+                    const int W2 = lanes2(order[rb]);
+                    int32_t re = rb;
+                    while (re < sg.v_end && lanes2(order[re]) == W2) ++re;
+                    const int per_item = kRingLanes / W2;
+                    for (int32_t vv = rb; vv < re; vv += per_item) {
+                        Item it{};
+                        it.v0 = vv;
+                        it.nv = std::min<int32_t>(per_item, re - vv);
+                        it.w = W2;
+                        it.slot0 = (int32_t)precs.size() * kRingLanes;
+                        it.comp = m->ncomp > 1 ? m->comp_of[order[vv]] : 0;
+                        for (int32_t q = 1; q < it.nv; ++q)
+                            if (m->ncomp > 1 && m->comp_of[order[vv + q]] != it.comp) it.comp = -1;
+                        m->pitems.push_back(it);
+                        PairRec rec;
+                        PairIds ids;
+                        std::memset(&rec, 0, sizeof(rec));
+                        std::memset(&ids, 0, sizeof(ids));
+                        float* val = reinterpret_cast<float*>(rec.r);
+                        // value k2 of tet `tet` (0 = A, 1 = B) of lane `lane`
+                        auto put = [&](int lane, int tet, int k2, float x) {
+                            val[(k2 / 2) * 4 * kRingLanes + 4 * lane + 2 * (k2 % 2) + tet] = x;
+                        };
+                        for (int q = 0; q < it.nv; ++q) {
+                            const int32_t w = vv + q;
+                            const int32_t i = order[w];
+                            const int32_t* rg = &ring[ring_off[i]];
+                            const int rn = ring_n(i);
+                            for (int l = 0; l < 2 * W2; ++l) ids.id[l / W2][q * W2 + l % W2] = l < rn ? iperm[rg[l]] : w;
+                            for (int32_t k2 = inc_off[i]; k2 < inc_off[i + 1]; ++k2) {
+                                const int slot = k2 - inc_off[i];
+                                const int lane = q * W2 + slot % W2, tet = slot / W2;
+                                const int32_t e = inc_tet[k2];
+                                const int loc = inc_loc[k2];
+                                double g[4][3];
+                                grads(e, g);
+                                int oth[3], n = 0;
+                                for (int j = 0; j < 4; ++j)
+                                    if (j != loc) oth[n++] = j;
+                                // slots relative to the group's first lane
+                                int32_t packed = 0;
+                                for (int qq = 0; qq < 3; ++qq) {
+                                    const int32_t w2 = m->tets[4 * (size_t)e + oth[qq]];
+                                    const int32_t l = (int32_t)(std::lower_bound(rg, rg + rn, w2) - rg);
+                                    packed |= ((l / W2) * kRingLanes + l % W2) << (8 * qq);
+                                }
+                                float pk;
+                                std::memcpy(&pk, &packed, 4);
+                                for (int jj = 0; jj < 3; ++jj)
+                                    for (int a = 0; a < 3; ++a) put(lane, tet, 3 * jj + a, (float)g[oth[jj]][a]);
+                                put(lane, tet, 9, (float)(2.0 * m->mu[e] * m->vol[e]));
+                                put(lane, tet, 10, (float)(m->lam[e] * m->vol[e]));
+                                put(lane, tet, 11, pk);
+                            }
+                        }
+                        precs.push_back(rec);
+                        pids.push_back(ids);
+                    }
+                    rb = re;
+                }
+            }
+        }
+        m->pitem_off[c + 1] = (int32_t)m->pitems.size();
+    }
+    m->nitems_pair = (int32_t)m->pitems.size();
+
     std::vector<float4> aux0(m->nfree), aux1(m->nfree), auxlo(m->nfree);
     std::vector<int32_t> comp(m->ncomp > 1 ? m->nfree : 0);
     for (int32_t w = 0; w < m->nfree; ++w) {
@@ -671,6 +757,9 @@ pbng_status build_layout(pbng_mesh* m) {
         PBNG_CUDA(m, upload(m->d_ring_lo, lblocks, st));
     }
     PBNG_CUDA(m, upload(m->d_items, m->items, st));
+    PBNG_CUDA(m, upload(m->d_prec, precs, st));
+    PBNG_CUDA(m, upload(m->d_pids, pids, st));
+    PBNG_CUDA(m, upload(m->d_pitems, m->pitems, st));
     PBNG_CUDA(m, upload(m->d_aux0, aux0, st));
     PBNG_CUDA(m, upload(m->d_aux1, aux1, st));
     PBNG_CUDA(m, upload(m->d_aux_lo, auxlo, st));
@@ -742,7 +831,7 @@ pbng_status build_layout(pbng_mesh* m) {
     PBNG_CUDA(m, ring_prepare());
     PBNG_CUDA(m, adjoint_prepare());
     PBNG_CUDA(m, ensure_buf(m->d_wg, sizeof(float2) * kMaxChunk));
-    m->ring_partials = ring_warps(m->nitems_ring);
+    m->ring_partials = ring_warps(std::max(m->nitems_ring, m->nitems_pair));
     PBNG_CUDA(m, ensure_buf(m->d_partial, sizeof(double) * (size_t)std::max(1, m->ring_partials + m->total_partials)));
     PBNG_CUDA(m, ensure_buf(m->d_comp_sq, sizeof(double) * (size_t)m->ncomp));
     PBNG_CUDA(m, ensure_buf(m->d_active, sizeof(int32_t) * (size_t)m->ncomp));
@@ -770,6 +859,8 @@ pbng_status build_layout(pbng_mesh* m) {
     d.vsq = m->ncomp > 1 ? (double*)m->d_vsq.p : nullptr;
     d.ring = (const RingBlock*)m->d_ring.p;
     d.ring_lo = (const RingLoBlock*)m->d_ring_lo.p;
+    d.prec = (const PairRec*)m->d_prec.p;
+    d.pids = (const PairIds*)m->d_pids.p;
     d.copy_shortfall = m->copy_shortfall;
     d.pn_x = (float)m->pn[0];
     d.pn_y = (float)m->pn[1];
@@ -823,9 +914,11 @@ pbng_status enqueue_residual(pbng_mesh* m, State s, bool compensated, double* pa
         PBNG_CUDA(m, cudaMemsetAsync(m->d_vsq.p, 0, sizeof(double) * (size_t)m->nfree, st));
     }
     if (m->nitems_ring > 0) {
-        PBNG_CUDA(m, launch_ring_residual(dm, s, (const Item*)m->d_items.p, m->nitems_ring, compensated,
-                                          partial, multi ? comp_sq : nullptr, m->model, (int32_t*)m->d_err.p, st,
-                                          extended && compensated));
+        const bool ext = extended && compensated;
+        PBNG_CUDA(m, launch_ring_residual(dm, s, (const Item*)(ext ? m->d_items.p : m->d_pitems.p),
+                                          ext ? m->nitems_ring : m->nitems_pair, compensated, partial,
+                                          multi ? comp_sq : nullptr, m->model, (int32_t*)m->d_err.p, st, ext,
+                                          m->ring_partials));
         m->kernel_launches++;
     }
     for (int c = 0; c < m->ncol; ++c) {
@@ -1006,10 +1099,14 @@ pbng_status enqueue_chunk(pbng_mesh* m, const pbng_params* p, int32_t K, bool wi
         for (const int c : seq) {
             if (m->tables[c].total_blocks <= 0) continue;
             if ((r = mark(kProfColour))) return r;
-            if (m->ring_colour[c])
+            if (m->ring_colour[c] && ext)
                 PBNG_CUDA(m, launch_ring_pass(m->dm, cur, (const Item*)m->d_items.p + m->item_off[c],
                                               m->item_off[c + 1] - m->item_off[c], pp, comp, m->sched[c],
-                                              (int32_t*)m->d_err.p, st, ext));
+                                              (int32_t*)m->d_err.p, st, true));
+            else if (m->ring_colour[c])
+                PBNG_CUDA(m, launch_ring_pass(m->dm, cur, (const Item*)m->d_pitems.p + m->pitem_off[c],
+                                              m->pitem_off[c + 1] - m->pitem_off[c], pp, comp, m->sched[c],
+                                              (int32_t*)m->d_err.p, st));
             else
                 PBNG_CUDA(m, launch_colour_pass(m->dm, cur, m->tables[c], pp, comp, (int32_t*)m->d_err.p, st));
             if ((r = mark(kProfColour))) return r;
@@ -2092,7 +2189,7 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
                 d.vsq = nullptr;
                 PBNG_CUDA(m, launch_ring_residual(d, k == 0 ? up : um, (const Item*)m->d_items.p, m->nitems_ring, true,
                                                   (double*)m->d_partial.p, nullptr, m->model, (int32_t*)m->d_err.p, st,
-                                                  true));
+                                                  true, m->ring_partials));
             }
             PBNG_CUDA(m, launch_adjoint_refine_rhs(m->nfree, (const float4*)m->d_gv.p, (const float4*)m->d_fp[0].p,
                                                    (const float4*)m->d_fp[1].p, (const float4*)m->d_fp[2].p,
@@ -2552,8 +2649,8 @@ pbng_status pbng_autotune(pbng_mesh* m, const float* u_dev, const pbng_params* p
     const int nc = (int)cands.size(), ncol = m->ncol;
     auto pass = [&](int c, RingSched sc) -> pbng_status {
         if (m->ring_colour[c])
-            PBNG_CUDA(m, launch_ring_pass(m->dm, scratch, (const Item*)m->d_items.p + m->item_off[c],
-                                          m->item_off[c + 1] - m->item_off[c], pp, comp, sc,
+            PBNG_CUDA(m, launch_ring_pass(m->dm, scratch, (const Item*)m->d_pitems.p + m->pitem_off[c],
+                                          m->pitem_off[c + 1] - m->pitem_off[c], pp, comp, sc,
                                           (int32_t*)m->d_err.p, st));
         else
             PBNG_CUDA(m, launch_colour_pass(m->dm, scratch, m->tables[c], pp, comp, (int32_t*)m->d_err.p, st));
@@ -2682,7 +2779,7 @@ void pbng_destroy(pbng_mesh* m) {
     DevBuf* bufs[] = {&m->d_lam[0], &m->d_lam[1], &m->d_lam[2], &m->d_gv, &m->d_diag, &m->d_hdl, &m->d_tv,
                       &m->d_tb, &m->d_dq_int, &m->d_dq_caller, &m->d_adj_partial,
                       &m->d_inc_off, &m->d_rec_a, &m->d_rec_b, &m->d_rec_c, &m->d_rec_d,
-                      &m->d_ring, &m->d_ring_lo, &m->d_items, &m->d_host_u, &m->d_vsq, &m->d_comp_off,
+                      &m->d_ring, &m->d_ring_lo, &m->d_items, &m->d_prec, &m->d_pids, &m->d_pitems, &m->d_host_u, &m->d_vsq, &m->d_comp_off,
                       &m->d_comp_list, &m->d_lam_hi, &m->d_lam_lo, &m->d_rhs, &m->d_fp[0], &m->d_fp[1], &m->d_fp[2],
                       &m->d_fp[3], &m->d_shift[0][0], &m->d_shift[0][1], &m->d_shift[1][0], &m->d_shift[1][1],
                       &m->d_maxabs, &m->d_refine_partial,

@@ -31,6 +31,33 @@ __device__ __forceinline__ float3 pair_diff(float4 hj, float4 lj, float3 uh, flo
     return d;
 }
 
+// q holds column 0 of adj(M) for the symmetric 4x4 M = N - t I (upper
+// triangle m00 .. m33); replace it with the column of adj(M) whose diagonal
+// entry is largest in magnitude (adj(M) = -p'(t) q q^T is negative
+// semidefinite, so its diagonal is -p'(t) q_k^2).  M is symmetric, so is
+// adj(M): the other diagonal and off-diagonal cofactors, in registers.
+__device__ __forceinline__ void adjugate_best_column(float m00, float m01, float m02, float m03, float m11, float m12,
+                                                     float m13, float m22, float m23, float m33, float* q) {
+    const float a11 = det3(m00, m02, m03, m02, m22, m23, m03, m23, m33);
+    const float a22 = det3(m00, m01, m03, m01, m11, m13, m03, m13, m33);
+    const float a33 = det3(m00, m01, m02, m01, m11, m12, m02, m12, m22);
+    const float a12 = -det3(m00, m02, m03, m01, m12, m13, m03, m23, m33);
+    const float a13 = det3(m00, m02, m03, m01, m12, m13, m02, m22, m23);
+    const float a23 = -det3(m00, m01, m03, m01, m11, m13, m02, m12, m23);
+    float best = -q[0];
+    int kb = 0;
+    if (-a11 > best) { best = -a11; kb = 1; }
+    if (-a22 > best) { best = -a22; kb = 2; }
+    if (-a33 > best) { kb = 3; }
+    if (kb == 1) {
+        q[0] = q[1]; q[1] = a11; q[2] = a12; q[3] = a13;
+    } else if (kb == 2) {
+        q[0] = q[2]; q[1] = a12; q[2] = a22; q[3] = a23;
+    } else if (kb == 3) {
+        q[0] = q[3]; q[1] = a13; q[2] = a23; q[3] = a33;
+    }
+}
+
 // Rotation part of F = I + H for the corotated energy (Section "Constitutive
 // Models", Eq. cor, with R the rotation of the polar decomposition in SO(3)),
 // as the unit quaternion q = (w, x, y, z) times `scale`.
@@ -93,28 +120,8 @@ __device__ __forceinline__ void polar_quaternion(const float* H, float n2, float
     q[3] = -(m01 * k12 - m11 * k02 + m12 * k01);
     // adj(M) = -p'(t) q q^T, so q_0^2 = -adj_00 / p'(t).  Beyond about 120
     // degrees column 0 is poorly scaled: take the column of adj(M) with the
-    // largest diagonal entry instead.  M is symmetric, so is adj(M); its other
-    // diagonal and off-diagonal cofactors, in registers:
-    if (!(-q[0] > 0.25f * dp)) {
-        const float a11 = det3(m00, m02, m03, m02, m22, m23, m03, m23, m33);
-        const float a22 = det3(m00, m01, m03, m01, m11, m13, m03, m13, m33);
-        const float a33 = det3(m00, m01, m02, m01, m11, m12, m02, m12, m22);
-        const float a12 = -det3(m00, m02, m03, m01, m12, m13, m03, m23, m33);
-        const float a13 = det3(m00, m02, m03, m01, m12, m13, m02, m22, m23);
-        const float a23 = -det3(m00, m01, m03, m01, m11, m13, m02, m12, m23);
-        float best = -q[0];
-        int kb = 0;
-        if (-a11 > best) { best = -a11; kb = 1; }
-        if (-a22 > best) { best = -a22; kb = 2; }
-        if (-a33 > best) { kb = 3; }
-        if (kb == 1) {
-            q[0] = q[1]; q[1] = a11; q[2] = a12; q[3] = a13;
-        } else if (kb == 2) {
-            q[0] = q[2]; q[1] = a12; q[2] = a22; q[3] = a23;
-        } else if (kb == 3) {
-            q[0] = q[3]; q[1] = a13; q[2] = a23; q[3] = a33;
-        }
-    }
+    // largest diagonal entry instead.
+    if (!(-q[0] > 0.25f * dp)) adjugate_best_column(m00, m01, m02, m03, m11, m12, m13, m22, m23, m33, q);
     const float qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     if (qq > 1e-30f && qq < 3.0e38f) {
         const float inv = scale * rsqrtf(qq);

@@ -47,6 +47,26 @@ struct __align__(16) RingLoBlock {
     float4 lc[32];   // g_j3 low words (xyz), 0
 };
 
+// Float32 passes (pbng_ring.cu): one 32-lane pair item.  A vertex of pair
+// width W owns W consecutive lanes, W the smallest power of two (>= 4)
+// holding half its incident tets and half its 1-ring.  Lane l of its group
+// holds its 1-ring vertices l and W + l (PairIds) and two of its incident
+// tets, A = tet l and B = tet W + l (PairRec; zero records where it has
+// fewer).  The twelve values of a tet (g_j1, g_j2, g_j3, a = 2 mu V,
+// b = lambda V, and the slots of its three other vertices among the item's
+// 64 1-ring slots as bytes, int bits) are interleaved so that value k of tet
+// A and of tet B are adjacent words: (r[k/2][lane].x, .y) for even k and
+// (.z, .w) for odd k, one operand of a packed f32x2 instruction.  1-ring
+// vertex l of a group whose first lane is f sits in slot
+// (l / W) 32 + f + (l % W).  Ids and records of an item are fetched by
+// separate bulk copies: the ids one item earlier than the records.
+struct __align__(16) PairRec {
+    float4 r[6][32];
+};
+struct __align__(16) PairIds {
+    int32_t id[2][32];  // 1-ring vertex ids of each lane (own id when padding)
+};
+
 struct DeviceMesh {
     int32_t nv;              // all vertices (free first, then clamped)
     int32_t nfree;
@@ -73,6 +93,10 @@ struct DeviceMesh {
     // Slot s is entry s % 32 of block s / 32 (RingBlock).
     const struct RingBlock* ring;  // [nslots / 32]
     const struct RingLoBlock* ring_lo;  // [nslots / 32] low words of the same records
+    // The same colours in pair items (float32 passes and residuals): one
+    // PairRec and one PairIds per item of the pair item list.
+    const struct PairRec* prec;
+    const struct PairIds* pids;
     // Test hook (pbng_test_set_copy_shortfall): bytes that each warp's first
     // record copy of a ring pass is expected to carry beyond its size, so
     // that its bounded wait runs out; 0 in normal use.
@@ -166,9 +190,12 @@ cudaError_t launch_inertia(int32_t nv, int32_t nfree, const int32_t* perm, float
                            cudaStream_t st);
 
 // Ring-layout kernels (pbng_ring.cu): persistent warps, each streaming its
-// items with TMA bulk copies and cp.async gathers.  The residual writes one
-// FP64 partial per warp of the grid (ring_warps(nitems) of them) or, with
-// comp_sq, per-component sums.
+// items with TMA bulk copies and cp.async gathers.  Float32 passes and
+// residuals (extended = false) take the pair item list (PairRec, PairIds),
+// extended ones the ring item list (RingBlock records and their low words).
+// A residual runs a grid of exactly grid_warps warps (a multiple of 8, at
+// least ring_warps() of its item list) and writes one FP64 partial per warp,
+// or, with comp_sq, per-component sums.
 // A colour pass's launch schedule: CTAs per SM of the persistent grid
 // (1..ring_max_ctas_per_sm()), the item order (0 strided, 1 blocked), and
 // whether the grid is trimmed to the fewest warps that take the same number
@@ -182,12 +209,12 @@ int ring_warps(int nitems);
 int ring_max_ctas_per_sm();
 cudaError_t ring_prepare();  // sets kernel attributes (call outside stream capture)
 // extended: float-float element forces from the float-pair records (needs
-// compensated and ring_lo), summed in FP64 (pbng_ff.cuh).
+// compensated and ring_lo), summed in float-float (pbng_ff.cuh).
 cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams p,
                              bool compensated, RingSched sc, int32_t* err, cudaStream_t st, bool extended = false);
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
                                  bool compensated, double* warp_partial, double* comp_sq, int model,
-                                 int32_t* err, cudaStream_t st, bool extended = false);
+                                 int32_t* err, cudaStream_t st, bool extended, int grid_warps);
 
 // Equilibrium adjoint (pbng_adjoint.cu).  Vertex kernels: one warp per
 // ring item; mode 0 computes the 3x3 diagonal blocks of H, mode 1 is one

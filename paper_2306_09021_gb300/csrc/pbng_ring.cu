@@ -1,25 +1,32 @@
-// Ring-layout colour pass and residual for sm_103a.
+// Ring-layout colour passes and residuals for sm_103a.
 //
-// Layout: every free vertex of a colour owns W consecutive record slots
-// (W = 4, 8, 16 or 32: the smallest power of two holding both its incident
-// tets and its 1-ring, the distinct vertices it shares a tet with).  Slot l
-// holds one incident tet (dN/dX of the other three vertices, 2 mu V,
-// lambda V, and the three vertices' positions in the 1-ring as bytes) and the
-// id of the l-th 1-ring vertex.  A warp's work item is 32 aligned slots =
-// 32 / W vertices, one W-lane group each.
+// Layout: every free vertex of a colour owns W consecutive lanes of a
+// 32-lane work item (W = 4, 8, 16 or 32), one W-lane group per vertex; its
+// lanes hold the ids of its 1-ring vertices (the distinct vertices it shares
+// a tet with) and records of its incident tets: dN/dX of the other three
+// vertices, 2 mu V, lambda V, and the positions of those vertices in the
+// item's 1-ring slots as bytes.
+//   * Float32 passes and residuals (pair_kernel) read pair items (PairRec,
+//     PairIds): two tets and two 1-ring vertices per lane, W the smallest
+//     power of two holding half of each, and the element terms of both tets
+//     in packed f32x2 arithmetic (pbng_pair.cuh).
+//   * Extended-precision ones (ext_kernel) read ring items (RingBlock and
+//     its low words RingLoBlock): one tet and one 1-ring vertex per lane,
+//     float-float element forces (pbng_ff.cuh).
 //
-// Each warp is persistent and runs its own three-stage pipeline, with no
-// block-wide barrier anywhere:
-//   * lane 0 fetches an item's records and 1-ring ids (one RingBlock) with a
-//     TMA 1D bulk copy (cp.async.bulk ... mbarrier::complete_tx) two items ahead;
-//   * once they land, every lane gathers the displacement pair of its 1-ring
-//     vertex (and the item's own vertices and aux data) with cp.async one item
-//     ahead, so each neighbour is read once per vertex update, not once per
-//     incident tet;
-//   * the compute forms u_j - u_i once per 1-ring vertex, passes the three a
-//     tet needs to its lane by warp shuffles, evaluates the element term
-//     (pbng_element.cuh), sums the W lanes and adds the vertex terms; the
-//     group's first lane queues the vertex's force and Hessian;
+// Each warp is persistent and runs its own pipeline, with no block-wide
+// barrier anywhere:
+//   * lane 0 fetches an item's ids and records with TMA 1D bulk copies
+//     (cp.async.bulk ... mbarrier::complete_tx) ahead of their use;
+//   * once the ids land, every lane gathers the displacement pairs of its
+//     1-ring vertices (and the item's own vertices and aux data) with
+//     cp.async one item ahead, so each neighbour is read once per vertex
+//     update, not once per incident tet;
+//   * the compute forms u_j - u_i once per 1-ring vertex, hands each tet the
+//     three it needs (shared memory for pair items, warp shuffles for ring
+//     items), evaluates the element terms, sums the W lanes and adds the
+//     vertex terms; in the float32 passes the group's first lane queues the
+//     vertex's force and Hessian;
 //   * when the warp's queue is nearly full (and at the end) all 32 lanes
 //     solve and write one queued vertex each (Eq. pbgn_dx, Eq. pbgn_update),
 //     instead of one lane per W-lane group solving while the others idle.
@@ -32,10 +39,9 @@
 #include "pbng_ff.cuh"
 #include "pbng_internal.h"
 #include "pbng_launch.cuh"
+#include "pbng_pair.cuh"
 
 #include <stdint.h>
-
-#include <type_traits>
 
 namespace pbng {
 namespace {
@@ -45,29 +51,24 @@ using el::kFull;
 using namespace async;
 
 constexpr int kWarps = kBlock / 32;
-// Three record stages (items requested two ahead) and 3 CTAs of 8 warps per
-// SM: with two stages and 4 CTAs (64 registers) the passes were 15 % slower,
-// the shorter pipeline exposing more TMA latency than the extra warps hide.
-constexpr int kRecStages = 3;                 // record stages; items are requested kRecStages - 1 ahead
-constexpr int kRecAhead = kRecStages - 1;
+// 2 CTAs of 8 warps per SM: the packed element terms of two tets per lane
+// take most of 128 registers, and the per-warp stages below half of an SM's
+// shared memory.
+constexpr int kCtasPerSm = 2;
 constexpr int kGatStages = 2;
 constexpr int kItemVerts = kRingLanes / 4;
-constexpr int kCtasPerSm = 3;
-// Extended-precision passes (float-float element forces) need more registers
-// than 3 CTAs of 8 warps leave.
-constexpr int kCtasPerSmExt = 2;
 constexpr int kQueue = 32;   // deferred vertex updates per warp
 
-using RecStage = RingBlock;
-static_assert(kRingLanes == 32, "one RingBlock per ring item");
+static_assert(kRingLanes == 32, "one record block per 32-lane item");
 
-struct __align__(16) GatStage {
-    float4 nh[kRingLanes];   // 1-ring displacement hi
-    float4 nl[kRingLanes];   // 1-ring displacement lo
+template <int NR>
+struct __align__(16) GatStageT {
+    float4 nh[NR];           // 1-ring displacement hi (pair items: u_j - u_i once formed)
+    float4 nl[NR];           // 1-ring displacement lo
     float4 oh[kItemVerts];   // own vertex hi
     float4 ol[kItemVerts];   // own vertex lo
-    float4 a0[kItemVerts];   // aux0 (f_ext, K), residual passes only
-    float4 a1[kItemVerts];   // aux1 (spring target, n.X - d), residual passes only
+    float4 a0[kItemVerts];   // aux0 (f_ext, K), residual and extended passes only
+    float4 a1[kItemVerts];   // aux1 (spring target, n.X - d), residual and extended passes only
 };
 
 // Force r (3) and modified Hessian A (6, upper triangle) of queued vertices,
@@ -80,78 +81,115 @@ struct __align__(16) UpdQueue {
     int32_t v[kQueue];
 };
 
-struct __align__(16) WarpSmem {
-    RecStage rec[kRecStages];
-    GatStage gat[kGatStages];
-    UpdQueue q;
-    Item desc[kRecStages];
-    unsigned long long bar[kRecStages];
-};
-
-static_assert(kCtasPerSm * (kWarps * sizeof(WarpSmem) + 1024) <= 228 * 1024,
-              "the per-warp stages of kCtasPerSm CTAs exceed an SM's shared memory");
-
-// Extended-precision passes also stage the low words of the item's records
-// (RingLoBlock), gathered with the 1-ring one item ahead.
+// Extended passes: three stages of ring records (items requested two ahead)
+// and of their low words, gathered with the 1-ring one item ahead.
+constexpr int kExtStages = 3;
 struct __align__(16) LoStage {
     float4 la[kRingLanes];
     float4 lb[kRingLanes];
     float4 lc[kRingLanes];
 };
-struct __align__(16) WarpSmemExt : WarpSmem {
+struct __align__(16) WarpSmemExt {
+    RingBlock rec[kExtStages];
+    GatStageT<kRingLanes> gat[kGatStages];
     LoStage lo[kGatStages];
+    Item desc[kExtStages];
+    unsigned long long bar[kExtStages];
 };
-static_assert(kCtasPerSmExt * (kWarps * sizeof(WarpSmemExt) + 1024) <= 228 * 1024,
-              "the per-warp stages of kCtasPerSmExt extended CTAs exceed an SM's shared memory");
 
-template <bool EXT>
-using SmemOf = typename std::conditional<EXT, WarpSmemExt, WarpSmem>::type;
+// Float32 passes: the ids of an item are needed one item before its records
+// (to gather its 1-ring), so they travel in their own bulk copies, two items
+// ahead, and the records one item ahead.
+constexpr int kIdStages = 3;
+constexpr int kRecStages = 2;
+struct __align__(16) WarpSmemPair {
+    PairRec rec[kRecStages];
+    PairIds ids[kIdStages];
+    GatStageT<2 * kRingLanes> gat[kGatStages];
+    UpdQueue q;
+    Item desc[kIdStages];
+    unsigned long long id_bar[kIdStages];
+    unsigned long long rec_bar[kRecStages];
+};
 
-constexpr int kRecBytes = (int)sizeof(RingBlock);
-static_assert(kRecBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+static_assert(kCtasPerSm * (kWarps * sizeof(WarpSmemPair) + 1024) <= 228 * 1024,
+              "the per-warp stages of kCtasPerSm CTAs exceed an SM's shared memory");
+static_assert(kCtasPerSm * (kWarps * sizeof(WarpSmemExt) + 1024) <= 228 * 1024,
+              "the per-warp stages of kCtasPerSm extended CTAs exceed an SM's shared memory");
+static_assert(sizeof(PairRec) % 16 == 0 && sizeof(PairIds) % 16 == 0 && sizeof(RingBlock) % 16 == 0,
+              "bulk copies move multiples of 16 bytes");
 
-// Lane 0: request the records and 1-ring ids of item `it` into stage r.  An
-// item whose whole component is frozen is marked skipped and fetches nothing.
-// `extra` bytes are expected beyond the copy (the timeout test hook).
-__device__ __forceinline__ void issue_records(const DeviceMesh& m, Item it, WarpSmem& S, int r,
-                                              uint32_t extra = 0u) {
-    it.skip = (it.comp >= 0 && m.comp_active && !m.comp_active[it.comp]) ? 1 : 0;
-    S.desc[r] = it;
-    unsigned long long* bar = S.bar + r;
-    if (it.skip) {
-        mbar_arrive_expect_tx(bar, 0);
-        return;
-    }
-    mbar_arrive_expect_tx(bar, kRecBytes + extra);
-    bulk_g2s(&S.rec[r], m.ring + (it.slot0 >> 5), kRecBytes, bar);
+// Whether item `it`'s whole component is frozen (then nothing is fetched).
+__device__ __forceinline__ int item_skipped(const DeviceMesh& m, const Item& it) {
+    return (it.comp >= 0 && m.comp_active && !m.comp_active[it.comp]) ? 1 : 0;
 }
 
-// All lanes: gather the 1-ring displacements and own-vertex data of the item
-// in record stage r into gather stage g.  AUX: also the vertices' aux data
-// (passes that add the vertex terms when the element sums are done).
-template <bool COMP, bool AUX, typename SM>
-__device__ __forceinline__ void issue_gathers(const DeviceMesh& m, const State& s, SM& S, int r, int g,
-                                              int lane) {
+// Lane 0: one bulk copy of `bytes` (0 when the item is skipped) plus
+// `extra` expected bytes (the timeout test hook) onto barrier `bar`.
+__device__ __forceinline__ void issue_copy(void* dst, const void* src, uint32_t bytes, unsigned long long* bar,
+                                           uint32_t extra = 0u) {
+    mbar_arrive_expect_tx(bar, bytes + extra);
+    if (bytes) bulk_g2s(dst, src, bytes, bar);
+}
+
+// Extended passes, lane 0: request the records and 1-ring ids of item `it`
+// into stage r.  `extra` bytes are expected beyond the copy (the timeout
+// test hook).
+__device__ __forceinline__ void ext_issue_records(const DeviceMesh& m, Item it, WarpSmemExt& S, int r,
+                                                  uint32_t extra = 0u) {
+    it.skip = item_skipped(m, it);
+    S.desc[r] = it;
+    issue_copy(&S.rec[r], m.ring + (it.slot0 >> 5), it.skip ? 0u : (uint32_t)sizeof(RingBlock), S.bar + r,
+               it.skip ? 0u : extra);
+}
+
+// Extended passes, all lanes: gather the 1-ring displacements, own-vertex
+// and aux data and record low words of the item in record stage r into
+// gather stage g.
+__device__ __forceinline__ void ext_issue_gathers(const DeviceMesh& m, const State& s, WarpSmemExt& S, int r, int g,
+                                                  int lane) {
     const Item it = S.desc[r];
     if (it.skip) return;
-    GatStage& G = S.gat[g];
+    auto& G = S.gat[g];
     const int id = S.rec[r].id[lane];
     cp_async16(G.nh + lane, s.hi + id);
-    if (COMP) cp_async16(G.nl + lane, s.lo + id);
+    cp_async16(G.nl + lane, s.lo + id);
+    if (lane < it.nv) {
+        const int v = it.v0 + lane;
+        cp_async16(G.oh + lane, s.hi + v);
+        cp_async16(G.ol + lane, s.lo + v);
+        cp_async16(G.a0 + lane, m.aux0 + v);
+        cp_async16(G.a1 + lane, m.aux1 + v);
+    }
+    const RingLoBlock& L = m.ring_lo[it.slot0 >> 5];
+    cp_async16(S.lo[g].la + lane, L.la + lane);
+    cp_async16(S.lo[g].lb + lane, L.lb + lane);
+    cp_async16(S.lo[g].lc + lane, L.lc + lane);
+}
+
+// Float32 passes, all lanes: gather the displacement pairs of the lane's two
+// 1-ring slots and the item's own vertices (AUX: and their aux data, for the
+// residual) of the item in id stage r into gather stage g.
+template <bool COMP, bool AUX>
+__device__ __forceinline__ void pair_issue_gathers(const DeviceMesh& m, const State& s, WarpSmemPair& S, int r, int g,
+                                                   int lane) {
+    const Item it = S.desc[r];
+    if (it.skip) return;
+    auto& G = S.gat[g];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int id = S.ids[r].id[h][lane];
+        cp_async16(G.nh + h * kRingLanes + lane, s.hi + id);
+        if (COMP) cp_async16(G.nl + h * kRingLanes + lane, s.lo + id);
+    }
     if (lane < it.nv) {
         const int v = it.v0 + lane;
         cp_async16(G.oh + lane, s.hi + v);
         if (COMP) cp_async16(G.ol + lane, s.lo + v);
-        if (AUX) {  // the float32 update passes add the vertex terms when the queue is flushed
+        if (AUX) {
             cp_async16(G.a0 + lane, m.aux0 + v);
             cp_async16(G.a1 + lane, m.aux1 + v);
         }
-    }
-    if constexpr (std::is_same<SM, WarpSmemExt>::value) {
-        const RingLoBlock& L = m.ring_lo[it.slot0 >> 5];
-        cp_async16(S.lo[g].la + lane, L.la + lane);
-        cp_async16(S.lo[g].lb + lane, L.lb + lane);
-        cp_async16(S.lo[g].lc + lane, L.lc + lane);
     }
 }
 
@@ -244,8 +282,8 @@ template <int W, bool UPDATE, int MODEL>
 __device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, WarpSmemExt& S, const Item& it, int r,
                                                  int g, int lane, PassParams pp, int32_t* err, double& rr,
                                                  double* comp_sq) {
-    const RecStage& R = S.rec[r];
-    const GatStage& G = S.gat[g];
+    const RingBlock& R = S.rec[r];
+    const auto& G = S.gat[g];
     const int j = lane / W;
     const bool active = j < it.nv;
     float3 uh = make_float3(0.f, 0.f, 0.f), ul = uh;
@@ -304,34 +342,64 @@ __device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, W
     }
 }
 
+// Float32: the element terms of the lane's two tets (A = tet l, B = tet
+// W + l of its group's vertex) in packed f32x2 arithmetic, their sum, the
+// W-lane sums of the group.  Each lane first forms u_j - u_i of its two
+// 1-ring slots in place in the gather stage; every tet then reads the three
+// differences it needs from there.  UPDATE: the sums go straight into the
+// warp's queue from the lanes that hold them; the vertex terms are added
+// when the queue is flushed.  Otherwise: the element sums in float32, their
+// W-lane sum and the vertex terms in float-float, and |r|^2 of the vertex.
 template <int W, bool COMP, bool UPDATE, int MODEL>
-__device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, WarpSmem& S, const Item& it, int r,
-                                               int g, int lane, uint32_t btab, int qn, double& rr,
-                                               double* comp_sq) {
-    const RecStage& R = S.rec[r];
-    const GatStage& G = S.gat[g];
+__device__ __forceinline__ void compute_item_pair(const DeviceMesh& m, State s, WarpSmemPair& S, const Item& it, int r,
+                                                  int g, int lane, uint32_t btab, int qn, double& rr,
+                                                  double* comp_sq) {
+    const PairRec& R = S.rec[r];
+    auto& G = S.gat[g];
     const int j = lane / W;
     const bool active = j < it.nv;
     const float3 zero3 = make_float3(0.f, 0.f, 0.f);
-    float3 uh = zero3, ul = zero3, d = zero3;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float3 uh = zero3, ul = zero3;
     if (active) {
         uh = f3(G.oh[j]);
         if (COMP) ul = f3(G.ol[j]);
-        d = el::pair_diff<COMP>(G.nh[lane], COMP ? G.nl[lane] : make_float4(0.f, 0.f, 0.f, 0.f), uh, ul);
     }
-    const float4 ra = R.ra[lane], rb = R.rb[lane], rc = R.rc[lane];
-    const int loc = __float_as_int(rc.w);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = h * kRingLanes + lane;  // only this lane reads or writes slot k here
+        float3 d = zero3;
+        if (active) d = el::pair_diff<COMP>(G.nh[k], COMP ? G.nl[k] : zero4, uh, ul);
+        G.nh[k] = make_float4(d.x, d.y, d.z, 0.f);
+    }
+    __syncwarp();
+    float4 q[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = R.r[k][lane];
+    // value k of the pair: (q[k/2].x, .y) for even k, (.z, .w) for odd k
+    const float2 g1[3] = {make_float2(q[0].x, q[0].y), make_float2(q[0].z, q[0].w), make_float2(q[1].x, q[1].y)};
+    const float2 g2[3] = {make_float2(q[1].z, q[1].w), make_float2(q[2].x, q[2].y), make_float2(q[2].z, q[2].w)};
+    const float2 g3[3] = {make_float2(q[3].x, q[3].y), make_float2(q[3].z, q[3].w), make_float2(q[4].x, q[4].y)};
+    const float2 a = make_float2(q[4].z, q[4].w), b = make_float2(q[5].x, q[5].y);
+    const int locA = __float_as_int(q[5].z), locB = __float_as_int(q[5].w);
     const int base = lane & ~(W - 1);
-    const int s1 = base + (loc & 255), s2 = base + ((loc >> 8) & 255), s3 = base + ((loc >> 16) & 255);
-    const float3 d1 = make_float3(__shfl_sync(kFull, d.x, s1), __shfl_sync(kFull, d.y, s1), __shfl_sync(kFull, d.z, s1));
-    const float3 d2 = make_float3(__shfl_sync(kFull, d.x, s2), __shfl_sync(kFull, d.y, s2), __shfl_sync(kFull, d.z, s2));
-    const float3 d3 = make_float3(__shfl_sync(kFull, d.x, s3), __shfl_sync(kFull, d.y, s3), __shfl_sync(kFull, d.z, s3));
-    float rv[3] = {0.f, 0.f, 0.f};
-    float A[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    el::element_math_m<UPDATE, MODEL, false>(f3(ra), f3(rb), f3(rc), ra.w, rb.w, d1, d2, d3, rv, A);
+    float2 dk[3][3];  // dk[k][c]: component c of u_jk - u_i, (tet A, tet B)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 dA = G.nh[base + ((locA >> (8 * k)) & 255)];
+        const float4 dB = G.nh[base + ((locB >> (8 * k)) & 255)];
+        dk[k][0] = make_float2(dA.x, dB.x);
+        dk[k][1] = make_float2(dA.y, dB.y);
+        dk[k][2] = make_float2(dA.z, dB.z);
+    }
+    float2 f2[3], A2[6];
+    pk::element_math_pair<UPDATE, MODEL>(g1, g2, g3, a, b, dk[0], dk[1], dk[2], f2, A2);
+    float rv[3], A[6];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rv[k] = f2[k].x + f2[k].y;
     if constexpr (UPDATE) {
-        // the element sums of the group's vertex go straight into the queue
-        // from the lanes that hold them; the vertex terms are added at flush
+#pragma unroll
+        for (int k = 0; k < 6; ++k) A[k] = A2[k].x + A2[k].y;
         float val[9] = {rv[0], rv[1], rv[2], A[0], A[1], A[2], A[3], A[4], A[5]};
         butterfly<9, W / 2>(val, lane);
         const int e = qn + j;
@@ -347,8 +415,6 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
         // a frozen vertex of a mixed item is not written
         S.q.v[e] = (it.comp < 0 && m.comp_active && !m.comp_active[m.comp[v]]) ? -1 : v;
     } else {
-        // the element terms of the lane in float32, their W-lane sum and the
-        // vertex terms in float-float
         ff::F2 rf[3] = {ff::mk(rv[0]), ff::mk(rv[1]), ff::mk(rv[2])};
 #pragma unroll
         for (int k = 0; k < 3; ++k) rf[k] = el::group_sum_ff<W>(rf[k]);
@@ -360,43 +426,20 @@ __device__ __forceinline__ void compute_item_w(const DeviceMesh& m, State s, War
     }
 }
 
-// The lane width is uniform over an item: dispatch once per item.
-template <bool COMP, bool UPDATE, int MODEL, bool EXT>
-__device__ __forceinline__ void compute_item(const DeviceMesh& m, State s, SmemOf<EXT>& S, const Item& it, int r,
-                                             int g, int lane, uint32_t btab, int qn, double& rr, double* comp_sq,
-                                             PassParams pp, int32_t* err) {
-    if (it.skip) return;  // uniform over the warp
-    if constexpr (EXT) {
-        switch (it.w) {
-            case 4: compute_item_ext<4, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
-            case 8: compute_item_ext<8, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
-            case 16: compute_item_ext<16, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
-            default: compute_item_ext<32, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
-        }
-        return;
-    }
-    switch (it.w) {
-        case 4: compute_item_w<4, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
-        case 8: compute_item_w<8, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
-        case 16: compute_item_w<16, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
-        default: compute_item_w<32, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
-    }
-}
-
 // All lanes: solve and write the qn queued vertices, one per lane.  The own
 // displacement is read again here; no other update of the pass writes it.
 template <bool COMP>
-__device__ __forceinline__ void flush_queue(const DeviceMesh& m, State s, const WarpSmem& S, int qn, int lane,
+__device__ __forceinline__ void flush_queue(const DeviceMesh& m, State s, const UpdQueue& Q, int qn, int lane,
                                             PassParams pp, int32_t* err) {
     __syncwarp();
     if (lane < qn) {
-        const int v = S.q.v[lane];
+        const int v = Q.v[lane];
         if (v >= 0) {
             float rv[3], A[6];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) rv[k] = S.q.val[k][lane];
+            for (int k = 0; k < 3; ++k) rv[k] = Q.val[k][lane];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) A[k] = S.q.val[3 + k][lane];
+            for (int k = 0; k < 6; ++k) A[k] = Q.val[3 + k][lane];
             const float3 uh = f3(s.hi[v]);
             const float3 ul = COMP ? f3(s.lo[v]) : make_float3(0.f, 0.f, 0.f);
             el::vertex_terms<COMP, true>(m, m.aux0[v], m.aux1[v], uh, ul, rv, A);
@@ -411,20 +454,8 @@ __device__ __forceinline__ void flush_queue(const DeviceMesh& m, State s, const 
 // blocked (warp gw takes a contiguous run of ceil(nitems / nw) items).  The
 // order only decides which warp updates which vertices of one colour; the
 // updates of a colour are independent, so the iterate is the same.
-// EXT: extended precision (compute_item_ext; COMP must be true).
-template <bool COMP, bool UPDATE, int MODEL, bool EXT>
-__global__ void __launch_bounds__(kBlock, EXT ? kCtasPerSmExt : kCtasPerSm)
-    ring_kernel(const DeviceMesh m, State s, const Item* __restrict__ items, int nitems, PassParams pp,
-                int32_t* err, double* partial, double* comp_sq, int blocked) {
-    static_assert(!EXT || COMP, "extended precision keeps the iterate as a float pair");
-    constexpr bool AUX = !UPDATE || EXT;
-    constexpr bool QUEUE = UPDATE && !EXT;
-    extern __shared__ __align__(128) unsigned char smem[];
-    pdl_release();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    SmemOf<EXT>& S = reinterpret_cast<SmemOf<EXT>*>(smem)[warp];
-    const int gw = (int)blockIdx.x * kWarps + warp, nw = (int)gridDim.x * kWarps;
-    int n, first, stride;
+__device__ __forceinline__ void item_range(int blocked, int nitems, int gw, int nw, int& n, int& first,
+                                           int& stride) {
     if (blocked) {
         const int per = (nitems + nw - 1) / nw;
         first = gw * per;
@@ -436,21 +467,43 @@ __global__ void __launch_bounds__(kBlock, EXT ? kCtasPerSmExt : kCtasPerSm)
         stride = nw;
         n = gw < nitems ? (nitems - gw + nw - 1) / nw : 0;
     }
+}
+
+// The warp's FP64 residual partial (one per warp of the grid; idle warps
+// write zero after the predecessor kernel).
+__device__ __forceinline__ void write_partial(double rr, int n, int lane, int gw, double* partial) {
+    if (n == 0) pdl_wait();  // idle warp: order its write after the predecessor
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
+    if (lane == 0) partial[gw] = rr;
+}
+
+// Extended-precision colour pass (UPDATE) or residual over ring items.
+template <bool UPDATE, int MODEL>
+__global__ void __launch_bounds__(kBlock, kCtasPerSm)
+    ext_kernel(const DeviceMesh m, State s, const Item* __restrict__ items, int nitems, PassParams pp,
+               int32_t* err, double* partial, double* comp_sq, int blocked) {
+    constexpr int RS = kExtStages, RA = kExtStages - 1;  // items' records are requested RA ahead
+    extern __shared__ __align__(128) unsigned char smem[];
+    pdl_release();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmemExt& S = reinterpret_cast<WarpSmemExt*>(smem)[warp];
+    const int gw = (int)blockIdx.x * kWarps + warp, nw = (int)gridDim.x * kWarps;
+    int n, first, stride;
+    item_range(blocked, nitems, gw, nw, n, first, stride);
     double rr = 0.0;
-    const uint32_t btab = QUEUE ? butterfly_table(lane) : 0u;
-    int qn = 0;                  // queued vertex updates (warp-uniform)
     int issued = 0, waited = 0;  // items whose records were requested / awaited
     bool ok = true;
     Item next{};                 // lane 0: next item to request, loaded one item early
     if (n > 0) {
         if (lane == 0) {
-            for (int i = 0; i < kRecStages; ++i) mbar_init(S.bar + i, 1);
+            for (int i = 0; i < RS; ++i) mbar_init(S.bar + i, 1);
             fence_mbar_init();
-            for (int i = 0; i < kRecAhead && i < n; ++i)
-                issue_records(m, items[first + i * stride], S, i, i == 0 ? (uint32_t)m.copy_shortfall : 0u);
-            if (n > kRecAhead) next = items[first + kRecAhead * stride];
+            for (int i = 0; i < RA && i < n; ++i)
+                ext_issue_records(m, items[first + i * stride], S, i, i == 0 ? (uint32_t)m.copy_shortfall : 0u);
+            if (n > RA) next = items[first + RA * stride];
         }
-        issued = n < kRecAhead ? n : kRecAhead;
+        issued = n < RA ? n : RA;
         __syncwarp();
         // Records, items and component flags are written by no kernel; the
         // iterate read from here on is written by the previous kernel.
@@ -458,49 +511,43 @@ __global__ void __launch_bounds__(kBlock, EXT ? kCtasPerSmExt : kCtasPerSm)
         ok = mbar_wait(S.bar + 0, 0);
         waited = ok ? 1 : 0;  // a stage whose wait gave up is drained again on abort
         if (__any_sync(kFull, !ok)) goto abort;
-        issue_gathers<COMP, AUX>(m, s, S, 0, 0, lane);
+        ext_issue_gathers(m, s, S, 0, 0, lane);
         cp_async_commit();
         for (int k = 0; k < n; ++k) {
-            // Record stage (k + kRecAhead) % kRecStages and gather stage
-            // (k+1)%2 were last read by item k-1, finished before the previous
-            // __syncwarp.
-            if (k + kRecAhead < n) {
+            // Record stage (k + RA) % RS and gather stage (k+1)%2 were last
+            // read by item k-1, finished before the previous __syncwarp.
+            if (k + RA < n) {
                 if (lane == 0) {
                     fence_proxy_async();
-                    issue_records(m, next, S, (k + kRecAhead) % kRecStages);
-                    if (k + kRecAhead + 1 < n) next = items[first + (k + kRecAhead + 1) * stride];
+                    ext_issue_records(m, next, S, (k + RA) % RS);
+                    if (k + RA + 1 < n) next = items[first + (k + RA + 1) * stride];
                 }
-                issued = k + kRecAhead + 1;
+                issued = k + RA + 1;
             }
             ok = true;
             if (k + 1 < n) {
-                ok = mbar_wait(S.bar + (k + 1) % kRecStages, ((k + 1) / kRecStages) & 1);
+                ok = mbar_wait(S.bar + (k + 1) % RS, ((k + 1) / RS) & 1);
                 waited = ok ? k + 2 : k + 1;
-                if (ok) issue_gathers<COMP, AUX>(m, s, S, (k + 1) % kRecStages, (k + 1) % kGatStages, lane);
+                if (ok) ext_issue_gathers(m, s, S, (k + 1) % RS, (k + 1) % kGatStages, lane);
             }
             cp_async_commit();
             cp_async_wait<1>();  // this lane's gathers of item k have landed
             if (__any_sync(kFull, !ok)) goto abort;
             __syncwarp();        // ... and the other lanes'
-            const Item it = S.desc[k % kRecStages];
-            compute_item<COMP, UPDATE, MODEL, EXT>(m, s, S, it, k % kRecStages, k % kGatStages, lane, btab, qn, rr,
-                                                   comp_sq, pp, err);
-            if (QUEUE) {
-                if (!it.skip) qn += it.nv;
-                if (qn > kQueue - kItemVerts || (k + 1 == n && qn > 0)) {
-                    flush_queue<COMP>(m, s, S, qn, lane, pp, err);
-                    qn = 0;
+            const Item it = S.desc[k % RS];
+            const int r = k % RS, g = k % kGatStages;
+            if (!it.skip) {  // uniform over the warp; the lane width too
+                switch (it.w) {
+                    case 4: compute_item_ext<4, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
+                    case 8: compute_item_ext<8, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
+                    case 16: compute_item_ext<16, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
+                    default: compute_item_ext<32, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
                 }
             }
             __syncwarp();
         }
     }
-    if (!UPDATE && partial) {
-        if (n == 0) pdl_wait();  // idle warp: order its write after the predecessor
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
-        if (lane == 0) partial[gw] = rr;
-    }
+    if (!UPDATE && partial) write_partial(rr, n, lane, gw, partial);
     return;
 
 abort:
@@ -508,7 +555,132 @@ abort:
     // warp started finish (bounded), then leave.
     if (lane == 0) {
         atomicOr(err, kErrTimeout);
-        for (int k = waited; k < issued; ++k) (void)mbar_wait(S.bar + k % kRecStages, (k / kRecStages) & 1);
+        for (int k = waited; k < issued; ++k) (void)mbar_wait(S.bar + k % RS, (k / RS) & 1);
+        if (!UPDATE && partial) partial[gw] = 0.0;
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+// Float32 passes, lane 0: request the ids of item `it` into id stage r
+// (`extra` expected bytes beyond the copy: the timeout test hook) and
+// record the item in desc[r].
+__device__ __forceinline__ void pair_issue_ids(const DeviceMesh& m, Item it, WarpSmemPair& S, int r,
+                                               uint32_t extra = 0u) {
+    it.skip = item_skipped(m, it);
+    S.desc[r] = it;
+    issue_copy(&S.ids[r], m.pids + (it.slot0 >> 5), it.skip ? 0u : (uint32_t)sizeof(PairIds), S.id_bar + r,
+               it.skip ? 0u : extra);
+}
+
+// Float32 passes, lane 0: request the records of the item in id stage r
+// into record stage q.
+__device__ __forceinline__ void pair_issue_rec(const DeviceMesh& m, WarpSmemPair& S, int r, int q) {
+    const Item it = S.desc[r];
+    issue_copy(&S.rec[q], m.prec + (it.slot0 >> 5), it.skip ? 0u : (uint32_t)sizeof(PairRec), S.rec_bar + q);
+}
+
+// Float32 colour pass (UPDATE) or residual over pair items.  Item k's ids
+// are requested at iteration k - 2 and awaited at k - 1, where its gathers
+// are issued; its records are requested at k - 1 and awaited at k.
+template <bool COMP, bool UPDATE, int MODEL>
+__global__ void __launch_bounds__(kBlock, kCtasPerSm)
+    pair_kernel(const DeviceMesh m, State s, const Item* __restrict__ items, int nitems, PassParams pp,
+                int32_t* err, double* partial, double* comp_sq, int blocked) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    pdl_release();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmemPair& S = reinterpret_cast<WarpSmemPair*>(smem)[warp];
+    const int gw = (int)blockIdx.x * kWarps + warp, nw = (int)gridDim.x * kWarps;
+    int n, first, stride;
+    item_range(blocked, nitems, gw, nw, n, first, stride);
+    double rr = 0.0;
+    const uint32_t btab = UPDATE ? butterfly_table(lane) : 0u;
+    int qn = 0;  // queued vertex updates (warp-uniform)
+    // items whose ids / records were requested, and those awaited (a stage
+    // whose wait gave up is drained again on abort)
+    int id_issued = 0, id_waited = 0, rec_issued = 0, rec_waited = 0;
+    bool ok = true;
+    Item next{};  // lane 0: the next item whose ids are requested
+    if (n > 0) {
+        if (lane == 0) {
+            for (int i = 0; i < kIdStages; ++i) mbar_init(S.id_bar + i, 1);
+            for (int i = 0; i < kRecStages; ++i) mbar_init(S.rec_bar + i, 1);
+            fence_mbar_init();
+            for (int i = 0; i < 2 && i < n; ++i)
+                pair_issue_ids(m, items[first + i * stride], S, i, i == 0 ? (uint32_t)m.copy_shortfall : 0u);
+            pair_issue_rec(m, S, 0, 0);
+            if (n > 2) next = items[first + 2 * stride];
+        }
+        id_issued = n < 2 ? n : 2;
+        rec_issued = 1;
+        __syncwarp();
+        // Records, ids, items and component flags are written by no kernel;
+        // the iterate read from here on is written by the previous kernel.
+        pdl_wait();
+        ok = mbar_wait(S.id_bar + 0, 0);
+        id_waited = ok ? 1 : 0;
+        if (__any_sync(kFull, !ok)) goto abort;
+        pair_issue_gathers<COMP, !UPDATE>(m, s, S, 0, 0, lane);
+        cp_async_commit();
+        for (int k = 0; k < n; ++k) {
+            // Id stage (k + 2) % 3 was last read by the gathers of item k - 1,
+            // record stage (k + 1) % 2 and gather stage (k + 1) % 2 by the
+            // compute of item k - 1, all finished before the previous
+            // __syncwarp.
+            if (lane == 0) {
+                fence_proxy_async();
+                if (k + 2 < n) {
+                    pair_issue_ids(m, next, S, (k + 2) % kIdStages);
+                    if (k + 3 < n) next = items[first + (k + 3) * stride];
+                }
+                if (k + 1 < n) pair_issue_rec(m, S, (k + 1) % kIdStages, (k + 1) % kRecStages);
+            }
+            if (k + 2 < n) id_issued = k + 3;
+            if (k + 1 < n) rec_issued = k + 2;
+            ok = true;
+            if (k + 1 < n) {
+                ok = mbar_wait(S.id_bar + (k + 1) % kIdStages, ((k + 1) / kIdStages) & 1);
+                id_waited = ok ? k + 2 : k + 1;
+                if (ok) pair_issue_gathers<COMP, !UPDATE>(m, s, S, (k + 1) % kIdStages, (k + 1) % kGatStages, lane);
+            }
+            cp_async_commit();
+            const bool rok = mbar_wait(S.rec_bar + k % kRecStages, (k / kRecStages) & 1);
+            rec_waited = rok ? k + 1 : k;
+            cp_async_wait<1>();  // this lane's gathers of item k have landed
+            if (__any_sync(kFull, !(ok && rok))) goto abort;
+            __syncwarp();        // ... and the other lanes'
+            const Item it = S.desc[k % kIdStages];
+            const int r = k % kRecStages, g = k % kGatStages;
+            if (!it.skip) {  // uniform over the warp; the lane width too
+                switch (it.w) {
+                    case 4: compute_item_pair<4, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
+                    case 8: compute_item_pair<8, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
+                    case 16: compute_item_pair<16, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
+                    default: compute_item_pair<32, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
+                }
+            }
+            if (UPDATE) {
+                if (!it.skip) qn += it.nv;
+                if (qn > kQueue - kItemVerts || (k + 1 == n && qn > 0)) {
+                    flush_queue<COMP>(m, s, S.q, qn, lane, pp, err);
+                    qn = 0;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (!UPDATE && partial) write_partial(rr, n, lane, gw, partial);
+    return;
+
+abort:
+    // An id or record copy did not complete in time: report it, let the
+    // copies this warp started finish (bounded), then leave.
+    if (lane == 0) {
+        atomicOr(err, kErrTimeout);
+        for (int k = id_waited; k < id_issued; ++k) (void)mbar_wait(S.id_bar + k % kIdStages, (k / kIdStages) & 1);
+        for (int k = rec_waited; k < rec_issued; ++k)
+            (void)mbar_wait(S.rec_bar + k % kRecStages, (k / kRecStages) & 1);
         if (!UPDATE && partial) partial[gw] = 0.0;
     }
     cp_async_wait<0>();
@@ -527,9 +699,9 @@ int sm_count() {
     return cached[dev];
 }
 
-int ring_ctas(int nitems, int ctas_per_sm, int balanced = 0, int max_cps = kCtasPerSm) {
+int ring_ctas(int nitems, int ctas_per_sm, int balanced = 0) {
     const int want = (nitems + kWarps - 1) / kWarps;
-    const int cps = ctas_per_sm < 1 ? 1 : (ctas_per_sm > max_cps ? max_cps : ctas_per_sm);
+    const int cps = ctas_per_sm < 1 ? 1 : (ctas_per_sm > kCtasPerSm ? kCtasPerSm : ctas_per_sm);
     const int cap = cps * sm_count();
     int grid = want < cap ? want : cap;
     if (balanced && grid > 0) {
@@ -541,23 +713,35 @@ int ring_ctas(int nitems, int ctas_per_sm, int balanced = 0, int max_cps = kCtas
     return grid;
 }
 
-template <bool COMP, bool UPDATE, bool EXT = false>
+// grid_warps > 0: a grid of exactly that many warps (a multiple of kWarps;
+// the residuals, whose partials are one per warp); else the schedule's.
+template <bool COMP, bool UPDATE, bool EXT>
 cudaError_t launch_impl(const DeviceMesh& m, State s, const Item* items, int nitems, PassParams pp,
-                        int32_t* err, double* partial, double* comp_sq, RingSched sc, cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    const int bytes = kWarps * (int)sizeof(SmemOf<EXT>);  // attribute set by ring_prepare()
-    // An extended residual writes the partials of the float32 residual's grid
-    // (2 CTAs per SM are resident, the rest follow); an extended update pass
-    // keeps its grid to what is resident.
-    const int grid = ring_ctas(nitems, sc.ctas_per_sm, sc.balanced, (EXT && UPDATE) ? kCtasPerSmExt : kCtasPerSm);
-    if (pp.model == el::kNeoHookean)
-        return launch_kernel(ring_kernel<COMP, UPDATE, el::kNeoHookean, EXT>, grid, kBlock, bytes, st, m, s, items,
-                             nitems, pp, err, partial, comp_sq, sc.blocked);
-    if (pp.model == el::kStableNeoHookean)
-        return launch_kernel(ring_kernel<COMP, UPDATE, el::kStableNeoHookean, EXT>, grid, kBlock, bytes, st, m, s,
-                             items, nitems, pp, err, partial, comp_sq, sc.blocked);
-    return launch_kernel(ring_kernel<COMP, UPDATE, el::kCorotated, EXT>, grid, kBlock, bytes, st, m, s, items, nitems,
-                         pp, err, partial, comp_sq, sc.blocked);
+                        int32_t* err, double* partial, double* comp_sq, RingSched sc, cudaStream_t st,
+                        int grid_warps = 0) {
+    if (nitems <= 0 && grid_warps <= 0) return cudaSuccess;
+    const int grid = grid_warps > 0 ? grid_warps / kWarps : ring_ctas(nitems, sc.ctas_per_sm, sc.balanced);
+    if constexpr (EXT) {
+        const int bytes = kWarps * (int)sizeof(WarpSmemExt);  // attribute set by ring_prepare()
+        if (pp.model == el::kNeoHookean)
+            return launch_kernel(ext_kernel<UPDATE, el::kNeoHookean>, grid, kBlock, bytes, st, m, s, items, nitems,
+                                 pp, err, partial, comp_sq, sc.blocked);
+        if (pp.model == el::kStableNeoHookean)
+            return launch_kernel(ext_kernel<UPDATE, el::kStableNeoHookean>, grid, kBlock, bytes, st, m, s, items,
+                                 nitems, pp, err, partial, comp_sq, sc.blocked);
+        return launch_kernel(ext_kernel<UPDATE, el::kCorotated>, grid, kBlock, bytes, st, m, s, items, nitems, pp,
+                             err, partial, comp_sq, sc.blocked);
+    } else {
+        const int bytes = kWarps * (int)sizeof(WarpSmemPair);
+        if (pp.model == el::kNeoHookean)
+            return launch_kernel(pair_kernel<COMP, UPDATE, el::kNeoHookean>, grid, kBlock, bytes, st, m, s, items,
+                                 nitems, pp, err, partial, comp_sq, sc.blocked);
+        if (pp.model == el::kStableNeoHookean)
+            return launch_kernel(pair_kernel<COMP, UPDATE, el::kStableNeoHookean>, grid, kBlock, bytes, st, m, s,
+                                 items, nitems, pp, err, partial, comp_sq, sc.blocked);
+        return launch_kernel(pair_kernel<COMP, UPDATE, el::kCorotated>, grid, kBlock, bytes, st, m, s, items, nitems,
+                             pp, err, partial, comp_sq, sc.blocked);
+    }
 }
 
 }  // namespace
@@ -567,19 +751,19 @@ int ring_warps(int nitems) { return nitems > 0 ? ring_ctas(nitems, kCtasPerSm) *
 int ring_max_ctas_per_sm() { return kCtasPerSm; }
 
 cudaError_t ring_prepare() {
-    // Three CTAs of 8 warps with their per-warp stages and queues need almost
+    // Two CTAs of 8 warps with their per-warp stages and queues need almost
     // all of an SM's shared memory: ask for the largest carveout.
-    const int bytes = kWarps * (int)sizeof(WarpSmem), bytes_ext = kWarps * (int)sizeof(WarpSmemExt);
+    const int bytes = kWarps * (int)sizeof(WarpSmemPair), bytes_ext = kWarps * (int)sizeof(WarpSmemExt);
     const void* fns[18] = {
-        (const void*)ring_kernel<true, true, 0, false>,  (const void*)ring_kernel<false, true, 0, false>,
-        (const void*)ring_kernel<true, false, 0, false>, (const void*)ring_kernel<false, false, 0, false>,
-        (const void*)ring_kernel<true, true, 1, false>,  (const void*)ring_kernel<false, true, 1, false>,
-        (const void*)ring_kernel<true, false, 1, false>, (const void*)ring_kernel<false, false, 1, false>,
-        (const void*)ring_kernel<true, true, 2, false>,  (const void*)ring_kernel<false, true, 2, false>,
-        (const void*)ring_kernel<true, false, 2, false>, (const void*)ring_kernel<false, false, 2, false>,
-        (const void*)ring_kernel<true, true, 0, true>,   (const void*)ring_kernel<true, false, 0, true>,
-        (const void*)ring_kernel<true, true, 1, true>,   (const void*)ring_kernel<true, false, 1, true>,
-        (const void*)ring_kernel<true, true, 2, true>,   (const void*)ring_kernel<true, false, 2, true>};
+        (const void*)pair_kernel<true, true, 0>,  (const void*)pair_kernel<false, true, 0>,
+        (const void*)pair_kernel<true, false, 0>, (const void*)pair_kernel<false, false, 0>,
+        (const void*)pair_kernel<true, true, 1>,  (const void*)pair_kernel<false, true, 1>,
+        (const void*)pair_kernel<true, false, 1>, (const void*)pair_kernel<false, false, 1>,
+        (const void*)pair_kernel<true, true, 2>,  (const void*)pair_kernel<false, true, 2>,
+        (const void*)pair_kernel<true, false, 2>, (const void*)pair_kernel<false, false, 2>,
+        (const void*)ext_kernel<true, 0>,         (const void*)ext_kernel<false, 0>,
+        (const void*)ext_kernel<true, 1>,         (const void*)ext_kernel<false, 1>,
+        (const void*)ext_kernel<true, 2>,         (const void*)ext_kernel<false, 2>};
     for (int k = 0; k < 18; ++k) {
         const void* f = fns[k];
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, k < 12 ? bytes : bytes_ext);
@@ -596,22 +780,24 @@ cudaError_t launch_ring_pass(const DeviceMesh& m, State s, const Item* items, in
         if (!compensated || !m.ring_lo) return cudaErrorInvalidValue;
         return launch_impl<true, true, true>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
     }
-    if (compensated) return launch_impl<true, true>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
-    return launch_impl<false, true>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
+    if (compensated) return launch_impl<true, true, false>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
+    return launch_impl<false, true, false>(m, s, items, nitems, p, err, nullptr, nullptr, sc, st);
 }
 
 cudaError_t launch_ring_residual(const DeviceMesh& m, State s, const Item* items, int nitems,
                                  bool compensated, double* warp_partial, double* comp_sq, int model, int32_t* err,
-                                 cudaStream_t st, bool extended) {
+                                 cudaStream_t st, bool extended, int grid_warps) {
     const PassParams pp{1.f, 0.f, model};
-    const RingSched sc{kCtasPerSm, 0, 0};  // ring_warps() partials
+    const RingSched sc{kCtasPerSm, 0, 0};
     double* part = comp_sq ? nullptr : warp_partial;
+    if (grid_warps <= 0 || grid_warps % kWarps) return cudaErrorInvalidValue;
     if (extended) {
         if (!compensated || !m.ring_lo) return cudaErrorInvalidValue;
-        return launch_impl<true, false, true>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
+        return launch_impl<true, false, true>(m, s, items, nitems, pp, err, part, comp_sq, sc, st, grid_warps);
     }
-    if (compensated) return launch_impl<true, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
-    return launch_impl<false, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st);
+    if (compensated)
+        return launch_impl<true, false, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st, grid_warps);
+    return launch_impl<false, false, false>(m, s, items, nitems, pp, err, part, comp_sq, sc, st, grid_warps);
 }
 
 }  // namespace pbng
