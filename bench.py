@@ -122,7 +122,8 @@ def config_of(args, p, desc, acc):
         "accel": ", ".join(f"{k}={v}" for k, v in acc.items()),
         "precision": args.precision,
         "model": args.model,
-        "kernels": ("1-ring layout, per-warp TMA bulk records + cp.async gathers, CUDA graph per step"
+        "kernels": ("1-ring pair items (two tets per lane, packed f32x2 element terms), per-warp TMA bulk "
+                    "ids/records + cp.async gathers, CUDA graph per step"
                     if args.kernel_path == 0 else "CSR layout, direct loads, CUDA graph per step"),
         "l2": "inputs larger than L2 (per-incidence records streamed every sweep)",
         "seed": "seeded synthetic inputs (workloads/)",
@@ -210,7 +211,7 @@ def kernel_sources_sha256():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_09021_gb300", "csrc")
     for name in ("pbng_async.cuh", "pbng_element.cuh", "pbng_ff.cuh", "pbng_internal.h", "pbng_kernels.cu",
-                 "pbng_launch.cuh", "pbng_ring.cu"):
+                 "pbng_launch.cuh", "pbng_pair.cuh", "pbng_ring.cu"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -418,7 +419,7 @@ def main():
     from paper_2306_09021_gb300 import measure_fp32_peak
     fp32_peak = measure_fp32_peak(stream)
     fp32_flops = None if tr is None else tr.get("fp32_flops_per_launch")
-    roofline = {"kernel": "ring_kernel<UPDATE=true> (colour pass)" if args.kernel_path == 0 else "colour_pass_kernel",
+    roofline = {"kernel": "pair_kernel<UPDATE=true> (colour pass)" if args.kernel_path == 0 else "colour_pass_kernel",
                 "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
                 "model": "per-pass gather bytes (96 B per incidence + 40 B per free vertex) per launch",

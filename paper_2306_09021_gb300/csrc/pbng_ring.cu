@@ -102,6 +102,7 @@ struct __align__(16) WarpSmemExt {
 // ahead, and the records one item ahead.
 constexpr int kIdStages = 3;
 constexpr int kRecStages = 2;
+static_assert(kIdStages == 3 && kRecStages == 2 && kGatStages == 2, "the pair pipeline advances its stages by hand");
 struct __align__(16) WarpSmemPair {
     PairRec rec[kRecStages];
     PairIds ids[kIdStages];
@@ -623,41 +624,43 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
         if (__any_sync(kFull, !ok)) goto abort;
         pair_issue_gathers<COMP, !UPDATE>(m, s, S, 0, 0, lane);
         cp_async_commit();
+        // stages and barrier parities, advanced each item: id stage of items
+        // k, k + 1, k + 2 and the parity of item k + 1's; record and gather
+        // stage of item k and the parity of its record barrier
+        int i0 = 0, i1 = 1, i2 = 2, ph1 = 0, r0 = 0, rph = 0;
         for (int k = 0; k < n; ++k) {
-            // Id stage (k + 2) % 3 was last read by the gathers of item k - 1,
-            // record stage (k + 1) % 2 and gather stage (k + 1) % 2 by the
-            // compute of item k - 1, all finished before the previous
-            // __syncwarp.
+            // Id stage i2 was last read by the gathers of item k - 1, record
+            // stage 1 - r0 and gather stage 1 - r0 by the compute of item
+            // k - 1, all finished before the previous __syncwarp.
             if (lane == 0) {
                 fence_proxy_async();
                 if (k + 2 < n) {
-                    pair_issue_ids(m, next, S, (k + 2) % kIdStages);
+                    pair_issue_ids(m, next, S, i2);
                     if (k + 3 < n) next = items[first + (k + 3) * stride];
                 }
-                if (k + 1 < n) pair_issue_rec(m, S, (k + 1) % kIdStages, (k + 1) % kRecStages);
+                if (k + 1 < n) pair_issue_rec(m, S, i1, r0 ^ 1);
             }
             if (k + 2 < n) id_issued = k + 3;
             if (k + 1 < n) rec_issued = k + 2;
             ok = true;
             if (k + 1 < n) {
-                ok = mbar_wait(S.id_bar + (k + 1) % kIdStages, ((k + 1) / kIdStages) & 1);
+                ok = mbar_wait(S.id_bar + i1, ph1);
                 id_waited = ok ? k + 2 : k + 1;
-                if (ok) pair_issue_gathers<COMP, !UPDATE>(m, s, S, (k + 1) % kIdStages, (k + 1) % kGatStages, lane);
+                if (ok) pair_issue_gathers<COMP, !UPDATE>(m, s, S, i1, r0 ^ 1, lane);
             }
             cp_async_commit();
-            const bool rok = mbar_wait(S.rec_bar + k % kRecStages, (k / kRecStages) & 1);
+            const bool rok = mbar_wait(S.rec_bar + r0, rph);
             rec_waited = rok ? k + 1 : k;
             cp_async_wait<1>();  // this lane's gathers of item k have landed
             if (__any_sync(kFull, !(ok && rok))) goto abort;
             __syncwarp();        // ... and the other lanes'
-            const Item it = S.desc[k % kIdStages];
-            const int r = k % kRecStages, g = k % kGatStages;
+            const Item it = S.desc[i0];
             if (!it.skip) {  // uniform over the warp; the lane width too
                 switch (it.w) {
-                    case 4: compute_item_pair<4, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
-                    case 8: compute_item_pair<8, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
-                    case 16: compute_item_pair<16, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
-                    default: compute_item_pair<32, COMP, UPDATE, MODEL>(m, s, S, it, r, g, lane, btab, qn, rr, comp_sq); break;
+                    case 4: compute_item_pair<4, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
+                    case 8: compute_item_pair<8, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
+                    case 16: compute_item_pair<16, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
+                    default: compute_item_pair<32, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
                 }
             }
             if (UPDATE) {
@@ -668,6 +671,12 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
                 }
             }
             __syncwarp();
+            i0 = i1;
+            i1 = i2;
+            i2 = i2 == kIdStages - 1 ? 0 : i2 + 1;
+            if (i1 == 0) ph1 ^= 1;
+            r0 ^= 1;
+            if (r0 == 0) rph ^= 1;
         }
     }
     if (!UPDATE && partial) write_partial(rr, n, lane, gw, partial);
