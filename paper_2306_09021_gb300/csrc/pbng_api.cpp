@@ -618,6 +618,8 @@ pbng_status build_layout(pbng_mesh* m) {
                 const Segment& sg = t.seg[k];
                 for (int32_t rb = sg.v_begin; rb < sg.v_end;) {
                     const int W2 = lanes2(order[rb]);
+                    // the pair kernel handles widths 4, 8 and 16 only
+                    if (W2 > kRingLanes / 2) return fail(m, PBNG_EINVAL, "pair item wider than 16 lanes");
                     int32_t re = rb;
                     while (re < sg.v_end && lanes2(order[re]) == W2) ++re;
                     const int per_item = kRingLanes / W2;

@@ -136,6 +136,63 @@ PBNG_FF_HD void matvec(const F2* M, const F2* x, F2* y) {
     for (int p = 0; p < 3; ++p) y[p] = add(add(mul(M[3 * p], x[0]), mul(M[3 * p + 1], x[1])), mul(M[3 * p + 2], x[2]));
 }
 
+// A running sum of float-float terms and products (Ogita, Rump and Oishi's
+// Sum2 / Dot2, 2005): the high words are summed by TwoSum into s, every
+// rounding error and every low-order part (the low words and the cross
+// products of a float-float product) into the float c.  The value s + c is
+// as accurate as if the sum had been formed with twice the precision, and is
+// normalised once, at the end, instead of after every term.
+struct Acc {
+    float s, c;
+};
+PBNG_FF_HD Acc acc_of(F2 x) { return Acc{x.h, x.l}; }
+// x y, exactly up to the low words' product
+PBNG_FF_HD Acc acc_prod(F2 x, F2 y) {
+    const float p = fmul(x.h, y.h);
+    return Acc{p, ffma(x.h, y.l, ffma(x.l, y.h, ffma(x.h, y.h, -p)))};
+}
+PBNG_FF_HD void acc_add(Acc& a, F2 x) {
+    const F2 t = two_sum(a.s, x.h);
+    a.s = t.h;
+    a.c = fadd(a.c, fadd(t.l, x.l));
+}
+PBNG_FF_HD void acc_add(Acc& a, float x) {
+    const F2 t = two_sum(a.s, x);
+    a.s = t.h;
+    a.c = fadd(a.c, t.l);
+}
+// a += x y
+PBNG_FF_HD void acc_fma(Acc& a, F2 x, F2 y) {
+    const float p = fmul(x.h, y.h);
+    const float e = ffma(x.h, y.h, -p);
+    const F2 t = two_sum(a.s, p);
+    a.s = t.h;
+    a.c = ffma(x.h, y.l, ffma(x.l, y.h, fadd(a.c, fadd(t.l, e))));
+}
+// a += x y for a float y
+PBNG_FF_HD void acc_fma(Acc& a, F2 x, float y) {
+    const float p = fmul(x.h, y);
+    const float e = ffma(x.h, y, -p);
+    const F2 t = two_sum(a.s, p);
+    a.s = t.h;
+    a.c = ffma(x.l, y, fadd(a.c, fadd(t.l, e)));
+}
+// s + c as a normalised pair (TwoSum: c may exceed s where the terms cancel)
+PBNG_FF_HD F2 acc_val(Acc a) { return two_sum(a.s, a.c); }
+// x0 y0 + x1 y1 + x2 y2
+PBNG_FF_HD F2 dot3(F2 x0, F2 y0, F2 x1, F2 y1, F2 x2, F2 y2) {
+    Acc a = acc_prod(x0, y0);
+    acc_fma(a, x1, y1);
+    acc_fma(a, x2, y2);
+    return acc_val(a);
+}
+// a b - c d
+PBNG_FF_HD F2 dif2(F2 a, F2 b, F2 c, F2 d) {
+    Acc t = acc_prod(a, b);
+    acc_fma(t, neg(c), d);
+    return acc_val(t);
+}
+
 enum { kCorotated = 0, kNeoHookean = 1, kStableNeoHookean = 2 };
 
 // f = V P(F) s of one element, with s = -g_i = g_j1 + g_j2 + g_j3 and
@@ -155,11 +212,15 @@ PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], co
 #pragma unroll
     for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            H[3 * p + c] = add(add(mul(d[0][p], g[0][c]), mul(d[1][p], g[1][c])), mul(d[2][p], g[2][c]));
+        for (int c = 0; c < 3; ++c) H[3 * p + c] = dot3(d[0][p], g[0][c], d[1][p], g[1][c], d[2][p], g[2][c]);
     F2 s[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s[c] = add(add(g[0][c], g[1][c]), g[2][c]);
+    for (int c = 0; c < 3; ++c) {
+        Acc t = acc_of(g[0][c]);
+        acc_add(t, g[1][c]);
+        acc_add(t, g[2][c]);
+        s[c] = acc_val(t);
+    }
     F2 F[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) F[k] = H[k];
@@ -168,27 +229,36 @@ PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], co
     F[8] = add(F[8], 1.0f);
     // cofactor matrix C = det(F) F^{-T}
     F2 C[9];
-    C[0] = mul_sub(F[4], F[8], F[5], F[7]);
-    C[1] = mul_sub(F[5], F[6], F[3], F[8]);
-    C[2] = mul_sub(F[3], F[7], F[4], F[6]);
-    C[3] = mul_sub(F[7], F[2], F[8], F[1]);
-    C[4] = mul_sub(F[8], F[0], F[6], F[2]);
-    C[5] = mul_sub(F[6], F[1], F[7], F[0]);
-    C[6] = mul_sub(F[1], F[5], F[2], F[4]);
-    C[7] = mul_sub(F[2], F[3], F[0], F[5]);
-    C[8] = mul_sub(F[0], F[4], F[1], F[3]);
-    const F2 J = add(add(mul(F[0], C[0]), mul(F[1], C[1])), mul(F[2], C[2]));
-    const F2 Jm1 = add(J, -1.0f);
+    C[0] = dif2(F[4], F[8], F[5], F[7]);
+    C[1] = dif2(F[5], F[6], F[3], F[8]);
+    C[2] = dif2(F[3], F[7], F[4], F[6]);
+    C[3] = dif2(F[7], F[2], F[8], F[1]);
+    C[4] = dif2(F[8], F[0], F[6], F[2]);
+    C[5] = dif2(F[6], F[1], F[7], F[0]);
+    C[6] = dif2(F[1], F[5], F[2], F[4]);
+    C[7] = dif2(F[2], F[3], F[0], F[5]);
+    C[8] = dif2(F[0], F[4], F[1], F[3]);
+    Acc jacc = acc_prod(F[0], C[0]);
+    acc_fma(jacc, F[1], C[1]);
+    acc_fma(jacc, F[2], C[2]);
+    acc_add(jacc, -1.0f);
+    const F2 Jm1 = acc_val(jacc);  // det F - 1
     F2 ws[3], Hs[3];  // C s, H s
-    matvec(C, s, ws);
-    matvec(H, s, Hs);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        ws[p] = dot3(C[3 * p], s[0], C[3 * p + 1], s[1], C[3 * p + 2], s[2]);
+        Hs[p] = dot3(H[3 * p], s[0], H[3 * p + 1], s[1], H[3 * p + 2], s[2]);
+    }
     F2 f[3];
     if (MODEL == kCorotated) {
         // R0 = I + K0 from the quaternion, exactly orthogonal up to
         // float-float rounding: K0 = 2 (w [v]x + [v]x^2) / |q|^2.
         const float w = q[0], x = q[1], y = q[2], z = q[3];
-        const F2 qq = add(add(two_prod(w, w), two_prod(x, x)), add(two_prod(y, y), two_prod(z, z)));
-        const F2 inv2 = mul(recip(qq), 2.0f);
+        Acc qa = acc_prod(mk(w), mk(w));
+        acc_fma(qa, mk(x), x);
+        acc_fma(qa, mk(y), y);
+        acc_fma(qa, mk(z), z);
+        const F2 inv2 = mul(recip(acc_val(qa)), 2.0f);
         const F2 xx = two_prod(x, x), yy = two_prod(y, y), zz = two_prod(z, z);
         const F2 xy = two_prod(x, y), xz = two_prod(x, z), yz = two_prod(y, z);
         const F2 wx = two_prod(w, x), wy = two_prod(w, y), wz = two_prod(w, z);
@@ -202,17 +272,23 @@ PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], co
         K[6] = mul(sub(xz, wy), inv2);
         K[7] = mul(add(yz, wx), inv2);
         K[8] = mul(neg(add(xx, yy)), inv2);
-        // M = R0^T F = I + K0^T + H + K0^T H.  Its skew part (float-float)
-        // gives the correction; its symmetric part S only needs float.
-        auto mentry = [&](int r, int c) -> F2 {  // (K0^T + H + K0^T H)_rc
-            F2 t = add(K[3 * c + r], H[3 * r + c]);
-            t = add(t, mul(K[r], H[c]));
-            t = add(t, mul(K[3 + r], H[3 + c]));
-            return add(t, mul(K[6 + r], H[6 + c]));
+        // M = R0^T F = I + K0^T + H + K0^T H, M_rc = K[3c + r] + H[3r + c] +
+        // sum_k K[3k + r] H[3k + c].  Its skew part (float-float, each
+        // difference M_rc - M_cr in one running sum) gives the correction;
+        // its symmetric part S only needs float.
+        auto skew = [&](int r, int c) -> float {  // M_rc - M_cr
+            Acc t = acc_of(K[3 * c + r]);
+            acc_add(t, H[3 * r + c]);
+            acc_add(t, neg(K[3 * r + c]));
+            acc_add(t, neg(H[3 * c + r]));
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                acc_fma(t, K[3 * k + r], H[3 * k + c]);
+                acc_fma(t, neg(K[3 * k + c]), H[3 * k + r]);
+            }
+            return fadd(t.s, t.c);
         };
-        const F2 m01 = mentry(0, 1), m10 = mentry(1, 0), m02 = mentry(0, 2), m20 = mentry(2, 0);
-        const F2 m12 = mentry(1, 2), m21 = mentry(2, 1);
-        const float ax = 0.5f * sub(m21, m12).h, ay = 0.5f * sub(m02, m20).h, az = 0.5f * sub(m10, m01).h;
+        const float ax = 0.5f * skew(2, 1), ay = 0.5f * skew(0, 2), az = 0.5f * skew(1, 0);
         // S = sym(M) in float: I + sym(K0^T + H + K0^T H)
         float S[9];
 #pragma unroll
@@ -243,8 +319,6 @@ PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], co
         // (R - I) s = K0 s + R0 (theta x s + theta x (theta x s) / 2); the
         // second term is of the order of the float32 rotation error, so float
         // suffices for it.
-        F2 Ks[3];
-        matvec(K, s, Ks);
         const float t1x = th[1] * s[2].h - th[2] * s[1].h;
         const float t1y = th[2] * s[0].h - th[0] * s[2].h;
         const float t1z = th[0] * s[1].h - th[1] * s[0].h;
@@ -256,8 +330,16 @@ PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], co
         for (int p = 0; p < 3; ++p) {
             const float corr = (K[3 * p].h * tsx + K[3 * p + 1].h * tsy + K[3 * p + 2].h * tsz) +
                                (p == 0 ? tsx : (p == 1 ? tsy : tsz));
-            const F2 rs = add(Ks[p], corr);
-            f[p] = add(mul(a, sub(Hs[p], rs)), mul(bJ, ws[p]));
+            // a (H s - (R - I) s) + b (J - 1) C s with (R - I) s = K0 s + corr;
+            // H s and K0 s nearly cancel (the rotation), so their difference
+            // is formed first
+            const F2 Ks = dot3(K[3 * p], s[0], K[3 * p + 1], s[1], K[3 * p + 2], s[2]);
+            Acc dd = acc_of(Hs[p]);
+            acc_add(dd, neg(Ks));
+            acc_add(dd, -corr);
+            Acc t = acc_prod(a, acc_val(dd));
+            acc_fma(t, bJ, ws[p]);
+            f[p] = acc_val(t);
         }
     } else {
         // (F - C) s = s + H s - C s
@@ -265,11 +347,13 @@ PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], co
         F2 kv = add(ha, b);
         F2 qs = mk(0.0f);
         if (MODEL == kStableNeoHookean) {
-            F2 hh = mk(0.0f);
+            Acc hh = acc_prod(H[0], H[0]);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) hh = add(hh, mul(H[k], H[k]));
-            const F2 trH = add(add(H[0], H[4]), H[8]);
-            const F2 ic3 = add(mul(trH, 2.0f), hh);  // I_C - 3
+            for (int k = 1; k < 9; ++k) acc_fma(hh, H[k], H[k]);
+            acc_fma(hh, H[0], 2.0f);
+            acc_fma(hh, H[4], 2.0f);
+            acc_fma(hh, H[8], 2.0f);
+            const F2 ic3 = acc_val(hh);  // I_C - 3 = 2 tr H + |H|^2
             // 1/6 and 5/12 are not floats: their float-pair values
             qs = mul(div(ic3, add(ic3, 4.0f)), mul(a, mk(0.16666667163f, -4.9670539e-9f)));
             kv = add(b, mul(a, mk(0.4166666567f, 9.9341078e-9f)));
@@ -277,10 +361,15 @@ PBNG_FF_HD void element_force(const F2 g[3][3], F2 a, F2 b, const F2 d[3][3], co
         const F2 kJ = mul(kv, Jm1);
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
-            const F2 fcs = sub(add(s[p], Hs[p]), ws[p]);
-            F2 t = add(mul(ha, fcs), mul(kJ, ws[p]));
-            if (MODEL == kStableNeoHookean) t = add(t, mul(qs, add(s[p], Hs[p])));
-            f[p] = t;
+            // (F - C) s = s + H s - C s, which cancels near F = I, first
+            Acc fc = acc_of(s[p]);
+            acc_add(fc, Hs[p]);
+            const F2 sh = acc_val(fc);  // F s
+            acc_add(fc, neg(ws[p]));
+            Acc t = acc_prod(ha, acc_val(fc));
+            acc_fma(t, kJ, ws[p]);
+            if (MODEL == kStableNeoHookean) acc_fma(t, qs, sh);
+            f[p] = acc_val(t);
         }
     }
 #pragma unroll

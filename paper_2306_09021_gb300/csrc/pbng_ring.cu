@@ -656,11 +656,12 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
             __syncwarp();        // ... and the other lanes'
             const Item it = S.desc[i0];
             if (!it.skip) {  // uniform over the warp; the lane width too
+                // pair widths are 4, 8 or 16: a ring colour's vertices have at
+                // most 32 tets and 32 1-ring vertices (the layout checks it)
                 switch (it.w) {
                     case 4: compute_item_pair<4, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
                     case 8: compute_item_pair<8, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
-                    case 16: compute_item_pair<16, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
-                    default: compute_item_pair<32, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
+                    default: compute_item_pair<16, COMP, UPDATE, MODEL>(m, s, S, it, r0, r0, lane, btab, qn, rr, comp_sq); break;
                 }
             }
             if (UPDATE) {
