@@ -605,7 +605,11 @@ def main():
                                     default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric"), 4000),
                                    ("adjoint_symmetric_auto_rho_refined",
                                     default_params(accel="chebyshev", rho=-1.0, colour_order="symmetric",
-                                                   precision="auto"), max_sw)):
+                                                   precision="auto"), max_sw),
+                                   # conjugate gradients with the symmetric sweep as
+                                   # preconditioner, refined (iterations count as sweeps)
+                                   ("adjoint_cg_refined",
+                                    default_params(accel="cg", colour_order="symmetric", precision="auto"), max_sw)):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 st, dE, dD, asw, arel = m.adjoint(u_eq, gd, 1e-5, cap, prm, raise_on_status=False)

@@ -53,7 +53,11 @@ typedef enum {
 
 typedef struct pbng_mesh pbng_mesh;   /* opaque, library-owned */
 
-enum { PBNG_ACCEL_NONE = 0, PBNG_ACCEL_CHEBYSHEV = 1, PBNG_ACCEL_SOR = 2 };
+/* Acceleration of the sweeps (pbng_params.accel).  PBNG_ACCEL_CG is taken
+ * by pbng_adjoint only (conjugate gradients preconditioned by the symmetric
+ * block Gauss-Seidel sweep, see there); every other entry point rejects it
+ * with PBNG_EINVAL. */
+enum { PBNG_ACCEL_NONE = 0, PBNG_ACCEL_CHEBYSHEV = 1, PBNG_ACCEL_SOR = 2, PBNG_ACCEL_CG = 3 };
 /* Precision of the sweep (pbng_params.precision).
  *   PBNG_PREC_FP32         iterate and element arithmetic float32
  *   PBNG_PREC_COMPENSATED  iterate as a float32 pair (hi + lo), element
@@ -250,13 +254,23 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
  * max_sweeps.  With the symmetric order the iteration is symmetric block
  * Gauss-Seidel on H, whose spectrum is real in [0, 1) at a stable
  * equilibrium (H positive definite).
+ * PBNG_ACCEL_CG (with PBNG_ORDER_SYMMETRIC only; EINVAL otherwise) uses the
+ * same sweep as the preconditioner of conjugate gradients instead of as a
+ * stationary iteration: each iteration runs one symmetric sweep from zero
+ * on the current residual (z = M^{-1} r with M = (D + L) D^{-1} (D + L^T),
+ * symmetric positive definite with H) and one matrix-free Hessian action,
+ * and counts as one sweep in max_sweeps and sweeps_out; a direction of
+ * non-positive curvature (H not positive definite) returns PBNG_EDIVERGED.
+ * Its residual is the recursive one of the iteration; with float32
+ * precision the true residual is evaluated at the end and reported.
  * Precision: the sweeps are float32 (multipliers and the Hessian action);
  * their relative residual stalls near 1e-7 (L/h)^2 on a mesh of L/h
  * elements across (2e-3 at 48^3 with Chebyshev).  With p->precision
  * PBNG_PREC_EXTENDED or PBNG_PREC_AUTO the solve is refined instead: the
  * multipliers accumulate as float pairs, each correction solves
  * H d = dL/du - H lambda with the float32 sweeps (to 1e-2 of its right-hand
- * side or to their floor), and the residual is formed by central differences
+ * side, 1e-3 with PBNG_ACCEL_CG, or to their floor), and the residual is
+ * formed by central differences
  * of the float-float force (PBNG_PREC_EXTENDED),
  * H lambda = -(F(u + eps lambda) - F(u - eps lambda)) / (2 eps), with
  * eps |lambda|_max = 1e-4 of the smallest element size; rel_tol then applies

@@ -17,7 +17,7 @@ STATUS_NAMES = {
     4: "PBNG_EDEGENERATE", 5: "PBNG_EDIVERGED", 6: "PBNG_ETIMEOUT", 7: "PBNG_ENOTCONVERGED",
 }
 
-ACCEL = {"none": 0, "chebyshev": 1, "sor": 2}
+ACCEL = {"none": 0, "chebyshev": 1, "sor": 2, "cg": 3}
 PRECISION = {"fp32": 0, "compensated": 1, "extended": 2, "auto": 3}
 MODEL = {"corotated": 0, "neohookean": 1, "stable_neohookean": 2}
 ORDER = {"forward": 0, "symmetric": 1}

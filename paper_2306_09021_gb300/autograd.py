@@ -52,14 +52,15 @@ class EquilibriumModel:
         self.body_accel = None if body_accel is None else np.asarray(body_accel, dtype=np.float64)
         self.rel_tol, self.max_sweeps = rel_tol, max_sweeps
         self.adjoint_tol, self.adjoint_max_sweeps = adjoint_tol, adjoint_max_sweeps
-        # symmetric colour order with automatic Chebyshev rho; the forward
-        # solve moves to extended precision at the float32 floor, the adjoint
-        # is refined with the float-float force (both past float32's floor)
+        # forward: symmetric colour order with automatic Chebyshev rho, moving
+        # to extended precision at the float32 floor; adjoint: conjugate
+        # gradients preconditioned by the symmetric block Gauss-Seidel sweep,
+        # refined with the float-float force (both past float32's floor)
         self.params = params if params is not None else default_params(
             model=model, accel="chebyshev", rho=-1.0, colour_order="symmetric", precision="auto")
         self.adjoint_params = (adjoint_params if adjoint_params is not None
-                               else default_params(model=model, accel="chebyshev", rho=-1.0,
-                                                   colour_order="symmetric", precision="auto"))
+                               else default_params(model=model, accel="cg", colour_order="symmetric",
+                                                   precision="auto"))
         self.adjoint_params.model = self.params.model
         self.u_last = None
         self.last_solve = None

@@ -581,6 +581,56 @@ __global__ void adjoint_accumulate_kernel(int n, const float4* __restrict__ d, f
     atomicMax(reinterpret_cast<int*>(maxabs), __float_as_int(mx));  // non-negative floats order as ints
 }
 
+// Conjugate gradients on the adjoint system (PBNG_ACCEL_CG), over the n
+// free rows: one FP64 partial per kVecBlock-thread block.
+__device__ __forceinline__ void vec_block_partial(double q, double* partial) {
+    __shared__ double sh[kVecBlock];
+    sh[threadIdx.x] = q;
+    __syncthreads();
+    for (int k = kVecBlock / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// x += a p, r -= a q; partial: |r|^2
+__global__ void __launch_bounds__(kVecBlock) acg_step_kernel(int n, float a, const float4* __restrict__ p,
+                                                             const float4* __restrict__ q, float4* x, float4* r,
+                                                             double* partial) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (w < n) {
+        const float4 pw = p[w], qw = q[w], xw = x[w], rw = r[w];
+        const float4 xn = make_float4(xw.x + a * pw.x, xw.y + a * pw.y, xw.z + a * pw.z, 0.f);
+        const float4 rn = make_float4(rw.x - a * qw.x, rw.y - a * qw.y, rw.z - a * qw.z, 0.f);
+        x[w] = xn;
+        r[w] = rn;
+        s = (double)rn.x * rn.x + (double)rn.y * rn.y + (double)rn.z * rn.z;
+    }
+    vec_block_partial(s, partial);
+}
+
+// partial: r . z
+__global__ void __launch_bounds__(kVecBlock) acg_dot_kernel(int n, const float4* __restrict__ r,
+                                                            const float4* __restrict__ z, double* partial) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (w < n) {
+        const float4 a = r[w], b = z[w];
+        s = (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z;
+    }
+    vec_block_partial(s, partial);
+}
+
+// p = z + b p
+__global__ void acg_dir_kernel(int n, float b, const float4* __restrict__ z, float4* p) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n) return;
+    const float4 zw = z[w], pw = p[w];
+    p[w] = make_float4(zw.x + b * pw.x, zw.y + b * pw.y, zw.z + b * pw.z, 0.f);
+}
+
 // gvec[w] = dL/du of internal free vertex w (caller layout in).
 __global__ void gather_rhs_kernel(int nfree, const int32_t* perm, const float* dLdu, float4* gv) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1098,6 +1148,25 @@ cudaError_t launch_adjoint_refine_rhs(int nfree, const float4* gv, const float4*
     if (nfree <= 0) return cudaSuccess;
     adjoint_refine_rhs_kernel<<<nblocks(nfree, kVecBlock), kVecBlock, 0, st>>>(nfree, gv, fp_hi, fp_lo, fm_hi, fm_lo,
                                                                                 inv2eps, rhs, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acg_step(int n, float a, const float4* p, const float4* q, float4* x, float4* r, double* partial,
+                            cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    acg_step_kernel<<<nblocks(n, kVecBlock), kVecBlock, 0, st>>>(n, a, p, q, x, r, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acg_dot(int n, const float4* r, const float4* z, double* partial, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    acg_dot_kernel<<<nblocks(n, kVecBlock), kVecBlock, 0, st>>>(n, r, z, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acg_dir(int n, float b, const float4* z, float4* p, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    acg_dir_kernel<<<nblocks(n, 256), 256, 0, st>>>(n, b, z, p);
     return cudaGetLastError();
 }
 

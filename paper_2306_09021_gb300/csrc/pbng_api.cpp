@@ -95,6 +95,8 @@ struct pbng_mesh {
     // refined adjoint (extended precision): multipliers as float pairs, the
     // correction's right-hand side, the forces at u +- eps lam, the shifted states
     DevBuf d_lam_hi, d_lam_lo, d_rhs, d_fp[4], d_shift[2][2], d_maxabs, d_refine_partial;
+    // conjugate-gradient adjoint (PBNG_ACCEL_CG): residual r and H p, FP64 block partials
+    DevBuf d_acg[2], d_acg_part[2];
     double h_min = 0.0;                // smallest rest element size (cube root of 6 V)
     // Newton-CG (pbng_newton_cg, pbng_force, pbng_hessian_apply): r, x, z, p, q
     DevBuf d_nw[5], d_nw_part[2], d_nw_sc, d_nw_flag;
@@ -2000,7 +2002,17 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
                          float* dL_dxD_dev, double rel_tol, int32_t max_sweeps, const pbng_params* p,
                          int32_t* sweeps_out, double* rel_residual_out) {
     if (!m) return PBNG_EINVAL;
-    if (!valid_params(p) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
+    // PBNG_ACCEL_CG (this entry point only): conjugate gradients with one
+    // symmetric block Gauss-Seidel sweep as the preconditioner
+    const bool cg = p && p->accel == PBNG_ACCEL_CG;
+    pbng_params pv{};
+    if (p) {
+        pv = *p;
+        if (cg) pv.accel = PBNG_ACCEL_NONE;
+    }
+    if (!p || !valid_params(&pv) || max_sweeps < 0 || !(rel_tol >= 0.0)) return fail(m, PBNG_EINVAL, "bad parameters");
+    if (cg && p->colour_order != PBNG_ORDER_SYMMETRIC)
+        return fail(m, PBNG_EINVAL, "conjugate gradients need the symmetric colour order (a symmetric preconditioner)");
     if (!u_eq_dev || !dLdu_dev || !dL_dlogE_dev) return fail(m, PBNG_EINVAL, "NULL argument");
     if (p->kernel_path != 0) return fail(m, PBNG_EINVAL, "the adjoint runs on the ring layout (kernel_path 0)");
     select_path(m, p);
@@ -2133,7 +2145,115 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
         }
         return rhs2 > 0.0 ? PBNG_ENOTCONVERGED : PBNG_OK;
     };
-    if (!refine) {
+    // Conjugate gradients on H d = rhs from d = 0 (in lam), preconditioned by
+    // one symmetric block Gauss-Seidel sweep from zero (the sweeps above
+    // with rhs in place of dL/du: z = M^{-1} r with M = (D + L) D^{-1}
+    // (D + L^T), symmetric positive definite with H).  Each iteration is one
+    // preconditioner sweep and one Hessian action, counted as one sweep;
+    // the recursive residual r decides the stop (tol of rhs, a stall, or
+    // the budget).  FP64 dot products, float32
+    // vectors.
+    if (cg) {
+        const size_t fb = sizeof(float4) * (size_t)std::max(1, m->nfree);
+        for (auto& b : m->d_acg) PBNG_CUDA(m, ensure_buf(b, fb));
+        for (auto& b : m->d_acg_part)
+            PBNG_CUDA(m, ensure_buf(b, sizeof(double) * (size_t)std::max(1, adj_vec_blocks(m->nfree))));
+    }
+    auto reduce2 = [&](const double* pa, int na, const double* pb, int nb, double* a, double* b) -> pbng_status {
+        PBNG_CUDA(m, launch_reduce(pa, na, (double*)m->d_scalar.p, st));
+        if (pb) PBNG_CUDA(m, launch_reduce(pb, nb, (double*)m->d_scalar.p + 1, st));
+        m->kernel_launches += pb ? 2 : 1;
+        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_scalar.p, sizeof(double) * (pb ? 2 : 1), cudaMemcpyDeviceToHost,
+                                     st));
+        pbng_status e = sync_with_err(m, st);
+        if (e) return e;
+        *a = m->h_pinned[0];
+        if (b) *b = m->h_pinned[1];
+        return PBNG_OK;
+    };
+    auto inner_cg = [&](const float4* rhs, double rhs2, double tol, bool stall_stop, double* rel_end) -> pbng_status {
+        float4* x = lam;
+        float4* pdir = (float4*)m->d_lam[1].p;
+        float4* z = (float4*)m->d_lam[2].p;
+        float4* r = (float4*)m->d_acg[0].p;
+        float4* q = (float4*)m->d_acg[1].p;
+        const int nb = adj_vec_blocks(m->nfree);
+        const size_t vb = sizeof(float4) * (size_t)m->nv, fb = sizeof(float4) * (size_t)m->nfree;
+        for (float4* b : {x, pdir}) PBNG_CUDA(m, cudaMemsetAsync(b, 0, vb, st));
+        PBNG_CUDA(m, cudaMemcpyAsync(r, rhs, fb, cudaMemcpyDeviceToDevice, st));
+        auto precondition = [&]() -> pbng_status {  // z = M^{-1} r
+            PBNG_CUDA(m, cudaMemsetAsync(z, 0, vb, st));
+            for (const int c : seq)
+                PBNG_CUDA(m, launch_adjoint_ring_sweep(m->dm, u, z, r, (const float4*)m->d_diag.p,
+                                                       (const Item*)m->d_items.p + m->item_off[c],
+                                                       m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
+                                                       m->model, st));
+            PBNG_CUDA(m, launch_acg_dot(m->nfree, r, z, (double*)m->d_acg_part[1].p, st));
+            m->kernel_launches += (int64_t)seq.size() + 1;
+            return PBNG_OK;
+        };
+        pbng_status e;
+        if ((e = precondition())) return e;
+        double rz = 0.0, rr = rhs2;
+        if ((e = reduce2((const double*)m->d_acg_part[1].p, nb, nullptr, 0, &rz, nullptr))) return e;
+        PBNG_CUDA(m, cudaMemcpyAsync(pdir, z, fb, cudaMemcpyDeviceToDevice, st));
+        std::vector<double> hist;
+        double irel = 1.0;
+        while (rhs2 > 0.0 && done < max_sweeps) {
+            // q = H p and p . H p
+            PBNG_CUDA(m, launch_adjoint_vertex(kAdjApply, m->dm, u, pdir, nullptr, (float4*)m->d_diag.p,
+                                               (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
+                                               (double*)m->d_adj_partial.p, st, q, m->model));
+            m->kernel_launches++;
+            double pq = 0.0;
+            if ((e = reduce2((const double*)m->d_adj_partial.p, adjoint_warps(m->nitems_ring), nullptr, 0, &pq,
+                             nullptr)))
+                return e;
+            // a non-positive curvature: H is not positive definite here
+            if (!(pq > 0.0) || !std::isfinite(pq) || !(rz > 0.0)) return PBNG_EDIVERGED;
+            const double a = rz / pq;
+            PBNG_CUDA(m, launch_acg_step(m->nfree, (float)a, pdir, q, x, r, (double*)m->d_acg_part[0].p, st));
+            m->kernel_launches++;
+            if ((e = precondition())) return e;
+            double rz2 = 0.0;
+            if ((e = reduce2((const double*)m->d_acg_part[0].p, nb, (const double*)m->d_acg_part[1].p, nb, &rr, &rz2)))
+                return e;
+            done++;
+            irel = std::sqrt(rr / rhs2);
+            *rel_end = irel;
+            if (!std::isfinite(irel) || irel > 1e3) return PBNG_EDIVERGED;
+            if (irel <= tol) return PBNG_OK;
+            // a stall: the best of the last kStallCg iterations not below half
+            // the best before them (one iteration gains far less than a
+            // sweep's residual check spans)
+            constexpr size_t kStallCg = 50;
+            hist.push_back(irel);
+            if (stall_stop && hist.size() >= 2 * kStallCg) {
+                const double recent = *std::min_element(hist.end() - kStallCg, hist.end());
+                const double before = *std::min_element(hist.begin(), hist.end() - kStallCg);
+                if (recent > 0.5 * before) return PBNG_OK;
+            }
+            const double b = rz2 / rz;
+            rz = rz2;
+            PBNG_CUDA(m, launch_acg_dir(m->nfree, (float)b, z, pdir, st));
+            m->kernel_launches++;
+        }
+        return rhs2 > 0.0 ? PBNG_ENOTCONVERGED : PBNG_OK;
+    };
+    if (cg && !refine) {
+        // one float32 solve; the reported residual is the true one
+        double irel = rel;
+        s = inner_cg((const float4*)m->d_gv.p, g2, rel_tol, false, &irel);
+        if (s == PBNG_OK || s == PBNG_ENOTCONVERGED || s == PBNG_EDIVERGED) {
+            result = s;
+            s = PBNG_OK;
+            double r2 = 0.0;
+            if (g2 > 0.0 && result != PBNG_EDIVERGED && !(s = adjoint_resid(m, u, lam, (const float4*)m->d_gv.p, &r2))) {
+                rel = std::sqrt(r2 / g2);
+                if (result == PBNG_OK && rel > rel_tol) result = PBNG_ENOTCONVERGED;
+            }
+        }
+    } else if (!refine) {
         double irel = rel;
         s = inner_solve((const float4*)m->d_gv.p, g2, rel_tol, false, &irel);
         if (g2 > 0.0) rel = irel;
@@ -2170,7 +2290,10 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
         result = g2 > 0.0 ? PBNG_ENOTCONVERGED : PBNG_OK;
         while (g2 > 0.0 && done < max_sweeps && s == PBNG_OK) {
             double irel = 1.0;
-            pbng_status is = inner_solve((const float4*)m->d_rhs.p, r2, 1e-2, true, &irel);
+            // each correction to 1e-2 (sweeps) or 1e-3 (conjugate gradients) of
+            // its right-hand side, both above the float32 floor of H d
+            pbng_status is = cg ? inner_cg((const float4*)m->d_rhs.p, r2, 1e-3, true, &irel)
+                                : inner_solve((const float4*)m->d_rhs.p, r2, 1e-2, true, &irel);
             if (is == PBNG_EDIVERGED) { result = is; break; }
             if (is != PBNG_OK && is != PBNG_ENOTCONVERGED) { s = is; break; }
             // lam += d, then the residual at the new lam
@@ -2784,7 +2907,8 @@ void pbng_destroy(pbng_mesh* m) {
                       &m->d_ring, &m->d_ring_lo, &m->d_items, &m->d_prec, &m->d_pids, &m->d_pitems, &m->d_host_u, &m->d_vsq, &m->d_comp_off,
                       &m->d_comp_list, &m->d_lam_hi, &m->d_lam_lo, &m->d_rhs, &m->d_fp[0], &m->d_fp[1], &m->d_fp[2],
                       &m->d_fp[3], &m->d_shift[0][0], &m->d_shift[0][1], &m->d_shift[1][0], &m->d_shift[1][1],
-                      &m->d_maxabs, &m->d_refine_partial,
+                      &m->d_maxabs, &m->d_refine_partial, &m->d_acg[0], &m->d_acg[1], &m->d_acg_part[0],
+                      &m->d_acg_part[1],
                       &m->d_aux0, &m->d_aux1, &m->d_aux_lo, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k, &m->d_wc_off, &m->d_wc_list, &m->d_wc_v,
                       &m->d_wc_b, &m->d_wc_k, &m->d_wc_c0,
