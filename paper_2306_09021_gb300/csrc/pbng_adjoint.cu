@@ -699,6 +699,9 @@ __device__ __forceinline__ void adj_issue_records(const DeviceMesh& m, Item it, 
     bulk_g2s(&S.rec[r], m.ring + (it.slot0 >> 5), (uint32_t)sizeof(RingBlock), S.bar + r);
 }
 
+// APPLY: the Hessian action needs neither the right-hand side nor the
+// diagonal block.
+template <bool APPLY>
 __device__ __forceinline__ void adj_issue_gathers(const DeviceMesh& m, const State& u, const float4* lam,
                                                   const float4* gv, const float4* diag, AdjWarpSmem& S, int r,
                                                   int g, int lane) {
@@ -713,17 +716,21 @@ __device__ __forceinline__ void adj_issue_gathers(const DeviceMesh& m, const Sta
         cp_async16(G.oh + lane, u.hi + v);
         cp_async16(G.ol + lane, u.lo + v);
         cp_async16(G.olam + lane, lam + v);
-        cp_async16(G.ogv + lane, gv + v);
-        cp_async16(G.od0 + lane, diag + 2 * v);
-        cp_async16(G.od1 + lane, diag + 2 * v + 1);
+        if (!APPLY) {
+            cp_async16(G.ogv + lane, gv + v);
+            cp_async16(G.od0 + lane, diag + 2 * v);
+            cp_async16(G.od1 + lane, diag + 2 * v + 1);
+        }
         cp_async16(G.oa0 + lane, m.aux0 + v);
         cp_async16(G.oa1 + lane, m.aux1 + v);
     }
 }
 
-template <int W, int MODEL>
+// APPLY: instead of the Gauss-Seidel update, hout[v] = (H lam)_v and
+// rr += lam_v . (H lam)_v.
+template <int W, int MODEL, bool APPLY>
 __device__ __forceinline__ void adj_ring_item(const DeviceMesh& m, float4* lam, const AdjWarpSmem& S, int r, int g,
-                                              int lane, int32_t* err) {
+                                              int lane, int32_t* err, float4* hout, double& rr) {
     const Item it = S.desc[r];
     const RingBlock& R = S.rec[r];
     const AdjGat& G = S.gat[g];
@@ -782,6 +789,13 @@ __device__ __forceinline__ void adj_ring_item(const DeviceMesh& m, float4* lam, 
     // the multipliers of a constraint's other vertices belong to other
     // colours (a constraint is an element of the colouring)
     weak_hessian(m, lam, v, acc, nullptr);
+    if constexpr (APPLY) {
+        const float h0 = acc[0] + K * li.x + nl * n[0], h1 = acc[1] + K * li.y + nl * n[1],
+                    h2 = acc[2] + K * li.z + nl * n[2];
+        hout[v] = make_float4(h0, h1, h2, 0.f);
+        rr += (double)li.x * h0 + (double)li.y * h1 + (double)li.z * h2;
+        return;
+    }
     const float4 gvv = G.ogv[j];
     const float r0 = gvv.x - (acc[0] + K * li.x + nl * n[0]);
     const float r1 = gvv.y - (acc[1] + K * li.y + nl * n[1]);
@@ -803,11 +817,13 @@ __device__ __forceinline__ void adj_ring_item(const DeviceMesh& m, float4* lam, 
 // Warp gw takes items gw, gw + nw, ... of one colour.  Every wait is bounded:
 // on a timeout the warp records it, lets its copies land (bounded) and
 // returns.
-template <int MODEL>
+// APPLY: the Hessian action of lam over the given items (any colours; lam
+// is only read), with one FP64 partial of lam . H lam per warp of the grid.
+template <int MODEL, bool APPLY>
 __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
     adjoint_ring_sweep_kernel(const DeviceMesh m, State u, float4* lam, const float4* __restrict__ gv,
                               const float4* __restrict__ diag, const Item* __restrict__ items, int nitems,
-                              int32_t* err) {
+                              int32_t* err, float4* out, double* partial) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     AdjWarpSmem& S = reinterpret_cast<AdjWarpSmem*>(smem)[warp];
@@ -816,6 +832,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
     const int first = gw, stride = nw;
     int issued = 0, waited = 0;  // items whose records were requested / awaited
     bool ok = true;
+    double rr = 0.0;
     Item next{};                 // lane 0: next item to request, loaded one item early
     if (n > 0) {
         if (lane == 0) {
@@ -829,7 +846,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
         ok = mbar_wait(S.bar + 0, 0);
         waited = ok ? 1 : 0;  // a stage whose wait gave up is drained again on abort
         if (__any_sync(kFull, !ok)) goto abort;
-        adj_issue_gathers(m, u, lam, gv, diag, S, 0, 0, lane);
+        adj_issue_gathers<APPLY>(m, u, lam, gv, diag, S, 0, 0, lane);
         cp_async_commit();
         for (int k = 0; k < n; ++k) {
             // Record stage (k + 2) % 3 and gather stage (k + 1) % 2 were last
@@ -846,7 +863,9 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
             if (k + 1 < n) {
                 ok = mbar_wait(S.bar + (k + 1) % kAdjRecStages, ((k + 1) / kAdjRecStages) & 1);
                 waited = ok ? k + 2 : k + 1;
-                if (ok) adj_issue_gathers(m, u, lam, gv, diag, S, (k + 1) % kAdjRecStages, (k + 1) % kAdjGatStages, lane);
+                if (ok)
+                    adj_issue_gathers<APPLY>(m, u, lam, gv, diag, S, (k + 1) % kAdjRecStages, (k + 1) % kAdjGatStages,
+                                             lane);
             }
             cp_async_commit();
             cp_async_wait<1>();  // this lane's gathers of item k have landed
@@ -854,13 +873,18 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
             __syncwarp();        // ... and the other lanes'
             const int r = k % kAdjRecStages, g = k % kAdjGatStages;
             switch (S.desc[r].w) {
-                case 4: adj_ring_item<4, MODEL>(m, lam, S, r, g, lane, err); break;
-                case 8: adj_ring_item<8, MODEL>(m, lam, S, r, g, lane, err); break;
-                case 16: adj_ring_item<16, MODEL>(m, lam, S, r, g, lane, err); break;
-                default: adj_ring_item<32, MODEL>(m, lam, S, r, g, lane, err); break;
+                case 4: adj_ring_item<4, MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr); break;
+                case 8: adj_ring_item<8, MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr); break;
+                case 16: adj_ring_item<16, MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr); break;
+                default: adj_ring_item<32, MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr); break;
             }
             __syncwarp();
         }
+    }
+    if (APPLY) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) rr += __shfl_xor_sync(kFull, rr, off);
+        if (lane == 0) partial[gw] = rr;
     }
     return;
 
@@ -868,6 +892,7 @@ abort:
     if (lane == 0) {
         atomicOr(err, kErrTimeout);
         for (int k = waited; k < issued; ++k) (void)mbar_wait(S.bar + k % kAdjRecStages, (k / kAdjRecStages) & 1);
+        if (APPLY) partial[gw] = 0.0;
     }
     cp_async_wait<0>();
     __syncwarp();
@@ -1040,9 +1065,12 @@ cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4
 
 cudaError_t adjoint_prepare() {
     const int bytes = kAdjWarps * (int)sizeof(AdjWarpSmem);
-    const void* fns[3] = {(const void*)adjoint_ring_sweep_kernel<el::kCorotated>,
-                          (const void*)adjoint_ring_sweep_kernel<el::kNeoHookean>,
-                          (const void*)adjoint_ring_sweep_kernel<el::kStableNeoHookean>};
+    const void* fns[6] = {(const void*)adjoint_ring_sweep_kernel<el::kCorotated, false>,
+                          (const void*)adjoint_ring_sweep_kernel<el::kNeoHookean, false>,
+                          (const void*)adjoint_ring_sweep_kernel<el::kStableNeoHookean, false>,
+                          (const void*)adjoint_ring_sweep_kernel<el::kCorotated, true>,
+                          (const void*)adjoint_ring_sweep_kernel<el::kNeoHookean, true>,
+                          (const void*)adjoint_ring_sweep_kernel<el::kStableNeoHookean, true>};
     for (const void* f : fns) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
         if (e == cudaSuccess)
@@ -1052,22 +1080,41 @@ cudaError_t adjoint_prepare() {
     return cudaSuccess;
 }
 
-cudaError_t launch_adjoint_ring_sweep(const DeviceMesh& m, State u, float4* lam, const float4* gv, const float4* diag,
-                                      const Item* items, int nitems, int32_t* err, int model, cudaStream_t st) {
+int adj_ring_grid(int nitems) {
+    const int want = nblocks(nitems, kAdjWarps), cap = kAdjCtasPerSm * adj_sm_count();
+    return want < cap ? want : cap;
+}
+
+template <bool APPLY>
+cudaError_t adj_ring_launch(const DeviceMesh& m, State u, float4* lam, const float4* gv, const float4* diag,
+                            const Item* items, int nitems, int32_t* err, int model, float4* out, double* partial,
+                            cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const int bytes = kAdjWarps * (int)sizeof(AdjWarpSmem);  // attribute set by adjoint_prepare()
-    const int want = nblocks(nitems, kAdjWarps), cap = kAdjCtasPerSm * adj_sm_count();
-    const int grid = want < cap ? want : cap;
+    const int grid = adj_ring_grid(nitems);
     if (model == el::kNeoHookean)
-        adjoint_ring_sweep_kernel<el::kNeoHookean><<<grid, kAdjWarps * 32, bytes, st>>>(m, u, lam, gv, diag, items,
-                                                                                        nitems, err);
+        adjoint_ring_sweep_kernel<el::kNeoHookean, APPLY><<<grid, kAdjWarps * 32, bytes, st>>>(
+            m, u, lam, gv, diag, items, nitems, err, out, partial);
     else if (model == el::kStableNeoHookean)
-        adjoint_ring_sweep_kernel<el::kStableNeoHookean><<<grid, kAdjWarps * 32, bytes, st>>>(m, u, lam, gv, diag,
-                                                                                              items, nitems, err);
+        adjoint_ring_sweep_kernel<el::kStableNeoHookean, APPLY><<<grid, kAdjWarps * 32, bytes, st>>>(
+            m, u, lam, gv, diag, items, nitems, err, out, partial);
     else
-        adjoint_ring_sweep_kernel<el::kCorotated><<<grid, kAdjWarps * 32, bytes, st>>>(m, u, lam, gv, diag, items,
-                                                                                      nitems, err);
+        adjoint_ring_sweep_kernel<el::kCorotated, APPLY><<<grid, kAdjWarps * 32, bytes, st>>>(
+            m, u, lam, gv, diag, items, nitems, err, out, partial);
     return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_ring_sweep(const DeviceMesh& m, State u, float4* lam, const float4* gv, const float4* diag,
+                                      const Item* items, int nitems, int32_t* err, int model, cudaStream_t st) {
+    return adj_ring_launch<false>(m, u, lam, gv, diag, items, nitems, err, model, nullptr, nullptr, st);
+}
+
+int adjoint_ring_apply_warps(int nitems) { return nitems > 0 ? adj_ring_grid(nitems) * kAdjWarps : 0; }
+
+cudaError_t launch_adjoint_ring_apply(const DeviceMesh& m, State u, const float4* lam, const Item* items, int nitems,
+                                      int32_t* err, int model, float4* out, double* partial, cudaStream_t st) {
+    return adj_ring_launch<true>(m, u, const_cast<float4*>(lam), nullptr, nullptr, items, nitems, err, model, out,
+                                 partial, st);
 }
 
 int vec_blocks(int n) { return nblocks(n, kBlock); }

@@ -1927,7 +1927,11 @@ pbng_status adjoint_setup(pbng_mesh* m) {
     PBNG_CUDA(m, ensure_buf(m->d_gv, sizeof(float4) * (size_t)std::max(1, m->nfree)));
     PBNG_CUDA(m, ensure_buf(m->d_diag, 2 * sizeof(float4) * (size_t)std::max(1, m->nfree)));
     PBNG_CUDA(m, ensure_buf(m->d_hdl, sizeof(float4) * (size_t)m->nv));
-    PBNG_CUDA(m, ensure_buf(m->d_adj_partial, sizeof(double) * (size_t)std::max(1, adjoint_warps(m->nitems_ring))));
+    // per-warp partials of the direct-load kernels and of the pipelined
+    // Hessian action, whose grids differ
+    PBNG_CUDA(m, ensure_buf(m->d_adj_partial,
+                            sizeof(double) * (size_t)std::max({1, adjoint_warps(m->nitems_ring),
+                                                               adjoint_ring_apply_warps(m->nitems_ring)})));
     double vmin = 0.0;
     for (int32_t e = 0; e < m->ne; ++e) vmin = (e == 0) ? m->vol[e] : std::min(vmin, m->vol[e]);
     m->h_min = std::cbrt(6.0 * vmin);
@@ -1959,7 +1963,8 @@ pbng_status newton_setup(pbng_mesh* m) {
     pbng_status s = adjoint_setup(m);
     if (s) return s;
     for (auto& b : m->d_nw) PBNG_CUDA(m, ensure_buf(b, sizeof(float4) * (size_t)m->nv));
-    const size_t np = (size_t)std::max(1, std::max(vec_blocks(m->nfree), adjoint_warps(m->nitems_ring)));
+    const size_t np = (size_t)std::max({1, vec_blocks(m->nfree), adjoint_warps(m->nitems_ring),
+                                        adjoint_ring_apply_warps(m->nitems_ring)});
     for (auto& b : m->d_nw_part) PBNG_CUDA(m, ensure_buf(b, sizeof(double) * np));
     PBNG_CUDA(m, ensure_buf(m->d_nw_sc, sizeof(double) * 4));
     PBNG_CUDA(m, ensure_buf(m->d_nw_flag, sizeof(int32_t)));
@@ -2200,14 +2205,14 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
         std::vector<double> hist;
         double irel = 1.0;
         while (rhs2 > 0.0 && done < max_sweeps) {
-            // q = H p and p . H p
-            PBNG_CUDA(m, launch_adjoint_vertex(kAdjApply, m->dm, u, pdir, nullptr, (float4*)m->d_diag.p,
-                                               (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
-                                               (double*)m->d_adj_partial.p, st, q, m->model));
+            // q = H p and p . H p (the pipelined action over every ring item)
+            PBNG_CUDA(m, launch_adjoint_ring_apply(m->dm, u, pdir, (const Item*)m->d_items.p, m->nitems_ring,
+                                                   (int32_t*)m->d_err.p, m->model, q, (double*)m->d_adj_partial.p,
+                                                   st));
             m->kernel_launches++;
             double pq = 0.0;
-            if ((e = reduce2((const double*)m->d_adj_partial.p, adjoint_warps(m->nitems_ring), nullptr, 0, &pq,
-                             nullptr)))
+            if ((e = reduce2((const double*)m->d_adj_partial.p, adjoint_ring_apply_warps(m->nitems_ring), nullptr, 0,
+                             &pq, nullptr)))
                 return e;
             // a non-positive curvature: H is not positive definite here
             if (!(pq > 0.0) || !std::isfinite(pq) || !(rz > 0.0)) return PBNG_EDIVERGED;
@@ -2393,10 +2398,9 @@ pbng_status pbng_hessian_apply(pbng_mesh* m, const float* u_dev, const float* p_
     PBNG_CUDA(m, launch_load(m->nv, m->nfree, u_dev, perm, (const float4*)m->d_dir_hi.p,
                              (const float4*)m->d_dir_lo.p, state_of(m, 3), st));
     PBNG_CUDA(m, launch_gather_vec(m->nv, m->nfree, perm, p_dev, (float4*)m->d_nw[3].p, st));
-    PBNG_CUDA(m, launch_adjoint_vertex(kAdjApply, m->dm, state_of(m, 3), (float4*)m->d_nw[3].p, nullptr,
-                                       (float4*)m->d_diag.p, (const Item*)m->d_items.p, m->nitems_ring,
-                                       (int32_t*)m->d_err.p, (double*)m->d_nw_part[0].p, st, (float4*)m->d_nw[4].p,
-                                       m->model));
+    PBNG_CUDA(m, launch_adjoint_ring_apply(m->dm, state_of(m, 3), (float4*)m->d_nw[3].p, (const Item*)m->d_items.p,
+                                           m->nitems_ring, (int32_t*)m->d_err.p, m->model, (float4*)m->d_nw[4].p,
+                                           (double*)m->d_nw_part[0].p, st));
     PBNG_CUDA(m, launch_scatter_vec(m->nv, m->nfree, perm, (const float4*)m->d_nw[4].p, hp_out_dev, st));
     m->kernel_launches += 4;
     PBNG_CUDA(m, cudaStreamSynchronize(st));
@@ -2470,10 +2474,9 @@ pbng_status pbng_newton_cg(pbng_mesh* m, float* u_dev, double rel_tol, int32_t m
         const double bnorm = std::sqrt(rr);
         int k = 0;
         while (k < max_cg) {
-            PBNG_CUDA(m, launch_adjoint_vertex(kAdjApply, m->dm, u0, pd, nullptr, (float4*)m->d_diag.p,
-                                               (const Item*)m->d_items.p, m->nitems_ring, (int32_t*)m->d_err.p,
-                                               part1, st, hq, m->model));
-            PBNG_CUDA(m, launch_reduce(part1, adjoint_warps(m->nitems_ring), sc + 1, st));
+            PBNG_CUDA(m, launch_adjoint_ring_apply(m->dm, u0, pd, (const Item*)m->d_items.p, m->nitems_ring,
+                                                   (int32_t*)m->d_err.p, m->model, hq, part1, st));
+            PBNG_CUDA(m, launch_reduce(part1, adjoint_ring_apply_warps(m->nitems_ring), sc + 1, st));
             PBNG_CUDA(m, launch_cg_update(n, sc, x, r, pd, hq, diag, z, part0, part1, flag, st));
             PBNG_CUDA(m, launch_reduce(part0, vec_blocks(n), sc + 2, st));
             PBNG_CUDA(m, launch_reduce(part1, vec_blocks(n), sc + 3, st));

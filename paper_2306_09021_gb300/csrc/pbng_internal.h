@@ -234,6 +234,13 @@ cudaError_t launch_adjoint_vertex(int mode, const DeviceMesh& m, State u, float4
 cudaError_t launch_adjoint_ring_sweep(const DeviceMesh& m, State u, float4* lam, const float4* gv, const float4* diag,
                                       const Item* items, int nitems, int32_t* err, int model, cudaStream_t st);
 cudaError_t adjoint_prepare();
+// The Hessian action out = H lam with the same pipeline, over any items (all
+// colours in one launch; lam is only read), one FP64 partial of
+// lam . H lam per warp of its grid (adjoint_ring_apply_warps(nitems)).
+int adjoint_ring_apply_warps(int nitems);
+cudaError_t launch_adjoint_ring_apply(const DeviceMesh& m, State u, const float4* lam, const Item* items, int nitems,
+                                      int32_t* err, int model, float4* out, double* partial, cudaStream_t st);
+
 // Preconditioned conjugate gradients on the free rows (pbng_adjoint.cu): the
 // scalars stay on the device in sc[0..3] = (r.z, p.Hp, new r.z, |r|^2); one
 // FP64 partial per kBlock threads (vec_blocks(n) of them).
