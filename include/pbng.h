@@ -454,8 +454,9 @@ pbng_status pbng_set_profiling(pbng_mesh* m, int32_t enable);
  * an asynchronous copy gives up after about two seconds of SM clock, records
  * kErrTimeout and lets the warp's other copies land before it returns; the
  * call then fails with PBNG_ETIMEOUT.  With bytes > 0 (a multiple of 16, at
- * most 1024) each warp's first record copy of every later ring pass is
- * expected to carry that many bytes more than it does, so that wait runs out
+ * most 1024) each warp's first bulk copy of every later ring pass (an
+ * item's records; in the float32 passes, its 1-ring ids) is expected to
+ * carry that many bytes more than it does, so that wait runs out
  * while every copy still completes.  0 restores normal operation.  Drops the
  * captured sweep graphs; EINVAL on a bad value. */
 pbng_status pbng_test_set_copy_shortfall(pbng_mesh* m, int32_t bytes);

@@ -98,8 +98,8 @@ struct DeviceMesh {
     const struct PairRec* prec;
     const struct PairIds* pids;
     // Test hook (pbng_test_set_copy_shortfall): bytes that each warp's first
-    // record copy of a ring pass is expected to carry beyond its size, so
-    // that its bounded wait runs out; 0 in normal use.
+    // bulk copy of a ring pass (records, or a pair item's ids) is expected to
+    // carry beyond its size, so that its bounded wait runs out; 0 in normal use.
     int32_t copy_shortfall;
     float pn_x, pn_y, pn_z;  // contact plane normal (unit)
     float k_contact;         // 0 = no plane
