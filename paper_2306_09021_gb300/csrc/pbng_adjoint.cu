@@ -728,13 +728,22 @@ __device__ __forceinline__ void adj_issue_gathers(const DeviceMesh& m, const Sta
 
 // APPLY: instead of the Gauss-Seidel update, hout[v] = (H lam)_v and
 // rr += lam_v . (H lam)_v.
-template <int W, int MODEL, bool APPLY>
+template <int W>
+__device__ __forceinline__ void adj_group_sums(float* acc) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] = el::group_sum<W>(acc[k]);
+}
+
+// The lane width W = it.w is a run-time value everywhere but in the W-lane
+// sums, so the kernel holds one copy of the element state and Hessian action.
+template <int MODEL, bool APPLY>
 __device__ __forceinline__ void adj_ring_item(const DeviceMesh& m, float4* lam, const AdjWarpSmem& S, int r, int g,
                                               int lane, int32_t* err, float4* hout, double& rr) {
     const Item it = S.desc[r];
     const RingBlock& R = S.rec[r];
     const AdjGat& G = S.gat[g];
-    const int j = lane / W;
+    const int W = it.w;
+    const int j = lane >> (__ffs(W) - 1);
     const bool active = j < it.nv;
     const int v = it.v0 + j;
     const float3 z3 = make_float3(0.f, 0.f, 0.f);
@@ -772,8 +781,12 @@ __device__ __forceinline__ void adj_ring_item(const DeviceMesh& m, float4* lam, 
     hess_action<MODEL>(E, ra.w, rb.w, dF, out);
     const float3 h = mat_g(out, gi);
     float acc[3] = {h.x, h.y, h.z};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) acc[k] = el::group_sum<W>(acc[k]);
+    switch (W) {  // warp-uniform
+        case 4: adj_group_sums<4>(acc); break;
+        case 8: adj_group_sums<8>(acc); break;
+        case 16: adj_group_sums<16>(acc); break;
+        default: adj_group_sums<32>(acc); break;
+    }
     if (!active || (lane & (W - 1)) != 0) return;
     // weak terms: springs K I, active plane contact k n n^T
     const float4 x0 = G.oa0[j], x1 = G.oa1[j];
@@ -872,12 +885,7 @@ __global__ void __launch_bounds__(kAdjWarps * 32, kAdjCtasPerSm)
             if (__any_sync(kFull, !ok)) goto abort;
             __syncwarp();        // ... and the other lanes'
             const int r = k % kAdjRecStages, g = k % kAdjGatStages;
-            switch (S.desc[r].w) {
-                case 4: adj_ring_item<4, MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr); break;
-                case 8: adj_ring_item<8, MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr); break;
-                case 16: adj_ring_item<16, MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr); break;
-                default: adj_ring_item<32, MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr); break;
-            }
+            adj_ring_item<MODEL, APPLY>(m, lam, S, r, g, lane, err, out, rr);
             __syncwarp();
         }
     }

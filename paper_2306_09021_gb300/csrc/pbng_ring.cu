@@ -279,13 +279,29 @@ __device__ __forceinline__ void store_sq(const DeviceMesh& m, int v, double q, d
 // which only scales the step, stays float32.  UPDATE: the group's first lane
 // solves and writes its vertex at once (Eq. pbgn_dx, Eq. pbgn_update).
 // Otherwise: |r|^2 of the vertex.
-template <int W, bool UPDATE, int MODEL>
+// The W-lane sums of the extended pass for a lane width known at compile
+// time (f in float-float; A, the update's Hessian, in float).
+template <int W, bool UPDATE>
+__device__ __forceinline__ void ext_group_sums(ff::F2* f, float* A) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = el::group_sum_ff<W>(f[k]);
+    if (UPDATE) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
+    }
+}
+
+// The lane width W = it.w is a run-time value everywhere but in the W-lane
+// sums: one copy of the long float-float element force per kernel instead
+// of one per width keeps the kernel within the instruction cache.
+template <bool UPDATE, int MODEL>
 __device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, WarpSmemExt& S, const Item& it, int r,
                                                  int g, int lane, PassParams pp, int32_t* err, double& rr,
                                                  double* comp_sq) {
     const RingBlock& R = S.rec[r];
     const auto& G = S.gat[g];
-    const int j = lane / W;
+    const int W = it.w;
+    const int j = lane >> (__ffs(W) - 1);
     const bool active = j < it.nv;
     float3 uh = make_float3(0.f, 0.f, 0.f), ul = uh;
     // u_j - u_i as an exact float pair: (hi_j - hi_i) by TwoSum, plus the low words
@@ -320,11 +336,11 @@ __device__ __forceinline__ void compute_item_ext(const DeviceMesh& m, State s, W
         make_float3(d[1][0].h, d[1][1].h, d[1][2].h), make_float3(d[2][0].h, d[2][1].h, d[2][2].h), A, q);
     ff::F2 f[3];
     ff::element_force<MODEL>(gg, ff::mk(ra.w, la.w), ff::mk(rb.w, lb.w), d, q, f);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) f[k] = el::group_sum_ff<W>(f[k]);
-    if (UPDATE) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) A[k] = el::group_sum<W>(A[k]);
+    switch (W) {  // warp-uniform
+        case 4: ext_group_sums<4, UPDATE>(f, A); break;
+        case 8: ext_group_sums<8, UPDATE>(f, A); break;
+        case 16: ext_group_sums<16, UPDATE>(f, A); break;
+        default: ext_group_sums<32, UPDATE>(f, A); break;
     }
     if (!active || (lane & (W - 1)) != 0) return;
     const int v = it.v0 + j;
@@ -537,14 +553,7 @@ __global__ void __launch_bounds__(kBlock, kCtasPerSm)
             __syncwarp();        // ... and the other lanes'
             const Item it = S.desc[k % RS];
             const int r = k % RS, g = k % kGatStages;
-            if (!it.skip) {  // uniform over the warp; the lane width too
-                switch (it.w) {
-                    case 4: compute_item_ext<4, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
-                    case 8: compute_item_ext<8, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
-                    case 16: compute_item_ext<16, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
-                    default: compute_item_ext<32, UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq); break;
-                }
-            }
+            if (!it.skip) compute_item_ext<UPDATE, MODEL>(m, s, S, it, r, g, lane, pp, err, rr, comp_sq);  // warp-uniform
             __syncwarp();
         }
     }
