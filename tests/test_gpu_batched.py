@@ -87,3 +87,36 @@ def test_auto_precision_batch_meets_the_tolerance_in_extended_residuals():
     # iterate it stopped at (resume keeps the float pairs)
     rel_again = m.sweep(u, 0, default_params(precision="extended", resume=1), want_residual=True)
     assert np.all(rel_again <= tol * (1 + 1e-6))
+
+
+def test_batched_cg_adjoint_matches_each_meshs_dense_adjoint(oracle_mod):
+    """One conjugate-gradient adjoint (refined) over a batch of three meshes
+    of uneven size: H is block diagonal over the meshes, so each mesh's
+    sensitivities must match the oracle's dense adjoint of that mesh alone."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    probs = W.batched_blocks(count=3, side_lo=3, side_hi=5, seed=21)
+    batch, mid, offs = W.concat_problems(probs)
+    rng = np.random.default_rng(4)
+    xeq, dldx, refs = [], [], []
+    for p in probs:
+        om = oracle_mod.OracleMesh.from_problem(p)
+        x, it, _ = om.newton(p.x0, 1e-11, 60)
+        assert it >= 0
+        g = 0.01 * rng.standard_normal(x.shape)
+        xeq.append(x)
+        dldx.append(g)
+        refs.append(om.adjoint(x, g))
+    xeq, dldx = np.vstack(xeq), np.vstack(dldx)
+    m = Mesh.from_problem(batch, mesh_id=mid)
+    u = torch.tensor(xeq - batch.X, dtype=torch.float32, device="cuda")
+    g = torch.tensor(dldx, dtype=torch.float32, device="cuda")
+    st, dE, dD, its, rel = m.adjoint(u, g, 1e-8, 20000,
+                                     default_params(accel="cg", colour_order="symmetric", precision="extended"))
+    assert st == 0 and rel <= 1e-8
+    dE, dD = dE.cpu().double().numpy(), dD.cpu().double().numpy()
+    te = np.cumsum([0] + [p.ne for p in probs])
+    td = np.cumsum([0] + [len(p.dirichlet) for p in probs])
+    for k, (dE_ref, dD_ref) in enumerate(refs):
+        e, d = dE[te[k]:te[k + 1]], dD[td[k]:td[k + 1]]
+        assert np.abs(e - dE_ref).max() <= 2e-5 * np.abs(dE_ref).max(), k
+        assert np.abs(d - dD_ref).max() <= 2e-5 * np.abs(dD_ref).max(), k

@@ -544,3 +544,61 @@ def test_host_buffer_sweep_on_a_batch_reports_every_component():
     assert len(r_host) == 3
     assert torch.equal(h, u.cpu())
     assert np.allclose(r_host, rel * r_start, rtol=1e-12, atol=0.0)
+
+
+def _full_pair_problem():
+    """A centre vertex with exactly 32 incident tets and 32 1-ring vertices:
+    two rings of 16 vertices (z = +-0.5, the lower one turned by half a step)
+    joined to the centre by the tets (c, a_i, a_i+1, b_i) and
+    (c, b_i, b_i+1, a_i+1).  Its pair item uses every lane of a 16-lane group
+    with both tets and both 1-ring slots filled, and its ring item all 32
+    lanes; the ring vertices have 3 tets and 5 neighbours.  Four ring
+    vertices are clamped; gravity loads it."""
+    n = 16
+    ang = 2 * np.pi * np.arange(n) / n
+    a = np.stack([np.cos(ang), np.sin(ang), np.full(n, 0.5)], 1)
+    b = np.stack([np.cos(ang + np.pi / n), np.sin(ang + np.pi / n), np.full(n, -0.5)], 1)
+    X = np.vstack([np.zeros((1, 3)), a, b])
+    A = lambda i: 1 + i % n
+    B = lambda i: 1 + n + i % n
+    tets = []
+    for i in range(n):
+        for t in ([0, A(i), A(i + 1), B(i)], [0, B(i), B(i + 1), A(i + 1)]):
+            P = X[t]
+            if np.linalg.det(P[1:] - P[0]) < 0:
+                t = [t[0], t[2], t[1], t[3]]
+            tets.append(t)
+    tets = np.array(tets, np.int32)
+    ne = len(tets)
+    dirichlet = np.array([A(0), A(8), B(4), B(12)], np.int32)
+    rng = np.random.default_rng(12)
+    x0 = X + 0.03 * rng.standard_normal(X.shape)
+    x0[dirichlet] = X[dirichlet]
+    return W.Problem(name="full_pair", X=X, tets=tets, young=np.full(ne, 1e5), poisson=np.full(ne, 0.3),
+                     dirichlet=dirichlet, x0=x0, body_accel=np.array([0.0, 0.0, -9.8]),
+                     density=np.full(ne, 1000.0))
+
+
+@pytest.mark.parametrize("precision", ["compensated", "extended"])
+def test_full_32_tet_32_ring_vertex_matches_the_oracle(oracle_mod, precision):
+    """The widest vertex the ring layout holds (32 tets, 32 1-ring vertices):
+    the float32 passes' pair item fills both tets and both 1-ring slots of all
+    16 lanes of its group, the extended passes' ring item all 32 lanes; 30
+    Chebyshev sweeps (to about 3e-4 of the initial residual) match the
+    oracle's positions and residual."""
+    from paper_2306_09021_gb300 import Mesh, default_params
+    p = _full_pair_problem()
+    assert np.bincount(p.tets.reshape(-1))[0] == 32
+    assert len(np.setdiff1d(np.unique(p.tets[np.any(p.tets == 0, axis=1)]), [0])) == 32
+    m = Mesh.from_problem(p)
+    sched = m.schedule()
+    assert all(c > 0 for c in sched["ctas_per_sm"])  # every colour in the ring layout
+    u = torch.tensor(p.x0 - p.X, dtype=torch.float32, device="cuda")
+    rel = m.sweep(u, 30, default_params(accel="chebyshev", precision=precision), want_residual=True)
+    om = _oracle(oracle_mod, p)
+    x_ora, st = om.sweeps(p.x0, 30, accel="chebyshev")
+    assert st == 0
+    x_gpu = u.cpu().double().numpy() + p.X
+    assert np.abs(x_gpu - x_ora).max() <= 1e-5 * np.abs(x_ora - p.X).max()
+    rr = om.residual(x_ora) / om.residual(p.x0)
+    assert abs(rel[0] - rr) <= 1e-3 * rr + RES_FLOOR
