@@ -594,18 +594,28 @@ __device__ __forceinline__ void vec_block_partial(double q, double* partial) {
     if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
 }
 
-// x += a p, r -= a q; partial: |r|^2
-__global__ void __launch_bounds__(kVecBlock) acg_step_kernel(int n, float a, const float4* __restrict__ p,
+// x += a p, r -= a q with a = sc[0] / sc[1] (r . z over p . H p, on the
+// device); partial: |r|^2.  A non-positive or non-finite p . H p (H not
+// positive definite) sets *flag and leaves x and r as they are.
+__global__ void __launch_bounds__(kVecBlock) acg_step_kernel(int n, const double* sc, int32_t* flag,
+                                                             const float4* __restrict__ p,
                                                              const float4* __restrict__ q, float4* x, float4* r,
                                                              double* partial) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    const double pq = sc[1];
+    const bool ok = pq > 0.0 && pq < 1e300 && !*flag;
+    if (!ok && w == 0) *flag = 1;
+    const float a = ok ? (float)(sc[0] / pq) : 0.0f;
     double s = 0.0;
     if (w < n) {
-        const float4 pw = p[w], qw = q[w], xw = x[w], rw = r[w];
-        const float4 xn = make_float4(xw.x + a * pw.x, xw.y + a * pw.y, xw.z + a * pw.z, 0.f);
-        const float4 rn = make_float4(rw.x - a * qw.x, rw.y - a * qw.y, rw.z - a * qw.z, 0.f);
-        x[w] = xn;
-        r[w] = rn;
+        const float4 rw = r[w];
+        float4 rn = rw;
+        if (ok) {
+            const float4 pw = p[w], qw = q[w], xw = x[w];
+            x[w] = make_float4(xw.x + a * pw.x, xw.y + a * pw.y, xw.z + a * pw.z, 0.f);
+            rn = make_float4(rw.x - a * qw.x, rw.y - a * qw.y, rw.z - a * qw.z, 0.f);
+            r[w] = rn;
+        }
         s = (double)rn.x * rn.x + (double)rn.y * rn.y + (double)rn.z * rn.z;
     }
     vec_block_partial(s, partial);
@@ -621,14 +631,6 @@ __global__ void __launch_bounds__(kVecBlock) acg_dot_kernel(int n, const float4*
         s = (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z;
     }
     vec_block_partial(s, partial);
-}
-
-// p = z + b p
-__global__ void acg_dir_kernel(int n, float b, const float4* __restrict__ z, float4* p) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= n) return;
-    const float4 zw = z[w], pw = p[w];
-    p[w] = make_float4(zw.x + b * pw.x, zw.y + b * pw.y, zw.z + b * pw.z, 0.f);
 }
 
 // gvec[w] = dL/du of internal free vertex w (caller layout in).
@@ -1206,22 +1208,16 @@ cudaError_t launch_adjoint_refine_rhs(int nfree, const float4* gv, const float4*
     return cudaGetLastError();
 }
 
-cudaError_t launch_acg_step(int n, float a, const float4* p, const float4* q, float4* x, float4* r, double* partial,
-                            cudaStream_t st) {
+cudaError_t launch_acg_step(int n, const double* sc, int32_t* flag, const float4* p, const float4* q, float4* x,
+                            float4* r, double* partial, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    acg_step_kernel<<<nblocks(n, kVecBlock), kVecBlock, 0, st>>>(n, a, p, q, x, r, partial);
+    acg_step_kernel<<<nblocks(n, kVecBlock), kVecBlock, 0, st>>>(n, sc, flag, p, q, x, r, partial);
     return cudaGetLastError();
 }
 
 cudaError_t launch_acg_dot(int n, const float4* r, const float4* z, double* partial, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     acg_dot_kernel<<<nblocks(n, kVecBlock), kVecBlock, 0, st>>>(n, r, z, partial);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_acg_dir(int n, float b, const float4* z, float4* p, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    acg_dir_kernel<<<nblocks(n, 256), 256, 0, st>>>(n, b, z, p);
     return cudaGetLastError();
 }
 

@@ -96,7 +96,7 @@ struct pbng_mesh {
     // correction's right-hand side, the forces at u +- eps lam, the shifted states
     DevBuf d_lam_hi, d_lam_lo, d_rhs, d_fp[4], d_shift[2][2], d_maxabs, d_refine_partial;
     // conjugate-gradient adjoint (PBNG_ACCEL_CG): residual r and H p, FP64 block partials
-    DevBuf d_acg[2], d_acg_part[2];
+    DevBuf d_acg[2], d_acg_part[2], d_acg_sc;  // + device scalars (4 doubles and a flag)
     double h_min = 0.0;                // smallest rest element size (cube root of 6 V)
     // Newton-CG (pbng_newton_cg, pbng_force, pbng_hessian_apply): r, x, z, p, q
     DevBuf d_nw[5], d_nw_part[2], d_nw_sc, d_nw_flag;
@@ -2156,37 +2156,28 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
     // (D + L^T), symmetric positive definite with H).  Each iteration is one
     // preconditioner sweep and one Hessian action, counted as one sweep;
     // the recursive residual r decides the stop (tol of rhs, a stall, or
-    // the budget).  FP64 dot products, float32
-    // vectors.
+    // the budget).  FP64 dot products kept on the device, float32 vectors.
     if (cg) {
         const size_t fb = sizeof(float4) * (size_t)std::max(1, m->nfree);
         for (auto& b : m->d_acg) PBNG_CUDA(m, ensure_buf(b, fb));
         for (auto& b : m->d_acg_part)
             PBNG_CUDA(m, ensure_buf(b, sizeof(double) * (size_t)std::max(1, adj_vec_blocks(m->nfree))));
+        PBNG_CUDA(m, ensure_buf(m->d_acg_sc, 5 * sizeof(double)));
     }
-    auto reduce2 = [&](const double* pa, int na, const double* pb, int nb, double* a, double* b) -> pbng_status {
-        PBNG_CUDA(m, launch_reduce(pa, na, (double*)m->d_scalar.p, st));
-        if (pb) PBNG_CUDA(m, launch_reduce(pb, nb, (double*)m->d_scalar.p + 1, st));
-        m->kernel_launches += pb ? 2 : 1;
-        PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, m->d_scalar.p, sizeof(double) * (pb ? 2 : 1), cudaMemcpyDeviceToHost,
-                                     st));
-        pbng_status e = sync_with_err(m, st);
-        if (e) return e;
-        *a = m->h_pinned[0];
-        if (b) *b = m->h_pinned[1];
-        return PBNG_OK;
-    };
     auto inner_cg = [&](const float4* rhs, double rhs2, double tol, bool stall_stop, double* rel_end) -> pbng_status {
         float4* x = lam;
         float4* pdir = (float4*)m->d_lam[1].p;
         float4* z = (float4*)m->d_lam[2].p;
         float4* r = (float4*)m->d_acg[0].p;
         float4* q = (float4*)m->d_acg[1].p;
-        const int nb = adj_vec_blocks(m->nfree);
+        double* sc = (double*)m->d_acg_sc.p;  // r.z, p.Hp, new r.z, |r|^2
+        int32_t* flag = (int32_t*)(sc + 4);
+        const int nb = adj_vec_blocks(m->nfree), na = adjoint_ring_apply_warps(m->nitems_ring);
         const size_t vb = sizeof(float4) * (size_t)m->nv, fb = sizeof(float4) * (size_t)m->nfree;
         for (float4* b : {x, pdir}) PBNG_CUDA(m, cudaMemsetAsync(b, 0, vb, st));
+        PBNG_CUDA(m, cudaMemsetAsync(sc, 0, 5 * sizeof(double), st));
         PBNG_CUDA(m, cudaMemcpyAsync(r, rhs, fb, cudaMemcpyDeviceToDevice, st));
-        auto precondition = [&]() -> pbng_status {  // z = M^{-1} r
+        auto precondition = [&](double* rz_out) -> pbng_status {  // z = M^{-1} r, r . z -> *rz_out
             PBNG_CUDA(m, cudaMemsetAsync(z, 0, vb, st));
             for (const int c : seq)
                 PBNG_CUDA(m, launch_adjoint_ring_sweep(m->dm, u, z, r, (const float4*)m->d_diag.p,
@@ -2194,54 +2185,51 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
                                                        m->item_off[c + 1] - m->item_off[c], (int32_t*)m->d_err.p,
                                                        m->model, st));
             PBNG_CUDA(m, launch_acg_dot(m->nfree, r, z, (double*)m->d_acg_part[1].p, st));
-            m->kernel_launches += (int64_t)seq.size() + 1;
+            PBNG_CUDA(m, launch_reduce((const double*)m->d_acg_part[1].p, nb, rz_out, st));
+            m->kernel_launches += (int64_t)seq.size() + 2;
             return PBNG_OK;
         };
         pbng_status e;
-        if ((e = precondition())) return e;
-        double rz = 0.0, rr = rhs2;
-        if ((e = reduce2((const double*)m->d_acg_part[1].p, nb, nullptr, 0, &rz, nullptr))) return e;
+        if ((e = precondition(sc))) return e;
         PBNG_CUDA(m, cudaMemcpyAsync(pdir, z, fb, cudaMemcpyDeviceToDevice, st));
+        // The scalars stay on the device; the host reads |r|^2 and the
+        // breakdown flag every kCheck iterations (and at the budget's end).
+        constexpr int kCheck = 8;
+        constexpr size_t kStallChecks = 7;  // a stall over about 56 iterations
         std::vector<double> hist;
-        double irel = 1.0;
+        int it = 0;
         while (rhs2 > 0.0 && done < max_sweeps) {
             // q = H p and p . H p (the pipelined action over every ring item)
             PBNG_CUDA(m, launch_adjoint_ring_apply(m->dm, u, pdir, (const Item*)m->d_items.p, m->nitems_ring,
                                                    (int32_t*)m->d_err.p, m->model, q, (double*)m->d_adj_partial.p,
                                                    st));
-            m->kernel_launches++;
-            double pq = 0.0;
-            if ((e = reduce2((const double*)m->d_adj_partial.p, adjoint_ring_apply_warps(m->nitems_ring), nullptr, 0,
-                             &pq, nullptr)))
-                return e;
-            // a non-positive curvature: H is not positive definite here
-            if (!(pq > 0.0) || !std::isfinite(pq) || !(rz > 0.0)) return PBNG_EDIVERGED;
-            const double a = rz / pq;
-            PBNG_CUDA(m, launch_acg_step(m->nfree, (float)a, pdir, q, x, r, (double*)m->d_acg_part[0].p, st));
-            m->kernel_launches++;
-            if ((e = precondition())) return e;
-            double rz2 = 0.0;
-            if ((e = reduce2((const double*)m->d_acg_part[0].p, nb, (const double*)m->d_acg_part[1].p, nb, &rr, &rz2)))
-                return e;
+            PBNG_CUDA(m, launch_reduce((const double*)m->d_adj_partial.p, na, sc + 1, st));
+            PBNG_CUDA(m, launch_acg_step(m->nfree, sc, flag, pdir, q, x, r, (double*)m->d_acg_part[0].p, st));
+            PBNG_CUDA(m, launch_reduce((const double*)m->d_acg_part[0].p, nb, sc + 3, st));
+            m->kernel_launches += 4;
+            if ((e = precondition(sc + 2))) return e;
+            PBNG_CUDA(m, launch_cg_dir(m->nfree, sc, z, pdir, flag, sc, st));  // p = z + b p; sc[0] = sc[2]
+            m->kernel_launches += 2;
             done++;
-            irel = std::sqrt(rr / rhs2);
+            if (++it % kCheck != 0 && done < max_sweeps) continue;
+            PBNG_CUDA(m, cudaMemcpyAsync(m->h_pinned, sc + 3, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+            if ((e = sync_with_err(m, st))) return e;
+            int32_t f = 0;
+            std::memcpy(&f, m->h_pinned + 1, sizeof(int32_t));
+            // a non-positive curvature: H is not positive definite here
+            if (f) return PBNG_EDIVERGED;
+            const double irel = std::sqrt(m->h_pinned[0] / rhs2);
             *rel_end = irel;
             if (!std::isfinite(irel) || irel > 1e3) return PBNG_EDIVERGED;
             if (irel <= tol) return PBNG_OK;
-            // a stall: the best of the last kStallCg iterations not below half
-            // the best before them (one iteration gains far less than a
-            // sweep's residual check spans)
-            constexpr size_t kStallCg = 50;
+            // a stall: the best of the last kStallChecks checks not below half
+            // the best before them
             hist.push_back(irel);
-            if (stall_stop && hist.size() >= 2 * kStallCg) {
-                const double recent = *std::min_element(hist.end() - kStallCg, hist.end());
-                const double before = *std::min_element(hist.begin(), hist.end() - kStallCg);
+            if (stall_stop && hist.size() >= 2 * kStallChecks) {
+                const double recent = *std::min_element(hist.end() - kStallChecks, hist.end());
+                const double before = *std::min_element(hist.begin(), hist.end() - kStallChecks);
                 if (recent > 0.5 * before) return PBNG_OK;
             }
-            const double b = rz2 / rz;
-            rz = rz2;
-            PBNG_CUDA(m, launch_acg_dir(m->nfree, (float)b, z, pdir, st));
-            m->kernel_launches++;
         }
         return rhs2 > 0.0 ? PBNG_ENOTCONVERGED : PBNG_OK;
     };
@@ -2911,7 +2899,7 @@ void pbng_destroy(pbng_mesh* m) {
                       &m->d_comp_list, &m->d_lam_hi, &m->d_lam_lo, &m->d_rhs, &m->d_fp[0], &m->d_fp[1], &m->d_fp[2],
                       &m->d_fp[3], &m->d_shift[0][0], &m->d_shift[0][1], &m->d_shift[1][0], &m->d_shift[1][1],
                       &m->d_maxabs, &m->d_refine_partial, &m->d_acg[0], &m->d_acg[1], &m->d_acg_part[0],
-                      &m->d_acg_part[1],
+                      &m->d_acg_part[1], &m->d_acg_sc,
                       &m->d_aux0, &m->d_aux1, &m->d_aux_lo, &m->d_comp, &m->d_perm, &m->d_dir_hi, &m->d_dir_lo,
                       &m->d_aux_base0, &m->d_aux_base1, &m->d_be_k, &m->d_wc_off, &m->d_wc_list, &m->d_wc_v,
                       &m->d_wc_b, &m->d_wc_k, &m->d_wc_c0,

@@ -275,12 +275,14 @@ cudaError_t launch_adjoint_refine_rhs(int nfree, const float4* gv, const float4*
 cudaError_t launch_adjoint_accumulate(int nfree, const float4* d, float4* lam_hi, float4* lam_lo, float* maxabs,
                                       cudaStream_t st);
 // Conjugate gradients on the adjoint system (PBNG_ACCEL_CG), n free rows,
-// one FP64 partial per block (adj_vec_blocks(n) of them): x += a p and
-// r -= a q with |r|^2 partials; r . z partials; p = z + b p.
-cudaError_t launch_acg_step(int n, float a, const float4* p, const float4* q, float4* x, float4* r, double* partial,
-                            cudaStream_t st);
+// one FP64 partial per block (adj_vec_blocks(n) of them), the scalars on the
+// device as in launch_cg_update (sc[0] = r . z, sc[1] = p . H p,
+// sc[2] = the new r . z): x += a p and r -= a q with a = sc[0] / sc[1] and
+// |r|^2 partials (a non-positive p . H p sets *flag and changes nothing);
+// r . z partials.  The direction update is launch_cg_dir.
+cudaError_t launch_acg_step(int n, const double* sc, int32_t* flag, const float4* p, const float4* q, float4* x,
+                            float4* r, double* partial, cudaStream_t st);
 cudaError_t launch_acg_dot(int n, const float4* r, const float4* z, double* partial, cudaStream_t st);
-cudaError_t launch_acg_dir(int n, float b, const float4* z, float4* p, cudaStream_t st);
 // The two-sided weak constraints' part of H_DF lam (into hdl, float4 rows).
 cudaError_t launch_adjoint_weak_clamped(int nwc, int nfree, const DeviceMesh& m, const float4* lam, float* hdl,
                                         cudaStream_t st);
