@@ -261,8 +261,10 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
  * symmetric positive definite with H) and one matrix-free Hessian action,
  * and counts as one sweep in max_sweeps and sweeps_out; a direction of
  * non-positive curvature (H not positive definite) returns PBNG_EDIVERGED.
- * Its residual is the recursive one of the iteration; with float32
- * precision the true residual is evaluated at the end and reported.
+ * Its residual is the recursive one of the iteration, read back every 8
+ * iterations (so a solve may run up to 7 iterations past its tolerance);
+ * with float32 precision the true residual is evaluated at the end and
+ * reported.
  * Precision: the sweeps are float32 (multipliers and the Hessian action);
  * their relative residual stalls near 1e-7 (L/h)^2 on a mesh of L/h
  * elements across (2e-3 at 48^3 with Chebyshev).  With p->precision
