@@ -271,8 +271,9 @@ pbng_status pbng_solve(pbng_mesh* m, float* u_dev, double rel_tol, int32_t max_s
  * PBNG_PREC_EXTENDED or PBNG_PREC_AUTO the solve is refined instead: the
  * multipliers accumulate as float pairs, each correction solves
  * H d = dL/du - H lambda with the float32 sweeps (to 1e-2 of its right-hand
- * side, 1e-3 with PBNG_ACCEL_CG, or to their floor), and the residual is
- * formed by central differences
+ * side, 1e-3 with PBNG_ACCEL_CG, or only to half of what is left to rel_tol
+ * when that is less, or to their floor), and the residual is formed by
+ * central differences
  * of the float-float force (PBNG_PREC_EXTENDED),
  * H lambda = -(F(u + eps lambda) - F(u - eps lambda)) / (2 eps), with
  * eps |lambda|_max = 1e-4 of the smallest element size; rel_tol then applies

@@ -2284,9 +2284,11 @@ pbng_status pbng_adjoint(pbng_mesh* m, const float* u_eq_dev, const float* dLdu_
         while (g2 > 0.0 && done < max_sweeps && s == PBNG_OK) {
             double irel = 1.0;
             // each correction to 1e-2 (sweeps) or 1e-3 (conjugate gradients) of
-            // its right-hand side, both above the float32 floor of H d
-            pbng_status is = cg ? inner_cg((const float4*)m->d_rhs.p, r2, 1e-3, true, &irel)
-                                : inner_solve((const float4*)m->d_rhs.p, r2, 1e-2, true, &irel);
+            // its right-hand side, both above the float32 floor of H d, or only
+            // to half of what is left to rel_tol when that is less
+            const double left = 0.5 * rel_tol * std::sqrt(g2 / r2);
+            pbng_status is = cg ? inner_cg((const float4*)m->d_rhs.p, r2, std::max(1e-3, left), true, &irel)
+                                : inner_solve((const float4*)m->d_rhs.p, r2, std::max(1e-2, left), true, &irel);
             if (is == PBNG_EDIVERGED) { result = is; break; }
             if (is != PBNG_OK && is != PBNG_ENOTCONVERGED) { s = is; break; }
             // lam += d, then the residual at the new lam
