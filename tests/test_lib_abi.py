@@ -54,3 +54,27 @@ def test_status_strings(lib):
     lib.pbng_status_string.restype = ctypes.c_char_p
     assert lib.pbng_status_string(0) == b"ok"
     assert lib.pbng_status_string(7) == b"not converged"
+
+
+def _header_constants():
+    """Every `NAME = value` enumerator and `#define NAME value` of pbng.h."""
+    text = open(os.path.join(ROOT, "include", "pbng.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\b(PBNG_[A-Z_0-9]+)\s*=\s*(-?\d+)", text)}
+    consts.update({k: int(v) for k, v in re.findall(r"#define\s+(PBNG_[A-Z_0-9]+)\s+(\d+)", text)})
+    return consts
+
+
+def test_binding_constants_match_the_header():
+    """The binding's names for the accelerations, precisions, models and
+    colour orders, and its size limits, are the header's values."""
+    from paper_2306_09021_gb300 import _lib
+    c = _header_constants()
+    maps = [(_lib.ACCEL, "PBNG_ACCEL_"), (_lib.PRECISION, "PBNG_PREC_"), (_lib.MODEL, "PBNG_MODEL_"),
+            (_lib.ORDER, "PBNG_ORDER_")]
+    for table, prefix in maps:
+        declared = {k[len(prefix):].lower(): v for k, v in c.items() if k.startswith(prefix)}
+        assert table == declared, prefix
+    assert _lib.MAX_COLOURS == c["PBNG_MAX_COLOURS"]
+    assert _lib.MAX_CTAS_PER_SM == c["PBNG_MAX_CTAS_PER_SM"]
+    assert _lib.MAX_SOLVE_EVENTS == c["PBNG_MAX_SOLVE_EVENTS"]
